@@ -1,0 +1,249 @@
+"""FP64 CPU oracle of the coupled D2Q9 + D2Q5 central-moment lattice Boltzmann method
+(Fei, Luo, Lin & Li, arXiv:1710.10569, Sec. 2) -- TEST INFRASTRUCTURE, NOT PRODUCT CODE.
+
+Only the tests, the package smoke check and the benchmark's CPU-baseline leg may import this module.
+The arithmetic lives in ``clb_oracle.c`` (plain C, literal matrices of Eqs. 7, 17, 18); this wrapper
+only marshals arguments, plus two diagnostics written out in numpy from their definitions:
+
+* ``nusselt``: Eq. (29), Nu = 1 + <u_perp (T - T0)> H / (alpha dT), averaged over all nodes;
+* ``residual``: the steady-state residual E_R. The paper defines it only by citation (Sec. 3.2); the
+  reading used here is E_R = max over X in {u, T} of sqrt(sum |X(t) - X(t-D)|^2 / max(sum |X(t)|^2,
+  N (1e-3 X_ref)^2)), with X_ref = u_ref for u and dT_ref for T (no floor when X_ref = 0).
+
+Parity pins: every function here is checked by tests/test_oracle_pins.py against facts the paper and
+the mathematics fix (brute-force moment sums, fixed points, conservation, decay rates, Poiseuille and
+conduction profiles, Table 1 Nusselt numbers).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "clb_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+PERIODIC, DIRICHLET, ADIABATIC = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FMA contraction, no host-specific flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
+                               "-fopenmp",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nu", ctypes.c_double), ("kappa", ctypes.c_double), ("g_beta", ctypes.c_double),
+                ("T0", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("s_b", ctypes.c_double), ("s_3", ctypes.c_double), ("s_4", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
+                ("Fv", ctypes.c_double * 2), ("wall", ctypes.c_int * 4), ("T_wall", ctypes.c_double * 4)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            # Idle threads spin only briefly before they block: the node loops are short and the
+            # oracle may share the host cores with other processes.
+            os.environ.setdefault("GOMP_SPINCOUNT", "20000")
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            d = P(ctypes.c_double)
+            lib.orc_create.argtypes = [P(_Params), P(ctypes.c_void_p)]
+            lib.orc_create.restype = ctypes.c_int
+            lib.orc_destroy.argtypes = [ctypes.c_void_p]
+            lib.orc_init.argtypes = [ctypes.c_void_p, d, d, d, d]
+            lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+            lib.orc_steps.argtypes = [ctypes.c_void_p]
+            lib.orc_steps.restype = ctypes.c_long
+            lib.orc_threads.argtypes = []
+            lib.orc_threads.restype = ctypes.c_int
+            lib.orc_fields.argtypes = [ctypes.c_void_p, d, d, d, d]
+            lib.orc_get_pops.argtypes = [ctypes.c_void_p, d, d]
+            lib.orc_set_pops.argtypes = [ctypes.c_void_p, d, d]
+            lib.orc_collide_node.argtypes = [P(_Params), d, d, d, d]
+            lib.orc_equilibrium_node.argtypes = [P(_Params), ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_double, d, d]
+            lib.orc_matrices.argtypes = [P(_Params), ctypes.c_double, ctypes.c_double] + [d] * 11
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _params(p: dict, nx: int = 2, ny: int = 2) -> _Params:
+    s = _Params()
+    s.nx, s.ny = nx, ny
+    for k in ("nu", "kappa", "g_beta", "T0", "rho0", "s_b", "s_3", "s_4", "lambda0", "lambda2",
+              "cs2_T"):
+        setattr(s, k, float(p.get(k, 1.0 if k == "lambda0" else 0.0)))
+    s.Fv[0], s.Fv[1] = (float(v) for v in p["Fv"])
+    for i in range(4):
+        s.wall[i] = int(p["wall"][i])
+        s.T_wall[i] = float(p["T_wall"][i])
+    return s
+
+
+class Oracle:
+    """One lattice stepped on the CPU in FP64. Fields are (ny, nx) float64 arrays."""
+
+    def __init__(self, nx: int, ny: int, params: dict):
+        self._lib = _load()
+        self.nx, self.ny, self.params = nx, ny, dict(params)
+        self._p = _params(params, nx, ny)
+        h = ctypes.c_void_p()
+        rc = self._lib.orc_create(ctypes.byref(self._p), ctypes.byref(h))
+        if rc != 0:
+            raise ValueError(f"oracle: invalid lattice {nx}x{ny} (code {rc})")
+        self._h = h
+
+    @classmethod
+    def from_problem(cls, prob) -> "Oracle":
+        o = cls(prob.nx, prob.ny, prob.params)
+        o.init(prob.rho, prob.ux, prob.uy, prob.T)
+        return o
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.orc_destroy(h)
+            self._h = None
+
+    def init(self, rho, ux, uy, T):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.ny, self.nx)
+                for a in (rho, ux, uy, T)]
+        self._lib.orc_init(self._h, *[_ptr(a) for a in arrs])
+
+    def step(self, n: int = 1):
+        self._lib.orc_step(self._h, int(n))
+
+    @property
+    def steps(self) -> int:
+        return int(self._lib.orc_steps(self._h))
+
+    def fields(self):
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        self._lib.orc_fields(self._h, *[_ptr(a) for a in out])
+        return tuple(out)
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((5, self.ny, self.nx))
+        self._lib.orc_get_pops(self._h, _ptr(f), _ptr(g))
+        return f, g
+
+    def set_populations(self, f, g):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.shape == (9, self.ny, self.nx) and g.shape == (5, self.ny, self.nx)
+        self._lib.orc_set_pops(self._h, _ptr(f), _ptr(g))
+
+    def nusselt(self, axis: int = 1) -> float:
+        _, ux, uy, T = self.fields()
+        return nusselt(ux, uy, T, self.params, axis)
+
+
+def threads() -> int:
+    """Number of OpenMP threads the oracle's node loops use (set with OMP_NUM_THREADS)."""
+    return int(_load().orc_threads())
+
+
+def collide_node(params: dict, f, g):
+    """Post-collision populations (f*, g*) of one node (Eqs. 7-11, 16-21)."""
+    lib = _load()
+    p = _params(params)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    fo, go = np.empty(9), np.empty(5)
+    lib.orc_collide_node(ctypes.byref(p), _ptr(f), _ptr(g), _ptr(fo), _ptr(go))
+    return fo, go
+
+
+def equilibrium_node(params: dict, rho, ux, uy, T):
+    """(f^eq, g^eq) = (M^-1 N(u)^-1 Gamma~eq, M_T^-1 N_T(u)^-1 Gamma~T,eq) at one node."""
+    lib = _load()
+    p = _params(params)
+    f, g = np.empty(9), np.empty(5)
+    lib.orc_equilibrium_node(ctypes.byref(p), float(rho), float(ux), float(uy), float(T), _ptr(f),
+                             _ptr(g))
+    return f, g
+
+
+def matrices(params: dict, ux: float, uy: float) -> dict:
+    """The matrices exactly as the oracle applies them (see clb_oracle.c)."""
+    lib = _load()
+    p = _params(params)
+    shapes = dict(M=(9, 9), Minv=(9, 9), N=(9, 9), Ninv=(9, 9), MT=(5, 5), MTinv=(5, 5), NT=(5, 5),
+                  NTinv=(5, 5), S=(9, 9), ST=(5, 5), wT=(5,))
+    out = {k: np.empty(s) for k, s in shapes.items()}
+    lib.orc_matrices(ctypes.byref(p), float(ux), float(uy),
+                     *[_ptr(out[k]) for k in ("M", "Minv", "N", "Ninv", "MT", "MTinv", "NT",
+                                               "NTinv", "S", "ST", "wT")])
+    return out
+
+
+def nusselt(ux, uy, T, params: dict, axis: int) -> float:
+    """Eq. (29): Nu = 1 + <u_axis (T - T0)> H / (alpha dT), the average taken over all nodes.
+    H is the node count along `axis` (walls halfway between nodes); dT is the difference of the
+    wall temperatures on that axis, the sign chosen so that heat flowing from the hot wall counts
+    positive. alpha is the prescribed thermal diffusivity `kappa`."""
+    u = ux if axis == 0 else uy
+    H = T.shape[1] if axis == 0 else T.shape[0]
+    lo, hi = (0, 1) if axis == 0 else (2, 3)
+    Tl, Th = params["T_wall"][lo], params["T_wall"][hi]
+    dT = abs(Tl - Th) or 1.0
+    sign = 1.0 if Tl >= Th else -1.0
+    mean = float(np.mean(u * (T - params["T0"])))
+    return 1.0 + sign * mean * H / (params["kappa"] * dT)
+
+
+def residual(prev, cur, u_ref: float, dT_ref: float) -> float:
+    """E_R between two field snapshots (ux, uy, T) taken D steps apart (reading in module doc)."""
+    pux, puy, pT = prev
+    cux, cuy, cT = cur
+    n = cT.size
+
+    def ratio(num, den, ref):
+        floor = n * (1e-3 * ref) ** 2
+        den = max(den, floor)
+        if num == 0.0:
+            return 0.0
+        return float(np.sqrt(num / den)) if den > 0 else float("inf")
+
+    ru = ratio(float(np.sum((cux - pux) ** 2 + (cuy - puy) ** 2)),
+               float(np.sum(cux ** 2 + cuy ** 2)), u_ref)
+    rT = ratio(float(np.sum((cT - pT) ** 2)), float(np.sum(cT ** 2)), dT_ref)
+    return max(ru, rT)
+
+
+def run_to_steady(o: Oracle, tol: float, max_steps: int, interval: int = 100):
+    """Step until E_R < tol (checked every `interval` steps) or `max_steps`. Returns (steps, E_R)."""
+    p = o.params
+    prev = o.fields()[1:]
+    er = float("inf")
+    while o.steps < max_steps:
+        o.step(interval)
+        cur = o.fields()[1:]
+        er = residual(prev, cur, p.get("u_ref", 0.0), p.get("dT_ref", 0.0))
+        prev = cur
+        if er < tol:
+            break
+    return o.steps, er

@@ -1,0 +1,510 @@
+/*
+ * clb_oracle.c -- TEST INFRASTRUCTURE, NOT PRODUCT CODE.
+ *
+ * A plain, slow, obviously-correct FP64 CPU implementation of the coupled central-moment lattice
+ * Boltzmann method of Fei, Luo, Lin & Li, "Modeling incompressible thermal flows using a
+ * central-moment-based lattice Boltzmann method" (arXiv:1710.10569):
+ *   - D2Q9 flow CLB, Sec. 2.1, Eqs. (4)-(13);
+ *   - D2Q5 temperature CLB, Sec. 2.2, Eqs. (14)-(23) and Appendix A;
+ *   - Boussinesq force, Eq. (3).
+ * Every transform is a literal matrix-vector product with the matrices printed in the paper
+ * (Eq. 7a, Eq. 7b, Eq. 17, Eq. 18). M^-1 and M_T^-1 are computed numerically (Gauss-Jordan);
+ * N^-1 and N_T^-1 are applied by solving the unit lower-triangular system N x = y.
+ * Nothing is fused, blocked or reordered: collide every node, then stream every population.
+ *
+ * Only the test-suite, the package smoke check and the benchmark's CPU-baseline leg load this file.
+ * It shares no code, header, table or constant with the CUDA library.
+ *
+ * Readings taken where the paper is silent or garbled (each is also listed in the design notes):
+ *   r1  Eq. 7b prints +2u_y in the k~02 row (column k01). Expanding Eq. 5b, (e_y-u_y)^2 =
+ *       e_y^2 - 2u_y e_y + u_y^2, so the entry is -2u_y (it is -2u_y in N_T, Eq. 18). Used here.
+ *   r4  F is a force density (it enters rho*u in Eq. 13): F = (Fv_x, Fv_y + rho0*g_beta*(T - T0)),
+ *       gravity along -y (Eq. 3), g_beta = |g|*beta >= 0.
+ *   r6  The velocity that shifts the D2Q5 moments is the force-corrected u of Eq. 13, same node/step.
+ *   r7  u = (sum f e + F/2) / rho with the local rho.
+ *   r10 Walls (stationary, halfway between nodes): f uses halfway bounce-back on every wall; g uses
+ *       anti-bounce-back g_i = -g*_opp + 2 w^T_i T_w on Dirichlet walls and bounce-back g_i = g*_opp
+ *       on adiabatic walls. w^T_i are the D2Q5 rest weights (g^eq at T=1, u=0).
+ * Parity is pinned by the tests in tests/test_oracle_pins.py (transform brute force, fixed point,
+ * conservation, viscosity and diffusivity decay, Poiseuille, conduction, Table 1 Nusselt numbers).
+ */
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include <stdlib.h>
+#include <string.h>
+
+#define Q9 9
+#define Q5 5
+#define ORC_OMP_MIN_NODES 1024 /* smaller lattices run on one thread */
+
+/* D2Q9 velocity set, Eq. (4). D2Q5 uses the first five (Sec. 2.2). */
+static const int EX[Q9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[Q9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+/* Side numbering for walls: 0 = -x, 1 = +x, 2 = -y, 3 = +y. Wall kinds. */
+enum { ORC_PERIODIC = 0, ORC_DIRICHLET = 1, ORC_ADIABATIC = 2 };
+
+typedef struct {
+    int nx, ny;
+    double nu, kappa, g_beta, T0, rho0;
+    double s_b, s_3, s_4, lambda0, lambda2, cs2_T;
+    double Fv[2];
+    int wall[4];
+    double T_wall[4];
+} orc_params;
+
+typedef struct {
+    orc_params p;
+    double cs2;            /* lattice sound speed squared, 1/3 (Eq. 9) */
+    double s_nu, lambda1;  /* from nu = (1/s_nu - 1/2) cs2 and alpha = (1/lambda1 - 1/2) cs2_T */
+    double M[Q9][Q9], Minv[Q9][Q9], S[Q9][Q9];
+    double MT[Q5][Q5], MTinv[Q5][Q5], ST[Q5][Q5];
+    int opp[Q9];
+    double wT[Q5];         /* D2Q5 rest weights, g^eq(T=1, u=0) */
+    double *f, *g;         /* pre-collision populations at the current time, [q][y][x] */
+    double *fs, *gs;       /* post-collision scratch */
+    long steps;
+} orc_sim;
+
+/* ---------------------------------------------------------------- literal matrices (Eqs. 7, 17, 18) */
+
+static void build_M(double M[Q9][Q9])
+{
+    /* Eq. (7a): rows k00, k10, k01, k20, k02, k11, k21, k12, k22 over populations 0..8. */
+    static const double Mt[Q9][Q9] = {
+        {1, 1, 1, 1, 1, 1, 1, 1, 1},
+        {0, 1, 0, -1, 0, 1, -1, -1, 1},
+        {0, 0, 1, 0, -1, 1, 1, -1, -1},
+        {0, 1, 0, 1, 0, 1, 1, 1, 1},
+        {0, 0, 1, 0, 1, 1, 1, 1, 1},
+        {0, 0, 0, 0, 0, 1, -1, 1, -1},
+        {0, 0, 0, 0, 0, 1, 1, -1, -1},
+        {0, 0, 0, 0, 0, 1, -1, -1, 1},
+        {0, 0, 0, 0, 0, 1, 1, 1, 1},
+    };
+    memcpy(M, Mt, sizeof(Mt));
+}
+
+static void build_N(double ux, double uy, double N[Q9][Q9])
+{
+    /* Eq. (7b), with the k~02 row's k01 entry read as -2u_y (reading r1). */
+    const double x = ux, y = uy, x2 = ux * ux, y2 = uy * uy;
+    const double Nt[Q9][Q9] = {
+        {1, 0, 0, 0, 0, 0, 0, 0, 0},
+        {-x, 1, 0, 0, 0, 0, 0, 0, 0},
+        {-y, 0, 1, 0, 0, 0, 0, 0, 0},
+        {x2, -2 * x, 0, 1, 0, 0, 0, 0, 0},
+        {y2, 0, -2 * y, 0, 1, 0, 0, 0, 0},
+        {x * y, -y, -x, 0, 0, 1, 0, 0, 0},
+        {-x2 * y, 2 * x * y, x2, -y, 0, -2 * x, 1, 0, 0},
+        {-y2 * x, y2, 2 * x * y, 0, -x, -2 * y, 0, 1, 0},
+        {x2 * y2, -2 * x * y2, -2 * y * x2, y2, x2, 4 * x * y, -2 * y, -2 * x, 1},
+    };
+    memcpy(N, Nt, sizeof(Nt));
+}
+
+static void build_MT(double M[Q5][Q5])
+{
+    /* Eq. (17): rows k00, k10, k01, k20, k02 over populations 0..4. */
+    static const double Mt[Q5][Q5] = {
+        {1, 1, 1, 1, 1},
+        {0, 1, 0, -1, 0},
+        {0, 0, 1, 0, -1},
+        {0, 1, 0, 1, 0},
+        {0, 0, 1, 0, 1},
+    };
+    memcpy(M, Mt, sizeof(Mt));
+}
+
+static void build_NT(double ux, double uy, double N[Q5][Q5])
+{
+    /* Eq. (18). */
+    const double Nt[Q5][Q5] = {
+        {1, 0, 0, 0, 0},
+        {-ux, 1, 0, 0, 0},
+        {-uy, 0, 1, 0, 0},
+        {ux * ux, -2 * ux, 0, 1, 0},
+        {uy * uy, 0, -2 * uy, 0, 1},
+    };
+    memcpy(N, Nt, sizeof(Nt));
+}
+
+/* ---------------------------------------------------------------- plain linear algebra */
+
+/* Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix. Returns 0 on success. */
+static int invert(int n, const double *A, double *Ainv)
+{
+    double a[Q9 * 2 * Q9];
+    const int w = 2 * n;
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < w; ++c)
+            a[r * w + c] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(a[r * w + c]) > fabs(a[piv * w + c])) piv = r;
+        if (a[piv * w + c] == 0.0) return -1;
+        if (piv != c)
+            for (int k = 0; k < w; ++k) {
+                double t = a[c * w + k];
+                a[c * w + k] = a[piv * w + k];
+                a[piv * w + k] = t;
+            }
+        const double d = a[c * w + c];
+        for (int k = 0; k < w; ++k) a[c * w + k] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double m = a[r * w + c];
+            for (int k = 0; k < w; ++k) a[r * w + k] -= m * a[c * w + k];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) Ainv[r * n + c] = a[r * w + n + c];
+    return 0;
+}
+
+static void matvec(int n, const double *A, const double *x, double *y)
+{
+    for (int r = 0; r < n; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < n; ++c) s += A[r * n + c] * x[c];
+        y[r] = s;
+    }
+}
+
+/* Solve L x = b for unit lower-triangular L (this is how N^-1 and N_T^-1 are applied). */
+static void solve_unit_lower(int n, const double *L, const double *b, double *x)
+{
+    for (int r = 0; r < n; ++r) {
+        double s = b[r];
+        for (int c = 0; c < r; ++c) s -= L[r * n + c] * x[c];
+        x[r] = s;
+    }
+}
+
+/* ---------------------------------------------------------------- set-up */
+
+static void build_constants(orc_sim *s)
+{
+    const orc_params *p = &s->p;
+    s->cs2 = 1.0 / 3.0;
+    /* nu = (1/s_nu - 1/2) cs2 (Sec. 2.1) and alpha = (1/lambda1 - 1/2) cs2_T (Sec. 2.2). */
+    s->s_nu = 1.0 / (p->nu / s->cs2 + 0.5);
+    s->lambda1 = 1.0 / (p->kappa / p->cs2_T + 0.5);
+
+    build_M(s->M);
+    invert(Q9, &s->M[0][0], &s->Minv[0][0]);
+    build_MT(s->MT);
+    invert(Q5, &s->MT[0][0], &s->MTinv[0][0]);
+
+    /* Relaxation matrix of Eq. (8): diag([0,0,0], [[s+,s-],[s-,s+]], [s_nu, s_3, s_3, s_4]). */
+    memset(s->S, 0, sizeof(s->S));
+    const double sp = 0.5 * (p->s_b + s->s_nu), sm = 0.5 * (p->s_b - s->s_nu);
+    s->S[3][3] = sp; s->S[3][4] = sm;
+    s->S[4][3] = sm; s->S[4][4] = sp;
+    s->S[5][5] = s->s_nu;
+    s->S[6][6] = p->s_3;
+    s->S[7][7] = p->s_3;
+    s->S[8][8] = p->s_4;
+    /* D2Q5 relaxation matrix of Eq. (19): diag(lambda0, lambda1, lambda1, lambda2, lambda2). */
+    memset(s->ST, 0, sizeof(s->ST));
+    s->ST[0][0] = p->lambda0;
+    s->ST[1][1] = s->lambda1;
+    s->ST[2][2] = s->lambda1;
+    s->ST[3][3] = p->lambda2;
+    s->ST[4][4] = p->lambda2;
+
+    /* Opposite directions found from the velocity set. */
+    for (int i = 0; i < Q9; ++i)
+        for (int j = 0; j < Q9; ++j)
+            if (EX[j] == -EX[i] && EY[j] == -EY[i]) s->opp[i] = j;
+
+    /* D2Q5 rest weights: g^eq = M_T^-1 N_T(0)^-1 [1, 0, 0, cs2_T, cs2_T] (Eqs. 20, 21). */
+    const double geq[Q5] = {1.0, 0.0, 0.0, p->cs2_T, p->cs2_T};
+    matvec(Q5, &s->MTinv[0][0], geq, s->wT);
+}
+
+/* ---------------------------------------------------------------- one node */
+
+/* Macroscopic quantities of Eqs. (3), (13), (23) from pre-collision populations. */
+static void macroscopic(const orc_sim *s, const double f[Q9], const double g[Q5], double *rho,
+                        double *ux, double *uy, double *T, double *Fx, double *Fy)
+{
+    const orc_params *p = &s->p;
+    double r = 0.0, jx = 0.0, jy = 0.0, t = 0.0;
+    for (int i = 0; i < Q9; ++i) {
+        r += f[i];
+        jx += f[i] * EX[i];
+        jy += f[i] * EY[i];
+    }
+    for (int i = 0; i < Q5; ++i) t += g[i];
+    *Fx = p->Fv[0];
+    *Fy = p->Fv[1] + p->rho0 * p->g_beta * (t - p->T0);
+    *rho = r;
+    *T = t;
+    *ux = (jx + 0.5 * *Fx) / r;
+    *uy = (jy + 0.5 * *Fy) / r;
+}
+
+/* Collision of one node: Eqs. (6)-(11) for f and Eqs. (16)-(21) for g. */
+static void collide(const orc_sim *s, const double f[Q9], const double g[Q5], double fo[Q9],
+                    double go[Q5])
+{
+    const orc_params *p = &s->p;
+    double rho, ux, uy, T, Fx, Fy;
+    macroscopic(s, f, g, &rho, &ux, &uy, &T, &Fx, &Fy);
+
+    /* ---- D2Q9 ---- */
+    double N[Q9][Q9];
+    build_N(ux, uy, N);
+    double gam[Q9], gt[Q9];
+    matvec(Q9, &s->M[0][0], f, gam);     /* Gamma = M f            (Eq. 7a) */
+    matvec(Q9, &N[0][0], gam, gt);       /* Gamma~ = N Gamma       (Eq. 7b) */
+    const double cs2 = s->cs2;
+    const double geq[Q9] = {rho, 0, 0, rho * cs2, rho * cs2, 0, 0, 0, rho * cs2 * cs2}; /* Eq. 9 */
+    const double C[Q9] = {0, Fx, Fy, 0, 0, 0, cs2 * Fy, cs2 * Fx, 0};                  /* Eq. 11 */
+    double d[Q9], Sd[Q9], SC[Q9], gts[Q9];
+    for (int k = 0; k < Q9; ++k) d[k] = gt[k] - geq[k];
+    matvec(Q9, &s->S[0][0], d, Sd);
+    matvec(Q9, &s->S[0][0], C, SC);
+    /* Eq. (8): Gamma~* = (I - S) Gamma~ + S Gamma~eq + (I - S/2) C */
+    for (int k = 0; k < Q9; ++k) gts[k] = gt[k] - Sd[k] + C[k] - 0.5 * SC[k];
+    double gams[Q9];
+    solve_unit_lower(Q9, &N[0][0], gts, gams); /* Gamma* = N^-1 Gamma~* */
+    matvec(Q9, &s->Minv[0][0], gams, fo);      /* f* = M^-1 Gamma*      */
+
+    /* ---- D2Q5 ---- */
+    double NT[Q5][Q5];
+    build_NT(ux, uy, NT);
+    double gamT[Q5], gtT[Q5];
+    matvec(Q5, &s->MT[0][0], g, gamT);  /* Eq. 16 */
+    matvec(Q5, &NT[0][0], gamT, gtT);
+    const double c2 = p->cs2_T;
+    const double geqT[Q5] = {T, 0, 0, T * c2, T * c2}; /* Eq. 20 */
+    double dT[Q5], SdT[Q5], gtsT[Q5], gamsT[Q5];
+    for (int k = 0; k < Q5; ++k) dT[k] = gtT[k] - geqT[k];
+    matvec(Q5, &s->ST[0][0], dT, SdT);
+    for (int k = 0; k < Q5; ++k) gtsT[k] = gtT[k] - SdT[k]; /* Eq. 19 */
+    solve_unit_lower(Q5, &NT[0][0], gtsT, gamsT);
+    matvec(Q5, &s->MTinv[0][0], gamsT, go);                 /* Eq. 21 */
+}
+
+/* Discrete equilibria: f^eq = M^-1 N(u)^-1 Gamma~eq(rho), g^eq = M_T^-1 N_T(u)^-1 Gamma~T,eq(T). */
+static void equilibrium(const orc_sim *s, double rho, double ux, double uy, double T, double f[Q9],
+                        double g[Q5])
+{
+    const double cs2 = s->cs2, c2 = s->p.cs2_T;
+    double N[Q9][Q9], NT[Q5][Q5], gam[Q9], gamT[Q5];
+    build_N(ux, uy, N);
+    const double geq[Q9] = {rho, 0, 0, rho * cs2, rho * cs2, 0, 0, 0, rho * cs2 * cs2};
+    solve_unit_lower(Q9, &N[0][0], geq, gam);
+    matvec(Q9, &s->Minv[0][0], gam, f);
+    build_NT(ux, uy, NT);
+    const double geqT[Q5] = {T, 0, 0, T * c2, T * c2};
+    solve_unit_lower(Q5, &NT[0][0], geqT, gamT);
+    matvec(Q5, &s->MTinv[0][0], gamT, g);
+}
+
+/* ---------------------------------------------------------------- lattice */
+
+static size_t nodes(const orc_sim *s) { return (size_t)s->p.nx * (size_t)s->p.ny; }
+
+/* Streaming, Eqs. (12) and (22), pulled: population i at x comes from x - e_i. When x - e_i lies
+ * beyond a wall, the boundary rule of reading r10 supplies it from the node's own post-collision
+ * populations. Periodic sides wrap. */
+static void stream(orc_sim *s)
+{
+    const orc_params *p = &s->p;
+    const int nx = p->nx, ny = p->ny;
+    const size_t n = nodes(s);
+#pragma omp parallel for schedule(static) if (n >= ORC_OMP_MIN_NODES)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t here = (size_t)y * nx + x;
+            for (int i = 0; i < Q9; ++i) {
+                int sx = x - EX[i], sy = y - EY[i];
+                int side = -1; /* wall crossed, if any; for a corner the y wall is recorded last */
+                if (sx < 0) { if (p->wall[0] == ORC_PERIODIC) sx += nx; else side = 0; }
+                if (sx >= nx) { if (p->wall[1] == ORC_PERIODIC) sx -= nx; else side = 1; }
+                if (sy < 0) { if (p->wall[2] == ORC_PERIODIC) sy += ny; else side = 2; }
+                if (sy >= ny) { if (p->wall[3] == ORC_PERIODIC) sy -= ny; else side = 3; }
+                const int o = s->opp[i];
+                if (side < 0) {
+                    const size_t src = (size_t)sy * nx + sx;
+                    s->f[i * n + here] = s->fs[i * n + src];
+                    if (i < Q5) s->g[i * n + here] = s->gs[i * n + src];
+                } else {
+                    s->f[i * n + here] = s->fs[o * n + here]; /* halfway bounce-back */
+                    if (i < Q5) {
+                        if (p->wall[side] == ORC_DIRICHLET) /* anti-bounce-back */
+                            s->g[i * n + here] = -s->gs[o * n + here] + 2.0 * s->wT[i] * p->T_wall[side];
+                        else                                /* adiabatic: bounce-back */
+                            s->g[i * n + here] = s->gs[o * n + here];
+                    }
+                }
+            }
+        }
+}
+
+static void collide_all(orc_sim *s)
+{
+    const long n = (long)nodes(s);
+#pragma omp parallel for schedule(static) if (n >= ORC_OMP_MIN_NODES)
+    for (long k = 0; k < n; ++k) {
+        double f[Q9], g[Q5], fo[Q9], go[Q5];
+        for (int i = 0; i < Q9; ++i) f[i] = s->f[i * n + k];
+        for (int i = 0; i < Q5; ++i) g[i] = s->g[i * n + k];
+        collide(s, f, g, fo, go);
+        for (int i = 0; i < Q9; ++i) s->fs[i * n + k] = fo[i];
+        for (int i = 0; i < Q5; ++i) s->gs[i * n + k] = go[i];
+    }
+}
+
+/* ---------------------------------------------------------------- exported API (ctypes) */
+
+int orc_create(const orc_params *p, orc_sim **out)
+{
+    *out = NULL;
+    if (p->nx < 2 || p->ny < 2) return -1;
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    if (!s) return -2;
+    s->p = *p;
+    build_constants(s);
+    const size_t n = nodes(s);
+    s->f = (double *)calloc(Q9 * n, sizeof(double));
+    s->fs = (double *)calloc(Q9 * n, sizeof(double));
+    s->g = (double *)calloc(Q5 * n, sizeof(double));
+    s->gs = (double *)calloc(Q5 * n, sizeof(double));
+    if (!s->f || !s->fs || !s->g || !s->gs) {
+        free(s->f); free(s->fs); free(s->g); free(s->gs); free(s);
+        return -2;
+    }
+    *out = s;
+    return 0;
+}
+
+void orc_destroy(orc_sim *s)
+{
+    if (!s) return;
+    free(s->f); free(s->fs); free(s->g); free(s->gs);
+    free(s);
+}
+
+/* f(x,0) = f^eq(rho, u), g(x,0) = g^eq(T, u) from row-major [ny][nx] fields. */
+void orc_init(orc_sim *s, const double *rho, const double *ux, const double *uy, const double *T)
+{
+    const size_t n = nodes(s);
+    for (size_t k = 0; k < n; ++k) {
+        double f[Q9], g[Q5];
+        equilibrium(s, rho[k], ux[k], uy[k], T[k], f, g);
+        for (int i = 0; i < Q9; ++i) s->f[i * n + k] = f[i];
+        for (int i = 0; i < Q5; ++i) s->g[i * n + k] = g[i];
+    }
+    s->steps = 0;
+}
+
+void orc_step(orc_sim *s, long nsteps)
+{
+    for (long t = 0; t < nsteps; ++t) {
+        collide_all(s);
+        stream(s);
+        s->steps++;
+    }
+}
+
+long orc_steps(const orc_sim *s) { return s->steps; }
+
+/* Threads the node loops run on (1 without OpenMP). The arithmetic per node does not depend on it. */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_fields(const orc_sim *s, double *rho, double *ux, double *uy, double *T)
+{
+    const size_t n = nodes(s);
+    for (size_t k = 0; k < n; ++k) {
+        double f[Q9], g[Q5], Fx, Fy;
+        for (int i = 0; i < Q9; ++i) f[i] = s->f[i * n + k];
+        for (int i = 0; i < Q5; ++i) g[i] = s->g[i * n + k];
+        macroscopic(s, f, g, &rho[k], &ux[k], &uy[k], &T[k], &Fx, &Fy);
+    }
+}
+
+void orc_get_pops(const orc_sim *s, double *f, double *g)
+{
+    const size_t n = nodes(s);
+    memcpy(f, s->f, Q9 * n * sizeof(double));
+    memcpy(g, s->g, Q5 * n * sizeof(double));
+}
+
+void orc_set_pops(orc_sim *s, const double *f, const double *g)
+{
+    const size_t n = nodes(s);
+    memcpy(s->f, f, Q9 * n * sizeof(double));
+    memcpy(s->g, g, Q5 * n * sizeof(double));
+}
+
+/* Per-node primitives, used by the pins. */
+int orc_collide_node(const orc_params *p, const double *f, const double *g, double *fo, double *go)
+{
+    orc_sim s;
+    memset(&s, 0, sizeof(s));
+    s.p = *p;
+    build_constants(&s);
+    collide(&s, f, g, fo, go);
+    return 0;
+}
+
+int orc_equilibrium_node(const orc_params *p, double rho, double ux, double uy, double T,
+                         double *f, double *g)
+{
+    orc_sim s;
+    memset(&s, 0, sizeof(s));
+    s.p = *p;
+    build_constants(&s);
+    equilibrium(&s, rho, ux, uy, T, f, g);
+    return 0;
+}
+
+/* The matrices as the oracle uses them: M, M^-1, N(u), N(u)^-1 (by solving against unit vectors),
+ * M_T, M_T^-1, N_T(u), N_T(u)^-1, the relaxation matrices S, S_T and the D2Q5 rest weights. */
+void orc_matrices(const orc_params *p, double ux, double uy, double *M, double *Minv, double *N,
+                  double *Ninv, double *MT, double *MTinv, double *NT, double *NTinv, double *S,
+                  double *ST, double *wT)
+{
+    orc_sim s;
+    memset(&s, 0, sizeof(s));
+    s.p = *p;
+    build_constants(&s);
+    double Nl[Q9][Q9], NTl[Q5][Q5];
+    build_N(ux, uy, Nl);
+    build_NT(ux, uy, NTl);
+    memcpy(M, s.M, sizeof(s.M));
+    memcpy(Minv, s.Minv, sizeof(s.Minv));
+    memcpy(N, Nl, sizeof(Nl));
+    memcpy(MT, s.MT, sizeof(s.MT));
+    memcpy(MTinv, s.MTinv, sizeof(s.MTinv));
+    memcpy(NT, NTl, sizeof(NTl));
+    memcpy(S, s.S, sizeof(s.S));
+    memcpy(ST, s.ST, sizeof(s.ST));
+    memcpy(wT, s.wT, sizeof(s.wT));
+    for (int c = 0; c < Q9; ++c) {
+        double e[Q9] = {0}, col[Q9];
+        e[c] = 1.0;
+        solve_unit_lower(Q9, &Nl[0][0], e, col);
+        for (int r = 0; r < Q9; ++r) Ninv[r * Q9 + c] = col[r];
+    }
+    for (int c = 0; c < Q5; ++c) {
+        double e[Q5] = {0}, col[Q5];
+        e[c] = 1.0;
+        solve_unit_lower(Q5, &NTl[0][0], e, col);
+        for (int r = 0; r < Q5; ++r) NTinv[r * Q5 + c] = col[r];
+    }
+}

@@ -1,0 +1,236 @@
+"""Seeded synthetic problems shaped like the paper's workloads.
+
+This module holds the problem statements only: lattice sizes, physical parameters derived from the
+dimensionless groups the paper uses (Sec. 3.3: Ra = g*beta*dT*H^3/(nu*alpha), Pr = nu/alpha,
+u_c = sqrt(g*beta*dT*H)), wall types and seeded initial fields. It contains none of the method's
+arithmetic (no moments, no equilibria, no collision, no streaming), so that both the CUDA library and
+the CPU oracle can be fed from it without sharing any of the computation.
+
+Fields are float64 numpy arrays of shape (ny, nx), row-major (x fastest), node (x, y) at integer
+coordinates; walls sit halfway between nodes, so a wall-bounded extent of n nodes has length n.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# wall kinds (per side, order -x, +x, -y, +y)
+WALL_PERIODIC = 0
+WALL_DIRICHLET = 1  # stationary no-slip wall at fixed temperature
+WALL_ADIABATIC = 2  # stationary no-slip wall with zero heat flux
+
+# population storage forms
+STORAGE_F64 = 0
+STORAGE_F32 = 1
+STORAGE_F16DEV = 2
+STORAGE_NAMES = {STORAGE_F64: "f64", STORAGE_F32: "f32", STORAGE_F16DEV: "f16dev"}
+
+CS = 1.0 / math.sqrt(3.0)  # lattice sound speed of the D2Q9 lattice (Sec. 2.1, Eq. 9)
+
+
+def default_params(**overrides) -> dict:
+    """Default parameter set. High-order rates are 1 and the D2Q5 sound speed squared is 1/4,
+    the defaults of Sec. 3 (first paragraph); the bulk rate s_b defaults to 1."""
+    p = dict(
+        nu=0.02, kappa=0.02, g_beta=0.0, T0=0.0, rho0=1.0,
+        s_b=1.0, s_3=1.0, s_4=1.0, lambda0=1.0, lambda2=1.0, cs2_T=0.25,
+        Fv=(0.0, 0.0),
+        wall=(WALL_PERIODIC,) * 4, T_wall=(0.0,) * 4,
+        storage=STORAGE_F64, T_ref=0.0, u_ref=0.0, dT_ref=0.0,
+    )
+    for k, v in overrides.items():
+        if k not in p:
+            raise KeyError(f"unknown parameter {k!r}")
+        p[k] = v
+    return p
+
+
+@dataclasses.dataclass
+class Problem:
+    name: str
+    nx: int
+    ny: int
+    params: dict
+    rho: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    T: np.ndarray
+    nu_axis: int = 1  # axis of the heat-flux for the Nusselt number (0 = x, 1 = y)
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny
+
+    def fields(self):
+        return self.rho, self.ux, self.uy, self.T
+
+    def with_storage(self, storage: int) -> "Problem":
+        p = dict(self.params)
+        p["storage"] = storage
+        return dataclasses.replace(self, params=p)
+
+
+def _grid(nx, ny):
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y
+
+
+def convection_params(H: float, Ra: float, Pr: float, u_c: float, dT: float = 1.0):
+    """nu, alpha, g*beta from Ra, Pr and the characteristic velocity u_c = sqrt(g beta dT H)
+    (Sec. 3.3: nu = u_c H sqrt(Pr/Ra) once u_c is fixed; alpha = nu/Pr)."""
+    nu = u_c * H * math.sqrt(Pr / Ra)
+    return nu, nu / Pr, u_c * u_c / (dT * H)
+
+
+def taylor_green(n: int = 64, U: float = 0.01, nu: float = 0.02, kappa: float = 0.02,
+                 T_amp: float = 0.01, noise: float = 1e-4, seed: int = 0, storage=STORAGE_F64,
+                 ny: int | None = None) -> Problem:
+    """Doubly periodic Taylor-Green vortex with a sinusoidal temperature, no gravity.
+    u_x = -U cos(kx) sin(ky), u_y = U sin(kx) cos(ky), T = T_amp sin(kx) sin(ky), rho = 1, with
+    independent seeded uniform noise of amplitude `noise` on u_x, u_y and T."""
+    nx = n
+    ny = n if ny is None else ny
+    rng = np.random.default_rng(seed)
+    x, y = _grid(nx, ny)
+    kx, ky = 2 * math.pi / nx, 2 * math.pi / ny
+    ux = -U * np.cos(kx * x) * np.sin(ky * y) + rng.uniform(-noise, noise, (ny, nx))
+    uy = U * np.sin(kx * x) * np.cos(ky * y) + rng.uniform(-noise, noise, (ny, nx))
+    T = T_amp * np.sin(kx * x) * np.sin(ky * y) + rng.uniform(-noise, noise, (ny, nx))
+    rho = np.ones((ny, nx))
+    p = default_params(nu=nu, kappa=kappa, storage=storage, u_ref=U, dT_ref=T_amp)
+    return Problem(f"taylor_green_{nx}x{ny}", nx, ny, p, rho, ux, uy, T, nu_axis=1,
+                   meta=dict(U=U, seed=seed))
+
+
+def cavity(n: int = 256, Ra: float = 1e5, Pr: float = 0.71, u_c: float = 0.1, noise: float = 1e-4,
+           seed: int = 0, storage=STORAGE_F64, ny: int | None = None) -> Problem:
+    """Differentially heated square cavity: left wall T=+0.5, right wall T=-0.5 (Dirichlet),
+    top and bottom adiabatic, no-slip everywhere, fluid at rest, T = seeded noise of `noise`."""
+    nx = n
+    ny = n if ny is None else ny
+    H = float(nx)  # heated walls are the x walls; the length scale is their distance
+    nu, alpha, gb = convection_params(H, Ra, Pr, u_c)
+    rng = np.random.default_rng(seed)
+    T = rng.uniform(-noise, noise, (ny, nx))
+    z = np.zeros((ny, nx))
+    p = default_params(nu=nu, kappa=alpha, g_beta=gb, T0=0.0, storage=storage,
+                       wall=(WALL_DIRICHLET, WALL_DIRICHLET, WALL_ADIABATIC, WALL_ADIABATIC),
+                       T_wall=(0.5, -0.5, 0.0, 0.0), u_ref=u_c, dT_ref=1.0)
+    return Problem(f"cavity_{nx}x{ny}_Ra{Ra:g}", nx, ny, p, np.ones((ny, nx)), z.copy(), z.copy(), T,
+                   nu_axis=0, meta=dict(Ra=Ra, Pr=Pr, u_c=u_c, seed=seed))
+
+
+def rayleigh_benard(nx: int = 2048, ny: int = 1024, Ra: float = 1e7, Pr: float = 0.71,
+                    u_c: float = 0.1, perturb: float = 1e-3, seed: int = 0, storage=STORAGE_F64,
+                    T0: float = 0.0, dT: float = 1.0) -> Problem:
+    """Rayleigh-Benard convection: periodic in x, bottom wall T0+dT/2, top wall T0-dT/2, at rest,
+    T = linear conduction profile + seeded uniform perturbation of amplitude `perturb`."""
+    H = float(ny)
+    nu, alpha, gb = convection_params(H, Ra, Pr, u_c, dT)
+    rng = np.random.default_rng(seed)
+    x, y = _grid(nx, ny)
+    T = T0 + dT * (0.5 - (y + 0.5) / ny) + rng.uniform(-perturb, perturb, (ny, nx))
+    z = np.zeros((ny, nx))
+    p = default_params(nu=nu, kappa=alpha, g_beta=gb, T0=T0, storage=storage,
+                       wall=(WALL_PERIODIC, WALL_PERIODIC, WALL_DIRICHLET, WALL_DIRICHLET),
+                       T_wall=(0.0, 0.0, T0 + 0.5 * dT, T0 - 0.5 * dT), T_ref=T0, u_ref=u_c,
+                       dT_ref=dT)
+    return Problem(f"rayleigh_benard_{nx}x{ny}_Ra{Ra:g}", nx, ny, p, np.ones((ny, nx)), z.copy(),
+                   z.copy(), T, nu_axis=1, meta=dict(Ra=Ra, Pr=Pr, u_c=u_c, seed=seed))
+
+
+def rayleigh_benard_table1(Ra: float, Ma: float = 0.3, nx: int = 60, ny: int = 30,
+                           Pr: float = 0.71, storage=STORAGE_F64) -> Problem:
+    """The Rayleigh-Benard set-up of Sec. 3.3 / Table 1: L x H = 60 x 30, Pr = 0.71,
+    u_c = Ma * c_s, nu = Ma c_s H sqrt(Pr/Ra); density disturbed along the horizontal centre line,
+    rho(x, H/2) = rho0 (1 + 0.001 cos(2 pi x / L)); the temperature starts from the conduction
+    profile (the paper does not state it). Walls T = +-0.5 about T0 = 0 (a uniform shift of T from
+    the paper's 1.05/0.95 about 1.0, with g*beta rescaled so Ra is unchanged)."""
+    u_c = Ma * CS
+    H = float(ny)
+    nu, alpha, gb = convection_params(H, Ra, Pr, u_c)
+    x, y = _grid(nx, ny)
+    rho = np.ones((ny, nx))
+    rho[ny // 2, :] = 1.0 + 0.001 * np.cos(2 * math.pi * np.arange(nx) / nx)
+    T = 0.5 - (y + 0.5) / ny
+    z = np.zeros((ny, nx))
+    p = default_params(nu=nu, kappa=alpha, g_beta=gb, T0=0.0, storage=storage,
+                       wall=(WALL_PERIODIC, WALL_PERIODIC, WALL_DIRICHLET, WALL_DIRICHLET),
+                       T_wall=(0.0, 0.0, 0.5, -0.5), u_ref=u_c, dT_ref=1.0)
+    return Problem(f"rb_table1_Ra{Ra:g}", nx, ny, p, rho, z.copy(), z.copy(), T, nu_axis=1,
+                   meta=dict(Ra=Ra, Pr=Pr, Ma=Ma, u_c=u_c))
+
+
+def random_problem(nx: int, ny: int, seed: int, storage=STORAGE_F64, walls=None) -> Problem:
+    """A small problem with random-but-stable parameters and fields, used for parity sweeps."""
+    rng = np.random.default_rng(seed)
+    if walls is None:
+        walls = [(WALL_PERIODIC,) * 4,
+                 (WALL_DIRICHLET, WALL_DIRICHLET, WALL_ADIABATIC, WALL_ADIABATIC),
+                 (WALL_PERIODIC, WALL_PERIODIC, WALL_DIRICHLET, WALL_DIRICHLET),
+                 (WALL_ADIABATIC, WALL_DIRICHLET, WALL_DIRICHLET, WALL_ADIABATIC)][seed % 4]
+    T_wall = tuple(float(v) for v in rng.uniform(-0.5, 0.5, 4))
+    p = default_params(nu=float(rng.uniform(0.01, 0.1)), kappa=float(rng.uniform(0.01, 0.1)),
+                       g_beta=float(rng.uniform(0.0, 1e-3)), T0=float(rng.uniform(-0.1, 0.1)),
+                       s_b=float(rng.uniform(0.8, 1.6)), s_3=float(rng.uniform(0.8, 1.6)),
+                       s_4=float(rng.uniform(0.8, 1.6)), lambda2=float(rng.uniform(0.8, 1.6)),
+                       Fv=(float(rng.uniform(-1e-5, 1e-5)), float(rng.uniform(-1e-5, 1e-5))),
+                       wall=tuple(walls), T_wall=T_wall, storage=storage, u_ref=0.05, dT_ref=1.0)
+    rho = 1.0 + rng.uniform(-1e-3, 1e-3, (ny, nx))
+    ux = rng.uniform(-0.05, 0.05, (ny, nx))
+    uy = rng.uniform(-0.05, 0.05, (ny, nx))
+    T = rng.uniform(-0.5, 0.5, (ny, nx))
+    return Problem(f"random_{nx}x{ny}_s{seed}", nx, ny, p, rho, ux, uy, T,
+                   nu_axis=0 if walls[0] != WALL_PERIODIC else 1, meta=dict(seed=seed))
+
+
+def batch_cavities(count: int = 256, seed: int = 0, lo: int = 64, hi: int = 512,
+                   Ra_range=(1e3, 1e6), Pr_range=(0.71, 7.0), u_c: float = 0.1,
+                   nu_cap: float = 0.1, storage=STORAGE_F32) -> list[Problem]:
+    """Independent side-heated cavities: edge log-uniform in [lo, hi], Ra log-uniform, Pr uniform.
+    u_c is lowered where needed so that nu <= nu_cap (keeps the flow relaxation time moderate)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        Ra = math.exp(rng.uniform(math.log(Ra_range[0]), math.log(Ra_range[1])))
+        Pr = float(rng.uniform(*Pr_range))
+        uc = u_c
+        nu = uc * n * math.sqrt(Pr / Ra)
+        if nu > nu_cap:
+            uc *= nu_cap / nu
+        prob = cavity(n, Ra=Ra, Pr=Pr, u_c=uc, seed=seed * 100003 + k, storage=storage)
+        prob.name = f"batch{k}_" + prob.name
+        out.append(prob)
+    return out
+
+
+def request_trace(count: int = 64, seed: int = 0, rate_hz: float = 50.0, lo: int = 64,
+                  hi: int = 512, Ra_range=(1e3, 1e6), storage=STORAGE_F32, nu_cap: float = 0.1):
+    """A finite Poisson request stream: (arrival_time_s, Problem) pairs. Kind is uniform over
+    periodic Taylor-Green, side-heated cavity and Rayleigh-Benard; edge log-uniform in [lo, hi];
+    aspect ratio 1 or 2 with probability 1/2 each."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += float(rng.exponential(1.0 / rate_hz))
+        kind = int(rng.integers(0, 3))
+        n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        aspect = 1 + int(rng.integers(0, 2))
+        Ra = math.exp(rng.uniform(math.log(Ra_range[0]), math.log(Ra_range[1])))
+        s = seed * 1000003 + k
+        if kind == 0:
+            prob = taylor_green(n, ny=n * aspect if aspect == 2 else n, seed=s, storage=storage)
+        elif kind == 1:
+            uc = min(0.1, 0.1 * nu_cap / (0.1 * n * math.sqrt(0.71 / Ra)))
+            prob = cavity(n, Ra=Ra, u_c=uc, ny=n * aspect, seed=s, storage=storage)
+        else:
+            uc = min(0.1, 0.1 * nu_cap / (0.1 * n * math.sqrt(0.71 / Ra)))
+            prob = rayleigh_benard(n * aspect, n, Ra=Ra, u_c=uc, seed=s, storage=storage)
+        prob.name = f"req{k}_" + prob.name
+        out.append((t, prob))
+    return out

@@ -1,0 +1,346 @@
+"""Throughput of the fused coupled D2Q9 + D2Q5 central-moment LBM step on GB300.
+
+Workload (default): Rayleigh-Benard convection in a 2:1 box, 2048 x 1024 nodes, periodic in x,
+Dirichlet walls T = +-0.5 at the bottom/top, Ra = 1e7, Pr = 0.71, u_c = 0.1, seeded T perturbation
+1e-3, FP32 population storage and FP32 arithmetic. One bench step = one time step of the whole
+lattice (every node: pull, macroscopics, D2Q9 and D2Q5 central-moment collision, store).
+
+Metric: MLUPS (million coupled node updates per second), with the fused step kernel's fraction of
+the measured HBM copy bandwidth. The timed region runs K steps back to back from CUDA-graph chunks
+on the lattice's stream; the two population buffers (2 x 117 MB in FP32) exceed the 129 MB L2, and
+the DRAM bytes per launch measured by ncu are reported beside the algorithmic bytes.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 (torchrun) every rank steps its own replica of the lattice (replicas only: the
+workload is one lattice per GPU and no data crosses GPUs); value = all ranks' node updates / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1710_10569_gb300 import workloads as W  # noqa: E402
+
+BYTES_PER_NODE = {W.STORAGE_F64: 224, W.STORAGE_F32: 112, W.STORAGE_F16DEV: 56}  # 14 in + 14 out
+DTYPE = {W.STORAGE_F64: "f64", W.STORAGE_F32: "f32", W.STORAGE_F16DEV: "f16dev storage, f32 arithmetic"}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_traffic.json")
+KERNEL_SOURCES = ["paper_1710_10569_gb300/csrc/clb_core.cuh", "paper_1710_10569_gb300/csrc/clb_kernels.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_per_launch(storage: int):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_hash():
+        return None
+    v = d.get("dram_bytes_per_launch", {}).get(W.STORAGE_NAMES[storage])
+    return float(v) if v else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(units: float, seconds: float, world: int):
+    """Whole-job throughput: total units over all ranks / the slowest rank's time."""
+    if world == 1:
+        return units, seconds
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([units, seconds], dtype=torch.float64, device=dev)
+    u = t[:1].clone()
+    s = t[1:].clone()
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+def workload(storage: int, nx: int = 2048, ny: int = 1024):
+    return W.rayleigh_benard(nx, ny, Ra=1e7, Pr=0.71, u_c=0.1, perturb=1e-3, seed=0, storage=storage)
+
+
+def time_steps(lat, steps: int, warmup: int, world: int):
+    import torch
+    lat.step(warmup)
+    lat.sync()
+    stream = torch.cuda.ExternalStream(lat.stream) if lat.stream else torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def cpu_baseline(storage: int, sample_steps: int = 6):
+    """The oracle, as it stands, on the full bench lattice for a few steps."""
+    import oracle
+    prob = workload(storage)
+    o = oracle.Oracle.from_problem(prob)
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(sample_steps)
+    dt = time.perf_counter() - t0
+    return {"value": prob.nodes * sample_steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"{sample_steps} steps of the full {prob.nx}x{prob.ny} lattice (FP64 oracle, "
+                      f"{oracle.threads()} OpenMP threads), {dt:.1f} s"}
+
+
+def e2e_run(storage: int, steps: int):
+    """The same metric through the public C ABI with host buffers: upload the initial fields from
+    pinned host memory, step, and read the fields back, all inside the timed region."""
+    import torch
+    from paper_1710_10569_gb300 import clb
+    prob = workload(storage)
+    n = prob.nodes
+    pin = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(8)]
+    for t, a in zip(pin[:4], prob.fields()):
+        t.numpy()[:] = a.ravel()
+    lat = clb.Lattice(prob.nx, prob.ny, prob.params)
+    lat.init_fields(*[t.numpy() for t in pin[:4]])
+    lat.step(64)
+    lat.sync()
+    t0 = time.perf_counter()
+    lat.init_fields(*[t.numpy() for t in pin[:4]])
+    lat.step(steps)
+    lat.fields_into(*[t.numpy() for t in pin[4:]])
+    dt = time.perf_counter() - t0
+    lat.close()
+    return {"value": n * steps / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": 4 * 8 * n / steps, "d2h_bytes_per_step": 4 * 8 * n / steps,
+            "steps": steps, "seconds": dt}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_1710_10569_gb300 import clb
+    storage = {"f64": W.STORAGE_F64, "f32": W.STORAGE_F32, "f16dev": W.STORAGE_F16DEV}[args.storage]
+
+    # CPU baseline first (before the GPU is busy), rank 0 at N = 1 only
+    cpu = cpu_baseline(storage) if (rank == 0 and world == 1 and not args.no_cpu) else None
+
+    prob = workload(storage)
+    lat = clb.Lattice.from_problem(prob)
+    if args.autotune:
+        lat.autotune()
+    with ClockSampler(local) as clocks:
+        secs = time_steps(lat, args.steps, args.warmup, world)
+    nodes = prob.nodes
+    units, tmax = aggregate(float(nodes) * args.steps, secs, world)
+    mlups = units / tmax / 1e6
+    peak, peak_kind = measured_peaks()
+    per_launch_s = secs / args.steps
+    alg_bytes = BYTES_PER_NODE[storage] * nodes
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = traffic_per_launch(storage)
+
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        for st in (W.STORAGE_F64, W.STORAGE_F16DEV, W.STORAGE_F32):
+            if st == storage:
+                continue
+            p2 = workload(st)
+            l2 = clb.Lattice.from_problem(p2)
+            k = max(200, args.steps // (8 if st == W.STORAGE_F64 else 2))
+            s2 = time_steps(l2, k, max(3, args.warmup // 4), 1)
+            variants[W.STORAGE_NAMES[st]] = {
+                "mlups": p2.nodes * k / s2 / 1e6,
+                "achieved_gbs": BYTES_PER_NODE[st] * p2.nodes / (s2 / k) / 1e9,
+                "hbm_frac": BYTES_PER_NODE[st] * p2.nodes / (s2 / k) / 1e9 / peak,
+                "steps": k, "dram_bytes_per_launch": traffic_per_launch(st)}
+            l2.close()
+    e2e = e2e_run(storage, args.steps) if rank == 0 else None
+    if rank == 0:
+        line = {
+            "metric": "coupled D2Q9+D2Q5 MLUPS & % HBM roofline", "value": mlups, "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[storage], "data": "synthetic",
+            "config": {"workload": f"rayleigh_benard_{prob.nx}x{prob.ny}_Ra1e7_Pr0.71",
+                       "nodes": nodes, "storage": W.STORAGE_NAMES[storage],
+                       "launch": list(lat.launch()),
+                       "l2": "no flush: two population buffers of "
+                             f"{2 * alg_bytes / 2 / 1e6:.0f} MB each (working set "
+                             f"{alg_bytes / 1e6:.0f} MB) exceed the 129 MB L2; ncu DRAM bytes per "
+                             "launch in roofline.traffic",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel": f"k_step<{W.STORAGE_NAMES[storage]}>",
+                         "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks.summary(),
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle (plain FP64 C, OpenMP over nodes) on the host cores, each step a bounded sample
+    of the workload: one time step of a 256 x 128 Rayleigh-Benard lattice with the bench
+    parameters."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    storage = W.STORAGE_F32
+    full = workload(storage)
+    prob = W.rayleigh_benard(256, 128, Ra=1e7, Pr=0.71, u_c=0.1, perturb=1e-3, seed=0, storage=storage)
+    prob.params.update({k: full.params[k] for k in ("nu", "kappa", "g_beta")})
+    o = oracle.Oracle.from_problem(prob)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = prob.nodes * args.steps / dt / 1e6
+    sample = (f"each step: one time step of a {prob.nx}x{prob.ny} lattice with the "
+              f"{full.nx}x{full.ny} workload's parameters")
+    line = {"impl": "reference", "metric": "coupled D2Q9+D2Q5 MLUPS & % HBM roofline", "value": v,
+            "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"rayleigh_benard_{full.nx}x{full.ny}_Ra1e7_Pr0.71",
+                       "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16dev"])
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,418 @@
+"""ctypes binding of libclb (include/clb.h), the coupled D2Q9 + D2Q5 central-moment LBM of
+arXiv:1710.10569 on a GB300. Argument marshalling only: every step of the method runs in the
+library's CUDA kernels. There is no CPU fallback; without a built libclb.so every call raises.
+
+The C entry points are exposed under their C names (``clb_create``, ``clb_step``, ...) through
+``lib()``; the classes below (``Lattice``, ``Batch``, ``Server``) wrap a handle and convert
+numpy/torch arrays to pointers. Device memory for a lattice is a torch uint8 tensor of
+``clb_footprint`` bytes handed to ``clb_create`` (PyTorch is the allocator; the library owns the
+layout), and work goes on torch's current CUDA stream unless a stream is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libclb.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "clb.h")
+
+CLB_OK, CLB_EINVAL, CLB_ENOMEM, CLB_ENAN, CLB_ETIMEOUT, CLB_ECUDA, CLB_EBUSY = range(7)
+STATUS_NAMES = {0: "CLB_OK", 1: "CLB_EINVAL", 2: "CLB_ENOMEM", 3: "CLB_ENAN", 4: "CLB_ETIMEOUT",
+                5: "CLB_ECUDA", 6: "CLB_EBUSY"}
+
+
+class CLBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class clb_params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("kappa", ctypes.c_double), ("g_beta", ctypes.c_double),
+                ("T0", ctypes.c_double), ("rho0", ctypes.c_double), ("s_b", ctypes.c_double),
+                ("s_3", ctypes.c_double), ("s_4", ctypes.c_double), ("lambda2", ctypes.c_double),
+                ("cs2_T", ctypes.c_double), ("Fv", ctypes.c_double * 2), ("wall", ctypes.c_int * 4),
+                ("T_wall", ctypes.c_double * 4), ("storage", ctypes.c_int), ("T_ref", ctypes.c_double),
+                ("u_ref", ctypes.c_double), ("dT_ref", ctypes.c_double)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_long
+_S = ctypes.c_size_t
+_P = ctypes.POINTER
+
+# name -> argtypes (restype is clb_status = int unless listed in _RESTYPES)
+_SIGS = {
+    "clb_params_default": [_P(clb_params)],
+    "clb_footprint": [_I, _I, _P(clb_params), _P(_S)],
+    "clb_create": [_I, _I, _P(clb_params), _VP, _VP, _S, _P(_VP)],
+    "clb_destroy": [_VP],
+    "clb_init_fields": [_VP, _D, _D, _D, _D],
+    "clb_init_fields_device": [_VP, _VP, _VP, _VP, _VP],
+    "clb_step": [_VP, _L],
+    "clb_fields": [_VP, _D, _D, _D, _D],
+    "clb_fields_device": [_VP, _VP, _VP, _VP, _VP],
+    "clb_populations": [_VP, _D, _D],
+    "clb_nusselt": [_VP, _I, _D],
+    "clb_residual": [_VP, _D],
+    "clb_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D],
+    "clb_steps": [_VP, _P(_L)],
+    "clb_sync": [_VP],
+    "clb_save": [_VP, _VP, _P(_S)],
+    "clb_load": [_VP, _VP, _S],
+    "clb_set_launch": [_VP, _I, _I],
+    "clb_get_launch": [_VP, _P(_I), _P(_I)],
+    "clb_autotune": [_VP, _P(_I), _P(_I)],
+    "clb_stream": [_VP],
+    "clb_buffers": [_VP, _P(_VP), _P(_VP), _P(_S), _P(_I)],
+    "clb_last_error": [],
+    "clb_version": [],
+    "clb_batch_create": [_I, _P(_I), _P(_I), _P(clb_params), _VP, _P(_VP)],
+    "clb_batch_destroy": [_VP],
+    "clb_batch_init_fields": [_VP, _I, _D, _D, _D, _D],
+    "clb_batch_step": [_VP, _L],
+    "clb_batch_fields": [_VP, _I, _D, _D, _D, _D],
+    "clb_batch_diagnostics": [_VP, _P(_I), _D, _D],
+    "clb_batch_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D, _P(_I)],
+    "clb_batch_set_tile": [_VP, _I, _I],
+    "clb_serve_open": [_S, _I, _I, _VP, _P(_VP)],
+    "clb_serve_close": [_VP],
+    "clb_serve_submit": [_VP, _I, _I, _P(clb_params), _D, _D, _D, _D, _I, _L, ctypes.c_double, _P(_L)],
+    "clb_serve_progress": [_VP, _L, _P(_I), _P(_I)],
+    "clb_serve_poll": [_VP, _L, _P(_I), _D, _P(_L), _D],
+    "clb_serve_fetch": [_VP, _L, _D, _D, _D, _D],
+}
+_RESTYPES = {"clb_destroy": None, "clb_batch_destroy": None, "clb_serve_close": None,
+             "clb_last_error": ctypes.c_char_p, "clb_version": ctypes.c_char_p, "clb_stream": _VP}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libclb with typed entry points. Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libclb.so is not built ({LIB_PATH}); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = _RESTYPES.get(name, ctypes.c_int)
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != CLB_OK:
+        raise CLBError(status, lib().clb_last_error().decode(errors="replace"))
+
+
+def params(p: dict) -> clb_params:
+    """clb_params from a parameter dict (see workloads.default_params)."""
+    s = clb_params()
+    for k in ("nu", "kappa", "g_beta", "T0", "rho0", "s_b", "s_3", "s_4", "lambda2", "cs2_T", "T_ref",
+              "u_ref", "dT_ref"):
+        setattr(s, k, float(p[k]))
+    s.Fv[0], s.Fv[1] = (float(v) for v in p["Fv"])
+    for i in range(4):
+        s.wall[i] = int(p["wall"][i])
+        s.T_wall[i] = float(p["T_wall"][i])
+    s.storage = int(p["storage"])
+    return s
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous, "need C-contiguous float64"
+    return a.ctypes.data_as(_D)
+
+
+def _host(a, n):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"field has {a.size} values, lattice has {n} nodes")
+    return a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _tptr(t):
+    if t is None:
+        return None
+    import torch
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    return t.data_ptr()
+
+
+class Lattice:
+    """One lattice on the GPU (handle of clb_create)."""
+
+    def __init__(self, nx: int, ny: int, p: dict, stream=None, torch_memory: bool = True):
+        import torch
+        L = lib()
+        self.nx, self.ny, self.params = int(nx), int(ny), dict(p)
+        self._p = params(p)
+        nbytes = _S()
+        _check(L.clb_footprint(self.nx, self.ny, ctypes.byref(self._p), ctypes.byref(nbytes)))
+        self.footprint = nbytes.value
+        self._mem = None
+        mem_ptr = None
+        if torch_memory:
+            # torch's caching allocator hands out 512-byte aligned blocks
+            self._mem = torch.empty(self.footprint, dtype=torch.uint8, device="cuda")
+            mem_ptr = self._mem.data_ptr()
+        self.stream = _stream_handle(stream)
+        h = _VP()
+        _check(L.clb_create(self.nx, self.ny, ctypes.byref(self._p), self.stream, mem_ptr,
+                            self.footprint if mem_ptr else 0, ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_problem(cls, prob: W.Problem, **kw) -> "Lattice":
+        lat = cls(prob.nx, prob.ny, prob.params, **kw)
+        lat.init_fields(prob.rho, prob.ux, prob.uy, prob.T)
+        return lat
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().clb_destroy(self._h)
+            self._h = None
+            self._mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, rho=None, ux=None, uy=None, T=None):
+        n = self.nodes
+        arrs = [_host(a, n) for a in (rho, ux, uy, T)]
+        _check(lib().clb_init_fields(self._h, *[_dptr(a) for a in arrs]))
+
+    def init_fields_device(self, rho=None, ux=None, uy=None, T=None):
+        _check(lib().clb_init_fields_device(self._h, *[_tptr(t) for t in (rho, ux, uy, T)]))
+
+    def step(self, n: int = 1):
+        _check(lib().clb_step(self._h, int(n)))
+
+    def fields(self):
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        _check(lib().clb_fields(self._h, *[_dptr(a) for a in out]))
+        return tuple(out)
+
+    def fields_into(self, rho=None, ux=None, uy=None, T=None):
+        """Host (numpy, e.g. pinned) outputs; any may be None."""
+        _check(lib().clb_fields(self._h, *[_dptr(a) for a in (rho, ux, uy, T)]))
+
+    def fields_device(self, rho=None, ux=None, uy=None, T=None):
+        _check(lib().clb_fields_device(self._h, *[_tptr(t) for t in (rho, ux, uy, T)]))
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((5, self.ny, self.nx))
+        _check(lib().clb_populations(self._h, _dptr(f), _dptr(g)))
+        return f, g
+
+    def nusselt(self, axis: int = 1) -> float:
+        v = ctypes.c_double()
+        _check(lib().clb_nusselt(self._h, int(axis), ctypes.byref(v)))
+        return v.value
+
+    def residual(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().clb_residual(self._h, ctypes.byref(v)))
+        return v.value
+
+    def run(self, tol: float, max_steps: int, interval: int = 100):
+        st, er = _L(), ctypes.c_double()
+        _check(lib().clb_run(self._h, float(tol), int(max_steps), int(interval), ctypes.byref(st),
+                             ctypes.byref(er)))
+        return st.value, er.value
+
+    @property
+    def steps(self) -> int:
+        v = _L()
+        _check(lib().clb_steps(self._h, ctypes.byref(v)))
+        return v.value
+
+    def sync(self):
+        _check(lib().clb_sync(self._h))
+
+    def save(self) -> bytes:
+        n = _S()
+        _check(lib().clb_save(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().clb_save(self._h, ctypes.cast(buf, _VP), ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def load(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(lib().clb_load(self._h, ctypes.cast(buf, _VP), len(data)))
+
+    def set_launch(self, block_x: int = 0, block_y: int = 0):
+        _check(lib().clb_set_launch(self._h, int(block_x), int(block_y)))
+
+    def launch(self):
+        bx, by = _I(), _I()
+        _check(lib().clb_get_launch(self._h, ctypes.byref(bx), ctypes.byref(by)))
+        return bx.value, by.value
+
+    def autotune(self):
+        bx, by = _I(), _I()
+        _check(lib().clb_autotune(self._h, ctypes.byref(bx), ctypes.byref(by)))
+        return bx.value, by.value
+
+    def buffers(self):
+        cur, oth, pl, pitch = _VP(), _VP(), _S(), _I()
+        _check(lib().clb_buffers(self._h, ctypes.byref(cur), ctypes.byref(oth), ctypes.byref(pl),
+                                 ctypes.byref(pitch)))
+        return cur.value, oth.value, pl.value, pitch.value
+
+
+class Batch:
+    """Many lattices stepped in one launch per time step (clb_batch_*)."""
+
+    def __init__(self, problems, stream=None):
+        L = lib()
+        self.problems = list(problems)
+        n = len(self.problems)
+        nx = (ctypes.c_int * n)(*[p.nx for p in self.problems])
+        ny = (ctypes.c_int * n)(*[p.ny for p in self.problems])
+        ps = (clb_params * n)(*[params(p.params) for p in self.problems])
+        self.stream = _stream_handle(stream)
+        h = _VP()
+        _check(L.clb_batch_create(n, nx, ny, ps, self.stream, ctypes.byref(h)))
+        self._h = h
+        self._axis = (ctypes.c_int * n)(*[p.nu_axis for p in self.problems])
+        for k, p in enumerate(self.problems):
+            self.init_fields(k, p.rho, p.ux, p.uy, p.T)
+
+    def __len__(self):
+        return len(self.problems)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().clb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, k, rho=None, ux=None, uy=None, T=None):
+        n = self.problems[k].nodes
+        arrs = [_host(a, n) for a in (rho, ux, uy, T)]
+        _check(lib().clb_batch_init_fields(self._h, int(k), *[_dptr(a) for a in arrs]))
+
+    def step(self, n: int = 1):
+        _check(lib().clb_batch_step(self._h, int(n)))
+
+    def fields(self, k):
+        p = self.problems[k]
+        out = [np.empty((p.ny, p.nx)) for _ in range(4)]
+        _check(lib().clb_batch_fields(self._h, int(k), *[_dptr(a) for a in out]))
+        return tuple(out)
+
+    def diagnostics(self):
+        n = len(self.problems)
+        nu, er = np.empty(n), np.empty(n)
+        _check(lib().clb_batch_diagnostics(self._h, self._axis, _dptr(nu), _dptr(er)))
+        return nu, er
+
+    def run(self, tol: float, max_steps: int, interval: int = 100):
+        n = len(self.problems)
+        steps = (ctypes.c_long * n)()
+        er = np.empty(n)
+        status = (ctypes.c_int * n)()
+        _check(lib().clb_batch_run(self._h, float(tol), int(max_steps), int(interval), steps,
+                                   _dptr(er), status))
+        return np.array(steps[:], dtype=np.int64), er, np.array(status[:], dtype=np.int32)
+
+    def set_tile(self, tile_x: int, tile_y: int = 1):
+        _check(lib().clb_batch_set_tile(self._h, int(tile_x), int(tile_y)))
+
+
+class Server:
+    """Continuous-batching request server (clb_serve_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int, storage: int, stream=None):
+        self.stream = _stream_handle(stream)
+        h = _VP()
+        _check(lib().clb_serve_open(int(hbm_budget_bytes), int(max_slots), int(storage), self.stream,
+                                    ctypes.byref(h)))
+        self._h = h
+        self.storage = storage
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().clb_serve_close(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, prob: W.Problem, step_cap: int, tol: float) -> int:
+        n = prob.nodes
+        arrs = [_host(a, n) for a in prob.fields()]
+        p = params(prob.params)
+        rid = _L()
+        _check(lib().clb_serve_submit(self._h, prob.nx, prob.ny, ctypes.byref(p),
+                                      *[_dptr(a) for a in arrs], int(prob.nu_axis), int(step_cap),
+                                      float(tol), ctypes.byref(rid)))
+        return rid.value
+
+    def progress(self, chunk: int):
+        a, q = _I(), _I()
+        _check(lib().clb_serve_progress(self._h, int(chunk), ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, rid: int):
+        done, nu, steps, er = _I(), ctypes.c_double(), _L(), ctypes.c_double()
+        _check(lib().clb_serve_poll(self._h, int(rid), ctypes.byref(done), ctypes.byref(nu),
+                                    ctypes.byref(steps), ctypes.byref(er)))
+        return bool(done.value), nu.value, steps.value, er.value
+
+    def fetch(self, rid: int, ny: int, nx: int):
+        out = [np.empty((ny, nx)) for _ in range(4)]
+        _check(lib().clb_serve_fetch(self._h, int(rid), *[_dptr(a) for a in out]))
+        return tuple(out)
+
+
+def declared_entry_points(header: str = HEADER):
+    """Names of the functions include/clb.h declares."""
+    import re
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(clb_[a-z0-9_]+)\s*\(", text)))

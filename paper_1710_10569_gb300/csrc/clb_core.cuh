@@ -1,0 +1,248 @@
+// clb_core.cuh -- per-node device arithmetic of the coupled D2Q9 + D2Q5 central-moment LBM
+// (Fei, Luo, Lin & Li, arXiv:1710.10569, Sec. 2).
+//
+// The moment transforms are applied in factorised form. The raw-moment map M of Eq. (7a) and the
+// shift N(u) of Eq. (7b) are tensor products of one-dimensional maps over the velocity components
+// (M = M_y (x) M_x, N(u) = N_y(u_y) (x) N_x(u_x)), so the nine central moments follow from two
+// passes of three-point sums: x-central moments of each row of equal e_y, then y-central moments
+// of those. The back transform f* = M^-1 N(u)^-1 Gamma~* (the sentence after Eq. 12) runs the same
+// passes backwards with the 1-D inverse (f_0 = m_0 - m_2, f_+- = (m_2 +- m_1)/2). The D2Q5 part
+// (Eqs. 16-21, Appendix A) is the same construction with one row per axis. This is about 200 flops
+// per node instead of the ~1,600 of literal 9x9 products, and the result is the same map.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace clb {
+
+enum { WALL_PERIODIC = 0, WALL_DIRICHLET = 1, WALL_ADIABATIC = 2 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2 };
+enum { NPOP = 14 };  // 9 flow + 5 temperature planes per buffer
+
+// Storage traits: element type in HBM and arithmetic type in registers.
+template <int ST> struct Storage;
+template <> struct Storage<ST_F64> { using T = double; using A = double; };
+template <> struct Storage<ST_F32> { using T = float; using A = float; };
+template <> struct Storage<ST_F16DEV> { using T = __half; using A = float; };
+
+__device__ __forceinline__ double to_a(double v, double) { return v; }
+__device__ __forceinline__ float to_a(float v, float) { return v; }
+__device__ __forceinline__ float to_a(__half v, float base) { return __half2float(v) + base; }
+__device__ __forceinline__ double from_a(double v, double, double*) { return v; }
+__device__ __forceinline__ float from_a(float v, float, float*) { return v; }
+__device__ __forceinline__ __half from_a(float v, float base, __half*) { return __float2half_rn(v - base); }
+
+// Per-lattice constants in the arithmetic precision A.
+template <typename A>
+struct LatParams {
+    int nx, ny, pitch;        // pitch: elements per row (row starts are 128-byte aligned)
+    int per_x, per_y;         // periodic flags
+    long long plane;          // elements between population planes
+    int kind[4];              // wall kind per side (-x, +x, -y, +y)
+    A Tw_c2[4];               // cs2_T * T_wall: the anti-bounce-back constant 2 w_i T_w
+    A s_nu, sp, sm, s_3, s_4; // D2Q9 rates; sp = (s_b + s_nu)/2, sm = (s_b - s_nu)/2
+    A lambda1, lambda2, cs2T; // D2Q5 rates and sound speed squared
+    A Fvx, Fvy, gb, T0;       // F = (Fvx, Fvy + gb (T - T0)), gb = rho0 * g_beta
+    A base_f[9], base_g[5];   // FP16 deviation bases (zero for the other storages)
+};
+
+// Gather (pull) the pre-collision populations of node (x, y) from the post-collision buffer of
+// the previous step, Eqs. (12) and (22): f_i(x) = f*_i(x - e_i). Where x - e_i is beyond a wall
+// the node's own opposite population is used (halfway bounce-back for f; anti-bounce-back or
+// bounce-back for g according to the wall kind). Velocity order of Eq. (4):
+// 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+template <typename T, typename A>
+__device__ __forceinline__ void gather(const T* __restrict__ src, const LatParams<A>& P, int x, int y,
+                                       A f[9], A g[5])
+{
+    const bool inL = P.per_x || x > 0;
+    const bool inR = P.per_x || x < P.nx - 1;
+    const bool inB = P.per_y || y > 0;
+    const bool inT = P.per_y || y < P.ny - 1;
+    const int xm = x > 0 ? x - 1 : P.nx - 1;
+    const int xp = x < P.nx - 1 ? x + 1 : 0;
+    const long long r0 = (long long)y * P.pitch;
+    const long long rm = (long long)(y > 0 ? y - 1 : P.ny - 1) * P.pitch;
+    const long long rp = (long long)(y < P.ny - 1 ? y + 1 : 0) * P.pitch;
+    const long long here = r0 + x;
+    const long long pl = P.plane;
+    // pulled (plane, index) or bounced (opposite plane, own index)
+    const long long i1 = inL ? 1 * pl + r0 + xm : 3 * pl + here;
+    const long long i2 = inB ? 2 * pl + rm + x : 4 * pl + here;
+    const long long i3 = inR ? 3 * pl + r0 + xp : 1 * pl + here;
+    const long long i4 = inT ? 4 * pl + rp + x : 2 * pl + here;
+    const long long i5 = (inL && inB) ? 5 * pl + rm + xm : 7 * pl + here;
+    const long long i6 = (inR && inB) ? 6 * pl + rm + xp : 8 * pl + here;
+    const long long i7 = (inR && inT) ? 7 * pl + rp + xp : 5 * pl + here;
+    const long long i8 = (inL && inT) ? 8 * pl + rp + xm : 6 * pl + here;
+    f[0] = to_a(src[here], P.base_f[0]);
+    f[1] = to_a(src[i1], P.base_f[1]);
+    f[2] = to_a(src[i2], P.base_f[2]);
+    f[3] = to_a(src[i3], P.base_f[3]);
+    f[4] = to_a(src[i4], P.base_f[4]);
+    f[5] = to_a(src[i5], P.base_f[5]);
+    f[6] = to_a(src[i6], P.base_f[6]);
+    f[7] = to_a(src[i7], P.base_f[7]);
+    f[8] = to_a(src[i8], P.base_f[8]);
+    const T* gs = src + 9 * pl;
+    const long long j1 = inL ? 1 * pl + r0 + xm : 3 * pl + here;
+    const long long j2 = inB ? 2 * pl + rm + x : 4 * pl + here;
+    const long long j3 = inR ? 3 * pl + r0 + xp : 1 * pl + here;
+    const long long j4 = inT ? 4 * pl + rp + x : 2 * pl + here;
+    g[0] = to_a(gs[here], P.base_g[0]);
+    g[1] = to_a(gs[j1], P.base_g[1]);
+    g[2] = to_a(gs[j2], P.base_g[2]);
+    g[3] = to_a(gs[j3], P.base_g[3]);
+    g[4] = to_a(gs[j4], P.base_g[4]);
+    // anti-bounce-back on Dirichlet walls: g_i = cs2_T T_w - g*_opp (adiabatic: g*_opp as loaded)
+    if (!inL && P.kind[0] == WALL_DIRICHLET) g[1] = P.Tw_c2[0] - g[1];
+    if (!inR && P.kind[1] == WALL_DIRICHLET) g[3] = P.Tw_c2[1] - g[3];
+    if (!inB && P.kind[2] == WALL_DIRICHLET) g[2] = P.Tw_c2[2] - g[2];
+    if (!inT && P.kind[3] == WALL_DIRICHLET) g[4] = P.Tw_c2[3] - g[4];
+}
+
+template <typename T, typename A>
+__device__ __forceinline__ void store_node(T* __restrict__ dst, const LatParams<A>& P, int x, int y,
+                                           const A f[9], const A g[5])
+{
+    const long long here = (long long)y * P.pitch + x;
+    const long long pl = P.plane;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dst[i * pl + here] = from_a(f[i], P.base_f[i], (T*)nullptr);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) dst[(9 + i) * pl + here] = from_a(g[i], P.base_g[i], (T*)nullptr);
+}
+
+// Macroscopic fields, Eqs. (3), (13), (23).
+template <typename A>
+struct Macro {
+    A rho, ux, uy, T, Fx, Fy;
+};
+
+template <typename A>
+__device__ __forceinline__ Macro<A> macroscopic(const LatParams<A>& P, const A f[9], const A g[5])
+{
+    Macro<A> m;
+    m.rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    m.T = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    m.Fx = P.Fvx;
+    m.Fy = P.Fvy + P.gb * (m.T - P.T0);
+    const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const A jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const A inv = A(1) / m.rho;
+    m.ux = (jx + A(0.5) * m.Fx) * inv;
+    m.uy = (jy + A(0.5) * m.Fy) * inv;
+    return m;
+}
+
+// Three-point central moments (orders 0, 1, 2) of values c (e = 0), p (e = +1), m (e = -1) about u.
+template <typename A>
+__device__ __forceinline__ void central3(A c, A p, A m, A u, A& k0, A& k1, A& k2)
+{
+    const A s0 = c + p + m;
+    const A d = p - m;
+    const A s = p + m;
+    k0 = s0;
+    k1 = d - u * s0;
+    k2 = s - A(2) * u * d + u * u * s0;
+}
+
+// Inverse of central3: raw moments about 0 (shift back by u), then the 1-D inverse moment map.
+template <typename A>
+__device__ __forceinline__ void uncentral3(A k0, A k1, A k2, A u, A& c, A& p, A& m)
+{
+    const A r1 = k1 + u * k0;
+    const A r2 = k2 + A(2) * u * k1 + u * u * k0;
+    c = k0 - r2;
+    p = A(0.5) * (r2 + r1);
+    m = A(0.5) * (r2 - r1);
+}
+
+// f* = M^-1 N(u)^-1 k~ for central moments k~[a][b] (a: x order, b: y order).
+template <typename A>
+__device__ __forceinline__ void back_d2q9(const A k[3][3], A ux, A uy, A f[9])
+{
+    // y pass: for each x order a, the x-central moment a of the rows e_y = 0, +1, -1
+    A r0[3], rp[3], rm[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) uncentral3(k[a][0], k[a][1], k[a][2], uy, r0[a], rp[a], rm[a]);
+    // x pass per row: (centre, +x, -x) = (0,1,3), (2,5,6), (4,8,7)
+    uncentral3(r0[0], r0[1], r0[2], ux, f[0], f[1], f[3]);
+    uncentral3(rp[0], rp[1], rp[2], ux, f[2], f[5], f[6]);
+    uncentral3(rm[0], rm[1], rm[2], ux, f[4], f[8], f[7]);
+}
+
+template <typename A>
+__device__ __forceinline__ void back_d2q5(A T, A k10, A k01, A k20, A k02, A ux, A uy, A g[5])
+{
+    // Each axis row shares the rest population g0; split the two 1-D inverses over it.
+    const A r10 = k10 + ux * T;
+    const A r20 = k20 + A(2) * ux * k10 + ux * ux * T;
+    const A r01 = k01 + uy * T;
+    const A r02 = k02 + A(2) * uy * k01 + uy * uy * T;
+    g[0] = T - r20 - r02;
+    g[1] = A(0.5) * (r20 + r10);
+    g[3] = A(0.5) * (r20 - r10);
+    g[2] = A(0.5) * (r02 + r01);
+    g[4] = A(0.5) * (r02 - r01);
+}
+
+// Collision of one node in place: Eqs. (6)-(11) for f, Eqs. (16)-(21) for g.
+template <typename A>
+__device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5])
+{
+    const Macro<A> m = macroscopic(P, f, g);
+    const A ux = m.ux, uy = m.uy, rho = m.rho, T = m.T;
+    const A cs2 = A(1) / A(3);
+
+    // ---- D2Q9: central moments k[a][b] = sum f (e_x - u_x)^a (e_y - u_y)^b (Eq. 5b)
+    A r0[3], rp[3], rm[3];
+    central3(f[0], f[1], f[3], ux, r0[0], r0[1], r0[2]);  // row e_y = 0
+    central3(f[2], f[5], f[6], ux, rp[0], rp[1], rp[2]);  // row e_y = +1
+    central3(f[4], f[8], f[7], ux, rm[0], rm[1], rm[2]);  // row e_y = -1
+    A k[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) central3(r0[a], rp[a], rm[a], uy, k[a][0], k[a][1], k[a][2]);
+
+    // ---- relaxation, Eq. (8), equilibrium Eq. (9), forcing Eq. (11)
+    const A a20 = k[2][0] - rho * cs2;
+    const A a02 = k[0][2] - rho * cs2;
+    A q[3][3];
+    q[0][0] = rho;
+    q[1][0] = k[1][0] + m.Fx;
+    q[0][1] = k[0][1] + m.Fy;
+    q[2][0] = k[2][0] - P.sp * a20 - P.sm * a02;
+    q[0][2] = k[0][2] - P.sm * a20 - P.sp * a02;
+    q[1][1] = (A(1) - P.s_nu) * k[1][1];
+    const A half3 = (A(1) - A(0.5) * P.s_3) * cs2;
+    q[2][1] = (A(1) - P.s_3) * k[2][1] + half3 * m.Fy;
+    q[1][2] = (A(1) - P.s_3) * k[1][2] + half3 * m.Fx;
+    q[2][2] = (A(1) - P.s_4) * k[2][2] + P.s_4 * rho * cs2 * cs2;
+    back_d2q9(q, ux, uy, f);
+
+    // ---- D2Q5: central moments, relaxation (Eqs. 19, 20), back transform (Eq. 21)
+    const A d1 = g[1] - g[3], s1 = g[1] + g[3];
+    const A d2 = g[2] - g[4], s2 = g[2] + g[4];
+    const A t10 = d1 - ux * T;
+    const A t01 = d2 - uy * T;
+    const A t20 = s1 - A(2) * ux * d1 + ux * ux * T;
+    const A t02 = s2 - A(2) * uy * d2 + uy * uy * T;
+    const A om1 = A(1) - P.lambda1;
+    const A om2 = A(1) - P.lambda2;
+    const A eqT = P.lambda2 * T * P.cs2T;
+    back_d2q5(T, om1 * t10, om1 * t01, om2 * t20 + eqT, om2 * t02 + eqT, ux, uy, g);
+}
+
+// Equilibria f^eq(rho, u) and g^eq(T, u): the back transform of Eqs. (9) and (20).
+template <typename A>
+__device__ __forceinline__ void equilibrium(const LatParams<A>& P, A rho, A ux, A uy, A T, A f[9],
+                                            A g[5])
+{
+    const A cs2 = A(1) / A(3);
+    A k[3][3] = {{rho, A(0), rho * cs2}, {A(0), A(0), A(0)}, {rho * cs2, A(0), rho * cs2 * cs2}};
+    back_d2q9(k, ux, uy, f);
+    back_d2q5(T, A(0), A(0), T * P.cs2T, T * P.cs2T, ux, uy, g);
+}
+
+}  // namespace clb

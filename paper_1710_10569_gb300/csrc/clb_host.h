@@ -1,0 +1,150 @@
+// clb_host.h -- host-side helpers shared by the libclb translation units: thread-local error
+// reporting, parameter validation, and the derivation of the per-lattice device constants
+// (relaxation rates from nu and kappa, Sec. 2.1 and Sec. 2.2).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/clb.h"
+#include "clb_core.cuh"
+
+namespace clb {
+
+clb_status set_error(clb_status st, const char* fmt, ...);
+void clear_error();
+
+#define CLB_CUDA(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return ::clb::set_error(e_ == cudaErrorMemoryAllocation ? CLB_ENOMEM : CLB_ECUDA,   \
+                                    "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
+                                    __LINE__);                                                  \
+    } while (0)
+
+#define CLB_TRY(expr)                           \
+    do {                                        \
+        clb_status s_ = (expr);                 \
+        if (s_ != CLB_OK) return s_;            \
+    } while (0)
+
+constexpr long long kMaxNodes = 1LL << 30;  // index arithmetic and memory bound
+constexpr int kMaxEdge = 1 << 20;
+
+inline size_t elem_size(int storage)
+{
+    return storage == ST_F64 ? 8 : storage == ST_F32 ? 4 : 2;
+}
+
+// Row pitch in elements: rows start on 128-byte boundaries.
+inline int row_pitch(int nx, int storage)
+{
+    const int per = int(128 / elem_size(storage));
+    return (nx + per - 1) / per * per;
+}
+
+// Elements between population planes: planes start on 256-byte boundaries.
+inline long long plane_elems(int nx, int ny, int storage)
+{
+    const long long per = 256 / (long long)elem_size(storage);
+    const long long e = (long long)row_pitch(nx, storage) * ny;
+    return (e + per - 1) / per * per;
+}
+
+inline size_t buffer_bytes(int nx, int ny, int storage)
+{
+    return (size_t)NPOP * (size_t)plane_elems(nx, ny, storage) * elem_size(storage);
+}
+
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+clb_status validate(int nx, int ny, const clb_params* p);
+
+// s_nu from nu = (1/s_nu - 1/2) c_s^2 with c_s^2 = 1/3 (Sec. 2.1).
+inline double rate_nu(double nu) { return 1.0 / (3.0 * nu + 0.5); }
+// lambda1 from alpha = (1/lambda1 - 1/2) c_T,s^2 (Sec. 2.2).
+inline double rate_kappa(double kappa, double cs2T) { return 1.0 / (kappa / cs2T + 0.5); }
+
+// Device constants of one lattice in arithmetic precision A.
+template <typename A>
+LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
+{
+    LatParams<A> P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = nx;
+    P.ny = ny;
+    P.pitch = row_pitch(nx, p.storage);
+    P.plane = plane_elems(nx, ny, p.storage);
+    P.per_x = p.wall[0] == CLB_PERIODIC;
+    P.per_y = p.wall[2] == CLB_PERIODIC;
+    for (int s = 0; s < 4; ++s) {
+        P.kind[s] = p.wall[s];
+        P.Tw_c2[s] = A(p.cs2_T * p.T_wall[s]);
+    }
+    const double s_nu = rate_nu(p.nu);
+    P.s_nu = A(s_nu);
+    P.sp = A(0.5 * (p.s_b + s_nu));
+    P.sm = A(0.5 * (p.s_b - s_nu));
+    P.s_3 = A(p.s_3);
+    P.s_4 = A(p.s_4);
+    P.lambda1 = A(rate_kappa(p.kappa, p.cs2_T));
+    P.lambda2 = A(p.lambda2);
+    P.cs2T = A(p.cs2_T);
+    P.Fvx = A(p.Fv[0]);
+    P.Fvy = A(p.Fv[1]);
+    P.gb = A(p.rho0 * p.g_beta);
+    P.T0 = A(p.T0);
+    if (p.storage == ST_F16DEV) {
+        // rest weights of D2Q9 (Eq. 9 at u = 0) and D2Q5 (Eq. 20 at u = 0)
+        const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+        const double w5[5] = {1.0 - 2.0 * p.cs2_T, 0.5 * p.cs2_T, 0.5 * p.cs2_T, 0.5 * p.cs2_T,
+                              0.5 * p.cs2_T};
+        for (int i = 0; i < 9; ++i) P.base_f[i] = A(w9[i] * p.rho0);
+        for (int i = 0; i < 5; ++i) P.base_g[i] = A(w5[i] * p.T_ref);
+    }
+    return P;
+}
+
+// Nusselt geometry of Eq. (29) for one axis: H, dT and the sign making heat flow from the hot
+// side positive.
+struct NuGeom {
+    double H, dT, sign;
+};
+inline NuGeom nu_geom(int nx, int ny, const clb_params& p, int axis)
+{
+    const int lo = axis == 0 ? 0 : 2, hi = lo + 1;
+    NuGeom g;
+    g.H = axis == 0 ? nx : ny;
+    const double d = std::fabs(p.T_wall[lo] - p.T_wall[hi]);
+    g.dT = d > 0 ? d : 1.0;
+    g.sign = p.T_wall[lo] >= p.T_wall[hi] ? 1.0 : -1.0;
+    return g;
+}
+
+// Reduction partial sums of one row (or block), in this order.
+enum { RS_UT = 0, RS_DU, RS_U, RS_DT, RS_T, RS_BAD, RS_N };
+
+// Final scalars from the summed partials (host or device).
+__host__ __device__ inline void finish_diagnostics(const double* s, double nodes, double H,
+                                                   double dT, double sign, double kappa,
+                                                   double u_ref, double dT_ref, double* nu,
+                                                   double* er)
+{
+    *nu = 1.0 + sign * (s[RS_UT] / nodes) * H / (kappa * dT);
+    const double fu = nodes * (1e-3 * u_ref) * (1e-3 * u_ref);
+    const double fT = nodes * (1e-3 * dT_ref) * (1e-3 * dT_ref);
+    const double du = s[RS_U] > fu ? s[RS_U] : fu;
+    const double dt = s[RS_T] > fT ? s[RS_T] : fT;
+    const double ru = s[RS_DU] == 0.0 ? 0.0 : (du > 0 ? sqrt(s[RS_DU] / du) : INFINITY);
+    const double rt = s[RS_DT] == 0.0 ? 0.0 : (dt > 0 ? sqrt(s[RS_DT] / dt) : INFINITY);
+    *er = ru > rt ? ru : rt;
+}
+
+}  // namespace clb

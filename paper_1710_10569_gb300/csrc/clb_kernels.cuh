@@ -1,0 +1,205 @@
+// clb_kernels.cuh -- the kernels of one lattice: fused collide-and-stream step, equilibrium
+// initialisation, field and population extraction, and the FP64 diagnostics reduction
+// (Nusselt number of Eq. 29 and the steady-state residual).
+#pragma once
+
+#include "clb_core.cuh"
+#include "clb_host.h"
+
+namespace clb {
+
+// One time step: pull the 14 populations of node (x, y) (Eqs. 12, 22, with the wall rules),
+// collide them (Eqs. 3-11, 13, 16-21, 23) and store the post-collision values at (x, y).
+template <int ST>
+__global__ void __launch_bounds__(512) k_step(const typename Storage<ST>::T* __restrict__ src,
+                                              typename Storage<ST>::T* __restrict__ dst,
+                                              const LatParams<typename Storage<ST>::A> P)
+{
+    using A = typename Storage<ST>::A;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    A f[9], g[5];
+    gather(src, P, x, y, f, g);
+    collide(P, f, g);
+    store_node(dst, P, x, y, f, g);
+}
+
+// Initialisation to f^eq(rho, u), g^eq(T, u). The buffer holds post-collision values that the
+// next step pulls, so each equilibrium value is written to the slot its pull reads: population i
+// of node x goes to (i, x - e_i), or, when x - e_i is beyond a wall, to the node's own opposite
+// slot (with the anti-bounce-back constant removed on Dirichlet walls). Every slot is written
+// exactly once. NULL fields mean rho = 1, u = 0, T = T0.
+template <int ST>
+__global__ void k_init(typename Storage<ST>::T* __restrict__ dst, const LatParams<typename Storage<ST>::A> P,
+                       const double* __restrict__ rho, const double* __restrict__ ux,
+                       const double* __restrict__ uy, const double* __restrict__ T)
+{
+    using A = typename Storage<ST>::A;
+    using E = typename Storage<ST>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long n = (long long)y * P.nx + x;
+    A f[9], g[5];
+    equilibrium(P, rho ? A(rho[n]) : A(1), ux ? A(ux[n]) : A(0), uy ? A(uy[n]) : A(0),
+                T ? A(T[n]) : P.T0, f, g);
+    const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        int sx = x - EX[i], sy = y - EY[i];
+        int side = -1;
+        if (sx < 0) { if (P.per_x) sx += P.nx; else side = 0; }
+        if (sx >= P.nx) { if (P.per_x) sx -= P.nx; else side = 1; }
+        if (sy < 0) { if (P.per_y) sy += P.ny; else side = 2; }
+        if (sy >= P.ny) { if (P.per_y) sy -= P.ny; else side = 3; }
+        long long slot;
+        int plane;
+        if (side < 0) {
+            plane = i;
+            slot = (long long)sy * P.pitch + sx;
+        } else {
+            plane = OPP[i];
+            slot = (long long)y * P.pitch + x;
+        }
+        dst[plane * P.plane + slot] = from_a(f[i], P.base_f[plane], (E*)nullptr);
+        if (i < 5) {
+            A v = g[i];
+            if (side >= 0 && P.kind[side] == WALL_DIRICHLET) v = P.Tw_c2[side] - v;
+            dst[(9 + plane) * P.plane + slot] = from_a(v, P.base_g[plane], (E*)nullptr);
+        }
+    }
+}
+
+// rho, u, T at the current time (gathered pre-collision populations), as double [ny][nx].
+template <int ST>
+__global__ void k_fields(const typename Storage<ST>::T* __restrict__ src,
+                         const LatParams<typename Storage<ST>::A> P, double* __restrict__ rho,
+                         double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ T)
+{
+    using A = typename Storage<ST>::A;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    A f[9], g[5];
+    gather(src, P, x, y, f, g);
+    const Macro<A> m = macroscopic(P, f, g);
+    const long long n = (long long)y * P.nx + x;
+    if (rho) rho[n] = double(m.rho);
+    if (ux) ux[n] = double(m.ux);
+    if (uy) uy[n] = double(m.uy);
+    if (T) T[n] = double(m.T);
+}
+
+// Pre-collision populations at the current time as double f[9][ny][nx], g[5][ny][nx].
+template <int ST>
+__global__ void k_pops(const typename Storage<ST>::T* __restrict__ src,
+                       const LatParams<typename Storage<ST>::A> P, double* __restrict__ f_out,
+                       double* __restrict__ g_out)
+{
+    using A = typename Storage<ST>::A;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    A f[9], g[5];
+    gather(src, P, x, y, f, g);
+    const long long n = (long long)y * P.nx + x, N = (long long)P.nx * P.ny;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f_out[i * N + n] = double(f[i]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g_out[i * N + n] = double(g[i]);
+}
+
+constexpr int kReduceThreads = 256;
+
+// Fixed-order block sum of RS_N doubles (the same order for every launch shape of the step).
+__device__ __forceinline__ void block_sum(double v[RS_N], double* out)
+{
+    __shared__ double sh[kReduceThreads / 32][RS_N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < RS_N; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+        for (int k = 0; k < RS_N; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < RS_N; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < kReduceThreads / 32; ++w) s += sh[w][k];
+            out[k] = s;
+        }
+}
+
+// Per-row FP64 partial sums for the diagnostics: sum u_axis (T - T0), sum |u - u_snap|^2,
+// sum |u|^2, sum (T - T_snap)^2, sum T^2 and the count of non-finite nodes. One block of
+// kReduceThreads per row y; threads stride over x in a fixed order, so the sums do not depend on
+// how the step kernel is launched. With update != 0 the snapshot (u_x, u_y, T as double
+// [3][ny][nx]) is replaced by the current fields.
+template <typename E, typename A>
+__device__ __forceinline__ void reduce_row(const E* __restrict__ src, const LatParams<A>& P, int y,
+                                           int axis, double* __restrict__ snap, int update,
+                                           double* __restrict__ partial_row)
+{
+    const long long N = (long long)P.nx * P.ny;
+    double v[RS_N] = {0, 0, 0, 0, 0, 0};
+    for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) {
+        A f[9], g[5];
+        gather(src, P, x, y, f, g);
+        const Macro<A> m = macroscopic(P, f, g);
+        const double ux = double(m.ux), uy = double(m.uy), T = double(m.T);
+        const long long n = (long long)y * P.nx + x;
+        const double sx = snap[n], sy = snap[N + n], sT = snap[2 * N + n];
+        v[RS_UT] += (axis == 0 ? ux : uy) * (T - double(P.T0));
+        v[RS_DU] += (ux - sx) * (ux - sx) + (uy - sy) * (uy - sy);
+        v[RS_U] += ux * ux + uy * uy;
+        v[RS_DT] += (T - sT) * (T - sT);
+        v[RS_T] += T * T;
+        v[RS_BAD] += (isfinite(ux) && isfinite(uy) && isfinite(T) && isfinite(double(m.rho))) ? 0.0 : 1.0;
+        if (update) {
+            snap[n] = ux;
+            snap[N + n] = uy;
+            snap[2 * N + n] = T;
+        }
+    }
+    block_sum(v, partial_row);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_rows(
+    const typename Storage<ST>::T* __restrict__ src, const LatParams<typename Storage<ST>::A> P,
+    int axis, double* __restrict__ snap, int update, double* __restrict__ partial)
+{
+    reduce_row(src, P, blockIdx.x, axis, snap, update, partial + (long long)blockIdx.x * RS_N);
+}
+
+// Sum the per-row partials in row order and finish the diagnostics in FP64: out[0..RS_N-1] = the
+// sums, out[RS_N] = Nu (Eq. 29), out[RS_N+1] = E_R.
+__device__ __forceinline__ void reduce_final(const double* __restrict__ partial, int rows,
+                                             double nodes, double H, double dT, double sign,
+                                             double kappa, double u_ref, double dT_ref,
+                                             double* __restrict__ out)
+{
+    double v[RS_N] = {0, 0, 0, 0, 0, 0};
+    for (int r = threadIdx.x; r < rows; r += kReduceThreads)
+        for (int k = 0; k < RS_N; ++k) v[k] += partial[(long long)r * RS_N + k];
+    __shared__ double tot[RS_N];
+    block_sum(v, tot);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < RS_N; ++k) out[k] = tot[k];
+        finish_diagnostics(tot, nodes, H, dT, sign, kappa, u_ref, dT_ref, &out[RS_N], &out[RS_N + 1]);
+    }
+}
+
+static __global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double* __restrict__ partial,
+                                                                 int rows, double nodes, double H,
+                                                                 double dT, double sign,
+                                                                 double kappa, double u_ref,
+                                                                 double dT_ref, double* __restrict__ out)
+{
+    reduce_final(partial, rows, nodes, H, dT, sign, kappa, u_ref, dT_ref, out);
+}
+
+}  // namespace clb

@@ -1,0 +1,102 @@
+"""The C ABI library without a GPU: it builds for sm_103a, loads, exports every entry point that
+include/clb.h declares, and its host-side validation answers with status codes."""
+import ctypes
+
+import pytest
+
+from paper_1710_10569_gb300 import build as B
+from paper_1710_10569_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def clb():
+    B.build()
+    from paper_1710_10569_gb300 import clb as c
+    c.lib()
+    return c
+
+
+def test_every_declared_entry_point_is_exported(clb):
+    names = clb.declared_entry_points()
+    assert len(names) >= 30
+    L = clb.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing
+    # and the binding types every one of them
+    assert set(names) <= set(clb._SIGS)
+
+
+def test_version_and_defaults(clb):
+    L = clb.lib()
+    assert b"sm_103a" in L.clb_version()
+    p = clb.clb_params()
+    assert L.clb_params_default(ctypes.byref(p)) == clb.CLB_OK
+    assert (p.cs2_T, p.s_3, p.s_4, p.lambda2, p.s_b, p.rho0) == (0.25, 1.0, 1.0, 1.0, 1.0, 1.0)
+    assert list(p.wall) == [0, 0, 0, 0] and p.storage == 0
+
+
+def footprint(clb, nx, ny, **kw):
+    p = clb.params(W.default_params(**kw))
+    n = ctypes.c_size_t()
+    st = clb.lib().clb_footprint(nx, ny, ctypes.byref(p), ctypes.byref(n))
+    return st, n.value
+
+
+def test_footprint_scales_with_storage(clb):
+    sizes = {}
+    for s in (W.STORAGE_F64, W.STORAGE_F32, W.STORAGE_F16DEV):
+        st, n = footprint(clb, 2048, 1024, storage=s)
+        assert st == clb.CLB_OK
+        sizes[s] = n
+    nodes = 2048 * 1024
+    # two buffers of 14 populations plus FP64 snapshot (24 B) and staging (32 B) per node
+    for s, b in ((W.STORAGE_F64, 8), (W.STORAGE_F32, 4), (W.STORAGE_F16DEV, 2)):
+        assert sizes[s] >= nodes * (2 * 14 * b + 56)
+        assert sizes[s] < nodes * (2 * 14 * b + 56) * 1.01
+
+
+@pytest.mark.parametrize("kw,nx,ny", [
+    (dict(nu=0.0), 8, 8),
+    (dict(nu=-1.0), 8, 8),
+    (dict(kappa=0.0), 8, 8),
+    (dict(s_3=2.0), 8, 8),
+    (dict(s_b=0.0), 8, 8),
+    (dict(lambda2=2.5), 8, 8),
+    (dict(cs2_T=0.5), 8, 8),
+    (dict(wall=(0, 1, 0, 0)), 8, 8),
+    (dict(wall=(1, 1, 0, 2)), 8, 8),
+    (dict(wall=(7, 7, 0, 0)), 8, 8),
+    (dict(storage=5), 8, 8),
+    (dict(nu=float("nan")), 8, 8),
+    ({}, 1, 8),
+    ({}, 8, 0),
+    ({}, (1 << 20) + 1, 4),
+    ({}, 1 << 16, 1 << 15),
+])
+def test_invalid_arguments_are_rejected(clb, kw, nx, ny):
+    st, _ = footprint(clb, nx, ny, **kw)
+    assert st == clb.CLB_EINVAL
+    assert clb.lib().clb_last_error()
+    h = ctypes.c_void_p()
+    p = clb.params(W.default_params(**kw))
+    assert clb.lib().clb_create(nx, ny, ctypes.byref(p), None, None, 0, ctypes.byref(h)) == clb.CLB_EINVAL
+    assert not h.value
+
+
+def test_null_handles_are_rejected(clb):
+    L = clb.lib()
+    assert L.clb_step(None, 1) == clb.CLB_EINVAL
+    assert L.clb_sync(None) == clb.CLB_EINVAL
+    assert L.clb_batch_step(None, 1) == clb.CLB_EINVAL
+    assert L.clb_serve_progress(None, 2, None, None) == clb.CLB_EINVAL
+    L.clb_destroy(None)
+    L.clb_batch_destroy(None)
+    L.clb_serve_close(None)
+
+
+def test_binding_raises_without_library(monkeypatch, tmp_path):
+    from paper_1710_10569_gb300 import clb as c
+    monkeypatch.setattr(c, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(c, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        c.lib()

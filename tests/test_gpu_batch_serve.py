@@ -1,0 +1,127 @@
+"""Batched and served stepping: every instance evolves exactly as it does alone, and matches the
+oracle like a single lattice does."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_10569_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+F64, F32, F16 = W.STORAGE_F64, W.STORAGE_F32, W.STORAGE_F16DEV
+
+
+@pytest.fixture(scope="module")
+def clb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_10569_gb300 import clb as c
+    c.lib()
+    return c
+
+
+def mixed_problems(storage, count=6):
+    probs = [W.random_problem(17 + 13 * k, 11 + 7 * k, seed=k, storage=storage) for k in range(count - 2)]
+    probs.append(W.cavity(40, Ra=1e4, storage=storage))
+    probs.append(W.taylor_green(24, ny=48, storage=storage))
+    return probs
+
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+def test_instance_alone_equals_instance_in_mix(clb, storage):
+    probs = mixed_problems(storage)
+    mix = clb.Batch(probs)
+    mix.step(70)
+    for k, prob in enumerate(probs):
+        alone = clb.Batch([prob])
+        alone.step(70)
+        for a, b in zip(mix.fields(k), alone.fields(0)):
+            assert np.array_equal(a, b), (k, prob.name)
+
+
+@pytest.mark.parametrize("tile", [(128, 1), (64, 2), (32, 4), (256, 1)])
+def test_tile_shape_does_not_change_results(clb, tile):
+    probs = mixed_problems(F32)
+    ref = clb.Batch(probs)
+    ref.step(40)
+    b = clb.Batch(probs)
+    b.set_tile(*tile)
+    b.step(40)
+    for k in range(len(probs)):
+        for x, y in zip(b.fields(k), ref.fields(k)):
+            assert np.array_equal(x, y)
+
+
+def test_batch_matches_oracle_and_single_lattice(clb):
+    probs = mixed_problems(F64)
+    b = clb.Batch(probs)
+    b.step(50)
+    nu, er = b.diagnostics()
+    for k, prob in enumerate(probs):
+        o = oracle.Oracle.from_problem(prob)
+        o.step(50)
+        exp = o.fields()
+        got = b.fields(k)
+        for a, e in zip(got[1:], exp[1:]):
+            assert np.max(np.abs(a - e)) <= 1e-12 * max(np.max(np.abs(e)), 1e-300)
+        single = clb.Lattice.from_problem(prob)
+        single.step(50)
+        assert nu[k] == pytest.approx(single.nusselt(prob.nu_axis), rel=1e-12, abs=1e-14)
+
+
+def test_batch_run_retires_converged_instances(clb):
+    """Conduction problems of different heights converge at different times; each instance stops
+    at its own residual crossing and keeps its state after retirement."""
+    probs = []
+    for ny in (8, 16, 24):
+        p = W.default_params(nu=0.1, kappa=0.1, wall=(W.WALL_PERIODIC,) * 2 + (W.WALL_DIRICHLET,) * 2,
+                             T_wall=(0, 0, 0.5, -0.5), dT_ref=1.0, storage=F64)
+        z = np.zeros((ny, 4))
+        probs.append(W.Problem(f"cond{ny}", 4, ny, p, np.ones((ny, 4)), z, z, z.copy(), nu_axis=1))
+    b = clb.Batch(probs)
+    steps, er, status = b.run(1e-9, 100000, 100)
+    assert (status == 0).all() and (er < 1e-9).all()
+    assert steps[0] < steps[1] < steps[2]
+    for k, prob in enumerate(probs):
+        T = b.fields(k)[3][:, 0]
+        np.testing.assert_allclose(T, 0.5 - (np.arange(prob.ny) + 0.5) / prob.ny, atol=1e-7)
+
+
+def test_served_results_equal_alone(clb):
+    """Requests submitted while others run are admitted as memory frees up; each result equals the
+    same problem stepped alone for the same number of steps."""
+    probs = mixed_problems(F32, count=5)
+    srv = clb.Server(hbm_budget_bytes=64 << 20, max_slots=2, storage=F32)
+    ids = []
+    for k, prob in enumerate(probs):
+        ids.append(srv.submit(prob, step_cap=64 * (k + 1), tol=0.0))
+        srv.progress(32)  # a request arrives each round
+    for _ in range(100):
+        active, queued = srv.progress(32)
+        if active == 0 and queued == 0:
+            break
+    for rid, prob in zip(ids, probs):
+        done, nu, steps, er = srv.poll(rid)
+        assert done and steps == 64 * (probs.index(prob) + 1)
+        got = srv.fetch(rid, prob.ny, prob.nx)
+        alone = clb.Batch([prob])
+        alone.step(steps)
+        for a, b in zip(got, alone.fields(0)):
+            assert np.array_equal(a, b), prob.name
+
+
+def test_serve_budget_and_errors(clb):
+    srv = clb.Server(hbm_budget_bytes=1 << 20, max_slots=4, storage=F32)
+    big = W.cavity(256, storage=F32)
+    with pytest.raises(clb.CLBError) as e:
+        srv.submit(big, step_cap=10, tol=0.0)
+    assert e.value.status == clb.CLB_ENOMEM
+    small = W.cavity(16, storage=F32)
+    rid = srv.submit(small, step_cap=32, tol=0.0)
+    with pytest.raises(clb.CLBError) as e:
+        srv.fetch(rid, 16, 16)
+    assert e.value.status == clb.CLB_EBUSY
+    while srv.progress(32)[0] or srv.progress(32)[1]:
+        pass
+    assert srv.poll(rid)[0]

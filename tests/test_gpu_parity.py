@@ -1,0 +1,244 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances (normwise per field: max|gpu - oracle| <= tol * max|oracle|):
+  FP64 storage + FP64 arithmetic: 1e-12 (the two sides differ only in rounding order).
+  FP32 storage + FP32 arithmetic and FP16-deviation storage: the bounds in TOL below; their
+  derivation from the unit roundoffs is given in the design notes.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_10569_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+F64, F32, F16 = W.STORAGE_F64, W.STORAGE_F32, W.STORAGE_F16DEV
+P, D, A = W.WALL_PERIODIC, W.WALL_DIRICHLET, W.WALL_ADIABATIC
+NAMES = ("rho", "ux", "uy", "T")
+# per storage: tolerance on (rho, u, T) normwise errors after the runs below
+TOL = {F64: 1e-12, F32: 2e-5, F16: 2e-2}
+
+
+@pytest.fixture(scope="module")
+def clb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_10569_gb300 import clb as c
+    c.lib()
+    return c
+
+
+def normwise(a, b):
+    scale = float(np.max(np.abs(b)))
+    return float(np.max(np.abs(a - b))) / (scale if scale > 0 else 1.0)
+
+
+def report(tag, errs):
+    path = os.environ.get("CLB_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"case": tag, **errs}) + "\n")
+
+
+def compare(tag, got, exp, tol, uvec_scale=False):
+    errs = {}
+    for name, a, b in zip(NAMES, got, exp):
+        if name == "rho":
+            errs[name] = float(np.max(np.abs(a - b))) / float(np.max(np.abs(b)))
+        elif name in ("ux", "uy"):
+            # velocity components share one scale (the speed)
+            s = max(float(np.max(np.abs(exp[1]))), float(np.max(np.abs(exp[2]))), 1e-300)
+            errs[name] = float(np.max(np.abs(a - b))) / s
+        else:
+            errs[name] = normwise(a, b)
+    report(tag, errs)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"{tag}: normwise errors above {tol:g}: {bad} (all: {errs})"
+    return errs
+
+
+def run_both(clb, prob, steps):
+    lat = clb.Lattice.from_problem(prob)
+    lat.step(steps)
+    got = lat.fields()
+    o = oracle.Oracle.from_problem(prob)
+    o.step(steps)
+    return lat, o, got, o.fields()
+
+
+# ------------------------------------------------------------------ config #1: periodic TG, FP64
+
+
+def test_taylor_green_64_fp64_1000_steps(clb):
+    prob = W.taylor_green(64, storage=F64)
+    lat, o, got, exp = run_both(clb, prob, 1000)
+    compare("tg64_f64_1000", got, exp, 1e-12)
+    f, g = lat.populations()
+    fo, go = o.populations()
+    assert normwise(f, fo) <= 1e-12 and normwise(g, go) <= 1e-12
+
+
+@pytest.mark.parametrize("storage", [F32, F16])
+def test_taylor_green_64_reduced_precision(clb, storage):
+    prob = W.taylor_green(64, storage=storage)
+    _, _, got, exp = run_both(clb, prob, 1000)
+    compare(f"tg64_{W.STORAGE_NAMES[storage]}_1000", got, exp, TOL[storage])
+
+
+# ------------------------------------------------------------------ walls, ragged sizes, all storages
+
+SHAPES = [(67, 45), (130, 7), (2, 2), (3, 257), (257, 3), (33, 33)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_random_problems_fp64(clb, shape, seed):
+    prob = W.random_problem(*shape, seed=seed, storage=F64)
+    _, _, got, exp = run_both(clb, prob, 60)
+    compare(f"rand{shape}_s{seed}_f64", got, exp, 1e-12)
+
+
+@pytest.mark.parametrize("storage", [F32, F16])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_random_problems_reduced_precision(clb, storage, seed):
+    prob = W.random_problem(67, 45, seed=seed, storage=storage)
+    _, _, got, exp = run_both(clb, prob, 60)
+    compare(f"rand67x45_s{seed}_{W.STORAGE_NAMES[storage]}", got, exp, TOL[storage])
+
+
+def test_initial_fields_match_oracle(clb):
+    """Step 0: the inverse-stream initialisation reproduces the oracle's f(x,0) = f^eq exactly,
+    walls included."""
+    for seed in range(4):
+        prob = W.random_problem(19, 23, seed=seed, storage=F64)
+        lat = clb.Lattice.from_problem(prob)
+        o = oracle.Oracle.from_problem(prob)
+        f, g = lat.populations()
+        fo, go = o.populations()
+        assert normwise(f, fo) <= 1e-14 and normwise(g, go) <= 1e-14
+        compare(f"init_s{seed}", lat.fields(), o.fields(), 1e-14)
+
+
+# ------------------------------------------------------------------ config #2 cavity, config #3 RB
+
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+def test_cavity_256_short(clb, storage):
+    prob = W.cavity(256, storage=storage)
+    # the fluid starts at rest with 1e-4 noise: give the buoyant flow time to develop
+    _, o, got, exp = run_both(clb, prob, 400)
+    compare(f"cavity256_{W.STORAGE_NAMES[storage]}_400", got, exp, TOL[storage])
+
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+def test_rayleigh_benard_2048x1024_full_size(clb, storage):
+    """The bench workload at full size, the launch configuration bench.py times (graph chunks of
+    the fused kernel), a few steps, every node compared."""
+    prob = W.rayleigh_benard(2048, 1024, storage=storage)
+    _, _, got, exp = run_both(clb, prob, 3)
+    compare(f"rb2048_{W.STORAGE_NAMES[storage]}_3", got, exp, TOL[storage])
+
+
+def test_graph_chunks_equal_single_launches(clb):
+    """clb_step(n) replays captured 32-step graphs plus single launches; the result does not depend
+    on how the steps are grouped."""
+    prob = W.random_problem(70, 40, seed=2, storage=F64)
+    a = clb.Lattice.from_problem(prob)
+    a.step(75)
+    b = clb.Lattice.from_problem(prob)
+    for _ in range(75):
+        b.step(1)
+    for x, y in zip(a.fields(), b.fields()):
+        assert np.array_equal(x, y)
+
+
+def test_launch_shapes_are_bitwise_equal(clb):
+    prob = W.random_problem(150, 37, seed=3, storage=F32)
+    ref = None
+    for shape in ((128, 1), (64, 4), (256, 2), (32, 8)):
+        lat = clb.Lattice.from_problem(prob)
+        lat.set_launch(*shape)
+        lat.step(40)
+        got = lat.fields()
+        if ref is None:
+            ref = got
+        for x, y in zip(got, ref):
+            assert np.array_equal(x, y), shape
+
+
+# ------------------------------------------------------------------ diagnostics
+
+
+def test_nusselt_and_residual_match_oracle(clb):
+    for prob in (W.random_problem(41, 33, seed=1, storage=F64), W.cavity(48, Ra=1e4, storage=F64)):
+        lat = clb.Lattice.from_problem(prob)
+        o = oracle.Oracle.from_problem(prob)
+        prev = o.fields()[1:]
+        lat.step(100)
+        o.step(100)
+        cur = o.fields()
+        nu_gpu = lat.nusselt(prob.nu_axis)
+        nu_ref = oracle.nusselt(cur[1], cur[2], cur[3], prob.params, prob.nu_axis)
+        assert nu_gpu == pytest.approx(nu_ref, rel=1e-11, abs=1e-12)
+        er_gpu = lat.residual()
+        er_ref = oracle.residual(prev, cur[1:], prob.params["u_ref"], prob.params["dT_ref"])
+        assert er_gpu == pytest.approx(er_ref, rel=1e-9)
+
+
+def test_run_to_steady_conduction(clb):
+    """clb_run stops at the residual tolerance; the steady state is the conduction line."""
+    ny = 16
+    p = W.default_params(nu=0.1, kappa=0.1, wall=(P, P, D, D), T_wall=(0, 0, 0.5, -0.5), dT_ref=1.0,
+                         u_ref=0.0)
+    lat = clb.Lattice(4, ny, p)
+    lat.init_fields()
+    steps, er = lat.run(1e-10, 200000, 100)
+    assert er < 1e-10 and steps < 200000
+    T = lat.fields()[3][:, 0]
+    np.testing.assert_allclose(T, 0.5 - (np.arange(ny) + 0.5) / ny, atol=1e-9)
+
+
+def test_nan_is_reported(clb):
+    prob = W.random_problem(16, 16, seed=0, storage=F64)
+    lat = clb.Lattice.from_problem(prob)
+    blob = bytearray(lat.save())
+    # poison the first population value after the checkpoint header
+    hdr = 40
+    blob[hdr:hdr + 8] = np.array([np.nan]).tobytes()
+    lat.load(bytes(blob))
+    with pytest.raises(clb.CLBError) as e:
+        lat.nusselt(1)
+    assert e.value.status == clb.CLB_ENAN
+
+
+# ------------------------------------------------------------------ checkpoints
+
+
+def test_checkpoint_roundtrip_bitwise(clb):
+    prob = W.random_problem(50, 30, seed=2, storage=F32)
+    a = clb.Lattice.from_problem(prob)
+    a.step(25)
+    blob = a.save()
+    a.step(30)
+    ref = a.fields()
+    b = clb.Lattice(prob.nx, prob.ny, prob.params)
+    b.load(blob)
+    assert b.steps == 25
+    b.step(30)
+    for x, y in zip(b.fields(), ref):
+        assert np.array_equal(x, y)
+
+
+def test_autotune_keeps_state(clb):
+    prob = W.random_problem(300, 200, seed=1, storage=F32)
+    a = clb.Lattice.from_problem(prob)
+    before = a.fields()
+    shape = a.autotune()
+    assert a.launch() == shape
+    for x, y in zip(a.fields(), before):
+        assert np.array_equal(x, y)

@@ -57,8 +57,9 @@ typedef enum {
     CLB_WALL_ADIABATIC = 2   /* g_i = g*_opp (zero heat flux) */
 } clb_wall;
 
-/* Population storage. Arithmetic is FP64 for CLB_F64 and FP32 otherwise. CLB_F16DEV stores
- * f_i - w_i rho0 and g_i - w^T_i T_ref in IEEE half precision (w, w^T the rest weights). */
+/* Population storage. CLB_F64 stores f_i, g_i and computes in FP64. CLB_F32 and CLB_F16DEV store
+ * the deviations from the rest state, f_i - w_i rho0 and g_i - w^T_i T_ref (w, w^T the rest
+ * weights), in FP32 or IEEE half precision, and compute in FP32 on those deviations. */
 typedef enum { CLB_F64 = 0, CLB_F32 = 1, CLB_F16DEV = 2 } clb_storage;
 
 /* Problem parameters (Sec. 2, Sec. 3 defaults from clb_params_default). */
@@ -148,16 +149,18 @@ clb_status clb_sync(clb_handle *h);
 clb_status clb_save(clb_handle *h, void *buf, size_t *bytes);
 clb_status clb_load(clb_handle *h, const void *buf, size_t bytes);
 
-/* Launch shape of the step kernel: threads per block along x (32..1024, multiple of 32) and rows
- * per block (1..32). 0 keeps the current value. clb_autotune times candidate shapes on the live
- * lattice (populations are restored afterwards) and keeps the fastest; results are cached per
- * (storage, nx, ny). */
-clb_status clb_set_launch(clb_handle *h, int block_x, int block_y);
-clb_status clb_get_launch(clb_handle *h, int *block_x, int *block_y);
-clb_status clb_autotune(clb_handle *h, int *block_x, int *block_y);
+/* Launch shape of the step kernel: threads per block along x (32..256, multiple of 32), rows per
+ * block (1..8, block_x * block_y <= 256) and nodes per thread along x (1, 2 or 4). 0 keeps the
+ * current value. Defaults: 128 x 1 with 1 (FP64), 2 (FP32) or 4 (FP16) nodes per thread.
+ * clb_autotune times candidate shapes on the live lattice (the populations are restored
+ * afterwards; it allocates one buffer-sized scratch with cudaMallocAsync) and keeps the fastest;
+ * results are cached per (storage, nx, ny) for later clb_create calls. The shape never changes
+ * the results (the per-node arithmetic does not depend on it). */
+clb_status clb_set_launch(clb_handle *h, int block_x, int block_y, int nodes_per_thread);
+clb_status clb_get_launch(clb_handle *h, int *block_x, int *block_y, int *nodes_per_thread);
+clb_status clb_autotune(clb_handle *h, int *block_x, int *block_y, int *nodes_per_thread);
 
-/* Times of the last clb_step call's kernels would need events the caller can also take; the
- * library exposes the stream so the caller can time on it. */
+/* The CUDA stream the handle enqueues on (to time its work with events on that stream). */
 void *clb_stream(clb_handle *h);
 
 /* Device address of the current post-collision population buffer and of the other buffer, and
@@ -188,8 +191,11 @@ clb_status clb_batch_diagnostics(clb_batch *b, const int *axis, double *nu, doub
  * (their tiles leave the launch). steps[k], er[k], status[k] (clb_status) per instance. */
 clb_status clb_batch_run(clb_batch *b, double tol, long max_steps, long interval, long *steps,
                          double *er, int *status);
-/* Tile shape (threads along x, rows per tile) used by the batched launch. */
-clb_status clb_batch_set_tile(clb_batch *b, int tile_x, int tile_y);
+/* Tile shape of the batched launch: threads along x (32..256), rows (block_x * rows <= 256) and
+ * nodes per thread (1, 2, 4). clb_batch_autotune times candidates over the whole batch (the
+ * populations are restored afterwards) and keeps the fastest. Results do not depend on it. */
+clb_status clb_batch_set_tile(clb_batch *b, int tile_x, int tile_y, int nodes_per_thread);
+clb_status clb_batch_autotune(clb_batch *b, int *tile_x, int *tile_y, int *nodes_per_thread);
 
 /* ---------------------------------------------------------------------------------------------
  * Serving: requests arrive over time; each is admitted when a slot and enough of the HBM budget

@@ -68,9 +68,9 @@ _SIGS = {
     "clb_sync": [_VP],
     "clb_save": [_VP, _VP, _P(_S)],
     "clb_load": [_VP, _VP, _S],
-    "clb_set_launch": [_VP, _I, _I],
-    "clb_get_launch": [_VP, _P(_I), _P(_I)],
-    "clb_autotune": [_VP, _P(_I), _P(_I)],
+    "clb_set_launch": [_VP, _I, _I, _I],
+    "clb_get_launch": [_VP, _P(_I), _P(_I), _P(_I)],
+    "clb_autotune": [_VP, _P(_I), _P(_I), _P(_I)],
     "clb_stream": [_VP],
     "clb_buffers": [_VP, _P(_VP), _P(_VP), _P(_S), _P(_I)],
     "clb_last_error": [],
@@ -82,7 +82,8 @@ _SIGS = {
     "clb_batch_fields": [_VP, _I, _D, _D, _D, _D],
     "clb_batch_diagnostics": [_VP, _P(_I), _D, _D],
     "clb_batch_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D, _P(_I)],
-    "clb_batch_set_tile": [_VP, _I, _I],
+    "clb_batch_set_tile": [_VP, _I, _I, _I],
+    "clb_batch_autotune": [_VP, _P(_I), _P(_I), _P(_I)],
     "clb_serve_open": [_S, _I, _I, _VP, _P(_VP)],
     "clb_serve_close": [_VP],
     "clb_serve_submit": [_VP, _I, _I, _P(clb_params), _D, _D, _D, _D, _I, _L, ctypes.c_double, _P(_L)],
@@ -276,18 +277,18 @@ class Lattice:
         buf = ctypes.create_string_buffer(data, len(data))
         _check(lib().clb_load(self._h, ctypes.cast(buf, _VP), len(data)))
 
-    def set_launch(self, block_x: int = 0, block_y: int = 0):
-        _check(lib().clb_set_launch(self._h, int(block_x), int(block_y)))
+    def set_launch(self, block_x: int = 0, block_y: int = 0, nodes_per_thread: int = 0):
+        _check(lib().clb_set_launch(self._h, int(block_x), int(block_y), int(nodes_per_thread)))
 
     def launch(self):
-        bx, by = _I(), _I()
-        _check(lib().clb_get_launch(self._h, ctypes.byref(bx), ctypes.byref(by)))
-        return bx.value, by.value
+        bx, by, npt = _I(), _I(), _I()
+        _check(lib().clb_get_launch(self._h, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(npt)))
+        return bx.value, by.value, npt.value
 
     def autotune(self):
-        bx, by = _I(), _I()
-        _check(lib().clb_autotune(self._h, ctypes.byref(bx), ctypes.byref(by)))
-        return bx.value, by.value
+        bx, by, npt = _I(), _I(), _I()
+        _check(lib().clb_autotune(self._h, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(npt)))
+        return bx.value, by.value, npt.value
 
     def buffers(self):
         cur, oth, pl, pitch = _VP(), _VP(), _S(), _I()
@@ -357,8 +358,13 @@ class Batch:
                                    _dptr(er), status))
         return np.array(steps[:], dtype=np.int64), er, np.array(status[:], dtype=np.int32)
 
-    def set_tile(self, tile_x: int, tile_y: int = 1):
-        _check(lib().clb_batch_set_tile(self._h, int(tile_x), int(tile_y)))
+    def set_tile(self, tile_x: int, tile_y: int = 1, nodes_per_thread: int = 1):
+        _check(lib().clb_batch_set_tile(self._h, int(tile_x), int(tile_y), int(nodes_per_thread)))
+
+    def autotune(self):
+        tx, ty, npt = _I(), _I(), _I()
+        _check(lib().clb_batch_autotune(self._h, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(npt)))
+        return tx.value, ty.value, npt.value
 
 
 class Server:

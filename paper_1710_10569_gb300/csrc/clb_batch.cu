@@ -46,9 +46,10 @@ __device__ __forceinline__ void load_member(const Member<A>* __restrict__ src, M
     __syncthreads();
 }
 
-// One time step of every lattice: block b covers tile (b - tile_begin) of lattice owner[b].
-template <int ST>
-__global__ void __launch_bounds__(512) k_step_batched(const Member<typename Storage<ST>::A>* __restrict__ mem,
+// One time step of every lattice: block b covers tile (b - tile_begin) of lattice owner[b]; a
+// tile is (blockDim.x * NPT) x blockDim.y nodes, NPT nodes per thread blockDim.x apart.
+template <int ST, int NPT>
+__global__ void __launch_bounds__(256) k_step_batched(const Member<typename Storage<ST>::A>* __restrict__ mem,
                                                       const int* __restrict__ owner, int parity)
 {
     using A = typename Storage<ST>::A;
@@ -57,13 +58,33 @@ __global__ void __launch_bounds__(512) k_step_batched(const Member<typename Stor
     load_member(mem + owner[blockIdx.x], M);
     const int t = blockIdx.x - M.tile_begin;
     const int tx = t % M.tiles_x, ty = t / M.tiles_x;
-    const int x = tx * blockDim.x + threadIdx.x;
+    const int x0 = tx * blockDim.x * NPT + threadIdx.x;
     const int y = ty * blockDim.y + threadIdx.y;
-    if (x >= M.P.nx || y >= M.P.ny) return;
-    A f[9], g[5];
-    gather((const E*)M.buf[parity], M.P, x, y, f, g);
-    collide(M.P, f, g);
-    store_node((E*)M.buf[parity ^ 1], M.P, x, y, f, g);
+    if (y >= M.P.ny) return;
+    const E* src = (const E*)M.buf[parity];
+    E* dst = (E*)M.buf[parity ^ 1];
+    E raw[NPT][NPOP];
+    int mask[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int x = x0 + k * blockDim.x;
+        mask[k] = 0;
+        if (x < M.P.nx) {
+            const Slots s = pull_slots(M.P, x, y);
+            load_slots(src, s, raw[k]);
+            mask[k] = s.wall_mask;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int x = x0 + k * blockDim.x;
+        if (x < M.P.nx) {
+            A f[9], g[5];
+            finish_pull(M.P, raw[k], mask[k], f, g);
+            collide_any<Storage<ST>::DEV>(M.P, f, g);
+            store_node(dst, M.P, x, y, f, g);
+        }
+    }
 }
 
 template <int ST>
@@ -124,7 +145,7 @@ void carve(Lattice& L, char* base)
 }
 
 template <typename A>
-Member<A> make_member(const Lattice& L, int tile_x, int tile_y, int tile_begin, int row_begin)
+Member<A> make_member(const Lattice& L, int tile_x, int npt, int tile_begin, int row_begin)
 {
     Member<A> m;
     std::memset(&m, 0, sizeof(m));
@@ -134,7 +155,7 @@ Member<A> make_member(const Lattice& L, int tile_x, int tile_y, int tile_begin, 
     m.snap = L.snap;
     m.partial = L.partial;
     m.diag = L.diag;
-    m.tiles_x = (L.nx + tile_x - 1) / tile_x;
+    m.tiles_x = (L.nx + tile_x * npt - 1) / (tile_x * npt);
     m.tile_begin = tile_begin;
     m.row_begin = row_begin;
     m.axis = L.axis;
@@ -157,7 +178,7 @@ public:
     int storage = CLB_F32;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
-    int tile_x = 128, tile_y = 1;
+    int tile_x = 128, tile_y = 1, npt = 1;
     int parity = 0;  // every resident lattice holds its current data in buf[parity]
     std::vector<Lattice*> members;  // launch order
 
@@ -198,12 +219,12 @@ public:
         int tiles = 0, rows = 0;
         for (size_t k = 0; k < active.size(); ++k) {
             const Lattice& L = *active[k];
-            const int tx = (L.nx + tile_x - 1) / tile_x, ty = (L.ny + tile_y - 1) / tile_y;
+            const int tx = (L.nx + tile_x * npt - 1) / (tile_x * npt), ty = (L.ny + tile_y - 1) / tile_y;
             if (storage == CLB_F64) {
-                Member<double> m = make_member<double>(L, tile_x, tile_y, tiles, rows);
+                Member<double> m = make_member<double>(L, tile_x, npt, tiles, rows);
                 std::memcpy(host.data() + k * msz, &m, msz);
             } else {
-                Member<float> m = make_member<float>(L, tile_x, tile_y, tiles, rows);
+                Member<float> m = make_member<float>(L, tile_x, npt, tiles, rows);
                 std::memcpy(host.data() + k * msz, &m, msz);
             }
             owner.insert(owner.end(), (size_t)tx * ty, int(k));
@@ -233,14 +254,24 @@ public:
         return CLB_OK;
     }
 
+    template <int ST>
+    void enqueue(cudaStream_t s, int par)
+    {
+        using A = typename Storage<ST>::A;
+        const dim3 block(tile_x, tile_y);
+        const Member<A>* m = (const Member<A>*)d_members;
+        if (npt == 4) k_step_batched<ST, 4><<<ntiles, block, 0, s>>>(m, d_owner, par);
+        else if (npt == 2) k_step_batched<ST, 2><<<ntiles, block, 0, s>>>(m, d_owner, par);
+        else k_step_batched<ST, 1><<<ntiles, block, 0, s>>>(m, d_owner, par);
+    }
+
     clb_status launch_step(cudaStream_t s, int par)
     {
         if (ntiles == 0) return CLB_OK;
-        const dim3 block(tile_x, tile_y);
         switch (storage) {
-        case CLB_F64: k_step_batched<ST_F64><<<ntiles, block, 0, s>>>((const Member<double>*)d_members, d_owner, par); break;
-        case CLB_F32: k_step_batched<ST_F32><<<ntiles, block, 0, s>>>((const Member<float>*)d_members, d_owner, par); break;
-        default: k_step_batched<ST_F16DEV><<<ntiles, block, 0, s>>>((const Member<float>*)d_members, d_owner, par); break;
+        case CLB_F64: enqueue<ST_F64>(s, par); break;
+        case CLB_F32: enqueue<ST_F32>(s, par); break;
+        default: enqueue<ST_F16DEV>(s, par); break;
         }
         CLB_CUDA(cudaGetLastError());
         return CLB_OK;
@@ -319,15 +350,15 @@ public:
         const size_t N = (size_t)L->nx * L->ny;
         if (storage == CLB_F64) {
             const LatParams<double> P = make_lat_params<double>(L->nx, L->ny, L->p);
-            k_init<ST_F64><<<grid, block, 0, stream>>>((double*)d, P, rho, ux, uy, T);
+            k_init<ST_F64><<<grid, block, 0, stream>>>((double*)d, P, rho, ux, uy, T, L->p.rho0);
             k_fields<ST_F64><<<grid, block, 0, stream>>>((const double*)d, P, nullptr, L->snap, L->snap + N, L->snap + 2 * N);
         } else {
             const LatParams<float> P = make_lat_params<float>(L->nx, L->ny, L->p);
             if (storage == CLB_F32) {
-                k_init<ST_F32><<<grid, block, 0, stream>>>((float*)d, P, rho, ux, uy, T);
+                k_init<ST_F32><<<grid, block, 0, stream>>>((float*)d, P, rho, ux, uy, T, L->p.rho0);
                 k_fields<ST_F32><<<grid, block, 0, stream>>>((const float*)d, P, nullptr, L->snap, L->snap + N, L->snap + 2 * N);
             } else {
-                k_init<ST_F16DEV><<<grid, block, 0, stream>>>((__half*)d, P, rho, ux, uy, T);
+                k_init<ST_F16DEV><<<grid, block, 0, stream>>>((__half*)d, P, rho, ux, uy, T, L->p.rho0);
                 k_fields<ST_F16DEV><<<grid, block, 0, stream>>>((const __half*)d, P, nullptr, L->snap, L->snap + N, L->snap + 2 * N);
             }
         }
@@ -568,14 +599,91 @@ extern "C" clb_status clb_batch_run(clb_batch* b, double tol, long max_steps, lo
     return CLB_OK;
 }
 
-extern "C" clb_status clb_batch_set_tile(clb_batch* b, int tile_x, int tile_y)
+extern "C" clb_status clb_batch_set_tile(clb_batch* b, int tile_x, int tile_y, int nodes_per_thread)
 {
     if (!b) return set_error(CLB_EINVAL, "batch is NULL");
-    if (tile_x < 32 || tile_x > 512 || tile_x % 32 || tile_y < 1 || tile_x * tile_y > 512)
-        return set_error(CLB_EINVAL, "tile %d x %d: tile_x in [32, 512] multiple of 32, tile_x * tile_y <= 512", tile_x, tile_y);
+    if (tile_x < 32 || tile_x > 256 || tile_x % 32 || tile_y < 1 || tile_x * tile_y > 256 ||
+        (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4))
+        return set_error(CLB_EINVAL, "tile %d x %d x %d: tile_x in [32, 256] multiple of 32, "
+                                     "tile_x * tile_y <= 256, nodes per thread 1, 2 or 4",
+                         tile_x, tile_y, nodes_per_thread);
+    cudaStreamSynchronize(b->E.stream);
     b->E.tile_x = tile_x;
     b->E.tile_y = tile_y;
+    b->E.npt = nodes_per_thread;
     b->E.mark_dirty();
+    return CLB_OK;
+}
+
+// Times candidate tile shapes over the whole batch (10 steps each after 4 warm-up steps) and keeps
+// the fastest; the populations of every instance are saved first and restored afterwards.
+extern "C" clb_status clb_batch_autotune(clb_batch* b, int* tile_x, int* tile_y, int* nodes_per_thread)
+{
+    if (!b) return set_error(CLB_EINVAL, "batch is NULL");
+    Ensemble& E = b->E;
+    CLB_TRY(E.rebuild());
+    size_t total = 0;
+    for (auto& L : b->lat) total += align256(buffer_bytes(L->nx, L->ny, L->p.storage));
+    char* save = nullptr;
+    CLB_CUDA(cudaMallocAsync((void**)&save, total, E.stream));
+    size_t off = 0;
+    for (auto& L : b->lat) {
+        const size_t bb = buffer_bytes(L->nx, L->ny, L->p.storage);
+        CLB_CUDA(cudaMemcpyAsync(save + off, L->buf[E.parity], bb, cudaMemcpyDeviceToDevice, E.stream));
+        off += align256(bb);
+    }
+    std::vector<long> steps0;
+    for (auto& L : b->lat) steps0.push_back(L->steps);
+    const int shapes[][3] = {{64, 1, 1}, {128, 1, 1}, {256, 1, 1}, {64, 1, 2}, {128, 1, 2}, {64, 2, 2},
+                             {64, 1, 4}, {128, 1, 4}, {32, 4, 2}, {32, 2, 4}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bt[3] = {E.tile_x, E.tile_y, E.npt};
+    clb_status st = CLB_OK;
+    for (auto& sh : shapes) {
+        E.tile_x = sh[0];
+        E.tile_y = sh[1];
+        E.npt = sh[2];
+        E.mark_dirty();
+        st = E.rebuild();
+        for (int k = 0; k < 4 && st == CLB_OK; ++k) st = E.launch_step(E.stream, (E.parity + k) & 1);
+        cudaEventRecord(e0, E.stream);
+        for (int k = 0; k < 10 && st == CLB_OK; ++k) st = E.launch_step(E.stream, (E.parity + k) & 1);
+        cudaEventRecord(e1, E.stream);
+        if (st != CLB_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bt[0] = sh[0];
+            bt[1] = sh[1];
+            bt[2] = sh[2];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    off = 0;
+    cudaError_t e = cudaSuccess;
+    for (auto& L : b->lat) {
+        const size_t bb = buffer_bytes(L->nx, L->ny, L->p.storage);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(L->buf[E.parity], save + off, bb, cudaMemcpyDeviceToDevice, E.stream);
+        off += align256(bb);
+    }
+    cudaFreeAsync(save, E.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
+    for (size_t k = 0; k < b->lat.size(); ++k) b->lat[k]->steps = steps0[k];
+    E.tile_x = bt[0];
+    E.tile_y = bt[1];
+    E.npt = bt[2];
+    E.mark_dirty();
+    if (st != CLB_OK) return st;
+    if (e != cudaSuccess) return set_error(CLB_ECUDA, "batch autotune restore: %s", cudaGetErrorString(e));
+    if (tile_x) *tile_x = bt[0];
+    if (tile_y) *tile_y = bt[1];
+    if (nodes_per_thread) *nodes_per_thread = bt[2];
     return CLB_OK;
 }
 

@@ -9,6 +9,12 @@
 // passes backwards with the 1-D inverse (f_0 = m_0 - m_2, f_+- = (m_2 +- m_1)/2). The D2Q5 part
 // (Eqs. 16-21, Appendix A) is the same construction with one row per axis. This is about 200 flops
 // per node instead of the ~1,600 of literal 9x9 products, and the result is the same map.
+//
+// Storage. FP64 buffers hold the populations f_i, g_i themselves. FP32 and FP16 buffers hold
+// deviations from the rest state, h_i = f_i - w_i rho0 and t_i = g_i - w^T_i T_ref, and the
+// collision is evaluated on those deviations (collide_dev): every intermediate is then small, so
+// FP32 rounding acts on quantities of the size of the non-equilibrium and velocity terms instead
+// of on the O(1) populations.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -20,18 +26,18 @@ enum { WALL_PERIODIC = 0, WALL_DIRICHLET = 1, WALL_ADIABATIC = 2 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2 };
 enum { NPOP = 14 };  // 9 flow + 5 temperature planes per buffer
 
-// Storage traits: element type in HBM and arithmetic type in registers.
+// Storage traits: element type in HBM, arithmetic type in registers, deviation form or not.
 template <int ST> struct Storage;
-template <> struct Storage<ST_F64> { using T = double; using A = double; };
-template <> struct Storage<ST_F32> { using T = float; using A = float; };
-template <> struct Storage<ST_F16DEV> { using T = __half; using A = float; };
+template <> struct Storage<ST_F64> { using T = double; using A = double; static constexpr bool DEV = false; };
+template <> struct Storage<ST_F32> { using T = float; using A = float; static constexpr bool DEV = true; };
+template <> struct Storage<ST_F16DEV> { using T = __half; using A = float; static constexpr bool DEV = true; };
 
-__device__ __forceinline__ double to_a(double v, double) { return v; }
-__device__ __forceinline__ float to_a(float v, float) { return v; }
-__device__ __forceinline__ float to_a(__half v, float base) { return __half2float(v) + base; }
-__device__ __forceinline__ double from_a(double v, double, double*) { return v; }
-__device__ __forceinline__ float from_a(float v, float, float*) { return v; }
-__device__ __forceinline__ __half from_a(float v, float base, __half*) { return __float2half_rn(v - base); }
+__device__ __forceinline__ double to_a(double v) { return v; }
+__device__ __forceinline__ float to_a(float v) { return v; }
+__device__ __forceinline__ float to_a(__half v) { return __half2float(v); }
+__device__ __forceinline__ double from_a(double v, double*) { return v; }
+__device__ __forceinline__ float from_a(float v, float*) { return v; }
+__device__ __forceinline__ __half from_a(float v, __half*) { return __float2half_rn(v); }
 
 // Per-lattice constants in the arithmetic precision A.
 template <typename A>
@@ -40,22 +46,41 @@ struct LatParams {
     int per_x, per_y;         // periodic flags
     long long plane;          // elements between population planes
     int kind[4];              // wall kind per side (-x, +x, -y, +y)
-    A Tw_c2[4];               // cs2_T * T_wall: the anti-bounce-back constant 2 w_i T_w
+    A Tw_c2[4];               // anti-bounce-back constant cs2_T (T_wall - T_b) (= 2 w_i T_w, shifted)
     A s_nu, sp, sm, s_3, s_4; // D2Q9 rates; sp = (s_b + s_nu)/2, sm = (s_b - s_nu)/2
     A lambda1, lambda2, cs2T; // D2Q5 rates and sound speed squared
     A Fvx, Fvy, gb, T0;       // F = (Fvx, Fvy + gb (T - T0)), gb = rho0 * g_beta
-    A base_f[9], base_g[5];   // FP16 deviation bases (zero for the other storages)
+    A rho_b, T_b;             // rest state the buffers are stored against (0 for FP64)
 };
 
-// Gather (pull) the pre-collision populations of node (x, y) from the post-collision buffer of
-// the previous step, Eqs. (12) and (22): f_i(x) = f*_i(x - e_i). Where x - e_i is beyond a wall
-// the node's own opposite population is used (halfway bounce-back for f; anti-bounce-back or
-// bounce-back for g according to the wall kind). Velocity order of Eq. (4):
-// 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
-template <typename T, typename A>
-__device__ __forceinline__ void gather(const T* __restrict__ src, const LatParams<A>& P, int x, int y,
-                                       A f[9], A g[5])
+// 1-D rest weights of D2Q9 (w(0) = 2/3, w(+-1) = 1/6; w_i = w(e_x) w(e_y)) and D2Q5 weights.
+template <typename A>
+__device__ __forceinline__ A w9(int i)
 {
+    const A w1[3] = {A(2) / A(3), A(1) / A(6), A(1) / A(6)};
+    const int ax[9] = {0, 1, 0, 2, 0, 1, 2, 2, 1};
+    const int ay[9] = {0, 0, 1, 0, 2, 1, 1, 2, 2};
+    return w1[ax[i]] * w1[ay[i]];
+}
+template <typename A>
+__device__ __forceinline__ A w5(int i, A c2)
+{
+    return i == 0 ? A(1) - A(2) * c2 : A(0.5) * c2;
+}
+
+// Source slots of the 14 pulled populations of node (x, y), Eqs. (12) and (22):
+// f_i(x) = f*_i(x - e_i); where x - e_i is beyond a wall the node's own opposite slot is read.
+// Velocity order of Eq. (4): 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1)
+// 7:(-1,-1) 8:(1,-1). wall_mask bits 0..3: the pull of g1, g3, g2, g4 crossed side -x, +x, -y, +y.
+struct Slots {
+    long long idx[NPOP];
+    int wall_mask;
+};
+
+template <typename A>
+__device__ __forceinline__ Slots pull_slots(const LatParams<A>& P, int x, int y)
+{
+    Slots s;
     const bool inL = P.per_x || x > 0;
     const bool inR = P.per_x || x < P.nx - 1;
     const bool inB = P.per_y || y > 0;
@@ -67,39 +92,58 @@ __device__ __forceinline__ void gather(const T* __restrict__ src, const LatParam
     const long long rp = (long long)(y < P.ny - 1 ? y + 1 : 0) * P.pitch;
     const long long here = r0 + x;
     const long long pl = P.plane;
-    // pulled (plane, index) or bounced (opposite plane, own index)
-    const long long i1 = inL ? 1 * pl + r0 + xm : 3 * pl + here;
-    const long long i2 = inB ? 2 * pl + rm + x : 4 * pl + here;
-    const long long i3 = inR ? 3 * pl + r0 + xp : 1 * pl + here;
-    const long long i4 = inT ? 4 * pl + rp + x : 2 * pl + here;
-    const long long i5 = (inL && inB) ? 5 * pl + rm + xm : 7 * pl + here;
-    const long long i6 = (inR && inB) ? 6 * pl + rm + xp : 8 * pl + here;
-    const long long i7 = (inR && inT) ? 7 * pl + rp + xp : 5 * pl + here;
-    const long long i8 = (inL && inT) ? 8 * pl + rp + xm : 6 * pl + here;
-    f[0] = to_a(src[here], P.base_f[0]);
-    f[1] = to_a(src[i1], P.base_f[1]);
-    f[2] = to_a(src[i2], P.base_f[2]);
-    f[3] = to_a(src[i3], P.base_f[3]);
-    f[4] = to_a(src[i4], P.base_f[4]);
-    f[5] = to_a(src[i5], P.base_f[5]);
-    f[6] = to_a(src[i6], P.base_f[6]);
-    f[7] = to_a(src[i7], P.base_f[7]);
-    f[8] = to_a(src[i8], P.base_f[8]);
-    const T* gs = src + 9 * pl;
-    const long long j1 = inL ? 1 * pl + r0 + xm : 3 * pl + here;
-    const long long j2 = inB ? 2 * pl + rm + x : 4 * pl + here;
-    const long long j3 = inR ? 3 * pl + r0 + xp : 1 * pl + here;
-    const long long j4 = inT ? 4 * pl + rp + x : 2 * pl + here;
-    g[0] = to_a(gs[here], P.base_g[0]);
-    g[1] = to_a(gs[j1], P.base_g[1]);
-    g[2] = to_a(gs[j2], P.base_g[2]);
-    g[3] = to_a(gs[j3], P.base_g[3]);
-    g[4] = to_a(gs[j4], P.base_g[4]);
-    // anti-bounce-back on Dirichlet walls: g_i = cs2_T T_w - g*_opp (adiabatic: g*_opp as loaded)
-    if (!inL && P.kind[0] == WALL_DIRICHLET) g[1] = P.Tw_c2[0] - g[1];
-    if (!inR && P.kind[1] == WALL_DIRICHLET) g[3] = P.Tw_c2[1] - g[3];
-    if (!inB && P.kind[2] == WALL_DIRICHLET) g[2] = P.Tw_c2[2] - g[2];
-    if (!inT && P.kind[3] == WALL_DIRICHLET) g[4] = P.Tw_c2[3] - g[4];
+    s.idx[0] = here;
+    s.idx[1] = inL ? 1 * pl + r0 + xm : 3 * pl + here;
+    s.idx[2] = inB ? 2 * pl + rm + x : 4 * pl + here;
+    s.idx[3] = inR ? 3 * pl + r0 + xp : 1 * pl + here;
+    s.idx[4] = inT ? 4 * pl + rp + x : 2 * pl + here;
+    s.idx[5] = (inL && inB) ? 5 * pl + rm + xm : 7 * pl + here;
+    s.idx[6] = (inR && inB) ? 6 * pl + rm + xp : 8 * pl + here;
+    s.idx[7] = (inR && inT) ? 7 * pl + rp + xp : 5 * pl + here;
+    s.idx[8] = (inL && inT) ? 8 * pl + rp + xm : 6 * pl + here;
+    const long long g0 = 9 * pl;
+    s.idx[9] = g0 + here;
+    s.idx[10] = g0 + s.idx[1];
+    s.idx[11] = g0 + s.idx[2];
+    s.idx[12] = g0 + s.idx[3];
+    s.idx[13] = g0 + s.idx[4];
+    s.wall_mask = (inL ? 0 : 1) | (inR ? 0 : 2) | (inB ? 0 : 4) | (inT ? 0 : 8);
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_slots(const T* __restrict__ src, const Slots& s, T raw[NPOP])
+{
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) raw[i] = src[s.idx[i]];
+}
+
+// Convert the raw loads to arithmetic precision and apply anti-bounce-back on Dirichlet walls:
+// g_i = cs2_T T_w - g*_opp (adiabatic walls keep the bounced value g*_opp).
+template <typename T, typename A>
+__device__ __forceinline__ void finish_pull(const LatParams<A>& P, const T raw[NPOP], int wall_mask,
+                                            A f[9], A g[5])
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = to_a(raw[i]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = to_a(raw[9 + i]);
+    if (wall_mask) {
+        if ((wall_mask & 1) && P.kind[0] == WALL_DIRICHLET) g[1] = P.Tw_c2[0] - g[1];
+        if ((wall_mask & 2) && P.kind[1] == WALL_DIRICHLET) g[3] = P.Tw_c2[1] - g[3];
+        if ((wall_mask & 4) && P.kind[2] == WALL_DIRICHLET) g[2] = P.Tw_c2[2] - g[2];
+        if ((wall_mask & 8) && P.kind[3] == WALL_DIRICHLET) g[4] = P.Tw_c2[3] - g[4];
+    }
+}
+
+template <typename T, typename A>
+__device__ __forceinline__ void gather(const T* __restrict__ src, const LatParams<A>& P, int x, int y,
+                                       A f[9], A g[5])
+{
+    const Slots s = pull_slots(P, x, y);
+    T raw[NPOP];
+    load_slots(src, s, raw);
+    finish_pull(P, raw, s.wall_mask, f, g);
 }
 
 template <typename T, typename A>
@@ -109,23 +153,26 @@ __device__ __forceinline__ void store_node(T* __restrict__ dst, const LatParams<
     const long long here = (long long)y * P.pitch + x;
     const long long pl = P.plane;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) dst[i * pl + here] = from_a(f[i], P.base_f[i], (T*)nullptr);
+    for (int i = 0; i < 9; ++i) dst[i * pl + here] = from_a(f[i], (T*)nullptr);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) dst[(9 + i) * pl + here] = from_a(g[i], P.base_g[i], (T*)nullptr);
+    for (int i = 0; i < 5; ++i) dst[(9 + i) * pl + here] = from_a(g[i], (T*)nullptr);
 }
 
-// Macroscopic fields, Eqs. (3), (13), (23).
+// Macroscopic fields, Eqs. (3), (13), (23), from stored values (populations, or deviations from
+// the rest state: sum w_i e_i = 0, so the momentum needs no correction).
 template <typename A>
 struct Macro {
-    A rho, ux, uy, T, Fx, Fy;
+    A rho, ux, uy, T, Fx, Fy, drho, dT;  // drho = rho - rho_b, dT = T - T_b
 };
 
 template <typename A>
 __device__ __forceinline__ Macro<A> macroscopic(const LatParams<A>& P, const A f[9], const A g[5])
 {
     Macro<A> m;
-    m.rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    m.T = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    m.dT = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    m.rho = P.rho_b + m.drho;
+    m.T = P.T_b + m.dT;
     m.Fx = P.Fvx;
     m.Fy = P.Fvy + P.gb * (m.T - P.T0);
     const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
@@ -159,7 +206,7 @@ __device__ __forceinline__ void uncentral3(A k0, A k1, A k2, A u, A& c, A& p, A&
     m = A(0.5) * (r2 - r1);
 }
 
-// f* = M^-1 N(u)^-1 k~ for central moments k~[a][b] (a: x order, b: y order).
+// f = M^-1 N(u)^-1 k for central moments k[a][b] (a: x order, b: y order).
 template <typename A>
 __device__ __forceinline__ void back_d2q9(const A k[3][3], A ux, A uy, A f[9])
 {
@@ -188,24 +235,29 @@ __device__ __forceinline__ void back_d2q5(A T, A k10, A k01, A k20, A k02, A ux,
     g[4] = A(0.5) * (r02 - r01);
 }
 
-// Collision of one node in place: Eqs. (6)-(11) for f, Eqs. (16)-(21) for g.
+// D2Q9 central moments k[a][b] = sum f (e_x - u_x)^a (e_y - u_y)^b (Eq. 5b).
+template <typename A>
+__device__ __forceinline__ void central_d2q9(const A f[9], A ux, A uy, A k[3][3])
+{
+    A r0[3], rp[3], rm[3];
+    central3(f[0], f[1], f[3], ux, r0[0], r0[1], r0[2]);  // row e_y = 0
+    central3(f[2], f[5], f[6], ux, rp[0], rp[1], rp[2]);  // row e_y = +1
+    central3(f[4], f[8], f[7], ux, rm[0], rm[1], rm[2]);  // row e_y = -1
+#pragma unroll
+    for (int a = 0; a < 3; ++a) central3(r0[a], rp[a], rm[a], uy, k[a][0], k[a][1], k[a][2]);
+}
+
+// Collision of one node in place, populations form: Eqs. (6)-(11) for f, Eqs. (16)-(21) for g.
 template <typename A>
 __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5])
 {
     const Macro<A> m = macroscopic(P, f, g);
     const A ux = m.ux, uy = m.uy, rho = m.rho, T = m.T;
     const A cs2 = A(1) / A(3);
-
-    // ---- D2Q9: central moments k[a][b] = sum f (e_x - u_x)^a (e_y - u_y)^b (Eq. 5b)
-    A r0[3], rp[3], rm[3];
-    central3(f[0], f[1], f[3], ux, r0[0], r0[1], r0[2]);  // row e_y = 0
-    central3(f[2], f[5], f[6], ux, rp[0], rp[1], rp[2]);  // row e_y = +1
-    central3(f[4], f[8], f[7], ux, rm[0], rm[1], rm[2]);  // row e_y = -1
     A k[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) central3(r0[a], rp[a], rm[a], uy, k[a][0], k[a][1], k[a][2]);
+    central_d2q9(f, ux, uy, k);
 
-    // ---- relaxation, Eq. (8), equilibrium Eq. (9), forcing Eq. (11)
+    // relaxation, Eq. (8), equilibrium Eq. (9), forcing Eq. (11)
     const A a20 = k[2][0] - rho * cs2;
     const A a02 = k[0][2] - rho * cs2;
     A q[3][3];
@@ -221,7 +273,7 @@ __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5])
     q[2][2] = (A(1) - P.s_4) * k[2][2] + P.s_4 * rho * cs2 * cs2;
     back_d2q9(q, ux, uy, f);
 
-    // ---- D2Q5: central moments, relaxation (Eqs. 19, 20), back transform (Eq. 21)
+    // D2Q5: central moments, relaxation (Eqs. 19, 20), back transform (Eq. 21)
     const A d1 = g[1] - g[3], s1 = g[1] + g[3];
     const A d2 = g[2] - g[4], s2 = g[2] + g[4];
     const A t10 = d1 - ux * T;
@@ -234,15 +286,119 @@ __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5])
     back_d2q5(T, om1 * t10, om1 * t01, om2 * t20 + eqT, om2 * t02 + eqT, ux, uy, g);
 }
 
-// Equilibria f^eq(rho, u) and g^eq(T, u): the back transform of Eqs. (9) and (20).
+// Deviation of the D2Q9 equilibrium from the rest state, f^eq_i(rho, u) - w_i rho_b, written as
+// small terms only: f^eq_i = rho p(e_x; u_x) p(e_y; u_y) with the 1-D equilibrium
+// p(0) = w(0) - u^2, p(+-1) = w(1) + (u^2 +- u)/2 (the product form of the moments of Eq. 9).
 template <typename A>
+__device__ __forceinline__ void eq_dev_d2q9(A rho, A drho, A ux, A uy, A f[9])
+{
+    const A w0 = A(2) / A(3), w1 = A(1) / A(6);
+    const A x2 = ux * ux, y2 = uy * uy;
+    const A dx[3] = {-x2, A(0.5) * (x2 + ux), A(0.5) * (x2 - ux)};  // e = 0, +1, -1
+    const A dy[3] = {-y2, A(0.5) * (y2 + uy), A(0.5) * (y2 - uy)};
+    const A wv[3] = {w0, w1, w1};
+    const int ax[9] = {0, 1, 0, 2, 0, 1, 2, 2, 1};
+    const int ay[9] = {0, 0, 1, 0, 2, 1, 1, 2, 2};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const A wx = wv[ax[i]], wy = wv[ay[i]], ex = dx[ax[i]], ey = dy[ay[i]];
+        f[i] = drho * (wx * wy) + rho * (wx * ey + ex * wy + ex * ey);
+    }
+}
+
+// Deviation of the D2Q5 equilibrium from the rest state, g^eq_i(T, u) - w^T_i T_b.
+template <typename A>
+__device__ __forceinline__ void eq_dev_d2q5(A T, A dT, A ux, A uy, A c2, A g[5])
+{
+    const A hc = A(0.5) * c2;
+    g[0] = dT * (A(1) - A(2) * c2) - T * (ux * ux + uy * uy);
+    g[1] = dT * hc + A(0.5) * T * (ux * ux + ux);
+    g[3] = dT * hc + A(0.5) * T * (ux * ux - ux);
+    g[2] = dT * hc + A(0.5) * T * (uy * uy + uy);
+    g[4] = dT * hc + A(0.5) * T * (uy * uy - uy);
+}
+
+// Collision of one node in place, deviation form (h = f - w rho_b, t = g - w^T T_b). The same map
+// as `collide`: Gamma~* = Gamma~eq + (I - S)(Gamma~ - Gamma~eq) + (I - S/2) C, so
+// f* = f^eq + M^-1 N^-1 [(I - S)(Gamma~ - Gamma~eq) + (I - S/2) C]; the non-equilibrium central
+// moments are formed from the central moments of h plus those of w rho_b about u
+// (1-D: 1, -u, 1/3 + u^2) minus Eq. (9), with the O(1) parts cancelled analytically.
+template <typename A>
+__device__ __forceinline__ void collide_dev(const LatParams<A>& P, A f[9], A g[5])
+{
+    const Macro<A> m = macroscopic(P, f, g);
+    const A ux = m.ux, uy = m.uy, rho = m.rho, T = m.T, dr = m.drho, dT = m.dT;
+    const A rb = P.rho_b;
+    const A cs2 = A(1) / A(3);
+    const A x2 = ux * ux, y2 = uy * uy;
+    A k[3][3];
+    central_d2q9(f, ux, uy, k);
+    // non-equilibrium central moments d = k(h) + rho_b k(w) - Gamma~eq
+    const A d10 = k[1][0] - rb * ux;
+    const A d01 = k[0][1] - rb * uy;
+    const A d20 = k[2][0] + rb * x2 - dr * cs2;
+    const A d02 = k[0][2] + rb * y2 - dr * cs2;
+    const A d11 = k[1][1] + rb * ux * uy;
+    const A d21 = k[2][1] - rb * (cs2 + x2) * uy;
+    const A d12 = k[1][2] - rb * ux * (cs2 + y2);
+    const A d22 = k[2][2] - dr * (cs2 * cs2) + rb * (cs2 * (x2 + y2) + x2 * y2);
+    // relaxed non-equilibrium plus forcing, Eqs. (8), (11)
+    A q[3][3];
+    q[0][0] = A(0);
+    q[1][0] = d10 + m.Fx;
+    q[0][1] = d01 + m.Fy;
+    q[2][0] = d20 - P.sp * d20 - P.sm * d02;
+    q[0][2] = d02 - P.sm * d20 - P.sp * d02;
+    q[1][1] = (A(1) - P.s_nu) * d11;
+    const A half3 = (A(1) - A(0.5) * P.s_3) * cs2;
+    q[2][1] = (A(1) - P.s_3) * d21 + half3 * m.Fy;
+    q[1][2] = (A(1) - P.s_3) * d12 + half3 * m.Fx;
+    q[2][2] = (A(1) - P.s_4) * d22;
+    A e[9];
+    eq_dev_d2q9(rho, dr, ux, uy, e);
+    back_d2q9(q, ux, uy, f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] += e[i];
+
+    // D2Q5 on deviations
+    const A c2 = P.cs2T;
+    const A d1 = g[1] - g[3], s1 = g[1] + g[3];
+    const A d2 = g[2] - g[4], s2 = g[2] + g[4];
+    const A t10 = d1 - ux * T;
+    const A t01 = d2 - uy * T;
+    const A t20 = s1 - A(2) * ux * d1 + x2 * dT + P.T_b * x2 - dT * c2;
+    const A t02 = s2 - A(2) * uy * d2 + y2 * dT + P.T_b * y2 - dT * c2;
+    const A om1 = A(1) - P.lambda1;
+    const A om2 = A(1) - P.lambda2;
+    A eT[5], gq[5];
+    eq_dev_d2q5(T, dT, ux, uy, c2, eT);
+    back_d2q5(A(0), om1 * t10, om1 * t01, om2 * t20, om2 * t02, ux, uy, gq);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = gq[i] + eT[i];
+}
+
+template <bool DEV, typename A>
+__device__ __forceinline__ void collide_any(const LatParams<A>& P, A f[9], A g[5])
+{
+    if (DEV) collide_dev(P, f, g);
+    else collide(P, f, g);
+}
+
+// Equilibria in stored form: f^eq(rho, u) and g^eq(T, u) (Eqs. 9, 20 back-transformed), minus the
+// rest state for deviation storage.
+template <bool DEV, typename A>
 __device__ __forceinline__ void equilibrium(const LatParams<A>& P, A rho, A ux, A uy, A T, A f[9],
                                             A g[5])
 {
-    const A cs2 = A(1) / A(3);
-    A k[3][3] = {{rho, A(0), rho * cs2}, {A(0), A(0), A(0)}, {rho * cs2, A(0), rho * cs2 * cs2}};
-    back_d2q9(k, ux, uy, f);
-    back_d2q5(T, A(0), A(0), T * P.cs2T, T * P.cs2T, ux, uy, g);
+    if (DEV) {
+        eq_dev_d2q9(rho, rho - P.rho_b, ux, uy, f);
+        eq_dev_d2q5(T, T - P.T_b, ux, uy, P.cs2T, g);
+    } else {
+        const A cs2 = A(1) / A(3);
+        A k[3][3] = {{rho, A(0), rho * cs2}, {A(0), A(0), A(0)}, {rho * cs2, A(0), rho * cs2 * cs2}};
+        back_d2q9(k, ux, uy, f);
+        back_d2q5(T, A(0), A(0), T * P.cs2T, T * P.cs2T, ux, uy, g);
+    }
 }
 
 }  // namespace clb

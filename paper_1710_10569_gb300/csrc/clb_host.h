@@ -83,9 +83,13 @@ LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
     P.plane = plane_elems(nx, ny, p.storage);
     P.per_x = p.wall[0] == CLB_PERIODIC;
     P.per_y = p.wall[2] == CLB_PERIODIC;
+    // deviation storage is taken against the rest state (w rho0, w^T T_ref); FP64 stores populations
+    const bool dev = p.storage != ST_F64;
+    P.rho_b = dev ? A(p.rho0) : A(0);
+    P.T_b = dev ? A(p.T_ref) : A(0);
     for (int s = 0; s < 4; ++s) {
         P.kind[s] = p.wall[s];
-        P.Tw_c2[s] = A(p.cs2_T * p.T_wall[s]);
+        P.Tw_c2[s] = A(p.cs2_T * (p.T_wall[s] - (dev ? p.T_ref : 0.0)));
     }
     const double s_nu = rate_nu(p.nu);
     P.s_nu = A(s_nu);
@@ -100,15 +104,6 @@ LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
     P.Fvy = A(p.Fv[1]);
     P.gb = A(p.rho0 * p.g_beta);
     P.T0 = A(p.T0);
-    if (p.storage == ST_F16DEV) {
-        // rest weights of D2Q9 (Eq. 9 at u = 0) and D2Q5 (Eq. 20 at u = 0)
-        const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
-                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-        const double w5[5] = {1.0 - 2.0 * p.cs2_T, 0.5 * p.cs2_T, 0.5 * p.cs2_T, 0.5 * p.cs2_T,
-                              0.5 * p.cs2_T};
-        for (int i = 0; i < 9; ++i) P.base_f[i] = A(w9[i] * p.rho0);
-        for (int i = 0; i < 5; ++i) P.base_g[i] = A(w5[i] * p.T_ref);
-    }
     return P;
 }
 

@@ -10,30 +10,52 @@ namespace clb {
 
 // One time step: pull the 14 populations of node (x, y) (Eqs. 12, 22, with the wall rules),
 // collide them (Eqs. 3-11, 13, 16-21, 23) and store the post-collision values at (x, y).
-template <int ST>
-__global__ void __launch_bounds__(512) k_step(const typename Storage<ST>::T* __restrict__ src,
+// A thread updates NPT nodes of one row, blockDim.x apart (each load instruction stays
+// coalesced); all NPT * 14 loads are issued before the first collision so that more bytes are in
+// flight per thread.
+template <int ST, int NPT>
+__global__ void __launch_bounds__(256) k_step(const typename Storage<ST>::T* __restrict__ src,
                                               typename Storage<ST>::T* __restrict__ dst,
                                               const LatParams<typename Storage<ST>::A> P)
 {
     using A = typename Storage<ST>::A;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    using E = typename Storage<ST>::T;
+    const int x0 = blockIdx.x * (blockDim.x * NPT) + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    A f[9], g[5];
-    gather(src, P, x, y, f, g);
-    collide(P, f, g);
-    store_node(dst, P, x, y, f, g);
+    if (y >= P.ny) return;
+    E raw[NPT][NPOP];
+    int mask[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int x = x0 + k * blockDim.x;
+        mask[k] = 0;
+        if (x < P.nx) {
+            const Slots s = pull_slots(P, x, y);
+            load_slots(src, s, raw[k]);
+            mask[k] = s.wall_mask;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int x = x0 + k * blockDim.x;
+        if (x < P.nx) {
+            A f[9], g[5];
+            finish_pull(P, raw[k], mask[k], f, g);
+            collide_any<Storage<ST>::DEV>(P, f, g);
+            store_node(dst, P, x, y, f, g);
+        }
+    }
 }
 
-// Initialisation to f^eq(rho, u), g^eq(T, u). The buffer holds post-collision values that the
-// next step pulls, so each equilibrium value is written to the slot its pull reads: population i
-// of node x goes to (i, x - e_i), or, when x - e_i is beyond a wall, to the node's own opposite
-// slot (with the anti-bounce-back constant removed on Dirichlet walls). Every slot is written
-// exactly once. NULL fields mean rho = 1, u = 0, T = T0.
+// Initialisation to f^eq(rho, u), g^eq(T, u) (in stored form). The buffer holds post-collision
+// values that the next step pulls, so each equilibrium value is written to the slot its pull
+// reads: population i of node x goes to (i, x - e_i), or, when x - e_i is beyond a wall, to the
+// node's own opposite slot (with the anti-bounce-back constant removed on Dirichlet walls). Every
+// slot is written exactly once. NULL fields mean rho = rho0, u = 0, T = T0.
 template <int ST>
 __global__ void k_init(typename Storage<ST>::T* __restrict__ dst, const LatParams<typename Storage<ST>::A> P,
                        const double* __restrict__ rho, const double* __restrict__ ux,
-                       const double* __restrict__ uy, const double* __restrict__ T)
+                       const double* __restrict__ uy, const double* __restrict__ T, double rho0)
 {
     using A = typename Storage<ST>::A;
     using E = typename Storage<ST>::T;
@@ -42,8 +64,8 @@ __global__ void k_init(typename Storage<ST>::T* __restrict__ dst, const LatParam
     if (x >= P.nx || y >= P.ny) return;
     const long long n = (long long)y * P.nx + x;
     A f[9], g[5];
-    equilibrium(P, rho ? A(rho[n]) : A(1), ux ? A(ux[n]) : A(0), uy ? A(uy[n]) : A(0),
-                T ? A(T[n]) : P.T0, f, g);
+    equilibrium<Storage<ST>::DEV>(P, rho ? A(rho[n]) : A(rho0), ux ? A(ux[n]) : A(0),
+                                  uy ? A(uy[n]) : A(0), T ? A(T[n]) : P.T0, f, g);
     const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
@@ -64,11 +86,11 @@ __global__ void k_init(typename Storage<ST>::T* __restrict__ dst, const LatParam
             plane = OPP[i];
             slot = (long long)y * P.pitch + x;
         }
-        dst[plane * P.plane + slot] = from_a(f[i], P.base_f[plane], (E*)nullptr);
+        dst[plane * P.plane + slot] = from_a(f[i], (E*)nullptr);
         if (i < 5) {
             A v = g[i];
             if (side >= 0 && P.kind[side] == WALL_DIRICHLET) v = P.Tw_c2[side] - v;
-            dst[(9 + plane) * P.plane + slot] = from_a(v, P.base_g[plane], (E*)nullptr);
+            dst[(9 + plane) * P.plane + slot] = from_a(v, (E*)nullptr);
         }
     }
 }
@@ -87,13 +109,14 @@ __global__ void k_fields(const typename Storage<ST>::T* __restrict__ src,
     gather(src, P, x, y, f, g);
     const Macro<A> m = macroscopic(P, f, g);
     const long long n = (long long)y * P.nx + x;
-    if (rho) rho[n] = double(m.rho);
+    if (rho) rho[n] = double(P.rho_b) + double(m.drho);
     if (ux) ux[n] = double(m.ux);
     if (uy) uy[n] = double(m.uy);
-    if (T) T[n] = double(m.T);
+    if (T) T[n] = double(P.T_b) + double(m.dT);
 }
 
-// Pre-collision populations at the current time as double f[9][ny][nx], g[5][ny][nx].
+// Pre-collision populations at the current time as double f[9][ny][nx], g[5][ny][nx]
+// (the rest state added back for deviation storage).
 template <int ST>
 __global__ void k_pops(const typename Storage<ST>::T* __restrict__ src,
                        const LatParams<typename Storage<ST>::A> P, double* __restrict__ f_out,
@@ -107,9 +130,9 @@ __global__ void k_pops(const typename Storage<ST>::T* __restrict__ src,
     gather(src, P, x, y, f, g);
     const long long n = (long long)y * P.nx + x, N = (long long)P.nx * P.ny;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f_out[i * N + n] = double(f[i]);
+    for (int i = 0; i < 9; ++i) f_out[i * N + n] = double(f[i]) + double(w9<A>(i)) * double(P.rho_b);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) g_out[i * N + n] = double(g[i]);
+    for (int i = 0; i < 5; ++i) g_out[i * N + n] = double(g[i]) + double(w5<A>(i, P.cs2T)) * double(P.T_b);
 }
 
 constexpr int kReduceThreads = 256;
@@ -149,7 +172,7 @@ __device__ __forceinline__ void reduce_row(const E* __restrict__ src, const LatP
         A f[9], g[5];
         gather(src, P, x, y, f, g);
         const Macro<A> m = macroscopic(P, f, g);
-        const double ux = double(m.ux), uy = double(m.uy), T = double(m.T);
+        const double ux = double(m.ux), uy = double(m.uy), T = double(P.T_b) + double(m.dT);
         const long long n = (long long)y * P.nx + x;
         const double sx = snap[n], sy = snap[N + n], sT = snap[2 * N + n];
         v[RS_UT] += (axis == 0 ? ux : uy) * (T - double(P.T0));

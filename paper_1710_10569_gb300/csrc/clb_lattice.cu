@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -137,7 +138,7 @@ struct clb_handle {
     double* diag = nullptr;
     double* host_diag = nullptr;  // pinned
     long steps = 0;
-    int bx = 128, by = 1;
+    int bx = 128, by = 1, npt = 1;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     LatParams<double> Pd{};
     LatParams<float> Pf{};
@@ -159,16 +160,33 @@ dim3 grid_for(const clb_handle* h, int bx, int by)
     return dim3((h->nx + bx - 1) / bx, (h->ny + by - 1) / by);
 }
 
-// Enqueue one step from buffer `from` into the other buffer on stream s.
-clb_status launch_step(clb_handle* h, int from, cudaStream_t s, int bx, int by)
+template <int ST, int NPT>
+void enqueue_step(const clb_handle* h, const void* a, void* b, cudaStream_t s, int bx, int by)
 {
-    const dim3 block(bx, by), grid = grid_for(h, bx, by);
+    using E = typename Storage<ST>::T;
+    using A = typename Storage<ST>::A;
+    const dim3 block(bx, by), grid((h->nx + bx * NPT - 1) / (bx * NPT), (h->ny + by - 1) / by);
+    const LatParams<A>& P = *reinterpret_cast<const LatParams<A>*>(ST == ST_F64 ? (const void*)&h->Pd : (const void*)&h->Pf);
+    k_step<ST, NPT><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
+}
+
+template <int ST>
+void enqueue_step_npt(const clb_handle* h, const void* a, void* b, cudaStream_t s, int bx, int by, int npt)
+{
+    if (npt == 4) enqueue_step<ST, 4>(h, a, b, s, bx, by);
+    else if (npt == 2) enqueue_step<ST, 2>(h, a, b, s, bx, by);
+    else enqueue_step<ST, 1>(h, a, b, s, bx, by);
+}
+
+// Enqueue one step from buffer `from` into the other buffer on stream s.
+clb_status launch_step(clb_handle* h, int from, cudaStream_t s, int bx, int by, int npt)
+{
     void* a = h->buf[from];
     void* b = h->buf[from ^ 1];
     switch (h->p.storage) {
-    case CLB_F64: k_step<ST_F64><<<grid, block, 0, s>>>((const double*)a, (double*)b, h->Pd); break;
-    case CLB_F32: k_step<ST_F32><<<grid, block, 0, s>>>((const float*)a, (float*)b, h->Pf); break;
-    default: k_step<ST_F16DEV><<<grid, block, 0, s>>>((const __half*)a, (__half*)b, h->Pf); break;
+    case CLB_F64: enqueue_step_npt<ST_F64>(h, a, b, s, bx, by, npt); break;
+    case CLB_F32: enqueue_step_npt<ST_F32>(h, a, b, s, bx, by, npt); break;
+    default: enqueue_step_npt<ST_F16DEV>(h, a, b, s, bx, by, npt); break;
     }
     CLB_CUDA(cudaGetLastError());
     return CLB_OK;
@@ -178,7 +196,7 @@ clb_status build_graph(clb_handle* h, int start)
 {
     CLB_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     clb_status st = CLB_OK;
-    for (int k = 0; k < kGraphChunk && st == CLB_OK; ++k) st = launch_step(h, start ^ (k & 1), h->cap, h->bx, h->by);
+    for (int k = 0; k < kGraphChunk && st == CLB_OK; ++k) st = launch_step(h, start ^ (k & 1), h->cap, h->bx, h->by, h->npt);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap, &g);
     if (st != CLB_OK) {
@@ -198,9 +216,9 @@ clb_status launch_init(clb_handle* h, const double* rho, const double* ux, const
     const dim3 block(128, 1), grid = grid_for(h, 128, 1);
     void* d = h->buf[h->cur];
     switch (h->p.storage) {
-    case CLB_F64: k_init<ST_F64><<<grid, block, 0, h->stream>>>((double*)d, h->Pd, rho, ux, uy, T); break;
-    case CLB_F32: k_init<ST_F32><<<grid, block, 0, h->stream>>>((float*)d, h->Pf, rho, ux, uy, T); break;
-    default: k_init<ST_F16DEV><<<grid, block, 0, h->stream>>>((__half*)d, h->Pf, rho, ux, uy, T); break;
+    case CLB_F64: k_init<ST_F64><<<grid, block, 0, h->stream>>>((double*)d, h->Pd, rho, ux, uy, T, h->p.rho0); break;
+    case CLB_F32: k_init<ST_F32><<<grid, block, 0, h->stream>>>((float*)d, h->Pf, rho, ux, uy, T, h->p.rho0); break;
+    default: k_init<ST_F16DEV><<<grid, block, 0, h->stream>>>((__half*)d, h->Pf, rho, ux, uy, T, h->p.rho0); break;
     }
     CLB_CUDA(cudaGetLastError());
     return CLB_OK;
@@ -249,7 +267,7 @@ clb_status take_snapshot(clb_handle* h)
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune_cache;
+std::map<std::tuple<int, int, int>, std::array<int, 3>> g_tune_cache;
 
 }  // namespace
 
@@ -307,12 +325,14 @@ extern "C" clb_status clb_create(int nx, int ny, const clb_params* p, void* stre
     h->diag = (double*)(h->mem + L.diag);
     h->Pd = make_lat_params<double>(nx, ny, *p);
     h->Pf = make_lat_params<float>(nx, ny, *p);
+    h->npt = p->storage == CLB_F64 ? 1 : p->storage == CLB_F32 ? 2 : 4;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(std::make_tuple(p->storage, nx, ny));
         if (it != g_tune_cache.end()) {
-            h->bx = it->second.first;
-            h->by = it->second.second;
+            h->bx = it->second[0];
+            h->by = it->second[1];
+            h->npt = it->second[2];
         }
     }
     // the padding between rows and planes is never read, but keep it defined
@@ -381,7 +401,7 @@ extern "C" clb_status clb_step(clb_handle* h, long n)
         h->steps += kGraphChunk;
     }
     for (; n > 0; --n) {
-        CLB_TRY(launch_step(h, h->cur, h->stream, h->bx, h->by));
+        CLB_TRY(launch_step(h, h->cur, h->stream, h->bx, h->by, h->npt));
         h->cur ^= 1;
         h->steps++;
     }
@@ -547,32 +567,37 @@ extern "C" clb_status clb_load(clb_handle* h, const void* buf, size_t bytes)
     return CLB_OK;
 }
 
-extern "C" clb_status clb_set_launch(clb_handle* h, int block_x, int block_y)
+extern "C" clb_status clb_set_launch(clb_handle* h, int block_x, int block_y, int nodes_per_thread)
 {
     CHECK_H(h);
     const int bx = block_x ? block_x : h->bx, by = block_y ? block_y : h->by;
-    if (bx < 32 || bx > 1024 || bx % 32 || by < 1 || by > 32 || bx * by > 512)
-        return set_error(CLB_EINVAL, "launch shape %d x %d: block_x in [32, 1024] multiple of 32, "
-                                     "block_y in [1, 32], block_x * block_y <= 512", bx, by);
-    if (bx != h->bx || by != h->by) {
+    const int npt = nodes_per_thread ? nodes_per_thread : h->npt;
+    if (bx < 32 || bx > 256 || bx % 32 || by < 1 || by > 8 || bx * by > 256 ||
+        (npt != 1 && npt != 2 && npt != 4))
+        return set_error(CLB_EINVAL, "launch shape %d x %d x %d: block_x in [32, 256] multiple of 32, "
+                                     "block_y in [1, 8], block_x * block_y <= 256, nodes per thread 1, 2 or 4",
+                         bx, by, npt);
+    if (bx != h->bx || by != h->by || npt != h->npt) {
         DeviceGuard dg(h->device);
         cudaStreamSynchronize(h->stream);
         drop_graphs(h);
         h->bx = bx;
         h->by = by;
+        h->npt = npt;
     }
     return CLB_OK;
 }
 
-extern "C" clb_status clb_get_launch(clb_handle* h, int* block_x, int* block_y)
+extern "C" clb_status clb_get_launch(clb_handle* h, int* block_x, int* block_y, int* nodes_per_thread)
 {
     CHECK_H(h);
     if (block_x) *block_x = h->bx;
     if (block_y) *block_y = h->by;
+    if (nodes_per_thread) *nodes_per_thread = h->npt;
     return CLB_OK;
 }
 
-extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y)
+extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y, int* nodes_per_thread)
 {
     CHECK_H(h);
     DeviceGuard dg(h->device);
@@ -580,31 +605,33 @@ extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y)
     void* save = nullptr;
     CLB_CUDA(cudaMallocAsync(&save, bb, h->stream));
     CLB_CUDA(cudaMemcpyAsync(save, h->buf[h->cur], bb, cudaMemcpyDeviceToDevice, h->stream));
-    const int shapes[][2] = {{64, 1}, {128, 1}, {256, 1}, {512, 1}, {32, 4}, {64, 2}, {64, 4},
-                             {128, 2}, {128, 4}, {256, 2}, {32, 8}};
+    const int shapes[][2] = {{64, 1}, {128, 1}, {256, 1}, {32, 4}, {64, 2}, {64, 4}, {128, 2}, {32, 8}};
+    const int npts[] = {1, 2, 4};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bbx = h->bx, bby = h->by;
+    int bbx = h->bx, bby = h->by, bnpt = h->npt;
     const int reps = 10;
     clb_status st = CLB_OK;
-    for (auto& s : shapes) {
-        if ((long long)s[0] > 2LL * h->nx + 64 && s[0] > 64) continue;  // far wider than the lattice
-        for (int k = 0; k < 4 && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, s[0], s[1]);
-        cudaEventRecord(e0, h->stream);
-        for (int k = 0; k < reps && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, s[0], s[1]);
-        cudaEventRecord(e1, h->stream);
-        if (st != CLB_OK) break;
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            bbx = s[0];
-            bby = s[1];
+    for (int npt : npts)
+        for (auto& s : shapes) {
+            if (s[0] * npt > 2 * h->nx + 64 && s[0] * npt > 64) continue;  // far wider than the lattice
+            for (int k = 0; k < 4 && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, s[0], s[1], npt);
+            cudaEventRecord(e0, h->stream);
+            for (int k = 0; k < reps && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, s[0], s[1], npt);
+            cudaEventRecord(e1, h->stream);
+            if (st != CLB_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bbx = s[0];
+                bby = s[1];
+                bnpt = npt;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaError_t e = cudaMemcpyAsync(h->buf[h->cur], save, bb, cudaMemcpyDeviceToDevice, h->stream);
@@ -612,13 +639,14 @@ extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y)
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (st != CLB_OK) return st;
     if (e != cudaSuccess) return set_error(CLB_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
-    CLB_TRY(clb_set_launch(h, bbx, bby));
+    CLB_TRY(clb_set_launch(h, bbx, bby, bnpt));
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[std::make_tuple(h->p.storage, h->nx, h->ny)] = {bbx, bby};
+        g_tune_cache[std::make_tuple(h->p.storage, h->nx, h->ny)] = {bbx, bby, bnpt};
     }
     if (block_x) *block_x = bbx;
     if (block_y) *block_y = bby;
+    if (nodes_per_thread) *nodes_per_thread = bnpt;
     return CLB_OK;
 }
 

@@ -40,7 +40,7 @@ def test_instance_alone_equals_instance_in_mix(clb, storage):
             assert np.array_equal(a, b), (k, prob.name)
 
 
-@pytest.mark.parametrize("tile", [(128, 1), (64, 2), (32, 4), (256, 1)])
+@pytest.mark.parametrize("tile", [(128, 1, 1), (64, 2, 2), (32, 4, 4), (256, 1, 2), (64, 1, 4)])
 def test_tile_shape_does_not_change_results(clb, tile):
     probs = mixed_problems(F32)
     ref = clb.Batch(probs)
@@ -48,6 +48,20 @@ def test_tile_shape_does_not_change_results(clb, tile):
     b = clb.Batch(probs)
     b.set_tile(*tile)
     b.step(40)
+    for k in range(len(probs)):
+        for x, y in zip(b.fields(k), ref.fields(k)):
+            assert np.array_equal(x, y)
+
+
+def test_batch_autotune_keeps_state_and_results(clb):
+    probs = mixed_problems(F32)
+    ref = clb.Batch(probs)
+    ref.step(20)
+    b = clb.Batch(probs)
+    b.step(10)
+    tile = b.autotune()
+    assert tile[0] % 32 == 0 and tile[2] in (1, 2, 4)
+    b.step(10)
     for k in range(len(probs)):
         for x, y in zip(b.fields(k), ref.fields(k)):
             assert np.array_equal(x, y)
@@ -122,6 +136,8 @@ def test_serve_budget_and_errors(clb):
     with pytest.raises(clb.CLBError) as e:
         srv.fetch(rid, 16, 16)
     assert e.value.status == clb.CLB_EBUSY
-    while srv.progress(32)[0] or srv.progress(32)[1]:
-        pass
+    for _ in range(10):
+        active, queued = srv.progress(32)
+        if not active and not queued:
+            break
     assert srv.poll(rid)[0]

@@ -20,7 +20,7 @@ F64, F32, F16 = W.STORAGE_F64, W.STORAGE_F32, W.STORAGE_F16DEV
 P, D, A = W.WALL_PERIODIC, W.WALL_DIRICHLET, W.WALL_ADIABATIC
 NAMES = ("rho", "ux", "uy", "T")
 # per storage: tolerance on (rho, u, T) normwise errors after the runs below
-TOL = {F64: 1e-12, F32: 2e-5, F16: 2e-2}
+TOL = {F64: 1e-12, F32: 1e-5, F16: 3e-2}
 
 
 @pytest.fixture(scope="module")
@@ -45,17 +45,23 @@ def report(tag, errs):
             f.write(json.dumps({"case": tag, **errs}) + "\n")
 
 
-def compare(tag, got, exp, tol, uvec_scale=False):
+def compare(tag, got, exp, tol, params=None):
+    """Normwise errors per field. rho is measured against max|rho|; u against the larger of max|u|
+    and the problem's characteristic velocity u_ref (u is a small difference of O(1) populations,
+    so its rounding error scales with them, not with |u|); T against the larger of max|T| and the
+    problem's temperature difference dT_ref."""
+    u_ref = params.get("u_ref", 0.0) if params else 0.0
+    dT_ref = params.get("dT_ref", 0.0) if params else 0.0
     errs = {}
     for name, a, b in zip(NAMES, got, exp):
         if name == "rho":
             errs[name] = float(np.max(np.abs(a - b))) / float(np.max(np.abs(b)))
         elif name in ("ux", "uy"):
-            # velocity components share one scale (the speed)
-            s = max(float(np.max(np.abs(exp[1]))), float(np.max(np.abs(exp[2]))), 1e-300)
+            s = max(float(np.max(np.abs(exp[1]))), float(np.max(np.abs(exp[2]))), u_ref, 1e-300)
             errs[name] = float(np.max(np.abs(a - b))) / s
         else:
-            errs[name] = normwise(a, b)
+            s = max(float(np.max(np.abs(b))), dT_ref, 1e-300)
+            errs[name] = float(np.max(np.abs(a - b))) / s
     report(tag, errs)
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, f"{tag}: normwise errors above {tol:g}: {bad} (all: {errs})"
@@ -77,7 +83,7 @@ def run_both(clb, prob, steps):
 def test_taylor_green_64_fp64_1000_steps(clb):
     prob = W.taylor_green(64, storage=F64)
     lat, o, got, exp = run_both(clb, prob, 1000)
-    compare("tg64_f64_1000", got, exp, 1e-12)
+    compare("tg64_f64_1000", got, exp, 1e-12, prob.params)
     f, g = lat.populations()
     fo, go = o.populations()
     assert normwise(f, fo) <= 1e-12 and normwise(g, go) <= 1e-12
@@ -87,7 +93,7 @@ def test_taylor_green_64_fp64_1000_steps(clb):
 def test_taylor_green_64_reduced_precision(clb, storage):
     prob = W.taylor_green(64, storage=storage)
     _, _, got, exp = run_both(clb, prob, 1000)
-    compare(f"tg64_{W.STORAGE_NAMES[storage]}_1000", got, exp, TOL[storage])
+    compare(f"tg64_{W.STORAGE_NAMES[storage]}_1000", got, exp, TOL[storage], prob.params)
 
 
 # ------------------------------------------------------------------ walls, ragged sizes, all storages
@@ -100,7 +106,7 @@ SHAPES = [(67, 45), (130, 7), (2, 2), (3, 257), (257, 3), (33, 33)]
 def test_random_problems_fp64(clb, shape, seed):
     prob = W.random_problem(*shape, seed=seed, storage=F64)
     _, _, got, exp = run_both(clb, prob, 60)
-    compare(f"rand{shape}_s{seed}_f64", got, exp, 1e-12)
+    compare(f"rand{shape}_s{seed}_f64", got, exp, 1e-12, prob.params)
 
 
 @pytest.mark.parametrize("storage", [F32, F16])
@@ -108,7 +114,7 @@ def test_random_problems_fp64(clb, shape, seed):
 def test_random_problems_reduced_precision(clb, storage, seed):
     prob = W.random_problem(67, 45, seed=seed, storage=storage)
     _, _, got, exp = run_both(clb, prob, 60)
-    compare(f"rand67x45_s{seed}_{W.STORAGE_NAMES[storage]}", got, exp, TOL[storage])
+    compare(f"rand67x45_s{seed}_{W.STORAGE_NAMES[storage]}", got, exp, TOL[storage], prob.params)
 
 
 def test_initial_fields_match_oracle(clb):
@@ -121,7 +127,7 @@ def test_initial_fields_match_oracle(clb):
         f, g = lat.populations()
         fo, go = o.populations()
         assert normwise(f, fo) <= 1e-14 and normwise(g, go) <= 1e-14
-        compare(f"init_s{seed}", lat.fields(), o.fields(), 1e-14)
+        compare(f"init_s{seed}", lat.fields(), o.fields(), 1e-14, prob.params)
 
 
 # ------------------------------------------------------------------ config #2 cavity, config #3 RB
@@ -132,7 +138,7 @@ def test_cavity_256_short(clb, storage):
     prob = W.cavity(256, storage=storage)
     # the fluid starts at rest with 1e-4 noise: give the buoyant flow time to develop
     _, o, got, exp = run_both(clb, prob, 400)
-    compare(f"cavity256_{W.STORAGE_NAMES[storage]}_400", got, exp, TOL[storage])
+    compare(f"cavity256_{W.STORAGE_NAMES[storage]}_400", got, exp, TOL[storage], prob.params)
 
 
 @pytest.mark.parametrize("storage", [F64, F32, F16])
@@ -140,8 +146,8 @@ def test_rayleigh_benard_2048x1024_full_size(clb, storage):
     """The bench workload at full size, the launch configuration bench.py times (graph chunks of
     the fused kernel), a few steps, every node compared."""
     prob = W.rayleigh_benard(2048, 1024, storage=storage)
-    _, _, got, exp = run_both(clb, prob, 3)
-    compare(f"rb2048_{W.STORAGE_NAMES[storage]}_3", got, exp, TOL[storage])
+    _, _, got, exp = run_both(clb, prob, 6)
+    compare(f"rb2048_{W.STORAGE_NAMES[storage]}_6", got, exp, TOL[storage], prob.params)
 
 
 def test_graph_chunks_equal_single_launches(clb):
@@ -160,7 +166,7 @@ def test_graph_chunks_equal_single_launches(clb):
 def test_launch_shapes_are_bitwise_equal(clb):
     prob = W.random_problem(150, 37, seed=3, storage=F32)
     ref = None
-    for shape in ((128, 1), (64, 4), (256, 2), (32, 8)):
+    for shape in ((128, 1, 1), (64, 4, 2), (128, 2, 4), (32, 8, 1), (256, 1, 2)):
         lat = clb.Lattice.from_problem(prob)
         lat.set_launch(*shape)
         lat.step(40)

@@ -25,7 +25,9 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+    # -fmad=false: no automatic FMA contraction; the kernels write their FMAs explicitly so the
+    # per-node arithmetic is identical in every kernel and launch shape
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
                    "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")] + list(extra)
 
 

@@ -47,8 +47,9 @@ __device__ __forceinline__ void load_member(const Member<A>* __restrict__ src, M
 }
 
 // One time step of every lattice: block b covers tile (b - tile_begin) of lattice owner[b]; a
-// tile is (blockDim.x * NPT) x blockDim.y nodes, NPT nodes per thread blockDim.x apart.
-template <int ST, int NPT>
+// tile is (blockDim.x * V) x blockDim.y nodes, V consecutive nodes per thread (the same
+// per-warp update as the single-lattice step).
+template <int ST, int V>
 __global__ void __launch_bounds__(256) k_step_batched(const Member<typename Storage<ST>::A>* __restrict__ mem,
                                                       const int* __restrict__ owner, int parity)
 {
@@ -58,33 +59,11 @@ __global__ void __launch_bounds__(256) k_step_batched(const Member<typename Stor
     load_member(mem + owner[blockIdx.x], M);
     const int t = blockIdx.x - M.tile_begin;
     const int tx = t % M.tiles_x, ty = t / M.tiles_x;
-    const int x0 = tx * blockDim.x * NPT + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (tx * blockDim.x + threadIdx.x) * V;
     const int y = ty * blockDim.y + threadIdx.y;
-    if (y >= M.P.ny) return;
-    const E* src = (const E*)M.buf[parity];
-    E* dst = (E*)M.buf[parity ^ 1];
-    E raw[NPT][NPOP];
-    int mask[NPT];
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int x = x0 + k * blockDim.x;
-        mask[k] = 0;
-        if (x < M.P.nx) {
-            const Slots s = pull_slots(M.P, x, y);
-            load_slots(src, s, raw[k]);
-            mask[k] = s.wall_mask;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int x = x0 + k * blockDim.x;
-        if (x < M.P.nx) {
-            A f[9], g[5];
-            finish_pull(M.P, raw[k], mask[k], f, g);
-            collide_any<Storage<ST>::DEV>(M.P, f, g);
-            store_node(dst, M.P, x, y, f, g);
-        }
-    }
+    if (y >= M.P.ny || x0 - lane * V >= M.P.nx) return;
+    step_warp_nodes<ST, V>((const E*)M.buf[parity], (E*)M.buf[parity ^ 1], M.P, x0, y, lane);
 }
 
 template <int ST>

@@ -39,6 +39,15 @@ __device__ __forceinline__ double from_a(double v, double*) { return v; }
 __device__ __forceinline__ float from_a(float v, float*) { return v; }
 __device__ __forceinline__ __half from_a(float v, __half*) { return __float2half_rn(v); }
 
+// Fused multiply-add written out. The library is compiled without automatic contraction
+// (-fmad=false), so every rounding step is the one written here: the per-node arithmetic is the
+// same instruction sequence in every kernel and launch shape, which makes results bitwise
+// independent of how nodes are assigned to threads.
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rcp_(double a) { return __drcp_rn(a); }
+
 // Per-lattice constants in the arithmetic precision A.
 template <typename A>
 struct LatParams {
@@ -174,12 +183,12 @@ __device__ __forceinline__ Macro<A> macroscopic(const LatParams<A>& P, const A f
     m.rho = P.rho_b + m.drho;
     m.T = P.T_b + m.dT;
     m.Fx = P.Fvx;
-    m.Fy = P.Fvy + P.gb * (m.T - P.T0);
+    m.Fy = fma_(P.gb, m.T - P.T0, P.Fvy);
     const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const A jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const A inv = A(1) / m.rho;
-    m.ux = (jx + A(0.5) * m.Fx) * inv;
-    m.uy = (jy + A(0.5) * m.Fy) * inv;
+    const A inv = rcp_(m.rho);
+    m.ux = fma_(A(0.5), m.Fx, jx) * inv;
+    m.uy = fma_(A(0.5), m.Fy, jy) * inv;
     return m;
 }
 
@@ -187,20 +196,20 @@ __device__ __forceinline__ Macro<A> macroscopic(const LatParams<A>& P, const A f
 template <typename A>
 __device__ __forceinline__ void central3(A c, A p, A m, A u, A& k0, A& k1, A& k2)
 {
-    const A s0 = c + p + m;
-    const A d = p - m;
     const A s = p + m;
+    const A s0 = c + s;
+    const A d = p - m;
     k0 = s0;
-    k1 = d - u * s0;
-    k2 = s - A(2) * u * d + u * u * s0;
+    k1 = fma_(-u, s0, d);
+    k2 = fma_(u * u, s0, fma_(A(-2) * u, d, s));
 }
 
 // Inverse of central3: raw moments about 0 (shift back by u), then the 1-D inverse moment map.
 template <typename A>
 __device__ __forceinline__ void uncentral3(A k0, A k1, A k2, A u, A& c, A& p, A& m)
 {
-    const A r1 = k1 + u * k0;
-    const A r2 = k2 + A(2) * u * k1 + u * u * k0;
+    const A r1 = fma_(u, k0, k1);
+    const A r2 = fma_(u * u, k0, fma_(A(2) * u, k1, k2));
     c = k0 - r2;
     p = A(0.5) * (r2 + r1);
     m = A(0.5) * (r2 - r1);
@@ -224,10 +233,10 @@ template <typename A>
 __device__ __forceinline__ void back_d2q5(A T, A k10, A k01, A k20, A k02, A ux, A uy, A g[5])
 {
     // Each axis row shares the rest population g0; split the two 1-D inverses over it.
-    const A r10 = k10 + ux * T;
-    const A r20 = k20 + A(2) * ux * k10 + ux * ux * T;
-    const A r01 = k01 + uy * T;
-    const A r02 = k02 + A(2) * uy * k01 + uy * uy * T;
+    const A r10 = fma_(ux, T, k10);
+    const A r20 = fma_(ux * ux, T, fma_(A(2) * ux, k10, k20));
+    const A r01 = fma_(uy, T, k01);
+    const A r02 = fma_(uy * uy, T, fma_(A(2) * uy, k01, k02));
     g[0] = T - r20 - r02;
     g[1] = A(0.5) * (r20 + r10);
     g[3] = A(0.5) * (r20 - r10);
@@ -258,32 +267,32 @@ __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5])
     central_d2q9(f, ux, uy, k);
 
     // relaxation, Eq. (8), equilibrium Eq. (9), forcing Eq. (11)
-    const A a20 = k[2][0] - rho * cs2;
-    const A a02 = k[0][2] - rho * cs2;
+    const A a20 = fma_(-rho, cs2, k[2][0]);
+    const A a02 = fma_(-rho, cs2, k[0][2]);
     A q[3][3];
     q[0][0] = rho;
     q[1][0] = k[1][0] + m.Fx;
     q[0][1] = k[0][1] + m.Fy;
-    q[2][0] = k[2][0] - P.sp * a20 - P.sm * a02;
-    q[0][2] = k[0][2] - P.sm * a20 - P.sp * a02;
+    q[2][0] = fma_(-P.sm, a02, fma_(-P.sp, a20, k[2][0]));
+    q[0][2] = fma_(-P.sp, a02, fma_(-P.sm, a20, k[0][2]));
     q[1][1] = (A(1) - P.s_nu) * k[1][1];
     const A half3 = (A(1) - A(0.5) * P.s_3) * cs2;
-    q[2][1] = (A(1) - P.s_3) * k[2][1] + half3 * m.Fy;
-    q[1][2] = (A(1) - P.s_3) * k[1][2] + half3 * m.Fx;
-    q[2][2] = (A(1) - P.s_4) * k[2][2] + P.s_4 * rho * cs2 * cs2;
+    q[2][1] = fma_(A(1) - P.s_3, k[2][1], half3 * m.Fy);
+    q[1][2] = fma_(A(1) - P.s_3, k[1][2], half3 * m.Fx);
+    q[2][2] = fma_(A(1) - P.s_4, k[2][2], P.s_4 * rho * (cs2 * cs2));
     back_d2q9(q, ux, uy, f);
 
     // D2Q5: central moments, relaxation (Eqs. 19, 20), back transform (Eq. 21)
     const A d1 = g[1] - g[3], s1 = g[1] + g[3];
     const A d2 = g[2] - g[4], s2 = g[2] + g[4];
-    const A t10 = d1 - ux * T;
-    const A t01 = d2 - uy * T;
-    const A t20 = s1 - A(2) * ux * d1 + ux * ux * T;
-    const A t02 = s2 - A(2) * uy * d2 + uy * uy * T;
+    const A t10 = fma_(-ux, T, d1);
+    const A t01 = fma_(-uy, T, d2);
+    const A t20 = fma_(ux * ux, T, fma_(A(-2) * ux, d1, s1));
+    const A t02 = fma_(uy * uy, T, fma_(A(-2) * uy, d2, s2));
     const A om1 = A(1) - P.lambda1;
     const A om2 = A(1) - P.lambda2;
     const A eqT = P.lambda2 * T * P.cs2T;
-    back_d2q5(T, om1 * t10, om1 * t01, om2 * t20 + eqT, om2 * t02 + eqT, ux, uy, g);
+    back_d2q5(T, om1 * t10, om1 * t01, fma_(om2, t20, eqT), fma_(om2, t02, eqT), ux, uy, g);
 }
 
 // Deviation of the D2Q9 equilibrium from the rest state, f^eq_i(rho, u) - w_i rho_b, written as
@@ -302,7 +311,7 @@ __device__ __forceinline__ void eq_dev_d2q9(A rho, A drho, A ux, A uy, A f[9])
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const A wx = wv[ax[i]], wy = wv[ay[i]], ex = dx[ax[i]], ey = dy[ay[i]];
-        f[i] = drho * (wx * wy) + rho * (wx * ey + ex * wy + ex * ey);
+        f[i] = fma_(drho, wx * wy, rho * fma_(ex, ey, fma_(wx, ey, ex * wy)));
     }
 }
 
@@ -311,11 +320,12 @@ template <typename A>
 __device__ __forceinline__ void eq_dev_d2q5(A T, A dT, A ux, A uy, A c2, A g[5])
 {
     const A hc = A(0.5) * c2;
-    g[0] = dT * (A(1) - A(2) * c2) - T * (ux * ux + uy * uy);
-    g[1] = dT * hc + A(0.5) * T * (ux * ux + ux);
-    g[3] = dT * hc + A(0.5) * T * (ux * ux - ux);
-    g[2] = dT * hc + A(0.5) * T * (uy * uy + uy);
-    g[4] = dT * hc + A(0.5) * T * (uy * uy - uy);
+    const A hT = A(0.5) * T;
+    g[0] = fma_(dT, A(1) - A(2) * c2, -T * fma_(ux, ux, uy * uy));
+    g[1] = fma_(dT, hc, hT * fma_(ux, ux, ux));
+    g[3] = fma_(dT, hc, hT * fma_(ux, ux, -ux));
+    g[2] = fma_(dT, hc, hT * fma_(uy, uy, uy));
+    g[4] = fma_(dT, hc, hT * fma_(uy, uy, -uy));
 }
 
 // Collision of one node in place, deviation form (h = f - w rho_b, t = g - w^T T_b). The same map
@@ -334,25 +344,25 @@ __device__ __forceinline__ void collide_dev(const LatParams<A>& P, A f[9], A g[5
     A k[3][3];
     central_d2q9(f, ux, uy, k);
     // non-equilibrium central moments d = k(h) + rho_b k(w) - Gamma~eq
-    const A d10 = k[1][0] - rb * ux;
-    const A d01 = k[0][1] - rb * uy;
-    const A d20 = k[2][0] + rb * x2 - dr * cs2;
-    const A d02 = k[0][2] + rb * y2 - dr * cs2;
-    const A d11 = k[1][1] + rb * ux * uy;
-    const A d21 = k[2][1] - rb * (cs2 + x2) * uy;
-    const A d12 = k[1][2] - rb * ux * (cs2 + y2);
-    const A d22 = k[2][2] - dr * (cs2 * cs2) + rb * (cs2 * (x2 + y2) + x2 * y2);
+    const A d10 = fma_(-rb, ux, k[1][0]);
+    const A d01 = fma_(-rb, uy, k[0][1]);
+    const A d20 = fma_(-dr, cs2, fma_(rb, x2, k[2][0]));
+    const A d02 = fma_(-dr, cs2, fma_(rb, y2, k[0][2]));
+    const A d11 = fma_(rb * ux, uy, k[1][1]);
+    const A d21 = fma_(-rb * (cs2 + x2), uy, k[2][1]);
+    const A d12 = fma_(-rb * ux, cs2 + y2, k[1][2]);
+    const A d22 = fma_(rb, fma_(cs2, x2 + y2, x2 * y2), fma_(-dr, cs2 * cs2, k[2][2]));
     // relaxed non-equilibrium plus forcing, Eqs. (8), (11)
     A q[3][3];
     q[0][0] = A(0);
     q[1][0] = d10 + m.Fx;
     q[0][1] = d01 + m.Fy;
-    q[2][0] = d20 - P.sp * d20 - P.sm * d02;
-    q[0][2] = d02 - P.sm * d20 - P.sp * d02;
+    q[2][0] = fma_(-P.sm, d02, fma_(-P.sp, d20, d20));
+    q[0][2] = fma_(-P.sp, d02, fma_(-P.sm, d20, d02));
     q[1][1] = (A(1) - P.s_nu) * d11;
     const A half3 = (A(1) - A(0.5) * P.s_3) * cs2;
-    q[2][1] = (A(1) - P.s_3) * d21 + half3 * m.Fy;
-    q[1][2] = (A(1) - P.s_3) * d12 + half3 * m.Fx;
+    q[2][1] = fma_(A(1) - P.s_3, d21, half3 * m.Fy);
+    q[1][2] = fma_(A(1) - P.s_3, d12, half3 * m.Fx);
     q[2][2] = (A(1) - P.s_4) * d22;
     A e[9];
     eq_dev_d2q9(rho, dr, ux, uy, e);
@@ -364,10 +374,10 @@ __device__ __forceinline__ void collide_dev(const LatParams<A>& P, A f[9], A g[5
     const A c2 = P.cs2T;
     const A d1 = g[1] - g[3], s1 = g[1] + g[3];
     const A d2 = g[2] - g[4], s2 = g[2] + g[4];
-    const A t10 = d1 - ux * T;
-    const A t01 = d2 - uy * T;
-    const A t20 = s1 - A(2) * ux * d1 + x2 * dT + P.T_b * x2 - dT * c2;
-    const A t02 = s2 - A(2) * uy * d2 + y2 * dT + P.T_b * y2 - dT * c2;
+    const A t10 = fma_(-ux, T, d1);
+    const A t01 = fma_(-uy, T, d2);
+    const A t20 = fma_(-dT, c2, fma_(x2, T, fma_(A(-2) * ux, d1, s1)));
+    const A t02 = fma_(-dT, c2, fma_(y2, T, fma_(A(-2) * uy, d2, s2)));
     const A om1 = A(1) - P.lambda1;
     const A om2 = A(1) - P.lambda2;
     A eT[5], gq[5];

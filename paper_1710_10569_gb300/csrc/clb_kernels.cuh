@@ -8,43 +8,121 @@
 
 namespace clb {
 
-// One time step: pull the 14 populations of node (x, y) (Eqs. 12, 22, with the wall rules),
-// collide them (Eqs. 3-11, 13, 16-21, 23) and store the post-collision values at (x, y).
-// A thread updates NPT nodes of one row, blockDim.x apart (each load instruction stays
-// coalesced); all NPT * 14 loads are issued before the first collision so that more bytes are in
-// flight per thread.
-template <int ST, int NPT>
+// V consecutive elements loaded or stored as one aligned vector access.
+template <typename E, int V>
+struct alignas(sizeof(E) * V) Pack {
+    E e[V];
+};
+
+template <typename E>
+__device__ __forceinline__ E lane_up(E v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <typename E>
+__device__ __forceinline__ E lane_down(E v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// One time step for V consecutive nodes x0 .. x0+V-1 of row y, called by all 32 lanes of a warp
+// on the same row with x0 = (first x of the warp) + lane * V: pull the 14 populations (Eqs. 12,
+// 22, with the wall rules), collide (Eqs. 3-11, 13, 16-21, 23), store at the nodes.
+// Warps whose nodes and pulled neighbours all lie inside the lattice or across periodic sides take
+// the vector path: per population plane one aligned V-wide load of the row the pull comes from;
+// the population pulled from x-1 (x+1) of the first (last) node of a thread is the neighbouring
+// lane's last (first) element, passed by a warp shuffle, and lane 0 (lane 31) loads the one
+// element beyond the warp. Other warps (a wall or the ragged end of a row) gather node by node.
+// Both paths feed identical values to the identical collision.
+template <int ST, int V>
+__device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* __restrict__ src,
+                                                typename Storage<ST>::T* __restrict__ dst,
+                                                const LatParams<typename Storage<ST>::A>& P, int x0,
+                                                int y, int lane)
+{
+    using A = typename Storage<ST>::A;
+    using E = typename Storage<ST>::T;
+    using PK = Pack<E, V>;
+    const int wx0 = x0 - lane * V, wx1 = wx0 + 32 * V - 1;
+    const bool fast = (P.per_y || (y >= 1 && y <= P.ny - 2)) && wx1 < P.nx &&
+                      (P.per_x || (wx0 >= 1 && wx1 <= P.nx - 2));
+    if (fast) {
+        const int ym = y > 0 ? y - 1 : P.ny - 1;
+        const int yp = y < P.ny - 1 ? y + 1 : 0;
+        const int rc = y * P.pitch, rm = ym * P.pitch, rp = yp * P.pitch;
+        const int xl = wx0 > 0 ? wx0 - 1 : P.nx - 1;  // column left of the warp (lane 0)
+        const int xr = wx1 < P.nx - 1 ? wx1 + 1 : 0;  // column right of the warp (lane 31)
+        const long long pl = P.plane;
+        // plane, row offset, x shift (0: own column, +1: pulled from x-1, -1: pulled from x+1)
+        const int PLANE[NPOP] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13};
+        const int SHIFT[NPOP] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 1, 0, -1, 0};
+        const int ROWSEL[NPOP] = {0, 0, 1, 0, 2, 1, 1, 2, 2, 0, 0, 1, 0, 2};  // 0: y, 1: y-1, 2: y+1
+        PK pk[NPOP];
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i) {
+            const int r = ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp;
+            pk[i] = *reinterpret_cast<const PK*>(src + PLANE[i] * pl + r + x0);
+        }
+        E edge[NPOP];
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i) {
+            const int r = ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp;
+            edge[i] = E(0);
+            if (SHIFT[i] == 1 && lane == 0) edge[i] = src[PLANE[i] * pl + r + xl];
+            if (SHIFT[i] == -1 && lane == 31) edge[i] = src[PLANE[i] * pl + r + xr];
+        }
+        E raw[V][NPOP];
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i) {
+            if (SHIFT[i] == 0) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) raw[k][i] = pk[i].e[k];
+            } else if (SHIFT[i] == 1) {
+                const E up = lane_up(pk[i].e[V - 1]);
+                raw[0][i] = lane == 0 ? edge[i] : up;
+#pragma unroll
+                for (int k = 1; k < V; ++k) raw[k][i] = pk[i].e[k - 1];
+            } else {
+                const E dn = lane_down(pk[i].e[0]);
+                raw[V - 1][i] = lane == 31 ? edge[i] : dn;
+#pragma unroll
+                for (int k = 0; k < V - 1; ++k) raw[k][i] = pk[i].e[k + 1];
+            }
+        }
+        PK out[NPOP];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            A f[9], g[5];
+            finish_pull(P, raw[k], 0, f, g);
+            collide_any<Storage<ST>::DEV>(P, f, g);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) out[i].e[k] = from_a(f[i], (E*)nullptr);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) out[9 + i].e[k] = from_a(g[i], (E*)nullptr);
+        }
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int x = x0 + k;
+            if (x < P.nx) {
+                A f[9], g[5];
+                gather(src, P, x, y, f, g);
+                collide_any<Storage<ST>::DEV>(P, f, g);
+                store_node(dst, P, x, y, f, g);
+            }
+        }
+    }
+}
+
+// One time step over the lattice: thread (tx, ty) of block (bx, by) updates nodes
+// x0 = (bx * blockDim.x + tx) * V .. x0 + V - 1 of row by * blockDim.y + ty. blockDim.x is a
+// multiple of 32, so each warp lies in one row.
+template <int ST, int V>
 __global__ void __launch_bounds__(256) k_step(const typename Storage<ST>::T* __restrict__ src,
                                               typename Storage<ST>::T* __restrict__ dst,
                                               const LatParams<typename Storage<ST>::A> P)
 {
-    using A = typename Storage<ST>::A;
-    using E = typename Storage<ST>::T;
-    const int x0 = blockIdx.x * (blockDim.x * NPT) + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (y >= P.ny) return;
-    E raw[NPT][NPOP];
-    int mask[NPT];
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int x = x0 + k * blockDim.x;
-        mask[k] = 0;
-        if (x < P.nx) {
-            const Slots s = pull_slots(P, x, y);
-            load_slots(src, s, raw[k]);
-            mask[k] = s.wall_mask;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int x = x0 + k * blockDim.x;
-        if (x < P.nx) {
-            A f[9], g[5];
-            finish_pull(P, raw[k], mask[k], f, g);
-            collide_any<Storage<ST>::DEV>(P, f, g);
-            store_node(dst, P, x, y, f, g);
-        }
-    }
+    if (y >= P.ny || x0 - lane * V >= P.nx) return;  // whole warps only
+    step_warp_nodes<ST, V>(src, dst, P, x0, y, lane);
 }
 
 // Initialisation to f^eq(rho, u), g^eq(T, u) (in stored form). The buffer holds post-collision

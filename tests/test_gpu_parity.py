@@ -1,9 +1,13 @@
 """CUDA path (through the C ABI) against the FP64 CPU oracle on the same seeded inputs.
 
-Tolerances (normwise per field: max|gpu - oracle| <= tol * max|oracle|):
+Tolerances (normwise per field, see compare()):
   FP64 storage + FP64 arithmetic: 1e-12 (the two sides differ only in rounding order).
-  FP32 storage + FP32 arithmetic and FP16-deviation storage: the bounds in TOL below; their
-  derivation from the unit roundoffs is given in the design notes.
+  FP32 deviation storage + FP32 arithmetic: 2 n u32 (floor 1e-6) after n steps, u32 = 2^-24: each
+    step adds at most a few roundings of size u32 relative to the velocity and temperature scales,
+    and they can add up coherently (linear growth).
+  FP16 deviation storage + FP32 arithmetic: 2 sqrt(n) u16, u16 = 2^-11: the half-precision store
+    of every population each step dominates; the roundings are independent, so they add like a
+    random walk.
 """
 import json
 import os
@@ -19,8 +23,15 @@ pytestmark = pytest.mark.gpu
 F64, F32, F16 = W.STORAGE_F64, W.STORAGE_F32, W.STORAGE_F16DEV
 P, D, A = W.WALL_PERIODIC, W.WALL_DIRICHLET, W.WALL_ADIABATIC
 NAMES = ("rho", "ux", "uy", "T")
-# per storage: tolerance on (rho, u, T) normwise errors after the runs below
-TOL = {F64: 1e-12, F32: 1e-5, F16: 3e-2}
+U32, U16 = 2.0 ** -24, 2.0 ** -11
+
+
+def tol(storage, steps):
+    if storage == F64:
+        return 1e-12
+    if storage == F32:
+        return max(1e-6, 2 * steps * U32)
+    return 2 * max(steps, 1) ** 0.5 * U16
 
 
 @pytest.fixture(scope="module")
@@ -93,7 +104,7 @@ def test_taylor_green_64_fp64_1000_steps(clb):
 def test_taylor_green_64_reduced_precision(clb, storage):
     prob = W.taylor_green(64, storage=storage)
     _, _, got, exp = run_both(clb, prob, 1000)
-    compare(f"tg64_{W.STORAGE_NAMES[storage]}_1000", got, exp, TOL[storage], prob.params)
+    compare(f"tg64_{W.STORAGE_NAMES[storage]}_1000", got, exp, tol(storage, 1000), prob.params)
 
 
 # ------------------------------------------------------------------ walls, ragged sizes, all storages
@@ -114,7 +125,7 @@ def test_random_problems_fp64(clb, shape, seed):
 def test_random_problems_reduced_precision(clb, storage, seed):
     prob = W.random_problem(67, 45, seed=seed, storage=storage)
     _, _, got, exp = run_both(clb, prob, 60)
-    compare(f"rand67x45_s{seed}_{W.STORAGE_NAMES[storage]}", got, exp, TOL[storage], prob.params)
+    compare(f"rand67x45_s{seed}_{W.STORAGE_NAMES[storage]}", got, exp, tol(storage, 60), prob.params)
 
 
 def test_initial_fields_match_oracle(clb):
@@ -138,7 +149,7 @@ def test_cavity_256_short(clb, storage):
     prob = W.cavity(256, storage=storage)
     # the fluid starts at rest with 1e-4 noise: give the buoyant flow time to develop
     _, o, got, exp = run_both(clb, prob, 400)
-    compare(f"cavity256_{W.STORAGE_NAMES[storage]}_400", got, exp, TOL[storage], prob.params)
+    compare(f"cavity256_{W.STORAGE_NAMES[storage]}_400", got, exp, tol(storage, 400), prob.params)
 
 
 @pytest.mark.parametrize("storage", [F64, F32, F16])
@@ -147,7 +158,7 @@ def test_rayleigh_benard_2048x1024_full_size(clb, storage):
     the fused kernel), a few steps, every node compared."""
     prob = W.rayleigh_benard(2048, 1024, storage=storage)
     _, _, got, exp = run_both(clb, prob, 6)
-    compare(f"rb2048_{W.STORAGE_NAMES[storage]}_6", got, exp, TOL[storage], prob.params)
+    compare(f"rb2048_{W.STORAGE_NAMES[storage]}_6", got, exp, tol(storage, 6), prob.params)
 
 
 def test_graph_chunks_equal_single_launches(clb):
@@ -163,10 +174,13 @@ def test_graph_chunks_equal_single_launches(clb):
         assert np.array_equal(x, y)
 
 
-def test_launch_shapes_are_bitwise_equal(clb):
-    prob = W.random_problem(150, 37, seed=3, storage=F32)
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+@pytest.mark.parametrize("walls", [(P, P, P, P), (D, D, A, A), (P, P, D, D)], ids=["periodic", "cavity", "rb"])
+def test_launch_shapes_are_bitwise_equal(clb, storage, walls):
+    """Vector interior path, scalar wall/ragged path and every launch shape give the same bits."""
+    prob = W.random_problem(333, 37, seed=3, storage=storage, walls=walls)
     ref = None
-    for shape in ((128, 1, 1), (64, 4, 2), (128, 2, 4), (32, 8, 1), (256, 1, 2)):
+    for shape in ((128, 1, 1), (64, 4, 2), (128, 2, 4), (32, 8, 1), (256, 1, 2), (32, 1, 4)):
         lat = clb.Lattice.from_problem(prob)
         lat.set_launch(*shape)
         lat.step(40)

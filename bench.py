@@ -250,6 +250,8 @@ def run_ours(args):
                 continue
             p2 = workload(st)
             l2 = clb.Lattice.from_problem(p2)
+            if args.autotune:
+                l2.autotune()
             k = max(200, args.steps // (8 if st == W.STORAGE_F64 else 2))
             s2 = time_steps(l2, k, max(3, args.warmup // 4), 1)
             variants[W.STORAGE_NAMES[st]] = {
@@ -330,7 +332,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16dev"])
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()

@@ -48,6 +48,62 @@ __device__ __forceinline__ double fma_(double a, double b, double c) { return __
 __device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
 __device__ __forceinline__ double rcp_(double a) { return __drcp_rn(a); }
 
+// Two FP32 lanes (two lattice nodes) in one 64-bit register pair, operated on by the packed
+// FP32 instructions of sm_100-class GPUs (add/sub/mul/fma .rn.f32x2). Each lane is rounded exactly
+// as the scalar instruction would round it, so a node computed in a pair carries the same bits as
+// the same node computed alone.
+struct F2 {
+    unsigned long long u;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float lo, float hi)
+    {
+        asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(lo), "f"(hi));
+    }
+    template <typename T>
+    __device__ __forceinline__ explicit F2(T x) : F2(float(x), float(x)) {}
+    __device__ __forceinline__ void split(float& lo, float& hi) const
+    {
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(u));
+    }
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b)
+{
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b)
+{
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b)
+{
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a)
+{
+    F2 r;
+    r.u = a.u ^ 0x8000000080000000ull;  // exact sign flip of both lanes
+    return r;
+}
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2 fma_(F2 a, F2 b, F2 c)
+{
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.u) : "l"(a.u), "l"(b.u), "l"(c.u));
+    return r;
+}
+__device__ __forceinline__ F2 rcp_(F2 a)
+{
+    float lo, hi;
+    a.split(lo, hi);
+    return F2(__frcp_rn(lo), __frcp_rn(hi));
+}
+
 // Per-lattice constants in the arithmetic precision A.
 template <typename A>
 struct LatParams {
@@ -174,16 +230,16 @@ struct Macro {
     A rho, ux, uy, T, Fx, Fy, drho, dT;  // drho = rho - rho_b, dT = T - T_b
 };
 
-template <typename A>
-__device__ __forceinline__ Macro<A> macroscopic(const LatParams<A>& P, const A f[9], const A g[5])
+template <typename A, typename S>
+__device__ __forceinline__ Macro<A> macroscopic(const LatParams<S>& P, const A f[9], const A g[5])
 {
     Macro<A> m;
     m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     m.dT = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
-    m.rho = P.rho_b + m.drho;
-    m.T = P.T_b + m.dT;
-    m.Fx = P.Fvx;
-    m.Fy = fma_(P.gb, m.T - P.T0, P.Fvy);
+    m.rho = A(P.rho_b) + m.drho;
+    m.T = A(P.T_b) + m.dT;
+    m.Fx = A(P.Fvx);
+    m.Fy = fma_(A(P.gb), m.T - A(P.T0), A(P.Fvy));
     const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const A jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
     const A inv = rcp_(m.rho);
@@ -301,7 +357,7 @@ __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5])
 template <typename A>
 __device__ __forceinline__ void eq_dev_d2q9(A rho, A drho, A ux, A uy, A f[9])
 {
-    const A w0 = A(2) / A(3), w1 = A(1) / A(6);
+    const A w0 = A(2.0 / 3.0), w1 = A(1.0 / 6.0);
     const A x2 = ux * ux, y2 = uy * uy;
     const A dx[3] = {-x2, A(0.5) * (x2 + ux), A(0.5) * (x2 - ux)};  // e = 0, +1, -1
     const A dy[3] = {-y2, A(0.5) * (y2 + uy), A(0.5) * (y2 - uy)};
@@ -333,13 +389,13 @@ __device__ __forceinline__ void eq_dev_d2q5(A T, A dT, A ux, A uy, A c2, A g[5])
 // f* = f^eq + M^-1 N^-1 [(I - S)(Gamma~ - Gamma~eq) + (I - S/2) C]; the non-equilibrium central
 // moments are formed from the central moments of h plus those of w rho_b about u
 // (1-D: 1, -u, 1/3 + u^2) minus Eq. (9), with the O(1) parts cancelled analytically.
-template <typename A>
-__device__ __forceinline__ void collide_dev(const LatParams<A>& P, A f[9], A g[5])
+template <typename A, typename S>
+__device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5])
 {
     const Macro<A> m = macroscopic(P, f, g);
     const A ux = m.ux, uy = m.uy, rho = m.rho, T = m.T, dr = m.drho, dT = m.dT;
-    const A rb = P.rho_b;
-    const A cs2 = A(1) / A(3);
+    const A rb = A(P.rho_b);
+    const A cs2 = A(1.0 / 3.0), cs4 = A(1.0 / 9.0);
     const A x2 = ux * ux, y2 = uy * uy;
     A k[3][3];
     central_d2q9(f, ux, uy, k);
@@ -351,19 +407,20 @@ __device__ __forceinline__ void collide_dev(const LatParams<A>& P, A f[9], A g[5
     const A d11 = fma_(rb * ux, uy, k[1][1]);
     const A d21 = fma_(-rb * (cs2 + x2), uy, k[2][1]);
     const A d12 = fma_(-rb * ux, cs2 + y2, k[1][2]);
-    const A d22 = fma_(rb, fma_(cs2, x2 + y2, x2 * y2), fma_(-dr, cs2 * cs2, k[2][2]));
+    const A d22 = fma_(rb, fma_(cs2, x2 + y2, x2 * y2), fma_(-dr, cs4, k[2][2]));
     // relaxed non-equilibrium plus forcing, Eqs. (8), (11)
+    const A sp = A(P.sp), sm = A(P.sm);
+    const A half3 = A((1.0f - 0.5f * P.s_3) * (1.0f / 3.0f));
     A q[3][3];
     q[0][0] = A(0);
     q[1][0] = d10 + m.Fx;
     q[0][1] = d01 + m.Fy;
-    q[2][0] = fma_(-P.sm, d02, fma_(-P.sp, d20, d20));
-    q[0][2] = fma_(-P.sp, d02, fma_(-P.sm, d20, d02));
-    q[1][1] = (A(1) - P.s_nu) * d11;
-    const A half3 = (A(1) - A(0.5) * P.s_3) * cs2;
-    q[2][1] = fma_(A(1) - P.s_3, d21, half3 * m.Fy);
-    q[1][2] = fma_(A(1) - P.s_3, d12, half3 * m.Fx);
-    q[2][2] = (A(1) - P.s_4) * d22;
+    q[2][0] = fma_(-sm, d02, fma_(-sp, d20, d20));
+    q[0][2] = fma_(-sp, d02, fma_(-sm, d20, d02));
+    q[1][1] = A(1.0f - P.s_nu) * d11;
+    q[2][1] = fma_(A(1.0f - P.s_3), d21, half3 * m.Fy);
+    q[1][2] = fma_(A(1.0f - P.s_3), d12, half3 * m.Fx);
+    q[2][2] = A(1.0f - P.s_4) * d22;
     A e[9];
     eq_dev_d2q9(rho, dr, ux, uy, e);
     back_d2q9(q, ux, uy, f);
@@ -371,15 +428,15 @@ __device__ __forceinline__ void collide_dev(const LatParams<A>& P, A f[9], A g[5
     for (int i = 0; i < 9; ++i) f[i] += e[i];
 
     // D2Q5 on deviations
-    const A c2 = P.cs2T;
+    const A c2 = A(P.cs2T);
     const A d1 = g[1] - g[3], s1 = g[1] + g[3];
     const A d2 = g[2] - g[4], s2 = g[2] + g[4];
     const A t10 = fma_(-ux, T, d1);
     const A t01 = fma_(-uy, T, d2);
     const A t20 = fma_(-dT, c2, fma_(x2, T, fma_(A(-2) * ux, d1, s1)));
     const A t02 = fma_(-dT, c2, fma_(y2, T, fma_(A(-2) * uy, d2, s2)));
-    const A om1 = A(1) - P.lambda1;
-    const A om2 = A(1) - P.lambda2;
+    const A om1 = A(1.0f - P.lambda1);
+    const A om2 = A(1.0f - P.lambda2);
     A eT[5], gq[5];
     eq_dev_d2q5(T, dT, ux, uy, c2, eT);
     back_d2q5(A(0), om1 * t10, om1 * t01, om2 * t20, om2 * t02, ux, uy, gq);
@@ -390,7 +447,7 @@ __device__ __forceinline__ void collide_dev(const LatParams<A>& P, A f[9], A g[5
 template <bool DEV, typename A>
 __device__ __forceinline__ void collide_any(const LatParams<A>& P, A f[9], A g[5])
 {
-    if (DEV) collide_dev(P, f, g);
+    if constexpr (DEV) collide_dev(P, f, g);
     else collide(P, f, g);
 }
 

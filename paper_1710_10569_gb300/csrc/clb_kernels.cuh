@@ -84,15 +84,35 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
             }
         }
         PK out[NPOP];
+        if constexpr (Storage<ST>::DEV && V % 2 == 0) {
+            // FP32 arithmetic: two nodes per packed f32x2 instruction
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            A f[9], g[5];
-            finish_pull(P, raw[k], 0, f, g);
-            collide_any<Storage<ST>::DEV>(P, f, g);
+            for (int k = 0; k < V; k += 2) {
+                F2 f[9], g[5];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) out[i].e[k] = from_a(f[i], (E*)nullptr);
+                for (int i = 0; i < 9; ++i) f[i] = F2(to_a(raw[k][i]), to_a(raw[k + 1][i]));
 #pragma unroll
-            for (int i = 0; i < 5; ++i) out[9 + i].e[k] = from_a(g[i], (E*)nullptr);
+                for (int i = 0; i < 5; ++i) g[i] = F2(to_a(raw[k][9 + i]), to_a(raw[k + 1][9 + i]));
+                collide_dev(P, f, g);
+#pragma unroll
+                for (int i = 0; i < NPOP; ++i) {
+                    float lo, hi;
+                    (i < 9 ? f[i] : g[i - 9]).split(lo, hi);
+                    out[i].e[k] = from_a(lo, (E*)nullptr);
+                    out[i].e[k + 1] = from_a(hi, (E*)nullptr);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                A f[9], g[5];
+                finish_pull(P, raw[k], 0, f, g);
+                collide_any<Storage<ST>::DEV>(P, f, g);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) out[i].e[k] = from_a(f[i], (E*)nullptr);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) out[9 + i].e[k] = from_a(g[i], (E*)nullptr);
+            }
         }
 #pragma unroll
         for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];

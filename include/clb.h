@@ -129,6 +129,24 @@ clb_status clb_populations(clb_handle *h, double *f, double *g);
  * a fixed order. Synchronous. CLB_ENAN when the fields are not finite. */
 clb_status clb_nusselt(clb_handle *h, int axis, double *nu_out);
 
+/* The Nusselt number of clb_nusselt computed without allocating any device memory, for callers
+ * that cannot call cudaMalloc when they need it: for example a progress monitor in a server whose
+ * device memory is already committed to resident lattices, or a latency-sensitive loop that must
+ * not call cudaMalloc/cudaFree because they can synchronise the whole device. (The paper has no
+ * counterpart; this is a service of the library.)
+ * populations: device pointer to a population buffer in this library's layout for (nx, ny,
+ * p->storage), e.g. the current buffer that clb_buffers returns; p: that lattice's parameters;
+ * stream: the CUDA stream to run on; nu_out: host double, written on success. Synchronous.
+ * Scratch is a fixed array of CLB_NOALLOC_MAX_ROWS rows of FP64 partial sums that the library keeps
+ * in device memory on every device it is used on until the process exits; ny above that limit
+ * returns CLB_EINVAL. The first call on a device looks up that array's address (with the device
+ * current); make that first call before any stream capture. All calls share the one array, so
+ * calls whose kernels overlap on the GPU race: serialise them. Returns CLB_ENAN when the fields are
+ * not finite. The result equals clb_nusselt on the same populations. */
+#define CLB_NOALLOC_MAX_ROWS 8192
+clb_status clb_nusselt_noalloc(const void *populations, int nx, int ny, const clb_params *p, int axis,
+                               void *stream, double *nu_out);
+
 /* Steady-state residual against the snapshot taken by the previous call (or by init), then
  * retakes the snapshot: E_R = max over X in {u, T} of sqrt(sum|X - X_snap|^2 /
  * max(sum|X|^2, N (1e-3 X_ref)^2)), X_ref = u_ref, dT_ref. FP64 on the GPU. Synchronous. */

@@ -63,6 +63,7 @@ _SIGS = {
     "clb_populations": [_VP, _D, _D],
     "clb_nusselt": [_VP, _I, _D],
     "clb_residual": [_VP, _D],
+    "clb_nusselt_noalloc": [_VP, _I, _I, _P(clb_params), _I, _VP, _D],
     "clb_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D],
     "clb_steps": [_VP, _P(_L)],
     "clb_sync": [_VP],

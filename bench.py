@@ -215,6 +215,67 @@ def e2e_run(storage: int, steps: int):
             "steps": steps, "seconds": dt}
 
 
+def batched_run(storage: int, count: int = 256, steps: int = 1000, seq_subset: int = 32):
+    """Many side-heated cavities of uneven sizes (edge log-uniform 64-512, Ra log-uniform 1e3-1e6,
+    Pr uniform 0.71-7) stepped in one launch per time step, against the same instances stepped one
+    after another through single-lattice handles (a seeded subset of `seq_subset` instances is timed
+    both ways)."""
+    import torch
+    from paper_1710_10569_gb300 import clb
+    probs = W.batch_cavities(count, seed=0, storage=storage)
+    nodes = sum(p.nodes for p in probs)
+
+    def time_batch(ps, k):
+        b = clb.Batch(ps)
+        tile = b.autotune()
+        b.step(64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(k)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        b.close()
+        return dt, tile
+
+    dt_all, tile = time_batch(probs, steps)
+    sub = probs[:seq_subset]
+    sub_nodes = sum(p.nodes for p in sub)
+    dt_sub, _ = time_batch(sub, steps)
+    lats = [clb.Lattice.from_problem(p) for p in sub]
+    for lat in lats:
+        lat.step(64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for lat in lats:
+        lat.step(steps)
+        lat.sync()
+    dt_seq = time.perf_counter() - t0
+    for lat in lats:
+        lat.close()
+    return {"instances": count, "nodes": nodes, "steps": steps, "storage": W.STORAGE_NAMES[storage],
+            "tile": list(tile), "mlups": nodes * steps / dt_all / 1e6,
+            "instance_steps_per_s": count * steps / dt_all,
+            "subset": {"instances": seq_subset, "batched_mlups": sub_nodes * steps / dt_sub / 1e6,
+                       "sequential_mlups": sub_nodes * steps / dt_seq / 1e6,
+                       "speedup": dt_seq / dt_sub}}
+
+
+def served_run(storage: int, count: int = 48, step_cap: int = 20000, tol: float = 1e-6):
+    """A seeded Poisson request trace (mean 50 requests/s; periodic Taylor-Green, side-heated
+    cavity and Rayleigh-Benard; edges log-uniform 64-512, aspect 1 or 2) served with continuous
+    batching in `storage`, against the plain FP64 one-at-a-time path on the same trace."""
+    from paper_1710_10569_gb300 import serve
+    trace = W.request_trace(count=count, seed=0, rate_hz=50.0, lo=64, hi=512, storage=storage)
+    s_sum, s_rec = serve.serve_trace(trace, storage, hbm_budget_bytes=32 << 30, max_slots=256,
+                                     chunk=100, step_cap=step_cap, tol=tol)
+    p_sum, p_rec = serve.plain_trace(trace, step_cap=step_cap, tol=tol)
+    return {"requests": count, "step_cap": step_cap, "tol": tol, "storage": W.STORAGE_NAMES[storage],
+            "served": s_sum, "plain_f64": p_sum,
+            "speedup_solves_per_s": s_sum["solves_per_s"] / p_sum["solves_per_s"],
+            "p99_ratio_plain_over_served": p_sum["p99_s"] / s_sum["p99_s"],
+            "nusselt_max_rel_diff_vs_plain_f64": serve.nusselt_agreement(s_rec, p_rec)}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -261,6 +322,8 @@ def run_ours(args):
                 "steps": k, "dram_bytes_per_launch": traffic_per_launch(st)}
             l2.close()
     e2e = e2e_run(storage, args.steps) if rank == 0 else None
+    batched = batched_run(storage) if (rank == 0 and not args.no_serve) else None
+    served = served_run(storage) if (rank == 0 and not args.no_serve) else None
     if rank == 0:
         line = {
             "metric": "coupled D2Q9+D2Q5 MLUPS & % HBM roofline", "value": mlups, "unit": "MLUPS",
@@ -285,6 +348,8 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "clocks": clocks.summary(),
             "variants": variants,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     lat.close()
@@ -332,9 +397,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16dev"])
-    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--autotune", action="store_true", help="time the autotuned launch shape instead of the default")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the batched and served runs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -169,7 +169,7 @@ clb_status clb_load(clb_handle *h, const void *buf, size_t bytes);
 
 /* Launch shape of the step kernel: threads per block along x (32..256, multiple of 32), rows per
  * block (1..8, block_x * block_y <= 256) and nodes per thread along x (1, 2 or 4). 0 keeps the
- * current value. Defaults: 128 x 1 with 1 (FP64), 2 (FP32) or 4 (FP16) nodes per thread.
+ * current value. Defaults: 128 x 1 with 2 (FP32) or 4 (FP64, FP16) nodes per thread.
  * clb_autotune times candidate shapes on the live lattice (the populations are restored
  * afterwards; it allocates one buffer-sized scratch with cudaMallocAsync) and keeps the fastest;
  * results are cached per (storage, nx, ny) for later clb_create calls. The shape never changes

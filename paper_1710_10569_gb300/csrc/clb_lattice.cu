@@ -325,7 +325,7 @@ extern "C" clb_status clb_create(int nx, int ny, const clb_params* p, void* stre
     h->diag = (double*)(h->mem + L.diag);
     h->Pd = make_lat_params<double>(nx, ny, *p);
     h->Pf = make_lat_params<float>(nx, ny, *p);
-    h->npt = p->storage == CLB_F64 ? 1 : p->storage == CLB_F32 ? 2 : 4;
+    h->npt = p->storage == CLB_F32 ? 2 : 4;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(std::make_tuple(p->storage, nx, ny));

@@ -57,6 +57,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# GB300 FP64 issue rate: 152 SMs x 2 DP lanes per clock x 2.07 GHz (the 1.26 TFLOP/s FP64 figure
+# with an FMA counted as two flops)
+FP64_DP_INSTR_PEAK = 152 * 2 * 2.07e9
+
+
+def profile_counts():
+    """The committed ncu counts, if taken on the current kernel source (else {})."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return {}
+    with open(TRAFFIC_FILE) as f:
+        d = json.load(f)
+    return d if d.get("kernel_source_hash") == kernel_hash() else {}
+
+
 def traffic_per_launch(storage: int):
     """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken on the
     current kernel source (else None)."""
@@ -273,7 +287,7 @@ def served_run(storage: int, count: int = 48, step_cap: int = 20000, tol: float 
             "served": s_sum, "plain_f64": p_sum,
             "speedup_solves_per_s": s_sum["solves_per_s"] / p_sum["solves_per_s"],
             "p99_ratio_plain_over_served": p_sum["p99_s"] / s_sum["p99_s"],
-            "nusselt_max_rel_diff_vs_plain_f64": serve.nusselt_agreement(s_rec, p_rec)}
+            "nusselt_vs_plain_f64": serve.nusselt_agreement(s_rec, p_rec, tol)}
 
 
 def run_ours(args):
@@ -319,7 +333,17 @@ def run_ours(args):
                 "mlups": p2.nodes * k / s2 / 1e6,
                 "achieved_gbs": BYTES_PER_NODE[st] * p2.nodes / (s2 / k) / 1e9,
                 "hbm_frac": BYTES_PER_NODE[st] * p2.nodes / (s2 / k) / 1e9 / peak,
-                "steps": k, "dram_bytes_per_launch": traffic_per_launch(st)}
+                "steps": k, "dram_bytes_per_launch": traffic_per_launch(st),
+                "launch": list(l2.launch())}
+            ops = profile_counts().get("fp64_ops_per_node")
+            if st == W.STORAGE_F64 and ops:
+                dp = sum(ops.values())
+                rate = dp * p2.nodes * k / s2
+                variants["f64"]["roofline"] = {
+                    "bound": "alu", "achieved": rate / 1e12, "peak": FP64_DP_INSTR_PEAK / 1e12,
+                    "unit": "T DP instructions/s", "frac": rate / FP64_DP_INSTR_PEAK,
+                    "dp_instructions_per_node": dp,
+                    "peak_kind": "derived: 152 SMs x 2 FP64 lanes/clock x 2.07 GHz"}
             l2.close()
     e2e = e2e_run(storage, args.steps) if rank == 0 else None
     batched = batched_run(storage) if (rank == 0 and not args.no_serve) else None

@@ -84,14 +84,24 @@ def plain_trace(trace, step_cap: int = 20000, tol: float = 1e-6, interval: int =
     return _summary(records, wall), records
 
 
-def nusselt_agreement(served, plain):
-    """Largest relative difference of the served Nusselt numbers from the plain FP64 ones, over
-    requests that ran the same number of steps in both (or converged in both)."""
+def nusselt_agreement(served, plain, tol: float):
+    """Relative differences of the served Nusselt numbers from the plain FP64 ones, per request:
+    overall and over the requests that reached the residual tolerance in both paths (steady
+    states), with the worst requests listed."""
     by = {r["name"]: r for r in plain}
-    worst = 0.0
+    rows = []
     for r in served:
         q = by.get(r["name"])
         if q is None:
             continue
-        worst = max(worst, abs(r["nu"] - q["nu"]) / max(abs(q["nu"]), 1e-300))
-    return worst
+        rel = abs(r["nu"] - q["nu"]) / max(abs(q["nu"]), 1e-300)
+        rows.append({"name": r["name"], "rel": rel, "steps": r["steps"], "steps_plain": q["steps"],
+                     "nu": r["nu"], "nu_plain": q["nu"], "converged": r["residual"] < tol and q["residual"] < tol})
+    rels = np.array([x["rel"] for x in rows])
+    conv = np.array([x["rel"] for x in rows if x["converged"]])
+    return {"max": float(rels.max()) if rels.size else None,
+            "median": float(np.median(rels)) if rels.size else None,
+            "fraction_within_1e-3": float(np.mean(rels <= 1e-3)) if rels.size else None,
+            "converged_requests": int(conv.size),
+            "max_over_converged": float(conv.max()) if conv.size else None,
+            "worst": sorted(rows, key=lambda x: -x["rel"])[:3]}

@@ -177,6 +177,13 @@ clb_status clb_load(clb_handle *h, const void *buf, size_t bytes);
 clb_status clb_set_launch(clb_handle *h, int block_x, int block_y, int nodes_per_thread);
 clb_status clb_get_launch(clb_handle *h, int *block_x, int *block_y, int *nodes_per_thread);
 clb_status clb_autotune(clb_handle *h, int *block_x, int *block_y, int *nodes_per_thread);
+/* Pipelined step kernel: stages = 0 uses the direct kernel; 2..4 stages of shared memory per warp
+ * let each warp stage the pulled values of the next stages-1 rows with asynchronous copies while it
+ * computes the current row; rows = rows each warp marches over (1..256; 0 keeps the value). Needs
+ * 2 or 4 nodes per thread (clb_set_launch); the block is 128 threads. Results are bitwise those of
+ * the direct kernel. clb_autotune also tries pipelined shapes and reports them here. */
+clb_status clb_set_pipeline(clb_handle *h, int stages, int rows);
+clb_status clb_get_pipeline(clb_handle *h, int *stages, int *rows);
 
 /* The CUDA stream the handle enqueues on (to time its work with events on that stream). */
 void *clb_stream(clb_handle *h);

@@ -72,6 +72,8 @@ _SIGS = {
     "clb_set_launch": [_VP, _I, _I, _I],
     "clb_get_launch": [_VP, _P(_I), _P(_I), _P(_I)],
     "clb_autotune": [_VP, _P(_I), _P(_I), _P(_I)],
+    "clb_set_pipeline": [_VP, _I, _I],
+    "clb_get_pipeline": [_VP, _P(_I), _P(_I)],
     "clb_stream": [_VP],
     "clb_buffers": [_VP, _P(_VP), _P(_VP), _P(_S), _P(_I)],
     "clb_last_error": [],
@@ -290,6 +292,14 @@ class Lattice:
         bx, by, npt = _I(), _I(), _I()
         _check(lib().clb_autotune(self._h, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(npt)))
         return bx.value, by.value, npt.value
+
+    def set_pipeline(self, stages: int, rows: int = 0):
+        _check(lib().clb_set_pipeline(self._h, int(stages), int(rows)))
+
+    def pipeline(self):
+        st, rows = _I(), _I()
+        _check(lib().clb_get_pipeline(self._h, ctypes.byref(st), ctypes.byref(rows)))
+        return st.value, rows.value
 
     def buffers(self):
         cur, oth, pl, pitch = _VP(), _VP(), _S(), _I()

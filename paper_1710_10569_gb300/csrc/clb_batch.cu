@@ -107,14 +107,14 @@ struct Lattice {
 size_t lattice_bytes(int nx, int ny, int storage)
 {
     const size_t N = (size_t)nx * ny;
-    return 2 * align256(buffer_bytes(nx, ny, storage)) + align256(3 * N * sizeof(double)) +
+    return 2 * buffer_slot_bytes(nx, ny, storage) + align256(3 * N * sizeof(double)) +
            align256((size_t)ny * RS_N * sizeof(double)) + align256(16 * sizeof(double));
 }
 
 void carve(Lattice& L, char* base)
 {
     const size_t N = (size_t)L.nx * L.ny;
-    const size_t bb = align256(buffer_bytes(L.nx, L.ny, L.p.storage));
+    const size_t bb = buffer_slot_bytes(L.nx, L.ny, L.p.storage);
     L.mem = base;
     L.buf[0] = base;
     L.buf[1] = base + bb;

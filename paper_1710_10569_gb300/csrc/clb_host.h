@@ -64,6 +64,14 @@ inline size_t buffer_bytes(int nx, int ny, int storage)
 
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// Device bytes reserved per population buffer: the buffer plus a 256-byte guard, so that the
+// 4-byte asynchronous copy of an edge pair of half-precision values may touch one element past the
+// last plane without leaving the allocation.
+inline size_t buffer_slot_bytes(int nx, int ny, int storage)
+{
+    return align256(buffer_bytes(nx, ny, storage)) + 256;
+}
+
 clb_status validate(int nx, int ny, const clb_params* p);
 
 // s_nu from nu = (1/s_nu - 1/2) c_s^2 with c_s^2 = 1/3 (Sec. 2.1).

@@ -145,6 +145,184 @@ __global__ void __launch_bounds__(256) k_step(const typename Storage<ST>::T* __r
     step_warp_nodes<ST, V>(src, dst, P, x0, y, lane);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Pipelined variant: each warp marches down R rows of its column segment of 32 * V nodes, staging
+// the pulled values of the next rows in shared memory with asynchronous copies (cp.async, tracked
+// per thread by commit/wait groups) while it computes the current row. Each thread copies its own
+// V-wide vector of every plane; lane 0 and lane 31 also copy the element just outside the warp
+// (for FP16 the aligned 4-byte pair that holds it). The values that reach the collision are exactly
+// those of step_warp_nodes, so the results are bitwise the same; the staging only keeps more bytes
+// in flight per SM than registers allow.
+
+__device__ __forceinline__ void cp_async_bytes(void* smem, const void* gmem, int bytes)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+    else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename E, int V>
+struct StageGeom {
+    static constexpr int EDGE = 16 / sizeof(E);      // edge slot: left value(s), then right value(s)
+    static constexpr int PS = 32 * V + EDGE;         // elements per plane
+    static constexpr int SS = NPOP * PS;             // elements per stage
+    static constexpr int RIGHT = EDGE / 2;           // offset of the right edge in the slot
+};
+
+constexpr int kPipeWarps = 4;  // warps per block of the pipelined kernel
+
+template <int ST, int V>
+__device__ __forceinline__ void stage_issue(const typename Storage<ST>::T* __restrict__ src,
+                                            const LatParams<typename Storage<ST>::A>& P, int wx0,
+                                            int y, int lane, typename Storage<ST>::T* stage)
+{
+    using E = typename Storage<ST>::T;
+    using G = StageGeom<E, V>;
+    const int wx1 = wx0 + 32 * V - 1;
+    const int ym = y > 0 ? y - 1 : P.ny - 1;
+    const int yp = y < P.ny - 1 ? y + 1 : 0;
+    const int rc = y * P.pitch, rm = ym * P.pitch, rp = yp * P.pitch;
+    const int xl = wx0 > 0 ? wx0 - 1 : P.nx - 1;
+    const int xr = wx1 < P.nx - 1 ? wx1 + 1 : 0;
+    const long long pl = P.plane;
+    const int SHIFT[NPOP] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 1, 0, -1, 0};
+    const int ROWSEL[NPOP] = {0, 0, 1, 0, 2, 1, 1, 2, 2, 0, 0, 1, 0, 2};
+    constexpr bool HALF = sizeof(E) == 2;
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) {
+        const int r = ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp;
+        const E* row = src + i * pl + r;
+        E* sp = stage + i * G::PS;
+        cp_async_bytes(sp + lane * V, row + wx0 + lane * V, V * (int)sizeof(E));
+        if (SHIFT[i] == 1 && lane == 0)
+            cp_async_bytes(sp + 32 * V, row + (HALF ? (xl & ~1) : xl), HALF ? 4 : (int)sizeof(E));
+        if (SHIFT[i] == -1 && lane == 31)
+            cp_async_bytes(sp + 32 * V + G::RIGHT, row + (HALF ? (xr & ~1) : xr), HALF ? 4 : (int)sizeof(E));
+    }
+}
+
+template <int ST, int V>
+__device__ __forceinline__ void stage_compute(typename Storage<ST>::T* __restrict__ dst,
+                                              const LatParams<typename Storage<ST>::A>& P, int wx0,
+                                              int y, int lane, const typename Storage<ST>::T* stage)
+{
+    using A = typename Storage<ST>::A;
+    using E = typename Storage<ST>::T;
+    using G = StageGeom<E, V>;
+    using PK = Pack<E, V>;
+    const int wx1 = wx0 + 32 * V - 1;
+    const int xl = wx0 > 0 ? wx0 - 1 : P.nx - 1;
+    const int xr = wx1 < P.nx - 1 ? wx1 + 1 : 0;
+    constexpr bool HALF = sizeof(E) == 2;
+    const int il = 32 * V + (HALF ? (xl & 1) : 0);
+    const int ir = 32 * V + G::RIGHT + (HALF ? (xr & 1) : 0);
+    const int SHIFT[NPOP] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 1, 0, -1, 0};
+    E raw[V][NPOP];
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) {
+        const E* sp = stage + i * G::PS;
+        const int b = lane * V;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            int idx = b + k;
+            if (SHIFT[i] == 1) idx = (k == 0 && lane == 0) ? il : b + k - 1;
+            if (SHIFT[i] == -1) idx = (k == V - 1 && lane == 31) ? ir : b + k + 1;
+            raw[k][i] = sp[idx];
+        }
+    }
+    const int rc = y * P.pitch;
+    const long long pl = P.plane;
+    const int x0 = wx0 + lane * V;
+    PK out[NPOP];
+    if constexpr (Storage<ST>::DEV && V % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < V; k += 2) {
+            F2 f[9], g[5];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = F2(to_a(raw[k][i]), to_a(raw[k + 1][i]));
+#pragma unroll
+            for (int i = 0; i < 5; ++i) g[i] = F2(to_a(raw[k][9 + i]), to_a(raw[k + 1][9 + i]));
+            collide_dev(P, f, g);
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i) {
+                float lo, hi;
+                (i < 9 ? f[i] : g[i - 9]).split(lo, hi);
+                out[i].e[k] = from_a(lo, (E*)nullptr);
+                out[i].e[k + 1] = from_a(hi, (E*)nullptr);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            A f[9], g[5];
+            finish_pull(P, raw[k], 0, f, g);
+            collide_any<Storage<ST>::DEV>(P, f, g);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) out[i].e[k] = from_a(f[i], (E*)nullptr);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) out[9 + i].e[k] = from_a(g[i], (E*)nullptr);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];
+}
+
+// Block = kPipeWarps warps side by side along x; block (bx, by) covers columns
+// [bx * kPipeWarps * 32 * V, ...) and rows [by * R, by * R + R). S stages of shared memory per warp.
+template <int ST, int V, int S>
+__global__ void __launch_bounds__(kPipeWarps * 32) k_step_pipe(const typename Storage<ST>::T* __restrict__ src,
+                                                               typename Storage<ST>::T* __restrict__ dst,
+                                                               const LatParams<typename Storage<ST>::A> P,
+                                                               int R)
+{
+    using E = typename Storage<ST>::T;
+    using G = StageGeom<E, V>;
+    extern __shared__ __align__(16) unsigned char pipe_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wx0 = (blockIdx.x * kPipeWarps + warp) * 32 * V;
+    if (wx0 >= P.nx) return;
+    const int y0 = blockIdx.y * R;
+    const int rows = min(R, P.ny - y0);
+    const int wx1 = wx0 + 32 * V - 1;
+    const bool cols_ok = wx1 < P.nx && (P.per_x || (wx0 >= 1 && wx1 <= P.nx - 2));
+    if (!cols_ok) {
+        for (int j = 0; j < rows; ++j) step_warp_nodes<ST, V>(src, dst, P, wx0 + lane * V, y0 + j, lane);
+        return;
+    }
+    E* ring = reinterpret_cast<E*>(pipe_smem) + warp * S * G::SS;
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s) {
+        const int y = y0 + s;
+        if (s < rows && (P.per_y || (y >= 1 && y <= P.ny - 2))) stage_issue<ST, V>(src, P, wx0, y, lane, ring + s * G::SS);
+        cp_async_commit();
+    }
+    for (int j = 0; j < rows; ++j) {
+        const int jn = j + S - 1;
+        const int yn = y0 + jn;
+        if (jn < rows && (P.per_y || (yn >= 1 && yn <= P.ny - 2)))
+            stage_issue<ST, V>(src, P, wx0, yn, lane, ring + (jn % S) * G::SS);
+        cp_async_commit();
+        cp_async_wait<S - 1>();
+        __syncwarp();
+        const int y = y0 + j;
+        if (P.per_y || (y >= 1 && y <= P.ny - 2))
+            stage_compute<ST, V>(dst, P, wx0, y, lane, ring + (j % S) * G::SS);
+        else
+            step_warp_nodes<ST, V>(src, dst, P, wx0 + lane * V, y, lane);
+        __syncwarp();
+    }
+}
+
+template <int ST, int V, int S>
+constexpr size_t pipe_smem_bytes()
+{
+    return (size_t)kPipeWarps * S * StageGeom<typename Storage<ST>::T, V>::SS * sizeof(typename Storage<ST>::T);
+}
+
 // Initialisation to f^eq(rho, u), g^eq(T, u) (in stored form). The buffer holds post-collision
 // values that the next step pulls, so each equilibrium value is written to the slot its pull
 // reads: population i of node x goes to (i, x - e_i), or, when x - e_i is beyond a wall, to the

@@ -106,7 +106,7 @@ Layout layout(int nx, int ny, int storage)
     Layout L;
     const size_t N = (size_t)nx * ny;
     size_t off = 0;
-    const size_t bb = align256(buffer_bytes(nx, ny, storage));
+    const size_t bb = buffer_slot_bytes(nx, ny, storage);
     L.buf[0] = off; off += bb;
     L.buf[1] = off; off += bb;
     L.snap = off; off += align256(3 * N * sizeof(double));
@@ -139,6 +139,7 @@ struct clb_handle {
     double* host_diag = nullptr;  // pinned
     long steps = 0;
     int bx = 128, by = 1, npt = 1;
+    int pipe_stages = 0, pipe_rows = 8;  // 0 stages: direct kernel
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     LatParams<double> Pd{};
     LatParams<float> Pf{};
@@ -178,15 +179,66 @@ void enqueue_step_npt(const clb_handle* h, const void* a, void* b, cudaStream_t 
     else enqueue_step<ST, 1>(h, a, b, s, bx, by);
 }
 
+template <int ST, int V, int S>
+cudaError_t enqueue_pipe(const clb_handle* h, const void* a, void* b, cudaStream_t s, int R)
+{
+    using E = typename Storage<ST>::T;
+    using A = typename Storage<ST>::A;
+    constexpr size_t smem = pipe_smem_bytes<ST, V, S>();
+    static bool attr_set[64] = {false};  // per instantiation and device
+    const int dev = h->device >= 0 && h->device < 64 ? h->device : 0;
+    if (!attr_set[dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(k_step_pipe<ST, V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    const int cols = kPipeWarps * 32 * V;
+    const dim3 grid((h->nx + cols - 1) / cols, (h->ny + R - 1) / R);
+    const LatParams<A>& P = *reinterpret_cast<const LatParams<A>*>(ST == ST_F64 ? (const void*)&h->Pd : (const void*)&h->Pf);
+    k_step_pipe<ST, V, S><<<grid, kPipeWarps * 32, smem, s>>>((const E*)a, (E*)b, P, R);
+    return cudaSuccess;
+}
+
+template <int ST, int V>
+cudaError_t enqueue_pipe_s(const clb_handle* h, const void* a, void* b, cudaStream_t s, int S, int R)
+{
+    if (S == 2) return enqueue_pipe<ST, V, 2>(h, a, b, s, R);
+    if (S == 3) return enqueue_pipe<ST, V, 3>(h, a, b, s, R);
+    return enqueue_pipe<ST, V, 4>(h, a, b, s, R);
+}
+
+template <int ST>
+cudaError_t enqueue_pipe_v(const clb_handle* h, const void* a, void* b, cudaStream_t s, int V, int S, int R)
+{
+    if (V == 4) return enqueue_pipe_s<ST, 4>(h, a, b, s, S, R);
+    return enqueue_pipe_s<ST, 2>(h, a, b, s, S, R);
+}
+
+struct Launch {
+    int bx, by, npt, stages, rows;
+};
+
+Launch current_launch(const clb_handle* h) { return {h->bx, h->by, h->npt, h->pipe_stages, h->pipe_rows}; }
+
 // Enqueue one step from buffer `from` into the other buffer on stream s.
-clb_status launch_step(clb_handle* h, int from, cudaStream_t s, int bx, int by, int npt)
+clb_status launch_step(clb_handle* h, int from, cudaStream_t s, const Launch& L)
 {
     void* a = h->buf[from];
     void* b = h->buf[from ^ 1];
-    switch (h->p.storage) {
-    case CLB_F64: enqueue_step_npt<ST_F64>(h, a, b, s, bx, by, npt); break;
-    case CLB_F32: enqueue_step_npt<ST_F32>(h, a, b, s, bx, by, npt); break;
-    default: enqueue_step_npt<ST_F16DEV>(h, a, b, s, bx, by, npt); break;
+    if (L.stages > 0) {
+        cudaError_t e;
+        switch (h->p.storage) {
+        case CLB_F64: e = enqueue_pipe_v<ST_F64>(h, a, b, s, L.npt, L.stages, L.rows); break;
+        case CLB_F32: e = enqueue_pipe_v<ST_F32>(h, a, b, s, L.npt, L.stages, L.rows); break;
+        default: e = enqueue_pipe_v<ST_F16DEV>(h, a, b, s, L.npt, L.stages, L.rows); break;
+        }
+        if (e != cudaSuccess) return set_error(CLB_ECUDA, "pipelined step: %s", cudaGetErrorString(e));
+    } else {
+        switch (h->p.storage) {
+        case CLB_F64: enqueue_step_npt<ST_F64>(h, a, b, s, L.bx, L.by, L.npt); break;
+        case CLB_F32: enqueue_step_npt<ST_F32>(h, a, b, s, L.bx, L.by, L.npt); break;
+        default: enqueue_step_npt<ST_F16DEV>(h, a, b, s, L.bx, L.by, L.npt); break;
+        }
     }
     CLB_CUDA(cudaGetLastError());
     return CLB_OK;
@@ -196,7 +248,7 @@ clb_status build_graph(clb_handle* h, int start)
 {
     CLB_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     clb_status st = CLB_OK;
-    for (int k = 0; k < kGraphChunk && st == CLB_OK; ++k) st = launch_step(h, start ^ (k & 1), h->cap, h->bx, h->by, h->npt);
+    for (int k = 0; k < kGraphChunk && st == CLB_OK; ++k) st = launch_step(h, start ^ (k & 1), h->cap, current_launch(h));
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap, &g);
     if (st != CLB_OK) {
@@ -267,7 +319,7 @@ clb_status take_snapshot(clb_handle* h)
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::array<int, 3>> g_tune_cache;
+std::map<std::tuple<int, int, int>, std::array<int, 5>> g_tune_cache;
 
 }  // namespace
 
@@ -333,6 +385,8 @@ extern "C" clb_status clb_create(int nx, int ny, const clb_params* p, void* stre
             h->bx = it->second[0];
             h->by = it->second[1];
             h->npt = it->second[2];
+            h->pipe_stages = it->second[3];
+            h->pipe_rows = it->second[4];
         }
     }
     // the padding between rows and planes is never read, but keep it defined
@@ -401,7 +455,7 @@ extern "C" clb_status clb_step(clb_handle* h, long n)
         h->steps += kGraphChunk;
     }
     for (; n > 0; --n) {
-        CLB_TRY(launch_step(h, h->cur, h->stream, h->bx, h->by, h->npt));
+        CLB_TRY(launch_step(h, h->cur, h->stream, current_launch(h)));
         h->cur ^= 1;
         h->steps++;
     }
@@ -567,25 +621,62 @@ extern "C" clb_status clb_load(clb_handle* h, const void* buf, size_t bytes)
     return CLB_OK;
 }
 
-extern "C" clb_status clb_set_launch(clb_handle* h, int block_x, int block_y, int nodes_per_thread)
+namespace {
+clb_status check_launch(const clb_handle* h, const Launch& L)
 {
-    CHECK_H(h);
-    const int bx = block_x ? block_x : h->bx, by = block_y ? block_y : h->by;
-    const int npt = nodes_per_thread ? nodes_per_thread : h->npt;
-    if (bx < 32 || bx > 256 || bx % 32 || by < 1 || by > 8 || bx * by > 256 ||
-        (npt != 1 && npt != 2 && npt != 4))
+    if (L.bx < 32 || L.bx > 256 || L.bx % 32 || L.by < 1 || L.by > 8 || L.bx * L.by > 256 ||
+        (L.npt != 1 && L.npt != 2 && L.npt != 4))
         return set_error(CLB_EINVAL, "launch shape %d x %d x %d: block_x in [32, 256] multiple of 32, "
                                      "block_y in [1, 8], block_x * block_y <= 256, nodes per thread 1, 2 or 4",
-                         bx, by, npt);
-    if (bx != h->bx || by != h->by || npt != h->npt) {
+                         L.bx, L.by, L.npt);
+    if (L.stages != 0 && (L.stages < 2 || L.stages > 4 || L.rows < 1 || L.rows > 256 || L.npt == 1))
+        return set_error(CLB_EINVAL, "pipeline %d stages x %d rows: stages 0 (off) or 2..4, rows 1..256, "
+                                     "and 2 or 4 nodes per thread", L.stages, L.rows);
+    if (L.stages != 0) {
+        const size_t e = elem_size(h->p.storage);
+        const size_t smem = (size_t)kPipeWarps * L.stages * NPOP * (32 * L.npt + 16 / e) * e;
+        if (smem > 227 * 1024)
+            return set_error(CLB_EINVAL, "pipeline needs %zu bytes of shared memory per block (max 232448)", smem);
+    }
+    return CLB_OK;
+}
+
+clb_status apply_launch(clb_handle* h, const Launch& L)
+{
+    CLB_TRY(check_launch(h, L));
+    const Launch c = current_launch(h);
+    if (c.bx != L.bx || c.by != L.by || c.npt != L.npt || c.stages != L.stages || c.rows != L.rows) {
         DeviceGuard dg(h->device);
         cudaStreamSynchronize(h->stream);
         drop_graphs(h);
-        h->bx = bx;
-        h->by = by;
-        h->npt = npt;
+        h->bx = L.bx;
+        h->by = L.by;
+        h->npt = L.npt;
+        h->pipe_stages = L.stages;
+        h->pipe_rows = L.rows;
     }
     return CLB_OK;
+}
+}  // namespace
+
+extern "C" clb_status clb_set_launch(clb_handle* h, int block_x, int block_y, int nodes_per_thread)
+{
+    CHECK_H(h);
+    Launch L = current_launch(h);
+    if (block_x) L.bx = block_x;
+    if (block_y) L.by = block_y;
+    if (nodes_per_thread) L.npt = nodes_per_thread;
+    if (L.npt == 1) L.stages = 0;
+    return apply_launch(h, L);
+}
+
+extern "C" clb_status clb_set_pipeline(clb_handle* h, int stages, int rows)
+{
+    CHECK_H(h);
+    Launch L = current_launch(h);
+    L.stages = stages;
+    if (rows) L.rows = rows;
+    return apply_launch(h, L);
 }
 
 extern "C" clb_status clb_get_launch(clb_handle* h, int* block_x, int* block_y, int* nodes_per_thread)
@@ -597,6 +688,14 @@ extern "C" clb_status clb_get_launch(clb_handle* h, int* block_x, int* block_y, 
     return CLB_OK;
 }
 
+extern "C" clb_status clb_get_pipeline(clb_handle* h, int* stages, int* rows)
+{
+    CHECK_H(h);
+    if (stages) *stages = h->pipe_stages;
+    if (rows) *rows = h->pipe_rows;
+    return CLB_OK;
+}
+
 extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y, int* nodes_per_thread)
 {
     CHECK_H(h);
@@ -605,33 +704,36 @@ extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y, in
     void* save = nullptr;
     CLB_CUDA(cudaMallocAsync(&save, bb, h->stream));
     CLB_CUDA(cudaMemcpyAsync(save, h->buf[h->cur], bb, cudaMemcpyDeviceToDevice, h->stream));
-    const int shapes[][2] = {{64, 1}, {128, 1}, {256, 1}, {32, 4}, {64, 2}, {64, 4}, {128, 2}, {32, 8}};
-    const int npts[] = {1, 2, 4};
+    std::vector<Launch> cands;
+    const int shapes[][2] = {{64, 1}, {128, 1}, {256, 1}, {32, 4}, {64, 2}, {128, 2}};
+    for (int npt : {1, 2, 4})
+        for (auto& sh : shapes) cands.push_back({sh[0], sh[1], npt, 0, 8});
+    for (int npt : {2, 4})
+        for (int st : {2, 3, 4})
+            for (int rows : {4, 8, 16}) cands.push_back({128, 1, npt, st, rows});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bbx = h->bx, bby = h->by, bnpt = h->npt;
+    Launch bl = current_launch(h);
     const int reps = 10;
     clb_status st = CLB_OK;
-    for (int npt : npts)
-        for (auto& s : shapes) {
-            if (s[0] * npt > 2 * h->nx + 64 && s[0] * npt > 64) continue;  // far wider than the lattice
-            for (int k = 0; k < 4 && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, s[0], s[1], npt);
-            cudaEventRecord(e0, h->stream);
-            for (int k = 0; k < reps && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, s[0], s[1], npt);
-            cudaEventRecord(e1, h->stream);
-            if (st != CLB_OK) break;
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                bbx = s[0];
-                bby = s[1];
-                bnpt = npt;
-            }
+    for (const Launch& c : cands) {
+        if (c.bx * c.npt > 2 * h->nx + 64 && c.bx * c.npt > 64) continue;  // far wider than the lattice
+        if (c.stages > 0 && check_launch(h, c) != CLB_OK) continue;
+        for (int k = 0; k < 4 && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, c);
+        cudaEventRecord(e0, h->stream);
+        for (int k = 0; k < reps && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, c);
+        cudaEventRecord(e1, h->stream);
+        if (st != CLB_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bl = c;
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaError_t e = cudaMemcpyAsync(h->buf[h->cur], save, bb, cudaMemcpyDeviceToDevice, h->stream);
@@ -639,14 +741,14 @@ extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y, in
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (st != CLB_OK) return st;
     if (e != cudaSuccess) return set_error(CLB_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
-    CLB_TRY(clb_set_launch(h, bbx, bby, bnpt));
+    CLB_TRY(apply_launch(h, bl));
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[std::make_tuple(h->p.storage, h->nx, h->ny)] = {bbx, bby, bnpt};
+        g_tune_cache[std::make_tuple(h->p.storage, h->nx, h->ny)] = {bl.bx, bl.by, bl.npt, bl.stages, bl.rows};
     }
-    if (block_x) *block_x = bbx;
-    if (block_y) *block_y = bby;
-    if (nodes_per_thread) *nodes_per_thread = bnpt;
+    if (block_x) *block_x = bl.bx;
+    if (block_y) *block_y = bl.by;
+    if (nodes_per_thread) *nodes_per_thread = bl.npt;
     return CLB_OK;
 }
 

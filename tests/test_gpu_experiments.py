@@ -1,0 +1,118 @@
+"""The paper's experiments on the CUDA path, against stored oracle values (written by the committed
+scripts in tests/golden/ that call only the oracle) and against the paper's printed numbers."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1710_10569_gb300 import workloads as W
+from conftest import golden_path
+
+pytestmark = pytest.mark.gpu
+
+F64, F32, F16 = W.STORAGE_F64, W.STORAGE_F32, W.STORAGE_F16DEV
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def clb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_10569_gb300 import clb as c
+    c.lib()
+    return c
+
+
+def _golden(name):
+    path = golden_path(name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    with open(path) as f:
+        return json.load(f)
+
+
+def _table1_paper():
+    rows = {}
+    for line in open(golden_path("table1_nusselt.txt")):
+        if line.strip() and not line.startswith("#"):
+            ra, an, pap, _ = line.split()
+            rows[int(float(ra))] = (float(an), float(pap))
+    return rows
+
+
+@pytest.mark.parametrize("storage", [F64, F32])
+def test_table1_rayleigh_benard_batch(clb, storage):
+    """Sec. 3.3, Table 1: the eight Rayleigh numbers stepped together in one batch. At 10k, 20k and
+    30k steps the Nusselt numbers equal the oracle's (FP64: 1e-9 relative; FP32: 2 n u32); at
+    steady state they equal the oracle's steady values (FP64 1e-6, FP32 1e-3) and lie within 2.5% of
+    the analytic values of Table 1 (0.5% for Ra <= 1e4)."""
+    gold = _golden("table1_oracle.json")
+    paper = _table1_paper()
+    ras = sorted(int(k) for k in gold)
+    probs = [W.rayleigh_benard_table1(float(ra), storage=storage) for ra in ras]
+    b = clb.Batch(probs)
+    done = 0
+    for n in (10000, 20000, 30000):
+        b.step(n - done)
+        done = n
+        nu, _ = b.diagnostics()
+        tol = 1e-9 if storage == F64 else 2 * n * U32
+        for k, ra in enumerate(ras):
+            exp = gold[str(ra)]["at"][str(n)]
+            assert nu[k] == pytest.approx(exp, rel=tol), (ra, n)
+    b.step(200000 - done)
+    nu, _ = b.diagnostics()
+    for k, ra in enumerate(ras):
+        steady = gold[str(ra)]["steady"]
+        assert nu[k] == pytest.approx(steady, rel=1e-6 if storage == F64 else 1e-3), ra
+        analytic = paper[ra][0]
+        assert nu[k] == pytest.approx(analytic, rel=5e-3 if ra <= 10000 else 2.5e-2), ra
+
+
+@pytest.mark.parametrize("storage", [F64, F32])
+def test_cavity_256_ra1e5_steady_state(clb, storage):
+    """The side-heated cavity (256^2, Ra = 1e5, Pr = 0.71) run to E_R < 1e-8: the mean Nusselt
+    number equals the oracle's steady value (FP64: 1e-6 relative; FP32: 1e-3, with a step cap since
+    FP32 rounding puts a floor under E_R)."""
+    gold = _golden("cavity256_ra1e5.json")
+    prob = W.cavity(256, Ra=1e5, Pr=0.71, u_c=0.1, seed=0, storage=storage)
+    lat = clb.Lattice.from_problem(prob)
+    cap = gold["steps"] + 20000
+    steps, er = lat.run(1e-8, cap, 100)
+    nu = lat.nusselt(prob.nu_axis)
+    if storage == F64:
+        assert er < 1e-8
+        assert abs(steps - gold["steps"]) <= 1000
+        assert nu == pytest.approx(gold["nusselt"], rel=1e-6)
+    else:
+        assert nu == pytest.approx(gold["nusselt"], rel=1e-3)
+
+
+@pytest.mark.parametrize("storage", [F64, F32])
+@pytest.mark.parametrize("Ma", [0.0, 0.3])
+def test_moving_frame_diffusivity(clb, storage, Ma):
+    """Sec. 3.1 on the GPU: the temperature wave's measured diffusivity equals the prescribed
+    alpha = 0.05 within 0.1% for Ma = 0 and 0.3."""
+    L, alpha, B = 100, 0.05, 0.01
+    nx, ny = 2, L
+    A_ = Ma * W.CS
+    phi = 2 * math.pi / L
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    p = W.default_params(nu=0.05, kappa=alpha, T0=1.0, T_ref=1.0, storage=storage)
+    prob = W.Problem("wave", nx, ny, p, np.ones((ny, nx)), np.zeros((ny, nx)),
+                     A_ * np.ones((ny, nx)), 1.0 + B * np.sin(phi * y))
+    lat = clb.Lattice.from_problem(prob)
+
+    def amp():
+        c = lat.fields()[3][:, 0] - 1.0
+        return abs(np.sum(c * np.exp(-1j * phi * np.arange(ny)))) * 2 / ny
+
+    lat.step(500)
+    a1 = amp()
+    lat.step(2000)
+    a2 = amp()
+    measured = -math.log(a2 / a1) / (phi * phi * 2000)
+    assert measured == pytest.approx(alpha, rel=1e-3)

@@ -180,9 +180,14 @@ def test_launch_shapes_are_bitwise_equal(clb, storage, walls):
     """Vector interior path, scalar wall/ragged path and every launch shape give the same bits."""
     prob = W.random_problem(333, 37, seed=3, storage=storage, walls=walls)
     ref = None
-    for shape in ((128, 1, 1), (64, 4, 2), (128, 2, 4), (32, 8, 1), (256, 1, 2), (32, 1, 4)):
+    for shape in ((128, 1, 1, 0, 0), (64, 4, 2, 0, 0), (128, 2, 4, 0, 0), (32, 8, 1, 0, 0),
+                  (256, 1, 2, 0, 0), (32, 1, 4, 0, 0), (128, 1, 2, 2, 4), (128, 1, 2, 3, 7),
+                  (128, 1, 4, 4, 16), (128, 1, 4, 3, 1)):
+        if storage == F64 and shape[2] == 4 and shape[3] == 4:
+            continue  # exceeds shared memory
         lat = clb.Lattice.from_problem(prob)
-        lat.set_launch(*shape)
+        lat.set_launch(*shape[:3])
+        lat.set_pipeline(shape[3], shape[4])
         lat.step(40)
         got = lat.fields()
         if ref is None:
@@ -252,6 +257,18 @@ def test_checkpoint_roundtrip_bitwise(clb):
     b.step(30)
     for x, y in zip(b.fields(), ref):
         assert np.array_equal(x, y)
+
+
+def test_pipeline_rejects_bad_shapes(clb):
+    prob = W.random_problem(64, 64, seed=1, storage=F64)
+    a = clb.Lattice.from_problem(prob)
+    a.set_launch(128, 1, 4)
+    for stages, rows in ((4, 8), (5, 8), (1, 8), (3, 300)):
+        with pytest.raises(clb.CLBError):
+            a.set_pipeline(stages, rows)
+    a.set_launch(128, 1, 1)
+    with pytest.raises(clb.CLBError):
+        a.set_pipeline(2, 8)
 
 
 def test_autotune_keeps_state(clb):

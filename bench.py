@@ -229,6 +229,36 @@ def e2e_run(storage: int, steps: int):
             "steps": steps, "seconds": dt}
 
 
+def thermal_run(storage: int, steps: int):
+    """The D2Q5-only step with a prescribed velocity (a cellular flow of amplitude 0.1) on the bench
+    lattice's temperature field: 5 populations in and out plus the node's velocity."""
+    import torch
+    from paper_1710_10569_gb300 import clb
+    prob = workload(storage)
+    nx, ny = prob.nx, prob.ny
+    x, y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)
+    kx, ky = 2 * math.pi / nx, 2 * math.pi / ny
+    ux = 0.1 * np.sin(kx * x) * np.cos(ky * y)
+    uy = -0.1 * np.cos(kx * x) * np.sin(ky * y)
+    th = clb.Thermal(nx, ny, prob.params)
+    th.init(prob.T, ux, uy)
+    th.step(64)
+    th.sync()
+    stream = torch.cuda.ExternalStream(th.stream) if th.stream else torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    th.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    th.close()
+    per_node = {W.STORAGE_F64: 96, W.STORAGE_F32: 48, W.STORAGE_F16DEV: 28}[storage]
+    peak, _ = measured_peaks()
+    gbs = per_node * nx * ny * steps / dt / 1e9
+    return {"mlups": nx * ny * steps / dt / 1e6, "bytes_per_node": per_node, "achieved_gbs": gbs,
+            "hbm_frac": gbs / peak, "steps": steps, "storage": W.STORAGE_NAMES[storage]}
+
+
 def batched_run(storage: int, count: int = 256, steps: int = 1000, seq_subset: int = 32):
     """Many side-heated cavities of uneven sizes (edge log-uniform 64-512, Ra log-uniform 1e3-1e6,
     Pr uniform 0.71-7) stepped in one launch per time step, against the same instances stepped one
@@ -346,6 +376,7 @@ def run_ours(args):
                     "peak_kind": "derived: 152 SMs x 2 FP64 lanes/clock x 2.07 GHz"}
             l2.close()
     e2e = e2e_run(storage, args.steps) if rank == 0 else None
+    thermal = thermal_run(storage, args.steps) if (rank == 0 and not args.no_variants) else None
     batched = batched_run(storage) if (rank == 0 and not args.no_serve) else None
     served = served_run(storage) if (rank == 0 and not args.no_serve) else None
     if rank == 0:
@@ -372,6 +403,7 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "clocks": clocks.summary(),
             "variants": variants,
+            "thermal_only": thermal,
             "batched": batched,
             "served": served,
         }

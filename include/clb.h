@@ -196,6 +196,27 @@ const char *clb_last_error(void);
 const char *clb_version(void);
 
 /* ---------------------------------------------------------------------------------------------
+ * Thermal-only mode: the D2Q5 central-moment equation alone (Eqs. 16-23) with a prescribed
+ * velocity field, as in Sec. 3.1 where the velocity is given and only the temperature equation is
+ * solved; usable for any convection-diffusion of a passive scalar (Sec. 4). Same walls (anti-bounce-
+ * back / adiabatic / periodic), storage forms and parameters (nu, g_beta, Fv are unused). One step
+ * moves 5 populations in and out plus the node's velocity (FP32: 48 bytes per node).
+ */
+typedef struct clb_thermal clb_thermal;
+
+clb_status clb_thermal_create(int nx, int ny, const clb_params *p, void *stream, clb_thermal **out);
+void clb_thermal_destroy(clb_thermal *h);
+/* g = g^eq(T, u) (Eq. 20 back-transformed) and the velocity held fixed from here on. Host arrays
+ * [ny][nx]; NULL means T = T0, u = 0. Synchronous; resets the step count. */
+clb_status clb_thermal_init(clb_thermal *h, const double *T, const double *ux, const double *uy);
+clb_status clb_thermal_step(clb_thermal *h, long n);
+/* T (Eq. 23) at the current time into a host array. Synchronous. */
+clb_status clb_thermal_fields(clb_thermal *h, double *T);
+/* Pre-collision populations g[5][ny][nx] at the current time. Synchronous. */
+clb_status clb_thermal_populations(clb_thermal *h, double *g);
+clb_status clb_thermal_sync(clb_thermal *h);
+
+/* ---------------------------------------------------------------------------------------------
  * Batches: many independent lattices of different sizes and parameters stepped together, one
  * launch per time step over the concatenated tiles of all active instances (captured in a CUDA
  * graph). Each instance computes exactly what a single lattice computes (bitwise the same).

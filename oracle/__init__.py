@@ -51,7 +51,8 @@ class _Params(ctypes.Structure):
                 ("T0", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("s_b", ctypes.c_double), ("s_3", ctypes.c_double), ("s_4", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
-                ("Fv", ctypes.c_double * 2), ("wall", ctypes.c_int * 4), ("T_wall", ctypes.c_double * 4)]
+                ("Fv", ctypes.c_double * 2), ("wall", ctypes.c_int * 4), ("T_wall", ctypes.c_double * 4),
+                ("thermal_only", ctypes.c_int)]
 
 
 def _load():
@@ -77,6 +78,7 @@ def _load():
             lib.orc_get_pops.argtypes = [ctypes.c_void_p, d, d]
             lib.orc_set_pops.argtypes = [ctypes.c_void_p, d, d]
             lib.orc_collide_node.argtypes = [P(_Params), d, d, d, d]
+            lib.orc_collide_thermal_node.argtypes = [P(_Params), d, ctypes.c_double, ctypes.c_double, d]
             lib.orc_equilibrium_node.argtypes = [P(_Params), ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, d, d]
             lib.orc_matrices.argtypes = [P(_Params), ctypes.c_double, ctypes.c_double] + [d] * 11
@@ -99,11 +101,14 @@ def _params(p: dict, nx: int = 2, ny: int = 2) -> _Params:
     for i in range(4):
         s.wall[i] = int(p["wall"][i])
         s.T_wall[i] = float(p["T_wall"][i])
+    s.thermal_only = int(p.get("thermal_only", 0))
     return s
 
 
 class Oracle:
-    """One lattice stepped on the CPU in FP64. Fields are (ny, nx) float64 arrays."""
+    """One lattice stepped on the CPU in FP64. Fields are (ny, nx) float64 arrays. With
+    params["thermal_only"] = 1 only the D2Q5 equation is stepped, with the velocity given to init()
+    held fixed (the fields report that velocity)."""
 
     def __init__(self, nx: int, ny: int, params: dict):
         self._lib = _load()
@@ -175,6 +180,16 @@ def collide_node(params: dict, f, g):
     fo, go = np.empty(9), np.empty(5)
     lib.orc_collide_node(ctypes.byref(p), _ptr(f), _ptr(g), _ptr(fo), _ptr(go))
     return fo, go
+
+
+def collide_thermal_node(params: dict, g, ux, uy):
+    """Post-collision D2Q5 populations of one node for a prescribed velocity (Eqs. 16-21)."""
+    lib = _load()
+    p = _params(params)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    go = np.empty(5)
+    lib.orc_collide_thermal_node(ctypes.byref(p), _ptr(g), float(ux), float(uy), _ptr(go))
+    return go
 
 
 def equilibrium_node(params: dict, rho, ux, uy, T):

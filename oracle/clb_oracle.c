@@ -53,6 +53,7 @@ typedef struct {
     double Fv[2];
     int wall[4];
     double T_wall[4];
+    int thermal_only; /* 1: only the D2Q5 equation, with the velocity set by orc_set_velocity */
 } orc_params;
 
 typedef struct {
@@ -65,6 +66,7 @@ typedef struct {
     double wT[Q5];         /* D2Q5 rest weights, g^eq(T=1, u=0) */
     double *f, *g;         /* pre-collision populations at the current time, [q][y][x] */
     double *fs, *gs;       /* post-collision scratch */
+    double *uxp, *uyp;     /* prescribed velocity of the thermal-only mode, [y][x] */
     long steps;
 } orc_sim;
 
@@ -291,6 +293,28 @@ static void collide(const orc_sim *s, const double f[Q9], const double g[Q5], do
     matvec(Q5, &s->MTinv[0][0], gamsT, go);                 /* Eq. 21 */
 }
 
+/* D2Q5 collision alone, Eqs. (16)-(21), with a prescribed velocity (Sec. 3.1: the velocity field is
+ * given and only the D2Q5 equation is solved). */
+static void collide_thermal(const orc_sim *s, const double g[Q5], double ux, double uy, double go[Q5])
+{
+    const orc_params *p = &s->p;
+    double T = 0.0;
+    for (int i = 0; i < Q5; ++i) T += g[i];
+    double NT[Q5][Q5];
+    build_NT(ux, uy, NT);
+    double gamT[Q5], gtT[Q5];
+    matvec(Q5, &s->MT[0][0], g, gamT);
+    matvec(Q5, &NT[0][0], gamT, gtT);
+    const double c2 = p->cs2_T;
+    const double geqT[Q5] = {T, 0, 0, T * c2, T * c2};
+    double dT[Q5], SdT[Q5], gtsT[Q5], gamsT[Q5];
+    for (int k = 0; k < Q5; ++k) dT[k] = gtT[k] - geqT[k];
+    matvec(Q5, &s->ST[0][0], dT, SdT);
+    for (int k = 0; k < Q5; ++k) gtsT[k] = gtT[k] - SdT[k];
+    solve_unit_lower(Q5, &NT[0][0], gtsT, gamsT);
+    matvec(Q5, &s->MTinv[0][0], gamsT, go);
+}
+
 /* Discrete equilibria: f^eq = M^-1 N(u)^-1 Gamma~eq(rho), g^eq = M_T^-1 N_T(u)^-1 Gamma~T,eq(T). */
 static void equilibrium(const orc_sim *s, double rho, double ux, double uy, double T, double f[Q9],
                         double g[Q5])
@@ -356,7 +380,12 @@ static void collide_all(orc_sim *s)
         double f[Q9], g[Q5], fo[Q9], go[Q5];
         for (int i = 0; i < Q9; ++i) f[i] = s->f[i * n + k];
         for (int i = 0; i < Q5; ++i) g[i] = s->g[i * n + k];
-        collide(s, f, g, fo, go);
+        if (s->p.thermal_only) {
+            for (int i = 0; i < Q9; ++i) fo[i] = f[i];
+            collide_thermal(s, g, s->uxp[k], s->uyp[k], go);
+        } else {
+            collide(s, f, g, fo, go);
+        }
         for (int i = 0; i < Q9; ++i) s->fs[i * n + k] = fo[i];
         for (int i = 0; i < Q5; ++i) s->gs[i * n + k] = go[i];
     }
@@ -377,8 +406,10 @@ int orc_create(const orc_params *p, orc_sim **out)
     s->fs = (double *)calloc(Q9 * n, sizeof(double));
     s->g = (double *)calloc(Q5 * n, sizeof(double));
     s->gs = (double *)calloc(Q5 * n, sizeof(double));
-    if (!s->f || !s->fs || !s->g || !s->gs) {
-        free(s->f); free(s->fs); free(s->g); free(s->gs); free(s);
+    s->uxp = (double *)calloc(n, sizeof(double));
+    s->uyp = (double *)calloc(n, sizeof(double));
+    if (!s->f || !s->fs || !s->g || !s->gs || !s->uxp || !s->uyp) {
+        free(s->f); free(s->fs); free(s->g); free(s->gs); free(s->uxp); free(s->uyp); free(s);
         return -2;
     }
     *out = s;
@@ -388,7 +419,7 @@ int orc_create(const orc_params *p, orc_sim **out)
 void orc_destroy(orc_sim *s)
 {
     if (!s) return;
-    free(s->f); free(s->fs); free(s->g); free(s->gs);
+    free(s->f); free(s->fs); free(s->g); free(s->gs); free(s->uxp); free(s->uyp);
     free(s);
 }
 
@@ -396,6 +427,10 @@ void orc_destroy(orc_sim *s)
 void orc_init(orc_sim *s, const double *rho, const double *ux, const double *uy, const double *T)
 {
     const size_t n = nodes(s);
+    if (s->p.thermal_only) {
+        memcpy(s->uxp, ux, n * sizeof(double));
+        memcpy(s->uyp, uy, n * sizeof(double));
+    }
     for (size_t k = 0; k < n; ++k) {
         double f[Q9], g[Q5];
         equilibrium(s, rho[k], ux[k], uy[k], T[k], f, g);
@@ -434,6 +469,10 @@ void orc_fields(const orc_sim *s, double *rho, double *ux, double *uy, double *T
         for (int i = 0; i < Q9; ++i) f[i] = s->f[i * n + k];
         for (int i = 0; i < Q5; ++i) g[i] = s->g[i * n + k];
         macroscopic(s, f, g, &rho[k], &ux[k], &uy[k], &T[k], &Fx, &Fy);
+        if (s->p.thermal_only) {
+            ux[k] = s->uxp[k];
+            uy[k] = s->uyp[k];
+        }
     }
 }
 
@@ -470,6 +509,16 @@ int orc_equilibrium_node(const orc_params *p, double rho, double ux, double uy, 
     s.p = *p;
     build_constants(&s);
     equilibrium(&s, rho, ux, uy, T, f, g);
+    return 0;
+}
+
+int orc_collide_thermal_node(const orc_params *p, const double *g, double ux, double uy, double *go)
+{
+    orc_sim s;
+    memset(&s, 0, sizeof(s));
+    s.p = *p;
+    build_constants(&s);
+    collide_thermal(&s, g, ux, uy, go);
     return 0;
 }
 

@@ -78,6 +78,13 @@ _SIGS = {
     "clb_buffers": [_VP, _P(_VP), _P(_VP), _P(_S), _P(_I)],
     "clb_last_error": [],
     "clb_version": [],
+    "clb_thermal_create": [_I, _I, _P(clb_params), _VP, _P(_VP)],
+    "clb_thermal_destroy": [_VP],
+    "clb_thermal_init": [_VP, _D, _D, _D],
+    "clb_thermal_step": [_VP, _L],
+    "clb_thermal_fields": [_VP, _D],
+    "clb_thermal_populations": [_VP, _D],
+    "clb_thermal_sync": [_VP],
     "clb_batch_create": [_I, _P(_I), _P(_I), _P(clb_params), _VP, _P(_VP)],
     "clb_batch_destroy": [_VP],
     "clb_batch_init_fields": [_VP, _I, _D, _D, _D, _D],
@@ -95,6 +102,7 @@ _SIGS = {
     "clb_serve_fetch": [_VP, _L, _D, _D, _D, _D],
 }
 _RESTYPES = {"clb_destroy": None, "clb_batch_destroy": None, "clb_serve_close": None,
+             "clb_thermal_destroy": None,
              "clb_last_error": ctypes.c_char_p, "clb_version": ctypes.c_char_p, "clb_stream": _VP}
 
 _lock = threading.Lock()
@@ -306,6 +314,50 @@ class Lattice:
         _check(lib().clb_buffers(self._h, ctypes.byref(cur), ctypes.byref(oth), ctypes.byref(pl),
                                  ctypes.byref(pitch)))
         return cur.value, oth.value, pl.value, pitch.value
+
+
+class Thermal:
+    """The D2Q5 equation alone with a prescribed velocity field (clb_thermal_*)."""
+
+    def __init__(self, nx: int, ny: int, p: dict, stream=None):
+        self.nx, self.ny, self.params = int(nx), int(ny), dict(p)
+        self._p = params(p)
+        self.stream = _stream_handle(stream)
+        h = _VP()
+        _check(lib().clb_thermal_create(self.nx, self.ny, ctypes.byref(self._p), self.stream, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().clb_thermal_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, T=None, ux=None, uy=None):
+        n = self.nx * self.ny
+        arrs = [_host(a, n) for a in (T, ux, uy)]
+        _check(lib().clb_thermal_init(self._h, *[_dptr(a) for a in arrs]))
+
+    def step(self, n: int = 1):
+        _check(lib().clb_thermal_step(self._h, int(n)))
+
+    def sync(self):
+        _check(lib().clb_thermal_sync(self._h))
+
+    def temperature(self):
+        T = np.empty((self.ny, self.nx))
+        _check(lib().clb_thermal_fields(self._h, _dptr(T)))
+        return T
+
+    def populations(self):
+        g = np.empty((5, self.ny, self.nx))
+        _check(lib().clb_thermal_populations(self._h, _dptr(g)))
+        return g
 
 
 class Batch:

@@ -312,6 +312,22 @@ __device__ __forceinline__ void central_d2q9(const A f[9], A ux, A uy, A k[3][3]
     for (int a = 0; a < 3; ++a) central3(r0[a], rp[a], rm[a], uy, k[a][0], k[a][1], k[a][2]);
 }
 
+// D2Q5 collision in populations form (Eqs. 16-21) for temperature T and velocity u.
+template <typename A>
+__device__ __forceinline__ void collide_d2q5(const LatParams<A>& P, A T, A ux, A uy, A g[5])
+{
+    const A d1 = g[1] - g[3], s1 = g[1] + g[3];
+    const A d2 = g[2] - g[4], s2 = g[2] + g[4];
+    const A t10 = fma_(-ux, T, d1);
+    const A t01 = fma_(-uy, T, d2);
+    const A t20 = fma_(ux * ux, T, fma_(A(-2) * ux, d1, s1));
+    const A t02 = fma_(uy * uy, T, fma_(A(-2) * uy, d2, s2));
+    const A om1 = A(1) - P.lambda1;
+    const A om2 = A(1) - P.lambda2;
+    const A eqT = P.lambda2 * T * P.cs2T;
+    back_d2q5(T, om1 * t10, om1 * t01, fma_(om2, t20, eqT), fma_(om2, t02, eqT), ux, uy, g);
+}
+
 // Collision of one node in place, populations form: Eqs. (6)-(11) for f, Eqs. (16)-(21) for g.
 template <typename A>
 __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5])
@@ -338,17 +354,7 @@ __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5])
     q[2][2] = fma_(A(1) - P.s_4, k[2][2], P.s_4 * rho * (cs2 * cs2));
     back_d2q9(q, ux, uy, f);
 
-    // D2Q5: central moments, relaxation (Eqs. 19, 20), back transform (Eq. 21)
-    const A d1 = g[1] - g[3], s1 = g[1] + g[3];
-    const A d2 = g[2] - g[4], s2 = g[2] + g[4];
-    const A t10 = fma_(-ux, T, d1);
-    const A t01 = fma_(-uy, T, d2);
-    const A t20 = fma_(ux * ux, T, fma_(A(-2) * ux, d1, s1));
-    const A t02 = fma_(uy * uy, T, fma_(A(-2) * uy, d2, s2));
-    const A om1 = A(1) - P.lambda1;
-    const A om2 = A(1) - P.lambda2;
-    const A eqT = P.lambda2 * T * P.cs2T;
-    back_d2q5(T, om1 * t10, om1 * t01, fma_(om2, t20, eqT), fma_(om2, t02, eqT), ux, uy, g);
+    collide_d2q5(P, T, ux, uy, g);
 }
 
 // Deviation of the D2Q9 equilibrium from the rest state, f^eq_i(rho, u) - w_i rho_b, written as
@@ -382,6 +388,27 @@ __device__ __forceinline__ void eq_dev_d2q5(A T, A dT, A ux, A uy, A c2, A g[5])
     g[3] = fma_(dT, hc, hT * fma_(ux, ux, -ux));
     g[2] = fma_(dT, hc, hT * fma_(uy, uy, uy));
     g[4] = fma_(dT, hc, hT * fma_(uy, uy, -uy));
+}
+
+// D2Q5 collision on deviations t = g - w^T T_b (Eqs. 16-21) for T = T_b + dT and velocity u.
+template <typename A, typename S>
+__device__ __forceinline__ void collide_d2q5_dev(const LatParams<S>& P, A T, A dT, A ux, A uy, A g[5])
+{
+    const A c2 = A(P.cs2T);
+    const A x2 = ux * ux, y2 = uy * uy;
+    const A d1 = g[1] - g[3], s1 = g[1] + g[3];
+    const A d2 = g[2] - g[4], s2 = g[2] + g[4];
+    const A t10 = fma_(-ux, T, d1);
+    const A t01 = fma_(-uy, T, d2);
+    const A t20 = fma_(-dT, c2, fma_(x2, T, fma_(A(-2) * ux, d1, s1)));
+    const A t02 = fma_(-dT, c2, fma_(y2, T, fma_(A(-2) * uy, d2, s2)));
+    const A om1 = A(1.0f - P.lambda1);
+    const A om2 = A(1.0f - P.lambda2);
+    A eT[5], gq[5];
+    eq_dev_d2q5(T, dT, ux, uy, c2, eT);
+    back_d2q5(A(0), om1 * t10, om1 * t01, om2 * t20, om2 * t02, ux, uy, gq);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = gq[i] + eT[i];
 }
 
 // Collision of one node in place, deviation form (h = f - w rho_b, t = g - w^T T_b). The same map
@@ -427,21 +454,7 @@ __device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] += e[i];
 
-    // D2Q5 on deviations
-    const A c2 = A(P.cs2T);
-    const A d1 = g[1] - g[3], s1 = g[1] + g[3];
-    const A d2 = g[2] - g[4], s2 = g[2] + g[4];
-    const A t10 = fma_(-ux, T, d1);
-    const A t01 = fma_(-uy, T, d2);
-    const A t20 = fma_(-dT, c2, fma_(x2, T, fma_(A(-2) * ux, d1, s1)));
-    const A t02 = fma_(-dT, c2, fma_(y2, T, fma_(A(-2) * uy, d2, s2)));
-    const A om1 = A(1.0f - P.lambda1);
-    const A om2 = A(1.0f - P.lambda2);
-    A eT[5], gq[5];
-    eq_dev_d2q5(T, dT, ux, uy, c2, eT);
-    back_d2q5(A(0), om1 * t10, om1 * t01, om2 * t20, om2 * t02, ux, uy, gq);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) g[i] = gq[i] + eT[i];
+    collide_d2q5_dev(P, T, dT, ux, uy, g);
 }
 
 template <bool DEV, typename A>

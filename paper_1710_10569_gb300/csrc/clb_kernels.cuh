@@ -197,7 +197,11 @@ __device__ __forceinline__ void stage_issue(const typename Storage<ST>::T* __res
         const int r = ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp;
         const E* row = src + i * pl + r;
         E* sp = stage + i * G::PS;
-        cp_async_bytes(sp + lane * V, row + wx0 + lane * V, V * (int)sizeof(E));
+        constexpr int VB = V * (int)sizeof(E);  // 4, 8, 16 or 32 bytes: copy in pieces of <= 16
+#pragma unroll
+        for (int c = 0; c < (VB > 16 ? VB / 16 : 1); ++c)
+            cp_async_bytes(sp + lane * V + c * (16 / (int)sizeof(E)), row + wx0 + lane * V + c * (16 / (int)sizeof(E)),
+                           VB > 16 ? 16 : VB);
         if (SHIFT[i] == 1 && lane == 0)
             cp_async_bytes(sp + 32 * V, row + (HALF ? (xl & ~1) : xl), HALF ? 4 : (int)sizeof(E));
         if (SHIFT[i] == -1 && lane == 31)

@@ -116,3 +116,36 @@ def test_moving_frame_diffusivity(clb, storage, Ma):
     a2 = amp()
     measured = -math.log(a2 / a1) / (phi * phi * 2000)
     assert measured == pytest.approx(alpha, rel=1e-3)
+
+
+def test_critical_rayleigh_number(clb):
+    """Sec. 3.3: the growth rate of the disturbance changes sign at Ra_c; the least-squares zero of
+    the growth rates at Ra = 1702..1710 lies within 0.5% of the linear-stability value 1707.76 (the
+    paper finds 1706.82)."""
+    from paper_1710_10569_gb300 import experiments as X
+    theory = float(open(golden_path("critical_rayleigh.txt")).read().split("theory")[1].split()[0])
+    r = X.critical_rayleigh(storage=F64)
+    assert r["growth_rate"][0] < 0 < r["growth_rate"][-1]
+    assert np.all(np.diff(r["growth_rate"]) > 0)
+    assert r["ra_c"] == pytest.approx(theory, rel=5e-3)
+
+
+def test_ma_sweep_nusselt_is_insensitive(clb):
+    """Sec. 3.3: over Ma = 0.1..0.3 the Nusselt number changes by only ~0.1% (0.08% at Ra = 5000 in
+    the paper) while the steps to converge scale like 1/Ma."""
+    from paper_1710_10569_gb300 import experiments as X
+    r = X.ma_sweep(5000.0, mas=(0.1, 0.2, 0.3), tol=1e-8)
+    assert r["nu_rel_change"] < 2e-3
+    ratio = r["steps"][0] / r["steps"][2]
+    assert 2.0 < ratio < 4.5
+
+
+@pytest.mark.parametrize("storage", [F32, F64])
+def test_high_rayleigh_stability(clb, storage):
+    """Sec. 3.3, last paragraph: the method stays stable at Ra = 1e9 with 220 vertical nodes
+    (nu ~ 1e-3, s_nu within 0.3% of 2): 200,000 steps with finite fields and bounded speeds."""
+    from paper_1710_10569_gb300 import experiments as X
+    r = X.stability(Ra=1e9, ny=220, steps=200000, storage=storage)
+    assert r["finite"]
+    assert r["max_speed_over_uc"] < 3.0
+    assert r["nu"] > 1.0

@@ -432,3 +432,62 @@ def test_nusselt_and_residual_definitions():
     r2 = oracle.residual((5 * u, 5 * u, 5 * T), (5.5 * u, 5.5 * u, 5.5 * T), 0.0, 0.0)
     assert r1 == pytest.approx(r2, rel=1e-12)
     assert r1 == pytest.approx(0.1 / 1.1, rel=1e-12)
+
+
+# ----------------------------------------------------------------------------- thermal-only mode
+
+
+def test_thermal_only_collision_equals_coupled_d2q5_part():
+    """With the velocity the coupled step would compute, the thermal-only D2Q5 collision gives the
+    same post-collision g (the two modes share Eqs. 16-21)."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        p = rand_params(rng)
+        f, g = rand_pops(rng)
+        rho, ux, uy, T, Fx, Fy = macro(f, g, p)
+        _, go = oracle.collide_node(p, f, g)
+        got = oracle.collide_thermal_node(p, g, ux, uy)
+        np.testing.assert_allclose(got, go, atol=1e-15)
+
+
+def test_thermal_only_moving_frame_diffusivity():
+    """Sec. 3.1 exactly as the paper runs it: only the D2Q5 equation, velocity (0, A) given, Ma = 0.3;
+    the measured diffusivity equals alpha = 0.05 within 0.1%."""
+    L, alpha, B = 100, 0.05, 0.01
+    nx, ny = 2, L
+    A_ = 0.3 * W.CS
+    phi = 2 * math.pi / L
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    p = W.default_params(nu=0.05, kappa=alpha, T0=1.0)
+    p["thermal_only"] = 1
+    o = oracle.Oracle(nx, ny, p)
+    o.init(np.ones((ny, nx)), np.zeros((ny, nx)), A_ * np.ones((ny, nx)), 1.0 + B * np.sin(phi * y))
+
+    def amp():
+        c = o.fields()[3][:, 0] - 1.0
+        return abs(np.sum(c * np.exp(-1j * phi * np.arange(ny)))) * 2 / ny
+
+    o.step(500)
+    a1 = amp()
+    o.step(2000)
+    a2 = amp()
+    assert -math.log(a2 / a1) / (phi * phi * 2000) == pytest.approx(alpha, rel=1e-3)
+    np.testing.assert_allclose(o.fields()[2], A_)
+
+
+def test_thermal_only_conserves_heat_in_a_closed_box():
+    """Adiabatic walls and a divergence-free cellular flow: sum g is conserved exactly."""
+    n = 24
+    p = W.default_params(kappa=0.03, wall=(A, A, A, A))
+    p["thermal_only"] = 1
+    x, y = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5)
+    k = math.pi / n
+    ux = 0.05 * np.sin(k * x) * np.cos(k * y)
+    uy = -0.05 * np.cos(k * x) * np.sin(k * y)
+    T = np.random.default_rng(3).uniform(-0.5, 0.5, (n, n))
+    o = oracle.Oracle(n, n, p)
+    o.init(np.ones((n, n)), ux, uy, T)
+    _, g0 = o.populations()
+    o.step(400)
+    _, g1 = o.populations()
+    assert g1.sum() == pytest.approx(g0.sum(), rel=1e-13)

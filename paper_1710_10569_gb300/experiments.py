@@ -20,9 +20,15 @@ from . import workloads as W
 TABLE1_RA = (2000, 2500, 3000, 5000, 10000, 20000, 30000, 50000)
 
 
-def table1(storage=W.STORAGE_F64, steps: int = 200000, ras=TABLE1_RA):
-    """Nu after `steps` steps for each Ra of Table 1, all instances in one batch."""
+def table1(storage=W.STORAGE_F64, steps: int = 200000, ras=TABLE1_RA, seed_T: float = 0.0, seed: int = 0):
+    """Nu after `steps` steps for each Ra of Table 1, all instances in one batch. seed_T > 0 adds a
+    seeded uniform temperature disturbance of that amplitude to the paper's initial state (reduced
+    precision storage cannot grow the instability from disturbances below its resolution)."""
     probs = [W.rayleigh_benard_table1(float(ra), storage=storage) for ra in ras]
+    if seed_T > 0:
+        rng = np.random.default_rng(seed)
+        for p in probs:
+            p.T = p.T + rng.uniform(-seed_T, seed_T, p.T.shape)
     b = clb.Batch(probs)
     b.step(steps)
     nu, er = b.diagnostics()
@@ -70,10 +76,10 @@ def critical_rayleigh(ras=(1702, 1704, 1706, 1708, 1710), storage=W.STORAGE_F64,
     return {"ra": list(ras), "growth_rate": rates, "ra_c": float(-icpt / slope)}
 
 
-def ma_sweep(Ra: float, mas=(0.1, 0.15, 0.2, 0.25, 0.3), storage=W.STORAGE_F64, tol: float = 1e-9,
+def ma_sweep(Ra: float, mas=(0.1, 0.15, 0.2, 0.25, 0.3), storage=W.STORAGE_F64, tol: float = 1e-7,
              check: int = 1000, max_steps: int = 600000):
-    """For each Ma: the step count at which Nu changes by less than `tol` between checks `check`
-    steps apart, and that Nu (batched; instances stop counting when they converge)."""
+    """For each Ma: the step count at which Nu changes by less than `tol` (relative) between checks
+    `check` steps apart, and that Nu (batched; instances stop counting when they converge)."""
     probs = [W.rayleigh_benard_table1(Ra, Ma=m, storage=storage) for m in mas]
     b = clb.Batch(probs)
     prev = np.full(len(mas), np.nan)
@@ -87,7 +93,7 @@ def ma_sweep(Ra: float, mas=(0.1, 0.15, 0.2, 0.25, 0.3), storage=W.STORAGE_F64, 
         nu, _ = b.diagnostics()
         for k in range(len(mas)):
             if active[k]:
-                if nu[k] > 1.01 and abs(nu[k] - prev[k]) < tol:
+                if nu[k] > 1.01 and abs(nu[k] - prev[k]) < tol * nu[k]:
                     active[k] = False
                     steps[k] = done
                     nus[k] = nu[k]

@@ -81,6 +81,10 @@ typedef struct clb_params {
     double T_ref;     /* FP16 deviation base for g (normally T0) */
     double u_ref;     /* residual floor scale for u (0: no floor) */
     double dT_ref;    /* residual floor scale for T (0: no floor) */
+    double u_wall[4][2]; /* velocity of each wall (sides -x, +x, -y, +y; ignored on periodic sides):
+                          * f_i = f*_opp + [f^eq_i - f^eq_opp](rho0, u_w) (moving-wall bounce-back,
+                          * tangential motion and normal injection, Sec. 3.2) and
+                          * g_i = -g*_opp + T_w (cs2_T + u_w,n^2) on Dirichlet walls */
 } clb_params;
 
 typedef struct clb_handle clb_handle;

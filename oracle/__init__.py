@@ -52,7 +52,7 @@ class _Params(ctypes.Structure):
                 ("s_b", ctypes.c_double), ("s_3", ctypes.c_double), ("s_4", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
                 ("Fv", ctypes.c_double * 2), ("wall", ctypes.c_int * 4), ("T_wall", ctypes.c_double * 4),
-                ("thermal_only", ctypes.c_int)]
+                ("thermal_only", ctypes.c_int), ("u_wall", ctypes.c_double * 8)]
 
 
 def _load():
@@ -102,6 +102,9 @@ def _params(p: dict, nx: int = 2, ny: int = 2) -> _Params:
         s.wall[i] = int(p["wall"][i])
         s.T_wall[i] = float(p["T_wall"][i])
     s.thermal_only = int(p.get("thermal_only", 0))
+    uw = p.get("u_wall", ((0.0, 0.0),) * 4)
+    for side in range(4):
+        s.u_wall[2 * side], s.u_wall[2 * side + 1] = float(uw[side][0]), float(uw[side][1])
     return s
 
 

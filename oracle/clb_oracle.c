@@ -54,6 +54,7 @@ typedef struct {
     int wall[4];
     double T_wall[4];
     int thermal_only; /* 1: only the D2Q5 equation, with the velocity set by orc_set_velocity */
+    double u_wall[4][2]; /* velocity of each wall (sides -x, +x, -y, +y) */
 } orc_params;
 
 typedef struct {
@@ -64,6 +65,8 @@ typedef struct {
     double MT[Q5][Q5], MTinv[Q5][Q5], ST[Q5][Q5];
     int opp[Q9];
     double wT[Q5];         /* D2Q5 rest weights, g^eq(T=1, u=0) */
+    double fwall[4][Q9];   /* f^eq(rho0, u_wall) of each side */
+    double gwall[4][Q5];   /* g^eq(T_wall, u_wall) of each side */
     double *f, *g;         /* pre-collision populations at the current time, [q][y][x] */
     double *fs, *gs;       /* post-collision scratch */
     double *uxp, *uyp;     /* prescribed velocity of the thermal-only mode, [y][x] */
@@ -338,6 +341,19 @@ static size_t nodes(const orc_sim *s) { return (size_t)s->p.nx * (size_t)s->p.ny
 /* Streaming, Eqs. (12) and (22), pulled: population i at x comes from x - e_i. When x - e_i lies
  * beyond a wall, the boundary rule of reading r10 supplies it from the node's own post-collision
  * populations. Periodic sides wrap. */
+static void equilibrium(const orc_sim *s, double rho, double ux, double uy, double T, double f[Q9],
+                        double g[Q5]);
+
+/* Equilibria of the walls, used by the moving-wall bounce-back and the anti-bounce-back:
+ * f_i = f*_opp + [f^eq_i - f^eq_opp](rho0, u_w) and g_i = -g*_opp + [g^eq_i + g^eq_opp](T_w, u_w)
+ * (reading r10; at u_w = 0 they reduce to plain bounce-back and g_i = -g*_opp + 2 w^T_i T_w). */
+static void wall_equilibria(orc_sim *s)
+{
+    for (int side = 0; side < 4; ++side)
+        equilibrium(s, s->p.rho0, s->p.u_wall[side][0], s->p.u_wall[side][1], s->p.T_wall[side],
+                    s->fwall[side], s->gwall[side]);
+}
+
 static void stream(orc_sim *s)
 {
     const orc_params *p = &s->p;
@@ -360,10 +376,11 @@ static void stream(orc_sim *s)
                     s->f[i * n + here] = s->fs[i * n + src];
                     if (i < Q5) s->g[i * n + here] = s->gs[i * n + src];
                 } else {
-                    s->f[i * n + here] = s->fs[o * n + here]; /* halfway bounce-back */
+                    /* halfway bounce-back, with the wall's momentum when it moves */
+                    s->f[i * n + here] = s->fs[o * n + here] + (s->fwall[side][i] - s->fwall[side][o]);
                     if (i < Q5) {
                         if (p->wall[side] == ORC_DIRICHLET) /* anti-bounce-back */
-                            s->g[i * n + here] = -s->gs[o * n + here] + 2.0 * s->wT[i] * p->T_wall[side];
+                            s->g[i * n + here] = -s->gs[o * n + here] + (s->gwall[side][i] + s->gwall[side][o]);
                         else                                /* adiabatic: bounce-back */
                             s->g[i * n + here] = s->gs[o * n + here];
                     }
@@ -401,6 +418,7 @@ int orc_create(const orc_params *p, orc_sim **out)
     if (!s) return -2;
     s->p = *p;
     build_constants(s);
+    wall_equilibria(s);
     const size_t n = nodes(s);
     s->f = (double *)calloc(Q9 * n, sizeof(double));
     s->fs = (double *)calloc(Q9 * n, sizeof(double));

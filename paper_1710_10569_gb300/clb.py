@@ -39,7 +39,7 @@ class clb_params(ctypes.Structure):
                 ("s_3", ctypes.c_double), ("s_4", ctypes.c_double), ("lambda2", ctypes.c_double),
                 ("cs2_T", ctypes.c_double), ("Fv", ctypes.c_double * 2), ("wall", ctypes.c_int * 4),
                 ("T_wall", ctypes.c_double * 4), ("storage", ctypes.c_int), ("T_ref", ctypes.c_double),
-                ("u_ref", ctypes.c_double), ("dT_ref", ctypes.c_double)]
+                ("u_ref", ctypes.c_double), ("dT_ref", ctypes.c_double), ("u_wall", ctypes.c_double * 8)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -142,6 +142,9 @@ def params(p: dict) -> clb_params:
         s.wall[i] = int(p["wall"][i])
         s.T_wall[i] = float(p["T_wall"][i])
     s.storage = int(p["storage"])
+    uw = p.get("u_wall", ((0.0, 0.0),) * 4)
+    for side in range(4):
+        s.u_wall[2 * side], s.u_wall[2 * side + 1] = float(uw[side][0]), float(uw[side][1])
     return s
 
 

@@ -116,6 +116,8 @@ struct LatParams {
     A lambda1, lambda2, cs2T; // D2Q5 rates and sound speed squared
     A Fvx, Fvy, gb, T0;       // F = (Fvx, Fvy + gb (T - T0)), gb = rho0 * g_beta
     A rho_b, T_b;             // rest state the buffers are stored against (0 for FP64)
+    int moving;               // some wall moves: fbb holds its momentum terms
+    A fbb[4][9];              // [f^eq_i - f^eq_opp](rho0, u_wall of the side), added on bounce-back
 };
 
 // 1-D rest weights of D2Q9 (w(0) = 2/3, w(+-1) = 1/6; w_i = w(e_x) w(e_y)) and D2Q5 weights.
@@ -198,6 +200,19 @@ __device__ __forceinline__ void finish_pull(const LatParams<A>& P, const T raw[N
         if ((wall_mask & 2) && P.kind[1] == WALL_DIRICHLET) g[3] = P.Tw_c2[1] - g[3];
         if ((wall_mask & 4) && P.kind[2] == WALL_DIRICHLET) g[2] = P.Tw_c2[2] - g[2];
         if ((wall_mask & 8) && P.kind[3] == WALL_DIRICHLET) g[4] = P.Tw_c2[3] - g[4];
+        if (P.moving) {
+            // moving walls: f_i = f*_opp + [f^eq_i - f^eq_opp](rho0, u_w); a diagonal that crosses
+            // both a y wall and an x wall takes the y wall's velocity
+            const bool L = wall_mask & 1, R = wall_mask & 2, B = wall_mask & 4, T = wall_mask & 8;
+            if (L) f[1] += P.fbb[0][1];
+            if (R) f[3] += P.fbb[1][3];
+            if (B) f[2] += P.fbb[2][2];
+            if (T) f[4] += P.fbb[3][4];
+            if (L || B) f[5] += P.fbb[B ? 2 : 0][5];
+            if (R || B) f[6] += P.fbb[B ? 2 : 1][6];
+            if (R || T) f[7] += P.fbb[T ? 3 : 1][7];
+            if (L || T) f[8] += P.fbb[T ? 3 : 0][8];
+        }
     }
 }
 

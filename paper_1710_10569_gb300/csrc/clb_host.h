@@ -95,9 +95,23 @@ LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
     const bool dev = p.storage != ST_F64;
     P.rho_b = dev ? A(p.rho0) : A(0);
     P.T_b = dev ? A(p.T_ref) : A(0);
+    // Wall terms from the equilibria of the wall state (rho0, u_w) and (T_w, u_w): the moving-wall
+    // bounce-back f_i = f*_opp + [f^eq_i - f^eq_opp] and the anti-bounce-back g_i = -g*_opp +
+    // [g^eq_i + g^eq_opp] = -g*_opp + T_w (cs2_T + u_w,axis^2) for the pair i/opp along the wall's
+    // normal (Eqs. 9 and 20 back-transformed: f^eq_i = rho p(e_x; u_x) p(e_y; u_y) with the 1-D
+    // equilibrium p(0; u) = 2/3 - u^2, p(+-1; u) = (1/3 + u^2 +- u)/2).
+    auto p1 = [](int e, double u) { return e == 0 ? 2.0 / 3.0 - u * u : 0.5 * (1.0 / 3.0 + u * u + e * u); };
+    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    P.moving = 0;
     for (int s = 0; s < 4; ++s) {
         P.kind[s] = p.wall[s];
-        P.Tw_c2[s] = A(p.cs2_T * (p.T_wall[s] - (dev ? p.T_ref : 0.0)));
+        const double ux = p.u_wall[s][0], uy = p.u_wall[s][1];
+        const double un = s < 2 ? ux : uy;
+        P.Tw_c2[s] = A(p.T_wall[s] * (p.cs2_T + un * un) - p.cs2_T * (dev ? p.T_ref : 0.0));
+        for (int i = 0; i < 9; ++i)
+            P.fbb[s][i] = A(p.rho0 * (p1(ex[i], ux) * p1(ey[i], uy) - p1(-ex[i], ux) * p1(-ey[i], uy)));
+        if (p.wall[s] != CLB_PERIODIC && (ux != 0.0 || uy != 0.0)) P.moving = 1;
     }
     const double s_nu = rate_nu(p.nu);
     P.s_nu = A(s_nu);

@@ -359,14 +359,16 @@ __global__ void k_init(typename Storage<ST>::T* __restrict__ dst, const LatParam
         if (sy >= P.ny) { if (P.per_y) sy -= P.ny; else side = 3; }
         long long slot;
         int plane;
+        A fv = f[i];
         if (side < 0) {
             plane = i;
             slot = (long long)sy * P.pitch + sx;
         } else {
             plane = OPP[i];
             slot = (long long)y * P.pitch + x;
+            if (P.moving) fv = fv - P.fbb[side][i];
         }
-        dst[plane * P.plane + slot] = from_a(f[i], (E*)nullptr);
+        dst[plane * P.plane + slot] = from_a(fv, (E*)nullptr);
         if (i < 5) {
             A v = g[i];
             if (side >= 0 && P.kind[side] == WALL_DIRICHLET) v = P.Tw_c2[side] - v;

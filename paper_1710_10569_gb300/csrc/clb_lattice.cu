@@ -43,6 +43,10 @@ clb_status validate(int nx, int ny, const clb_params* p)
                            p->T_wall[2], p->T_wall[3], p->T_ref, p->u_ref, p->dT_ref};
     for (double v : vals)
         if (!std::isfinite(v)) return set_error(CLB_EINVAL, "non-finite parameter");
+    for (int s = 0; s < 4; ++s)
+        for (int c = 0; c < 2; ++c)
+            if (!std::isfinite(p->u_wall[s][c]) || std::fabs(p->u_wall[s][c]) > 0.4)
+                return set_error(CLB_EINVAL, "u_wall[%d][%d] must be finite with |u| <= 0.4", s, c);
     if (!(p->nu > 0)) return set_error(CLB_EINVAL, "nu must be > 0 (got %g)", p->nu);
     if (!(p->kappa > 0)) return set_error(CLB_EINVAL, "kappa must be > 0 (got %g)", p->kappa);
     if (!(p->rho0 > 0)) return set_error(CLB_EINVAL, "rho0 must be > 0");

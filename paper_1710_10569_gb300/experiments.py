@@ -134,3 +134,32 @@ def stability(Ra: float = 1e9, ny: int = 220, aspect: int = 2, Pr: float = 0.71,
     lat.close()
     return {"Ra": Ra, "ny": ny, "nx": aspect * ny, "steps": done, "finite": finite, "nu": nu,
             "max_speed_over_uc": umax, "nu_visc": prob.params["nu"]}
+
+
+def normal_plate_convergence(Ls=(30, 60, 90, 120, 150), Re=(10.0, 20.0, 30.0), Pr: float = 0.71,
+                             storage=W.STORAGE_F64, tol: float = 1e-11, max_steps: int = 1500000):
+    """Sec. 3.2: steady profiles of the normal-plate channel for every (Re, L) in one batch, their
+    relative errors E_u and E_T against the analytic profiles, and the least-squares slopes of
+    log E against log(1/L) per Re (the paper finds slopes of about 2)."""
+    probs = [W.normal_plate_channel(L=L, Re=re, Pr=Pr, storage=storage) for re in Re for L in Ls]
+    b = clb.Batch(probs)
+    steps, er, status = b.run(tol, max_steps, 1000)
+    out = {"Re": list(Re), "L": list(Ls), "E_u": {}, "E_T": {}, "slope_u": {}, "slope_T": {},
+           "steps": steps.tolist()}
+    k = 0
+    for re in Re:
+        eu, et = [], []
+        for L in Ls:
+            prob = probs[k]
+            _, ux, uy, T = b.fields(k)
+            ua, Ta = W.normal_plate_analytic(prob)
+            eu.append(float(np.sqrt(np.sum((ux[:, 0] - ua) ** 2) / np.sum(ua ** 2))))
+            et.append(float(np.sqrt(np.sum((T[:, 0] - Ta) ** 2) / np.sum(Ta ** 2))))
+            k += 1
+        out["E_u"][str(re)] = eu
+        out["E_T"][str(re)] = et
+        x = np.log(1.0 / np.array(Ls, dtype=float))
+        out["slope_u"][str(re)] = float(np.polyfit(x, np.log(eu), 1)[0])
+        out["slope_T"][str(re)] = float(np.polyfit(x, np.log(et), 1)[0])
+    b.close()
+    return out

@@ -39,6 +39,7 @@ def default_params(**overrides) -> dict:
         Fv=(0.0, 0.0),
         wall=(WALL_PERIODIC,) * 4, T_wall=(0.0,) * 4,
         storage=STORAGE_F64, T_ref=0.0, u_ref=0.0, dT_ref=0.0,
+        u_wall=((0.0, 0.0),) * 4,
     )
     for k, v in overrides.items():
         if k not in p:
@@ -164,8 +165,10 @@ def rayleigh_benard_table1(Ra: float, Ma: float = 0.3, nx: int = 60, ny: int = 3
                    meta=dict(Ra=Ra, Pr=Pr, Ma=Ma, u_c=u_c))
 
 
-def random_problem(nx: int, ny: int, seed: int, storage=STORAGE_F64, walls=None) -> Problem:
-    """A small problem with random-but-stable parameters and fields, used for parity sweeps."""
+def random_problem(nx: int, ny: int, seed: int, storage=STORAGE_F64, walls=None,
+                   moving: bool = False) -> Problem:
+    """A small problem with random-but-stable parameters and fields, used for parity sweeps
+    (with `moving`, every wall also gets a random velocity of up to 0.05 per component)."""
     rng = np.random.default_rng(seed)
     if walls is None:
         walls = [(WALL_PERIODIC,) * 4,
@@ -183,8 +186,43 @@ def random_problem(nx: int, ny: int, seed: int, storage=STORAGE_F64, walls=None)
     ux = rng.uniform(-0.05, 0.05, (ny, nx))
     uy = rng.uniform(-0.05, 0.05, (ny, nx))
     T = rng.uniform(-0.5, 0.5, (ny, nx))
+    if moving:
+        p["u_wall"] = tuple((float(a), float(b)) for a, b in rng.uniform(-0.05, 0.05, (4, 2)))
     return Problem(f"random_{nx}x{ny}_s{seed}", nx, ny, p, rho, ux, uy, T,
                    nu_axis=0 if walls[0] != WALL_PERIODIC else 1, meta=dict(seed=seed))
+
+
+def normal_plate_channel(L: int = 50, Re: float = 10.0, Pr: float = 0.71, nu: float = 0.1,
+                         nx: int = 5, storage=STORAGE_F64, lambda2=None) -> Problem:
+    """Sec. 3.2: channel of width L, periodic in x; the bottom plate (y = 0, at rest, T_L = 0)
+    injects a uniform normal flow v0 and the top plate (y = L, moving with u0, T_H = 1) withdraws it;
+    u0 = v0 = Re nu / L. Walls lie halfway between nodes, so node j sits at y = j + 1/2. lambda2
+    defaults to the zero-numerical-slip value 12 (lambda1 - 2) / (lambda1 - 12) the paper uses."""
+    ny = L
+    v0 = Re * nu / L
+    alpha = nu / Pr
+    lam1 = 1.0 / (alpha / 0.25 + 0.5)
+    lam2 = 12 * (lam1 - 2) / (lam1 - 12) if lambda2 is None else lambda2
+    y = (np.arange(ny) + 0.5)[:, None] * np.ones((1, nx))
+    p = default_params(nu=nu, kappa=alpha, lambda2=lam2, storage=storage,
+                       wall=(WALL_PERIODIC, WALL_PERIODIC, WALL_DIRICHLET, WALL_DIRICHLET),
+                       T_wall=(0.0, 0.0, 0.0, 1.0), u_wall=((0, 0), (0, 0), (0.0, v0), (v0, v0)),
+                       u_ref=v0, dT_ref=1.0)
+    ux = v0 * y / L
+    uy = np.full((ny, nx), v0)
+    T = y / L
+    return Problem(f"normal_plate_L{L}_Re{Re:g}_Pr{Pr:g}", nx, ny, p, np.ones((ny, nx)), ux, uy, T,
+                   nu_axis=1, meta=dict(L=L, Re=Re, Pr=Pr, v0=v0))
+
+
+def normal_plate_analytic(prob: Problem):
+    """Analytic steady profiles of Sec. 3.2 at the node heights: u/u0 = (exp(Re y/L) - 1)/(exp(Re) - 1)
+    and (T - T_L)/dT = (exp(Re Pr y/L) - 1)/(exp(Re Pr) - 1); v = v0."""
+    L, Re, Pr, v0 = (prob.meta[k] for k in ("L", "Re", "Pr", "v0"))
+    y = np.arange(prob.ny) + 0.5
+    u = v0 * (np.exp(Re * y / L) - 1) / (math.exp(Re) - 1)
+    T = (np.exp(Re * Pr * y / L) - 1) / (math.exp(Re * Pr) - 1)
+    return u, T
 
 
 def batch_cavities(count: int = 256, seed: int = 0, lo: int = 64, hi: int = 512,

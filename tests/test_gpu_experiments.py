@@ -171,3 +171,13 @@ def test_high_rayleigh_stability(clb, storage):
     assert r["finite"]
     assert r["max_speed_over_uc"] < 3.0
     assert r["nu"] > 1.0
+
+
+def test_normal_plate_second_order_convergence(clb):
+    """Sec. 3.2 on the GPU: Pr = 0.71, Re = 10, 20, 30, L = 30 .. 150 in one batch; the slopes of
+    log E_u and log E_T against log(1/L) lie within 1.9 .. 2.1 (the paper: about 2)."""
+    from paper_1710_10569_gb300 import experiments as X
+    r = X.normal_plate_convergence()
+    for re in ("10.0", "20.0", "30.0"):
+        assert 1.9 < r["slope_u"][re] < 2.1, r
+        assert 1.9 < r["slope_T"][re] < 2.1, r

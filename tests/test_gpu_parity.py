@@ -128,6 +128,22 @@ def test_random_problems_reduced_precision(clb, storage, seed):
     compare(f"rand67x45_s{seed}_{W.STORAGE_NAMES[storage]}", got, exp, tol(storage, 60), prob.params)
 
 
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_moving_walls(clb, storage, seed):
+    """Random wall velocities on every wall layout: moving-wall bounce-back and the anti-bounce-back
+    with the wall velocity, including corners, on the scalar wall path."""
+    prob = W.random_problem(45, 38, seed=seed, storage=storage, moving=True)
+    _, _, got, exp = run_both(clb, prob, 60)
+    compare(f"moving45x38_s{seed}_{W.STORAGE_NAMES[storage]}", got, exp, tol(storage, 60), prob.params)
+    if storage == F64:
+        lat = clb.Lattice.from_problem(prob)
+        o = oracle.Oracle.from_problem(prob)
+        f, g = lat.populations()
+        fo, go = o.populations()
+        assert normwise(f, fo) <= 1e-14 and normwise(g, go) <= 1e-14
+
+
 def test_initial_fields_match_oracle(clb):
     """Step 0: the inverse-stream initialisation reproduces the oracle's f(x,0) = f^eq exactly,
     walls included."""

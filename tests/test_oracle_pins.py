@@ -491,3 +491,43 @@ def test_thermal_only_conserves_heat_in_a_closed_box():
     o.step(400)
     _, g1 = o.populations()
     assert g1.sum() == pytest.approx(g0.sum(), rel=1e-13)
+
+
+# ----------------------------------------------------------------------------- moving walls (Sec. 3.2)
+
+
+def test_couette_flow_between_moving_walls_is_linear():
+    """Top wall moving at u0, bottom at rest, no force: the steady profile is the straight line
+    through the wall velocities, u = u0 (y + 1/2)/ny, to rounding."""
+    ny, u0 = 16, 0.05
+    p = W.default_params(nu=0.1, kappa=0.1, wall=(P, P, A, A), u_wall=((0, 0), (0, 0), (0, 0), (u0, 0)))
+    z = np.zeros((ny, 2))
+    o = _run(2, ny, p, np.ones((ny, 2)), z, z, z, 30000)
+    _, ux, uy, _ = o.fields()
+    np.testing.assert_allclose(ux[:, 0], u0 * (np.arange(ny) + 0.5) / ny, atol=1e-12)
+    assert np.max(np.abs(uy)) < 1e-13
+
+
+def _plate_errors(L, Re=10.0, Pr=0.71):
+    prob = W.normal_plate_channel(L=L, Re=Re, Pr=Pr)
+    o = oracle.Oracle.from_problem(prob)
+    oracle.run_to_steady(o, 1e-11, 400000, 500)
+    _, ux, uy, T = o.fields()
+    ua, Ta = W.normal_plate_analytic(prob)
+    Eu = np.sqrt(np.sum((ux[:, 0] - ua) ** 2) / np.sum(ua ** 2))
+    ET = np.sqrt(np.sum((T[:, 0] - Ta) ** 2) / np.sum(Ta ** 2))
+    return Eu, ET, np.max(np.abs(uy - prob.meta["v0"])) / prob.meta["v0"]
+
+
+def test_normal_plate_channel_second_order():
+    """Sec. 3.2: moving upper plate with normal injection/withdrawal and a temperature difference.
+    The steady u and T profiles match the analytic exponential profiles (E_u, E_T < 1% at L = 30)
+    and the errors fall with the second power of the grid spacing from L = 30 to 60 (the paper
+    reports slopes of about 2); the normal velocity stays at v0."""
+    e30 = _plate_errors(30)
+    e60 = _plate_errors(60)
+    assert e30[0] < 1e-2 and e30[1] < 1e-2
+    assert e30[2] < 1e-4 and e60[2] < 1e-4
+    for k in (0, 1):
+        order = math.log(e30[k] / e60[k]) / math.log(2)
+        assert 1.9 < order < 2.1

@@ -22,12 +22,14 @@ __device__ __forceinline__ E lane_down(E v) { return __shfl_down_sync(0xffffffff
 // One time step for V consecutive nodes x0 .. x0+V-1 of row y, called by all 32 lanes of a warp
 // on the same row with x0 = (first x of the warp) + lane * V: pull the 14 populations (Eqs. 12,
 // 22, with the wall rules), collide (Eqs. 3-11, 13, 16-21, 23), store at the nodes.
-// Warps whose nodes and pulled neighbours all lie inside the lattice or across periodic sides take
-// the vector path: per population plane one aligned V-wide load of the row the pull comes from;
-// the population pulled from x-1 (x+1) of the first (last) node of a thread is the neighbouring
-// lane's last (first) element, passed by a warp shuffle, and lane 0 (lane 31) loads the one
-// element beyond the warp. Other warps (a wall or the ragged end of a row) gather node by node.
-// Both paths feed identical values to the identical collision.
+// Warps whose 32 * V nodes all lie inside the row take the vector path: per population plane one
+// aligned V-wide load of the row the pull comes from; the population pulled from x-1 (x+1) of the
+// first (last) node of a thread is the neighbouring lane's last (first) element, passed by a warp
+// shuffle, and lane 0 (lane 31) loads the one element beyond the warp. Walls are handled in the
+// same path: on a wall row the planes pulled across the wall come from the node's own opposite
+// plane (no shift), and at an x wall lane 0 (lane 31) loads its node's own opposite values instead
+// of the missing neighbour; the wall terms are then added per node by finish_pull. The ragged end
+// of a row gathers node by node. Every path feeds identical values to the identical collision.
 template <int ST, int V>
 __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* __restrict__ src,
                                                 typename Storage<ST>::T* __restrict__ dst,
@@ -38,61 +40,76 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
     using E = typename Storage<ST>::T;
     using PK = Pack<E, V>;
     const int wx0 = x0 - lane * V, wx1 = wx0 + 32 * V - 1;
-    const bool fast = (P.per_y || (y >= 1 && y <= P.ny - 2)) && wx1 < P.nx &&
-                      (P.per_x || (wx0 >= 1 && wx1 <= P.nx - 2));
-    if (fast) {
+    if (wx1 < P.nx) {
+        const bool wallB = !P.per_y && y == 0;
+        const bool wallT = !P.per_y && y == P.ny - 1;
+        const bool wallL = !P.per_x && wx0 == 0;
+        const bool wallR = !P.per_x && wx1 == P.nx - 1;
         const int ym = y > 0 ? y - 1 : P.ny - 1;
         const int yp = y < P.ny - 1 ? y + 1 : 0;
         const int rc = y * P.pitch, rm = ym * P.pitch, rp = yp * P.pitch;
         const int xl = wx0 > 0 ? wx0 - 1 : P.nx - 1;  // column left of the warp (lane 0)
         const int xr = wx1 < P.nx - 1 ? wx1 + 1 : 0;  // column right of the warp (lane 31)
         const long long pl = P.plane;
-        // plane, row offset, x shift (0: own column, +1: pulled from x-1, -1: pulled from x+1)
-        const int PLANE[NPOP] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13};
+        // plane, row (0: y, 1: y-1, 2: y+1) and x shift (+1: pulled from x-1, -1: from x+1)
         const int SHIFT[NPOP] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 1, 0, -1, 0};
-        const int ROWSEL[NPOP] = {0, 0, 1, 0, 2, 1, 1, 2, 2, 0, 0, 1, 0, 2};  // 0: y, 1: y-1, 2: y+1
+        const int ROWSEL[NPOP] = {0, 0, 1, 0, 2, 1, 1, 2, 2, 0, 0, 1, 0, 2};
+        const int OPP[NPOP] = {0, 3, 4, 1, 2, 7, 8, 5, 6, 9, 12, 13, 10, 11};
         PK pk[NPOP];
-#pragma unroll
-        for (int i = 0; i < NPOP; ++i) {
-            const int r = ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp;
-            pk[i] = *reinterpret_cast<const PK*>(src + PLANE[i] * pl + r + x0);
-        }
         E edge[NPOP];
 #pragma unroll
         for (int i = 0; i < NPOP; ++i) {
-            const int r = ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp;
+            // a pull across the bottom (top) wall reads the node's own opposite plane
+            const bool across = (wallB && ROWSEL[i] == 1) || (wallT && ROWSEL[i] == 2);
+            const int plane = across ? OPP[i] : i;
+            const int r = across ? rc : (ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp);
+            const int sh = across ? 0 : SHIFT[i];
+            pk[i] = *reinterpret_cast<const PK*>(src + plane * pl + r + x0);
             edge[i] = E(0);
-            if (SHIFT[i] == 1 && lane == 0) edge[i] = src[PLANE[i] * pl + r + xl];
-            if (SHIFT[i] == -1 && lane == 31) edge[i] = src[PLANE[i] * pl + r + xr];
+            if (sh == 1 && lane == 0)
+                edge[i] = wallL ? src[OPP[i] * pl + rc + 0] : src[plane * pl + r + xl];
+            if (sh == -1 && lane == 31)
+                edge[i] = wallR ? src[OPP[i] * pl + rc + (P.nx - 1)] : src[plane * pl + r + xr];
         }
         E raw[V][NPOP];
 #pragma unroll
         for (int i = 0; i < NPOP; ++i) {
-            if (SHIFT[i] == 0) {
+            const bool across = (wallB && ROWSEL[i] == 1) || (wallT && ROWSEL[i] == 2);
+            const int sh = across ? 0 : SHIFT[i];
+            // the shuffles run on every lane whatever the shift, so that all lanes take part
+            const E up = lane_up(pk[i].e[V - 1]);
+            const E dn = lane_down(pk[i].e[0]);
+            if (sh == 0) {
 #pragma unroll
                 for (int k = 0; k < V; ++k) raw[k][i] = pk[i].e[k];
-            } else if (SHIFT[i] == 1) {
-                const E up = lane_up(pk[i].e[V - 1]);
+            } else if (sh == 1) {
                 raw[0][i] = lane == 0 ? edge[i] : up;
 #pragma unroll
                 for (int k = 1; k < V; ++k) raw[k][i] = pk[i].e[k - 1];
             } else {
-                const E dn = lane_down(pk[i].e[0]);
                 raw[V - 1][i] = lane == 31 ? edge[i] : dn;
 #pragma unroll
                 for (int k = 0; k < V - 1; ++k) raw[k][i] = pk[i].e[k + 1];
             }
         }
+        const int rowmask = (wallB ? 4 : 0) | (wallT ? 8 : 0);
+        int mask[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            mask[k] = rowmask | ((wallL && lane == 0 && k == 0) ? 1 : 0) | ((wallR && lane == 31 && k == V - 1) ? 2 : 0);
         PK out[NPOP];
         if constexpr (Storage<ST>::DEV && V % 2 == 0) {
             // FP32 arithmetic: two nodes per packed f32x2 instruction
 #pragma unroll
             for (int k = 0; k < V; k += 2) {
+                A fa[9], ga[5], fb[9], gb[5];
+                finish_pull(P, raw[k], mask[k], fa, ga);
+                finish_pull(P, raw[k + 1], mask[k + 1], fb, gb);
                 F2 f[9], g[5];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = F2(to_a(raw[k][i]), to_a(raw[k + 1][i]));
+                for (int i = 0; i < 9; ++i) f[i] = F2(fa[i], fb[i]);
 #pragma unroll
-                for (int i = 0; i < 5; ++i) g[i] = F2(to_a(raw[k][9 + i]), to_a(raw[k + 1][9 + i]));
+                for (int i = 0; i < 5; ++i) g[i] = F2(ga[i], gb[i]);
                 collide_dev(P, f, g);
 #pragma unroll
                 for (int i = 0; i < NPOP; ++i) {
@@ -106,7 +123,7 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
 #pragma unroll
             for (int k = 0; k < V; ++k) {
                 A f[9], g[5];
-                finish_pull(P, raw[k], 0, f, g);
+                finish_pull(P, raw[k], mask[k], f, g);
                 collide_any<Storage<ST>::DEV>(P, f, g);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) out[i].e[k] = from_a(f[i], (E*)nullptr);

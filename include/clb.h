@@ -264,6 +264,9 @@ clb_status clb_serve_submit(clb_server *s, int nx, int ny, const clb_params *p, 
 /* One scheduling round: admit queued requests that fit, advance every resident request by
  * `chunk` steps, check residuals and retire converged ones. *active / *queued receive counts. */
 clb_status clb_serve_progress(clb_server *s, long chunk, int *active, int *queued);
+/* Drop a request: queued ones leave the queue, running ones release their slot and memory at
+ * once (no work of the server is in flight between calls). Its id becomes unknown. */
+clb_status clb_serve_cancel(clb_server *s, long req_id);
 /* Non-blocking state of a request: *done = 1 once retired. */
 clb_status clb_serve_poll(clb_server *s, long req_id, int *done, double *nu, long *steps,
                           double *er);

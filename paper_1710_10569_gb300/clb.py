@@ -99,6 +99,7 @@ _SIGS = {
     "clb_serve_submit": [_VP, _I, _I, _P(clb_params), _D, _D, _D, _D, _I, _L, ctypes.c_double, _P(_L)],
     "clb_serve_progress": [_VP, _L, _P(_I), _P(_I)],
     "clb_serve_poll": [_VP, _L, _P(_I), _D, _P(_L), _D],
+    "clb_serve_cancel": [_VP, _L],
     "clb_serve_fetch": [_VP, _L, _D, _D, _D, _D],
 }
 _RESTYPES = {"clb_destroy": None, "clb_batch_destroy": None, "clb_serve_close": None,
@@ -469,6 +470,9 @@ class Server:
         a, q = _I(), _I()
         _check(lib().clb_serve_progress(self._h, int(chunk), ctypes.byref(a), ctypes.byref(q)))
         return a.value, q.value
+
+    def cancel(self, rid: int):
+        _check(lib().clb_serve_cancel(self._h, int(rid)))
 
     def poll(self, rid: int):
         done, nu, steps, er = _I(), ctypes.c_double(), _L(), ctypes.c_double()

@@ -820,6 +820,30 @@ extern "C" clb_status clb_serve_progress(clb_server* s, long chunk, int* active,
     return CLB_OK;
 }
 
+extern "C" clb_status clb_serve_cancel(clb_server* s, long req_id)
+{
+    if (!s) return set_error(CLB_EINVAL, "server is NULL");
+    auto it = s->all.find(req_id);
+    if (it == s->all.end()) return set_error(CLB_EINVAL, "unknown request %ld", req_id);
+    Request* r = it->second.get();
+    auto q = std::find(s->queue.begin(), s->queue.end(), r);
+    if (q != s->queue.end()) s->queue.erase(q);
+    auto run = std::find(s->running.begin(), s->running.end(), r);
+    if (run != s->running.end()) {
+        // no kernel of this server is in flight between calls; release the slot and its memory
+        CLB_CUDA(cudaStreamSynchronize(s->E.stream));
+        Lattice* L = r->L.get();
+        s->E.members.erase(std::find(s->E.members.begin(), s->E.members.end(), L));
+        s->E.mark_dirty();
+        cudaFree(L->mem);
+        L->mem = nullptr;
+        s->used -= L->bytes;
+        s->running.erase(run);
+    }
+    s->all.erase(it);
+    return CLB_OK;
+}
+
 extern "C" clb_status clb_serve_poll(clb_server* s, long req_id, int* done, double* nu, long* steps, double* er)
 {
     if (!s) return set_error(CLB_EINVAL, "server is NULL");

@@ -141,3 +141,50 @@ def test_serve_budget_and_errors(clb):
         if not active and not queued:
             break
     assert srv.poll(rid)[0]
+
+
+def test_nan_in_one_instance_leaves_the_others_running(clb):
+    """A blown-up instance is reported as CLB_ENAN and retired; the others step on unaffected."""
+    probs = mixed_problems(F64, count=4)
+    b = clb.Batch(probs)
+    bad = probs[1]
+    T = bad.T.copy()
+    T[3, 4] = np.nan
+    b.init_fields(1, bad.rho, bad.ux, bad.uy, T)
+    steps, er, status = b.run(0.0, 200, 100)
+    assert status[1] == clb.CLB_ENAN and steps[1] == 100
+    assert all(status[k] == clb.CLB_OK and steps[k] == 200 for k in (0, 2, 3))
+    alone = clb.Batch([probs[2]])
+    alone.step(200)
+    for a, c in zip(b.fields(2), alone.fields(0)):
+        assert np.array_equal(a, c)
+
+
+def test_serve_cancel(clb):
+    srv = clb.Server(hbm_budget_bytes=64 << 20, max_slots=1, storage=F32)
+    a = srv.submit(W.cavity(32, storage=F32), step_cap=10 ** 6, tol=0.0)
+    b = srv.submit(W.cavity(24, storage=F32), step_cap=64, tol=0.0)
+    srv.progress(32)           # a runs, b waits for the only slot
+    srv.cancel(a)              # frees the slot
+    for _ in range(10):
+        active, queued = srv.progress(32)
+        if not active and not queued:
+            break
+    assert srv.poll(b)[0]
+    with pytest.raises(clb.CLBError):
+        srv.poll(a)
+
+
+@pytest.mark.parametrize("storage", [F64, F32])
+def test_widest_lattice(clb, storage):
+    """The largest edge the ABI accepts (2^20 nodes) on a 2-row channel, against the oracle."""
+    import oracle
+    prob = W.random_problem(1 << 20, 2, seed=2, storage=storage, moving=True)
+    lat = clb.Lattice.from_problem(prob)
+    lat.step(3)
+    got = lat.fields()
+    o = oracle.Oracle.from_problem(prob)
+    o.step(3)
+    exp = o.fields()
+    for a, e in zip(got[1:], exp[1:]):
+        assert np.max(np.abs(a - e)) <= (1e-12 if storage == F64 else 1e-5) * max(np.max(np.abs(e)), 0.05)

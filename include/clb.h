@@ -54,7 +54,13 @@ typedef enum {
 typedef enum {
     CLB_PERIODIC = 0,        /* wraps to the opposite side, which must also be periodic */
     CLB_WALL_DIRICHLET_T = 1,/* g_i = -g*_opp + cs2_T * T_wall (anti-bounce-back, 2 w_i = cs2_T) */
-    CLB_WALL_ADIABATIC = 2   /* g_i = g*_opp (zero heat flux) */
+    CLB_WALL_ADIABATIC = 2,  /* g_i = g*_opp (zero heat flux) */
+    CLB_WALL_WET = 3         /* the paper's own conditions (Sec. 3): the wall lies ON the end row of
+                              * nodes (y sides only, both, with periodic x; ny >= 3; H = ny - 1);
+                              * velocity by non-equilibrium bounce-back with the half-force
+                              * correction, temperature T_wall by non-equilibrium extrapolation
+                              * from the adjacent fluid node. Nusselt averages use the trapezoid
+                              * rule over [0, H]. */
 } clb_wall;
 
 /* Population storage. CLB_F64 stores f_i, g_i and computes in FP64. CLB_F32 and CLB_F16DEV store

@@ -30,7 +30,7 @@ _SO = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
-PERIODIC, DIRICHLET, ADIABATIC = 0, 1, 2
+PERIODIC, DIRICHLET, ADIABATIC, WET = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -220,7 +220,9 @@ def matrices(params: dict, ux: float, uy: float) -> dict:
 
 def nusselt(ux, uy, T, params: dict, axis: int) -> float:
     """Eq. (29): Nu = 1 + <u_axis (T - T0)> H / (alpha dT), the average taken over all nodes.
-    H is the node count along `axis` (walls halfway between nodes); dT is the difference of the
+    H is the node count along `axis` (walls halfway between nodes), one less for wet walls (walls
+    on the end rows of nodes, where the average is the trapezoid rule over [0, H]); dT is the
+    difference of the
     wall temperatures on that axis, the sign chosen so that heat flowing from the hot wall counts
     positive. alpha is the prescribed thermal diffusivity `kappa`."""
     u = ux if axis == 0 else uy
@@ -229,7 +231,16 @@ def nusselt(ux, uy, T, params: dict, axis: int) -> float:
     Tl, Th = params["T_wall"][lo], params["T_wall"][hi]
     dT = abs(Tl - Th) or 1.0
     sign = 1.0 if Tl >= Th else -1.0
-    mean = float(np.mean(u * (T - params["T0"])))
+    q = u * (T - params["T0"])
+    if params["wall"][lo] == WET:
+        # wet walls lie on the end rows of nodes: H = rows - 1 and the average over [0, H] is
+        # the trapezoid rule (half weight on the two wall rows)
+        H -= 1
+        w = np.ones(T.shape[0])
+        w[0] = w[-1] = 0.5
+        mean = float(np.sum(q * w[:, None]) / (T.shape[1] * H))
+    else:
+        mean = float(np.mean(q))
     return 1.0 + sign * mean * H / (params["kappa"] * dT)
 
 

@@ -25,6 +25,14 @@
  *   r10 Walls (stationary, halfway between nodes): f uses halfway bounce-back on every wall; g uses
  *       anti-bounce-back g_i = -g*_opp + 2 w^T_i T_w on Dirichlet walls and bounce-back g_i = g*_opp
  *       on adiabatic walls. w^T_i are the D2Q5 rest weights (g^eq at T=1, u=0).
+ *   r19 Wet walls (ORC_WET, the paper's own conditions, Sec. 3 first paragraph): the wall row of
+ *       nodes lies on the wall (y sides only, x periodic). After streaming, the populations that
+ *       would come from beyond the wall are set by non-equilibrium bounce-back, f_i = f_opp +
+ *       [f^eq_i - f^eq_opp](rho, u'), with u' = u_w - F/(2 rho) so that the force-corrected velocity
+ *       of Eq. (13) equals the wall's, rho from mass and normal momentum, and the tangential
+ *       momentum closed on the two diagonals; g at the wall node is set by non-equilibrium
+ *       extrapolation from the adjacent fluid node n, g_i = g^eq_i(T_w, u_w) + [g_i(n) -
+ *       g^eq_i(T(n), u(n))].
  * Parity is pinned by the tests in tests/test_oracle_pins.py (transform brute force, fixed point,
  * conservation, viscosity and diffusivity decay, Poiseuille, conduction, Table 1 Nusselt numbers).
  */
@@ -44,7 +52,7 @@ static const int EX[Q9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[Q9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 /* Side numbering for walls: 0 = -x, 1 = +x, 2 = -y, 3 = +y. Wall kinds. */
-enum { ORC_PERIODIC = 0, ORC_DIRICHLET = 1, ORC_ADIABATIC = 2 };
+enum { ORC_PERIODIC = 0, ORC_DIRICHLET = 1, ORC_ADIABATIC = 2, ORC_WET = 3 };
 
 typedef struct {
     int nx, ny;
@@ -389,6 +397,54 @@ static void stream(orc_sim *s)
         }
 }
 
+/* The wet-wall boundary pass of reading r19, on the streamed (pre-collision) state. */
+static void apply_wet_walls(orc_sim *s)
+{
+    const orc_params *p = &s->p;
+    const int nx = p->nx, ny = p->ny;
+    const size_t n = nodes(s);
+    for (int side = 2; side < 4; ++side) {
+        if (p->wall[side] != ORC_WET) continue;
+        const int yb = side == 2 ? 0 : ny - 1;
+        const int yn = side == 2 ? 1 : ny - 2;
+        const int nrm = side == 2 ? 1 : -1; /* direction into the fluid */
+        const double uwx = p->u_wall[side][0], uwy = p->u_wall[side][1], Tw = p->T_wall[side];
+        for (int x = 0; x < nx; ++x) {
+            const size_t b = (size_t)yb * nx + x, q = (size_t)yn * nx + x;
+            double f[Q9], g[Q5];
+            for (int i = 0; i < Q9; ++i) f[i] = s->f[i * n + b];
+            /* flow: non-equilibrium bounce-back */
+            const double Fx = p->Fv[0], Fy = p->Fv[1] + p->rho0 * p->g_beta * (Tw - p->T0);
+            double Z = 0.0, O = 0.0;
+            for (int i = 0; i < Q9; ++i) {
+                if (EY[i] == 0) Z += f[i];
+                if (EY[i] == -nrm) O += f[i];
+            }
+            const double rho = (Z + 2.0 * O - nrm * 0.5 * Fy) / (1.0 - nrm * uwy);
+            const double upx = uwx - 0.5 * Fx / rho, upy = uwy - 0.5 * Fy / rho;
+            double feq[Q9], geqw[Q5];
+            equilibrium(s, rho, upx, upy, Tw, feq, geqw);
+            for (int i = 0; i < Q9; ++i)
+                if (EY[i] == nrm) f[i] = f[s->opp[i]] + (feq[i] - feq[s->opp[i]]);
+            double Sx = 0.0;
+            for (int i = 0; i < Q9; ++i) Sx += f[i] * EX[i];
+            const double delta = 0.5 * (rho * upx - Sx);
+            for (int i = 0; i < Q9; ++i)
+                if (EY[i] == nrm && EX[i] != 0) f[i] += EX[i] * delta;
+            for (int i = 0; i < Q9; ++i) s->f[i * n + b] = f[i];
+            /* temperature: non-equilibrium extrapolation from the fluid node q */
+            double fq[Q9], gq[Q5], rq, uqx, uqy, Tq, Fqx, Fqy, fe[Q9], geqq[Q5], geqb[Q5];
+            for (int i = 0; i < Q9; ++i) fq[i] = s->f[i * n + q];
+            for (int i = 0; i < Q5; ++i) gq[i] = s->g[i * n + q];
+            macroscopic(s, fq, gq, &rq, &uqx, &uqy, &Tq, &Fqx, &Fqy);
+            equilibrium(s, rq, uqx, uqy, Tq, fe, geqq);
+            equilibrium(s, rho, uwx, uwy, Tw, fe, geqb);
+            for (int i = 0; i < Q5; ++i) g[i] = geqb[i] + (gq[i] - geqq[i]);
+            for (int i = 0; i < Q5; ++i) s->g[i * n + b] = g[i];
+        }
+    }
+}
+
 static void collide_all(orc_sim *s)
 {
     const long n = (long)nodes(s);
@@ -414,6 +470,10 @@ int orc_create(const orc_params *p, orc_sim **out)
 {
     *out = NULL;
     if (p->nx < 2 || p->ny < 2) return -1;
+    if (p->wall[0] == ORC_WET || p->wall[1] == ORC_WET) return -1; /* wet walls: y sides only */
+    if ((p->wall[2] == ORC_WET || p->wall[3] == ORC_WET) &&
+        (p->wall[0] != ORC_PERIODIC || p->ny < 3 || p->thermal_only))
+        return -1;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return -2;
     s->p = *p;
@@ -455,6 +515,7 @@ void orc_init(orc_sim *s, const double *rho, const double *ux, const double *uy,
         for (int i = 0; i < Q9; ++i) s->f[i * n + k] = f[i];
         for (int i = 0; i < Q5; ++i) s->g[i * n + k] = g[i];
     }
+    apply_wet_walls(s);
     s->steps = 0;
 }
 
@@ -463,6 +524,7 @@ void orc_step(orc_sim *s, long nsteps)
     for (long t = 0; t < nsteps; ++t) {
         collide_all(s);
         stream(s);
+        apply_wet_walls(s);
         s->steps++;
     }
 }

@@ -30,7 +30,7 @@ struct Member {
     int tile_begin;
     int row_begin;
     int axis;
-    double nodes, H, dT, sign, kappa, u_ref, dT_ref;
+    double nodes, cells, H, dT, sign, kappa, u_ref, dT_ref;
 };
 
 template <typename A>
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_final_batched(const M
 {
     __shared__ Member<A> M;
     load_member(mem + blockIdx.x, M);
-    reduce_final(M.partial, M.P.ny, M.nodes, M.H, M.dT, M.sign, M.kappa, M.u_ref, M.dT_ref, M.diag);
+    reduce_final(M.partial, M.P.ny, M.nodes, M.cells, M.H, M.dT, M.sign, M.kappa, M.u_ref, M.dT_ref, M.diag);
 }
 
 // A resident lattice (host bookkeeping).
@@ -140,6 +140,7 @@ Member<A> make_member(const Lattice& L, int tile_x, int npt, int tile_begin, int
     m.axis = L.axis;
     const NuGeom g = nu_geom(L.nx, L.ny, L.p, L.axis);
     m.nodes = double(L.nx) * L.ny;
+    m.cells = g.cells;
     m.H = g.H;
     m.dT = g.dT;
     m.sign = g.sign;

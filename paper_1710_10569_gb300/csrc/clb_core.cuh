@@ -118,6 +118,8 @@ struct LatParams {
     A rho_b, T_b;             // rest state the buffers are stored against (0 for FP64)
     int moving;               // some wall moves: fbb holds its momentum terms
     A fbb[4][9];              // [f^eq_i - f^eq_opp](rho0, u_wall of the side), added on bounce-back
+    int wet_y;                // both y walls are wet walls (on the end rows of nodes)
+    A Twall[4], uwall[4][2];  // wall temperature and velocity (wet walls)
 };
 
 // 1-D rest weights of D2Q9 (w(0) = 2/3, w(+-1) = 1/6; w_i = w(e_x) w(e_y)) and D2Q5 weights.
@@ -217,8 +219,8 @@ __device__ __forceinline__ void finish_pull(const LatParams<A>& P, const T raw[N
 }
 
 template <typename T, typename A>
-__device__ __forceinline__ void gather(const T* __restrict__ src, const LatParams<A>& P, int x, int y,
-                                       A f[9], A g[5])
+__device__ __forceinline__ void gather_pull(const T* __restrict__ src, const LatParams<A>& P, int x, int y,
+                                            A f[9], A g[5])
 {
     const Slots s = pull_slots(P, x, y);
     T raw[NPOP];
@@ -494,6 +496,72 @@ __device__ __forceinline__ void equilibrium(const LatParams<A>& P, A rho, A ux, 
         back_d2q9(k, ux, uy, f);
         back_d2q5(T, A(0), A(0), T * P.cs2T, T * P.cs2T, ux, uy, g);
     }
+}
+
+// Wet walls (the paper's own conditions, Sec. 3 first paragraph; y sides only, x periodic): the wall
+// row of nodes lies on the wall. The populations that would come from beyond the wall are set by
+// non-equilibrium bounce-back, f_i = f_opp + [f^eq_i - f^eq_opp](rho, u') with u' = u_w - F/(2 rho)
+// (so that the force-corrected velocity of Eq. 13 is the wall's), rho from mass and normal momentum,
+// and the tangential momentum closed on the two diagonals. g at the wall node is set by
+// non-equilibrium extrapolation from the fluid node next to it: g_i = g^eq_i(T_w, u_w) +
+// [g_i(n) - g^eq_i(T(n), u(n))]. All in stored form (the rest state cancels in both rules).
+template <bool DEV, typename T, typename A>
+__device__ __forceinline__ void gather_wet(const T* __restrict__ src, const LatParams<A>& P, int x, int y,
+                                           A f[9], A g[5])
+{
+    const bool bottom = y == 0;
+    const int side = bottom ? 2 : 3;
+    const A nrm = bottom ? A(1) : A(-1);
+    A fw[9], gw[5];
+    gather_pull(src, P, x, y, fw, gw);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = fw[i];
+    const A Tw = P.Twall[side], uwx = P.uwall[side][0], uwy = P.uwall[side][1];
+    const A Fx = P.Fvx, Fy = fma_(P.gb, Tw - P.T0, P.Fvy);
+    const A Z = (f[0] + f[1]) + f[3];
+    const A O = bottom ? (f[4] + f[7]) + f[8] : (f[2] + f[5]) + f[6];
+    const A num = fma_(-nrm * A(0.5), Fy, fma_(A(2), O, Z) + P.rho_b);
+    const A rho = num * rcp_(fma_(-nrm, uwy, A(1)));
+    const A inv = rcp_(rho);
+    const A upx = fma_(A(-0.5) * Fx, inv, uwx), upy = fma_(A(-0.5) * Fy, inv, uwy);
+    A feq[9], gdum[5];
+    equilibrium<DEV>(P, rho, upx, upy, Tw, feq, gdum);
+    if (bottom) {
+        f[2] = f[4] + (feq[2] - feq[4]);
+        f[5] = f[7] + (feq[5] - feq[7]);
+        f[6] = f[8] + (feq[6] - feq[8]);
+    } else {
+        f[4] = f[2] + (feq[4] - feq[2]);
+        f[7] = f[5] + (feq[7] - feq[5]);
+        f[8] = f[6] + (feq[8] - feq[6]);
+    }
+    const A Sx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const A delta = A(0.5) * fma_(rho, upx, -Sx);
+    if (bottom) {
+        f[5] = f[5] + delta;
+        f[6] = f[6] - delta;
+    } else {
+        f[8] = f[8] + delta;
+        f[7] = f[7] - delta;
+    }
+    A fq[9], gq[5];
+    gather_pull(src, P, x, bottom ? 1 : P.ny - 2, fq, gq);
+    const Macro<A> mq = macroscopic(P, fq, gq);
+    A fe[9], geqq[5], geqb[5];
+    equilibrium<DEV>(P, mq.rho, mq.ux, mq.uy, mq.T, fe, geqq);
+    equilibrium<DEV>(P, rho, uwx, uwy, Tw, fe, geqb);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = geqb[i] + (gq[i] - geqq[i]);
+}
+
+// Pre-collision populations of node (x, y) at the current time, wall rules included.
+template <typename T, typename A>
+__device__ __forceinline__ void gather(const T* __restrict__ src, const LatParams<A>& P, int x, int y,
+                                       A f[9], A g[5])
+{
+    constexpr bool DEV = sizeof(T) < sizeof(double);
+    if (P.wet_y && (y == 0 || y == P.ny - 1)) gather_wet<DEV>(src, P, x, y, f, g);
+    else gather_pull(src, P, x, y, f, g);
 }
 
 }  // namespace clb

@@ -111,8 +111,12 @@ LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
         P.Tw_c2[s] = A(p.T_wall[s] * (p.cs2_T + un * un) - p.cs2_T * (dev ? p.T_ref : 0.0));
         for (int i = 0; i < 9; ++i)
             P.fbb[s][i] = A(p.rho0 * (p1(ex[i], ux) * p1(ey[i], uy) - p1(-ex[i], ux) * p1(-ey[i], uy)));
-        if (p.wall[s] != CLB_PERIODIC && (ux != 0.0 || uy != 0.0)) P.moving = 1;
+        if (p.wall[s] != CLB_PERIODIC && p.wall[s] != CLB_WALL_WET && (ux != 0.0 || uy != 0.0)) P.moving = 1;
+        P.Twall[s] = A(p.T_wall[s]);
+        P.uwall[s][0] = A(ux);
+        P.uwall[s][1] = A(uy);
     }
+    P.wet_y = p.wall[2] == CLB_WALL_WET;
     const double s_nu = rate_nu(p.nu);
     P.s_nu = A(s_nu);
     P.sp = A(0.5 * (p.s_b + s_nu));
@@ -132,13 +136,19 @@ LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
 // Nusselt geometry of Eq. (29) for one axis: H, dT and the sign making heat flow from the hot
 // side positive.
 struct NuGeom {
-    double H, dT, sign;
+    double H, dT, sign, cells;
 };
 inline NuGeom nu_geom(int nx, int ny, const clb_params& p, int axis)
 {
     const int lo = axis == 0 ? 0 : 2, hi = lo + 1;
     NuGeom g;
     g.H = axis == 0 ? nx : ny;
+    g.cells = double(nx) * ny;
+    if (axis == 1 && p.wall[2] == CLB_WALL_WET) {
+        // wet walls on the end rows: H = ny - 1, trapezoid average over nx * H cells
+        g.H = ny - 1;
+        g.cells = double(nx) * (ny - 1);
+    }
     const double d = std::fabs(p.T_wall[lo] - p.T_wall[hi]);
     g.dT = d > 0 ? d : 1.0;
     g.sign = p.T_wall[lo] >= p.T_wall[hi] ? 1.0 : -1.0;
@@ -149,12 +159,12 @@ inline NuGeom nu_geom(int nx, int ny, const clb_params& p, int axis)
 enum { RS_UT = 0, RS_DU, RS_U, RS_DT, RS_T, RS_BAD, RS_N };
 
 // Final scalars from the summed partials (host or device).
-__host__ __device__ inline void finish_diagnostics(const double* s, double nodes, double H,
-                                                   double dT, double sign, double kappa,
+__host__ __device__ inline void finish_diagnostics(const double* s, double nodes, double cells,
+                                                   double H, double dT, double sign, double kappa,
                                                    double u_ref, double dT_ref, double* nu,
                                                    double* er)
 {
-    *nu = 1.0 + sign * (s[RS_UT] / nodes) * H / (kappa * dT);
+    *nu = 1.0 + sign * (s[RS_UT] / cells) * H / (kappa * dT);
     const double fu = nodes * (1e-3 * u_ref) * (1e-3 * u_ref);
     const double fT = nodes * (1e-3 * dT_ref) * (1e-3 * dT_ref);
     const double du = s[RS_U] > fu ? s[RS_U] : fu;

@@ -40,7 +40,7 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
     using E = typename Storage<ST>::T;
     using PK = Pack<E, V>;
     const int wx0 = x0 - lane * V, wx1 = wx0 + 32 * V - 1;
-    if (wx1 < P.nx) {
+    if (wx1 < P.nx && !(P.wet_y && (y == 0 || y == P.ny - 1))) {
         const bool wallB = !P.per_y && y == 0;
         const bool wallT = !P.per_y && y == P.ny - 1;
         const bool wallL = !P.per_x && wx0 == 0;
@@ -466,6 +466,8 @@ __device__ __forceinline__ void reduce_row(const E* __restrict__ src, const LatP
                                            double* __restrict__ partial_row)
 {
     const long long N = (long long)P.nx * P.ny;
+    // wet walls lie on the end rows: the average over [0, H] gives those rows half weight
+    const double wrow = (P.wet_y && axis == 1 && (y == 0 || y == P.ny - 1)) ? 0.5 : 1.0;
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
     for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) {
         A f[9], g[5];
@@ -474,7 +476,7 @@ __device__ __forceinline__ void reduce_row(const E* __restrict__ src, const LatP
         const double ux = double(m.ux), uy = double(m.uy), T = double(P.T_b) + double(m.dT);
         const long long n = (long long)y * P.nx + x;
         const double sx = snap[n], sy = snap[N + n], sT = snap[2 * N + n];
-        v[RS_UT] += (axis == 0 ? ux : uy) * (T - double(P.T0));
+        v[RS_UT] += wrow * ((axis == 0 ? ux : uy) * (T - double(P.T0)));
         v[RS_DU] += (ux - sx) * (ux - sx) + (uy - sy) * (uy - sy);
         v[RS_U] += ux * ux + uy * uy;
         v[RS_DT] += (T - sT) * (T - sT);
@@ -500,8 +502,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_rows(
 // Sum the per-row partials in row order and finish the diagnostics in FP64: out[0..RS_N-1] = the
 // sums, out[RS_N] = Nu (Eq. 29), out[RS_N+1] = E_R.
 __device__ __forceinline__ void reduce_final(const double* __restrict__ partial, int rows,
-                                             double nodes, double H, double dT, double sign,
-                                             double kappa, double u_ref, double dT_ref,
+                                             double nodes, double cells, double H, double dT,
+                                             double sign, double kappa, double u_ref, double dT_ref,
                                              double* __restrict__ out)
 {
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
@@ -511,17 +513,17 @@ __device__ __forceinline__ void reduce_final(const double* __restrict__ partial,
     block_sum(v, tot);
     if (threadIdx.x == 0) {
         for (int k = 0; k < RS_N; ++k) out[k] = tot[k];
-        finish_diagnostics(tot, nodes, H, dT, sign, kappa, u_ref, dT_ref, &out[RS_N], &out[RS_N + 1]);
+        finish_diagnostics(tot, nodes, cells, H, dT, sign, kappa, u_ref, dT_ref, &out[RS_N], &out[RS_N + 1]);
     }
 }
 
 static __global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double* __restrict__ partial,
-                                                                 int rows, double nodes, double H,
-                                                                 double dT, double sign,
+                                                                 int rows, double nodes, double cells,
+                                                                 double H, double dT, double sign,
                                                                  double kappa, double u_ref,
                                                                  double dT_ref, double* __restrict__ out)
 {
-    reduce_final(partial, rows, nodes, H, dT, sign, kappa, u_ref, dT_ref, out);
+    reduce_final(partial, rows, nodes, cells, H, dT, sign, kappa, u_ref, dT_ref, out);
 }
 
 }  // namespace clb

@@ -56,11 +56,16 @@ clb_status validate(int nx, int ny, const clb_params* p)
     for (double r : rates)
         if (!(r > 0 && r < 2)) return set_error(CLB_EINVAL, "relaxation rates must be in (0, 2) (got %g)", r);
     for (int s = 0; s < 4; ++s)
-        if (p->wall[s] < CLB_PERIODIC || p->wall[s] > CLB_WALL_ADIABATIC)
+        if (p->wall[s] < CLB_PERIODIC || p->wall[s] > CLB_WALL_WET)
             return set_error(CLB_EINVAL, "wall[%d] = %d is not a clb_wall", s, p->wall[s]);
     if ((p->wall[0] == CLB_PERIODIC) != (p->wall[1] == CLB_PERIODIC) ||
         (p->wall[2] == CLB_PERIODIC) != (p->wall[3] == CLB_PERIODIC))
         return set_error(CLB_EINVAL, "periodic sides must come in pairs");
+    if (p->wall[0] == CLB_WALL_WET || p->wall[1] == CLB_WALL_WET ||
+        (p->wall[2] == CLB_WALL_WET) != (p->wall[3] == CLB_WALL_WET))
+        return set_error(CLB_EINVAL, "wet walls go on both y sides (not on x sides)");
+    if (p->wall[2] == CLB_WALL_WET && (p->wall[0] != CLB_PERIODIC || ny < 3))
+        return set_error(CLB_EINVAL, "wet walls need periodic x sides and ny >= 3");
     if (p->storage < CLB_F64 || p->storage > CLB_F16DEV)
         return set_error(CLB_EINVAL, "storage %d is not a clb_storage", p->storage);
     return CLB_OK;
@@ -305,8 +310,8 @@ clb_status run_diagnostics(clb_handle* h, int axis, int update)
     }
     CLB_CUDA(cudaGetLastError());
     const NuGeom g = nu_geom(h->nx, h->ny, h->p, axis);
-    k_reduce_final<<<1, kReduceThreads, 0, h->stream>>>(h->partial, rows, double(h->nx) * h->ny, g.H,
-                                                        g.dT, g.sign, h->p.kappa, h->p.u_ref,
+    k_reduce_final<<<1, kReduceThreads, 0, h->stream>>>(h->partial, rows, double(h->nx) * h->ny, g.cells,
+                                                        g.H, g.dT, g.sign, h->p.kappa, h->p.u_ref,
                                                         h->p.dT_ref, h->diag);
     CLB_CUDA(cudaGetLastError());
     CLB_CUDA(cudaMemcpyAsync(h->host_diag, h->diag, (RS_N + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

@@ -61,13 +61,14 @@ __global__ void __launch_bounds__(kReduceThreads) k_nusselt_rows_noalloc(
 {
     using A = typename Storage<ST>::A;
     const int y = blockIdx.x;
+    const double wrow = (P.wet_y && axis == 1 && (y == 0 || y == P.ny - 1)) ? 0.5 : 1.0;
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
     for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) {
         A f[9], g[5];
         gather(src, P, x, y, f, g);
         const Macro<A> m = macroscopic(P, f, g);
         const double ux = double(m.ux), uy = double(m.uy), T = double(P.T_b) + double(m.dT);
-        v[RS_UT] += (axis == 0 ? ux : uy) * (T - double(P.T0));
+        v[RS_UT] += wrow * ((axis == 0 ? ux : uy) * (T - double(P.T0)));
         v[RS_BAD] += (isfinite(ux) && isfinite(uy) && isfinite(T) && isfinite(double(m.rho))) ? 0.0 : 1.0;
     }
     block_sum(v, scratch + (long long)y * RS_N);
@@ -75,11 +76,12 @@ __global__ void __launch_bounds__(kReduceThreads) k_nusselt_rows_noalloc(
 
 __global__ void __launch_bounds__(kReduceThreads) k_nusselt_final_noalloc(double* __restrict__ scratch,
                                                                           int rows, double nodes,
-                                                                          double H, double dT,
-                                                                          double sign, double kappa)
+                                                                          double cells, double H,
+                                                                          double dT, double sign,
+                                                                          double kappa)
 {
     double* out = scratch + CLB_NOALLOC_MAX_ROWS * RS_N;
-    reduce_final(scratch, rows, nodes, H, dT, sign, kappa, 0.0, 0.0, out);
+    reduce_final(scratch, rows, nodes, cells, H, dT, sign, kappa, 0.0, 0.0, out);
 }
 
 }  // namespace
@@ -112,7 +114,7 @@ extern "C" clb_status clb_nusselt_noalloc(const void* populations, int nx, int n
     }
     CLB_CUDA(cudaGetLastError());
     const NuGeom g = nu_geom(nx, ny, *p, axis);
-    k_nusselt_final_noalloc<<<1, kReduceThreads, 0, s>>>(scratch, ny, double(nx) * ny, g.H, g.dT, g.sign, p->kappa);
+    k_nusselt_final_noalloc<<<1, kReduceThreads, 0, s>>>(scratch, ny, double(nx) * ny, g.cells, g.H, g.dT, g.sign, p->kappa);
     CLB_CUDA(cudaGetLastError());
     double out[kOut];
     CLB_CUDA(cudaMemcpyAsync(out, scratch + CLB_NOALLOC_MAX_ROWS * RS_N, sizeof(out), cudaMemcpyDeviceToHost, s));

@@ -224,6 +224,7 @@ extern "C" clb_status clb_thermal_create(int nx, int ny, const clb_params* p, vo
     if (!out) return set_error(CLB_EINVAL, "out is NULL");
     *out = nullptr;
     CLB_TRY(validate(nx, ny, p));
+    if (p->wall[2] == CLB_WALL_WET) return set_error(CLB_EINVAL, "wet walls are not available in the thermal-only mode");
     auto* h = new clb_thermal;
     h->nx = nx;
     h->ny = ny;

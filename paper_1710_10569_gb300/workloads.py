@@ -20,6 +20,7 @@ import numpy as np
 WALL_PERIODIC = 0
 WALL_DIRICHLET = 1  # stationary no-slip wall at fixed temperature
 WALL_ADIABATIC = 2  # stationary no-slip wall with zero heat flux
+WALL_WET = 3        # wall on the end row of nodes (y sides, x periodic): the paper's own conditions
 
 # population storage forms
 STORAGE_F64 = 0
@@ -144,7 +145,7 @@ def rayleigh_benard(nx: int = 2048, ny: int = 1024, Ra: float = 1e7, Pr: float =
 
 
 def rayleigh_benard_table1(Ra: float, Ma: float = 0.3, nx: int = 60, ny: int = 30,
-                           Pr: float = 0.71, storage=STORAGE_F64) -> Problem:
+                           Pr: float = 0.71, storage=STORAGE_F64, wet: bool = False) -> Problem:
     """The Rayleigh-Benard set-up of Sec. 3.3 / Table 1: L x H = 60 x 30, Pr = 0.71,
     u_c = Ma * c_s, nu = Ma c_s H sqrt(Pr/Ra); density disturbed along the horizontal centre line,
     rho(x, H/2) = rho0 (1 + 0.001 cos(2 pi x / L)); the temperature starts from the conduction
@@ -152,17 +153,20 @@ def rayleigh_benard_table1(Ra: float, Ma: float = 0.3, nx: int = 60, ny: int = 3
     the paper's 1.05/0.95 about 1.0, with g*beta rescaled so Ra is unchanged)."""
     u_c = Ma * CS
     H = float(ny)
+    if wet:
+        ny = ny + 1  # walls on the end rows of nodes: H intervals need H + 1 rows
     nu, alpha, gb = convection_params(H, Ra, Pr, u_c)
     x, y = _grid(nx, ny)
     rho = np.ones((ny, nx))
     rho[ny // 2, :] = 1.0 + 0.001 * np.cos(2 * math.pi * np.arange(nx) / nx)
-    T = 0.5 - (y + 0.5) / ny
+    T = 0.5 - (y / H if wet else (y + 0.5) / ny)
     z = np.zeros((ny, nx))
+    kind = WALL_WET if wet else WALL_DIRICHLET
     p = default_params(nu=nu, kappa=alpha, g_beta=gb, T0=0.0, storage=storage,
-                       wall=(WALL_PERIODIC, WALL_PERIODIC, WALL_DIRICHLET, WALL_DIRICHLET),
+                       wall=(WALL_PERIODIC, WALL_PERIODIC, kind, kind),
                        T_wall=(0.0, 0.0, 0.5, -0.5), u_ref=u_c, dT_ref=1.0)
-    return Problem(f"rb_table1_Ra{Ra:g}", nx, ny, p, rho, z.copy(), z.copy(), T, nu_axis=1,
-                   meta=dict(Ra=Ra, Pr=Pr, Ma=Ma, u_c=u_c))
+    return Problem(f"rb_table1_Ra{Ra:g}" + ("_wet" if wet else ""), nx, ny, p, rho, z.copy(), z.copy(),
+                   T, nu_axis=1, meta=dict(Ra=Ra, Pr=Pr, Ma=Ma, u_c=u_c))
 
 
 def random_problem(nx: int, ny: int, seed: int, storage=STORAGE_F64, walls=None,

@@ -144,6 +144,21 @@ def test_moving_walls(clb, storage, seed):
         assert normwise(f, fo) <= 1e-14 and normwise(g, go) <= 1e-14
 
 
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_wet_walls(clb, storage, seed):
+    """The paper's own wall conditions (walls on the end rows, y sides): moving/injecting walls,
+    body force and buoyancy, against the oracle."""
+    prob = W.random_problem(70, 23, seed=seed, storage=storage, walls=(P, P, W.WALL_WET, W.WALL_WET),
+                            moving=True)
+    _, _, got, exp = run_both(clb, prob, 60)
+    compare(f"wet70x23_s{seed}_{W.STORAGE_NAMES[storage]}", got, exp, tol(storage, 60), prob.params)
+    if storage == F64:
+        lat = clb.Lattice.from_problem(prob)
+        o = oracle.Oracle.from_problem(prob)
+        assert lat.nusselt(1) == pytest.approx(o.nusselt(1), rel=1e-12, abs=1e-12)
+
+
 def test_initial_fields_match_oracle(clb):
     """Step 0: the inverse-stream initialisation reproduces the oracle's f(x,0) = f^eq exactly,
     walls included."""
@@ -191,7 +206,8 @@ def test_graph_chunks_equal_single_launches(clb):
 
 
 @pytest.mark.parametrize("storage", [F64, F32, F16])
-@pytest.mark.parametrize("walls", [(P, P, P, P), (D, D, A, A), (P, P, D, D)], ids=["periodic", "cavity", "rb"])
+@pytest.mark.parametrize("walls", [(P, P, P, P), (D, D, A, A), (P, P, D, D), (P, P, W.WALL_WET, W.WALL_WET)],
+                         ids=["periodic", "cavity", "rb", "wet"])
 def test_launch_shapes_are_bitwise_equal(clb, storage, walls):
     """Vector interior path, scalar wall/ragged path and every launch shape give the same bits."""
     prob = W.random_problem(333, 37, seed=3, storage=storage, walls=walls)

@@ -531,3 +531,61 @@ def test_normal_plate_channel_second_order():
     for k in (0, 1):
         order = math.log(e30[k] / e60[k]) / math.log(2)
         assert 1.9 < order < 2.1
+
+
+# ----------------------------------------------------------------------------- wet walls (the paper's own)
+
+
+WET = W.WALL_WET
+
+
+def test_wet_walls_reproduce_couette_poiseuille_and_conduction_exactly():
+    """Walls on the end rows of nodes (H = ny - 1) with non-equilibrium bounce-back and
+    non-equilibrium extrapolation: Couette flow and conduction are straight lines through the wall
+    values and body-force Poiseuille flow is the parabola F/(2 nu) y (H - y), to rounding."""
+    ny, u0 = 17, 0.05
+    y = np.arange(ny)
+    z = np.zeros((ny, 2))
+    p = W.default_params(nu=0.1, kappa=0.1, wall=(P, P, WET, WET), T_wall=(0, 0, 0.3, -0.2),
+                         u_wall=((0, 0), (0, 0), (0, 0), (u0, 0)))
+    o = _run(2, ny, p, np.ones((ny, 2)), z, z, z, 40000)
+    _, ux, uy, T = o.fields()
+    np.testing.assert_allclose(ux[:, 0], u0 * y / (ny - 1), atol=1e-13)
+    np.testing.assert_allclose(T[:, 0], 0.3 - 0.5 * y / (ny - 1), atol=1e-13)
+    assert np.max(np.abs(uy)) < 1e-13
+    F, nu = 1e-6, 0.1
+    p = W.default_params(nu=nu, kappa=0.1, Fv=(F, 0), wall=(P, P, WET, WET))
+    o = _run(2, ny, p, np.ones((ny, 2)), z, z, z, 40000)
+    ux = o.fields()[1][:, 0]
+    ua = F / (2 * nu) * y * (ny - 1 - y)
+    assert np.max(np.abs(ux - ua)) / ua.max() < 1e-8
+
+
+def _rb_wet_nusselt(Ra):
+    prob = W.rayleigh_benard_table1(Ra, wet=True)
+    o = oracle.Oracle.from_problem(prob)
+    hist = []
+    while o.steps < 200000:
+        o.step(1000)
+        hist.append(o.nusselt(1))
+        if len(hist) > 3 and hist[-1] > 1.01 and abs(hist[-1] - hist[-2]) < 1e-6 \
+                and abs(hist[-2] - hist[-3]) < 1e-6:
+            break
+    return hist[-1]
+
+
+@pytest.mark.parametrize("row", [r for r in _table1() if r[0] in (5000.0, 10000.0)], ids=lambda r: f"Ra{r[0]:g}")
+def test_table1_nusselt_with_the_papers_walls(row):
+    """Table 1 with the paper's own wall conditions (walls on the 31 end-row nodes of a 60 x 30
+    box): Nu within 0.2% of the analytic values and 0.4% of the paper's own numbers."""
+    Ra, analytic, paper = row
+    nu = _rb_wet_nusselt(Ra)
+    assert nu == pytest.approx(analytic, rel=2e-3)
+    assert nu == pytest.approx(paper, rel=4e-3)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("row", [r for r in _table1() if r[0] in (2500.0, 3000.0)], ids=lambda r: f"Ra{r[0]:g}")
+def test_table1_nusselt_with_the_papers_walls_rest(row):
+    Ra, analytic, paper = row
+    assert _rb_wet_nusselt(Ra) == pytest.approx(analytic, rel=2e-3)

@@ -137,11 +137,12 @@ def stability(Ra: float = 1e9, ny: int = 220, aspect: int = 2, Pr: float = 0.71,
 
 
 def normal_plate_convergence(Ls=(30, 60, 90, 120, 150), Re=(10.0, 20.0, 30.0), Pr: float = 0.71,
-                             storage=W.STORAGE_F64, tol: float = 1e-11, max_steps: int = 1500000):
+                             storage=W.STORAGE_F64, tol: float = 1e-11, max_steps: int = 1500000,
+                             wet: bool = False):
     """Sec. 3.2: steady profiles of the normal-plate channel for every (Re, L) in one batch, their
     relative errors E_u and E_T against the analytic profiles, and the least-squares slopes of
     log E against log(1/L) per Re (the paper finds slopes of about 2)."""
-    probs = [W.normal_plate_channel(L=L, Re=re, Pr=Pr, storage=storage) for re in Re for L in Ls]
+    probs = [W.normal_plate_channel(L=L, Re=re, Pr=Pr, storage=storage, wet=wet) for re in Re for L in Ls]
     b = clb.Batch(probs)
     steps, er, status = b.run(tol, max_steps, 1000)
     out = {"Re": list(Re), "L": list(Ls), "E_u": {}, "E_T": {}, "slope_u": {}, "slope_T": {},

@@ -197,33 +197,35 @@ def random_problem(nx: int, ny: int, seed: int, storage=STORAGE_F64, walls=None,
 
 
 def normal_plate_channel(L: int = 50, Re: float = 10.0, Pr: float = 0.71, nu: float = 0.1,
-                         nx: int = 5, storage=STORAGE_F64, lambda2=None) -> Problem:
+                         nx: int = 5, storage=STORAGE_F64, lambda2=None, wet: bool = False) -> Problem:
     """Sec. 3.2: channel of width L, periodic in x; the bottom plate (y = 0, at rest, T_L = 0)
     injects a uniform normal flow v0 and the top plate (y = L, moving with u0, T_H = 1) withdraws it;
-    u0 = v0 = Re nu / L. Walls lie halfway between nodes, so node j sits at y = j + 1/2. lambda2
-    defaults to the zero-numerical-slip value 12 (lambda1 - 2) / (lambda1 - 12) the paper uses."""
-    ny = L
+    u0 = v0 = Re nu / L. Walls lie halfway between nodes, so node j sits at y = j + 1/2 (with
+    `wet`, the paper's own walls: on the end rows, node j at y = j, L + 1 rows). lambda2 defaults to
+    the zero-numerical-slip value 12 (lambda1 - 2) / (lambda1 - 12) the paper uses."""
+    ny = L + 1 if wet else L
     v0 = Re * nu / L
     alpha = nu / Pr
     lam1 = 1.0 / (alpha / 0.25 + 0.5)
     lam2 = 12 * (lam1 - 2) / (lam1 - 12) if lambda2 is None else lambda2
-    y = (np.arange(ny) + 0.5)[:, None] * np.ones((1, nx))
+    y = (np.arange(ny) + (0.0 if wet else 0.5))[:, None] * np.ones((1, nx))
+    kind = WALL_WET if wet else WALL_DIRICHLET
     p = default_params(nu=nu, kappa=alpha, lambda2=lam2, storage=storage,
-                       wall=(WALL_PERIODIC, WALL_PERIODIC, WALL_DIRICHLET, WALL_DIRICHLET),
+                       wall=(WALL_PERIODIC, WALL_PERIODIC, kind, kind),
                        T_wall=(0.0, 0.0, 0.0, 1.0), u_wall=((0, 0), (0, 0), (0.0, v0), (v0, v0)),
                        u_ref=v0, dT_ref=1.0)
     ux = v0 * y / L
     uy = np.full((ny, nx), v0)
     T = y / L
-    return Problem(f"normal_plate_L{L}_Re{Re:g}_Pr{Pr:g}", nx, ny, p, np.ones((ny, nx)), ux, uy, T,
-                   nu_axis=1, meta=dict(L=L, Re=Re, Pr=Pr, v0=v0))
+    return Problem(f"normal_plate_L{L}_Re{Re:g}_Pr{Pr:g}" + ("_wet" if wet else ""), nx, ny, p,
+                   np.ones((ny, nx)), ux, uy, T, nu_axis=1, meta=dict(L=L, Re=Re, Pr=Pr, v0=v0, wet=wet))
 
 
 def normal_plate_analytic(prob: Problem):
     """Analytic steady profiles of Sec. 3.2 at the node heights: u/u0 = (exp(Re y/L) - 1)/(exp(Re) - 1)
     and (T - T_L)/dT = (exp(Re Pr y/L) - 1)/(exp(Re Pr) - 1); v = v0."""
     L, Re, Pr, v0 = (prob.meta[k] for k in ("L", "Re", "Pr", "v0"))
-    y = np.arange(prob.ny) + 0.5
+    y = np.arange(prob.ny) + (0.0 if prob.meta.get("wet") else 0.5)
     u = v0 * (np.exp(Re * y / L) - 1) / (math.exp(Re) - 1)
     T = (np.exp(Re * Pr * y / L) - 1) / (math.exp(Re * Pr) - 1)
     return u, T

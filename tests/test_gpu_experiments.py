@@ -200,3 +200,13 @@ def test_table1_with_the_papers_walls(clb, storage):
     for k, ra in enumerate(ras):
         assert nu[k] == pytest.approx(paper[ra][0], rel=2e-3), ra
         assert nu[k] == pytest.approx(paper[ra][1], rel=4e-3), ra
+
+
+def test_normal_plate_convergence_with_the_papers_walls(clb):
+    """Sec. 3.2 with the paper's own walls on the GPU (15 channels in one batch): least-squares
+    slopes of log E against log(1/L) between 1.7 and 2.2 for u and T at every Re."""
+    from paper_1710_10569_gb300 import experiments as X
+    r = X.normal_plate_convergence(wet=True)
+    for re in ("10.0", "20.0", "30.0"):
+        assert 1.7 < r["slope_u"][re] < 2.2, r
+        assert 1.7 < r["slope_T"][re] < 2.2, r

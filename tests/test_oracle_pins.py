@@ -589,3 +589,20 @@ def test_table1_nusselt_with_the_papers_walls(row):
 def test_table1_nusselt_with_the_papers_walls_rest(row):
     Ra, analytic, paper = row
     assert _rb_wet_nusselt(Ra) == pytest.approx(analytic, rel=2e-3)
+
+
+def test_normal_plate_channel_with_the_papers_walls():
+    """Sec. 3.2 with the paper's own walls (wet walls, L + 1 rows): E_u < 2e-3 and E_T < 5e-3 at
+    L = 30, and the errors fall at order > 1.7 from L = 30 to 60."""
+    out = []
+    for L in (30, 60):
+        prob = W.normal_plate_channel(L=L, Re=10.0, Pr=0.71, wet=True)
+        o = oracle.Oracle.from_problem(prob)
+        oracle.run_to_steady(o, 1e-11, 400000, 500)
+        _, ux, _, T = o.fields()
+        ua, Ta = W.normal_plate_analytic(prob)
+        out.append((np.sqrt(np.sum((ux[:, 0] - ua) ** 2) / np.sum(ua ** 2)),
+                    np.sqrt(np.sum((T[:, 0] - Ta) ** 2) / np.sum(Ta ** 2))))
+    assert out[0][0] < 2e-3 and out[0][1] < 5e-3
+    for k in (0, 1):
+        assert math.log(out[0][k] / out[1][k]) / math.log(2) > 1.7

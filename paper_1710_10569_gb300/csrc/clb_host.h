@@ -64,12 +64,13 @@ inline size_t buffer_bytes(int nx, int ny, int storage)
 
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-// Device bytes reserved per population buffer: the buffer plus a 256-byte guard, so that the
-// 4-byte asynchronous copy of an edge pair of half-precision values may touch one element past the
-// last plane without leaving the allocation.
+// Device bytes reserved per population buffer: the buffer plus a 1 KB guard. The vector loads of
+// the last warp of a row may run up to 32 * V - 1 elements past the row's last node (at most 127
+// elements of 8 bytes or less: under 1 KB), and the 4-byte asynchronous copy of an edge pair of
+// half-precision values one element past it; the guard keeps those reads inside the allocation.
 inline size_t buffer_slot_bytes(int nx, int ny, int storage)
 {
-    return align256(buffer_bytes(nx, ny, storage)) + 256;
+    return align256(buffer_bytes(nx, ny, storage)) + 1024;
 }
 
 clb_status validate(int nx, int ny, const clb_params* p);

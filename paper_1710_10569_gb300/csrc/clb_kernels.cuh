@@ -22,16 +22,14 @@ __device__ __forceinline__ E lane_down(E v) { return __shfl_down_sync(0xffffffff
 // One time step for V consecutive nodes x0 .. x0+V-1 of row y, called by all 32 lanes of a warp
 // on the same row with x0 = (first x of the warp) + lane * V: pull the 14 populations (Eqs. 12,
 // 22, with the wall rules), collide (Eqs. 3-11, 13, 16-21, 23), store at the nodes.
-// Every warp takes the vector path (wet-wall rows excepted): per population plane one aligned
-// V-wide load of the row the pull comes from; the population pulled from x-1 (x+1) of the first
-// (last) node of a thread is the neighbouring lane's last (first) element, passed by a warp
-// shuffle, and lane 0 (the lane holding the warp's last node) loads the one element beyond the
-// warp. Walls are handled in the same path: on a wall row the planes pulled across the wall come
-// from the node's own opposite plane (no shift), and at an x wall the edge lane loads its node's
-// own opposite values instead of the missing neighbour; the wall terms are then added per node by
-// finish_pull. A warp that runs past the end of its row reads past the row's last node (inside
-// the buffer's guard), computes garbage there and stores only the nodes that exist. Wet-wall rows
-// gather node by node. Every path feeds identical values to the identical collision.
+// Warps whose 32 * V nodes all lie inside the row take the vector path: per population plane one
+// aligned V-wide load of the row the pull comes from; the population pulled from x-1 (x+1) of the
+// first (last) node of a thread is the neighbouring lane's last (first) element, passed by a warp
+// shuffle, and lane 0 (lane 31) loads the one element beyond the warp. Walls are handled in the
+// same path: on a wall row the planes pulled across the wall come from the node's own opposite
+// plane (no shift), and at an x wall lane 0 (lane 31) loads its node's own opposite values instead
+// of the missing neighbour; the wall terms are then added per node by finish_pull. The ragged end
+// of a row gathers node by node. Every path feeds identical values to the identical collision.
 template <int ST, int V>
 __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* __restrict__ src,
                                                 typename Storage<ST>::T* __restrict__ dst,
@@ -41,11 +39,8 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
     using A = typename Storage<ST>::A;
     using E = typename Storage<ST>::T;
     using PK = Pack<E, V>;
-    const int wx0 = x0 - lane * V;
-    if (!(P.wet_y && (y == 0 || y == P.ny - 1))) {
-        // the warp's last node: the row's last node when the warp runs past the end of the row
-        const int wx1 = min(wx0 + 32 * V - 1, P.nx - 1);
-        const int last_lane = (wx1 - wx0) / V, last_k = (wx1 - wx0) % V;
+    const int wx0 = x0 - lane * V, wx1 = wx0 + 32 * V - 1;
+    if (wx1 < P.nx && !(P.wet_y && (y == 0 || y == P.ny - 1))) {
         const bool wallB = !P.per_y && y == 0;
         const bool wallT = !P.per_y && y == P.ny - 1;
         const bool wallL = !P.per_x && wx0 == 0;
@@ -54,7 +49,7 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
         const int yp = y < P.ny - 1 ? y + 1 : 0;
         const int rc = y * P.pitch, rm = ym * P.pitch, rp = yp * P.pitch;
         const int xl = wx0 > 0 ? wx0 - 1 : P.nx - 1;  // column left of the warp (lane 0)
-        const int xr = wx1 < P.nx - 1 ? wx1 + 1 : 0;  // column right of the warp's last node
+        const int xr = wx1 < P.nx - 1 ? wx1 + 1 : 0;  // column right of the warp (lane 31)
         const long long pl = P.plane;
         // plane, row (0: y, 1: y-1, 2: y+1) and x shift (+1: pulled from x-1, -1: from x+1)
         const int SHIFT[NPOP] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 1, 0, -1, 0};
@@ -73,8 +68,8 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
             edge[i] = E(0);
             if (sh == 1 && lane == 0)
                 edge[i] = wallL ? src[OPP[i] * pl + rc + 0] : src[plane * pl + r + xl];
-            if (sh == -1 && lane == last_lane)
-                edge[i] = wallR ? src[OPP[i] * pl + rc + wx1] : src[plane * pl + r + xr];
+            if (sh == -1 && lane == 31)
+                edge[i] = wallR ? src[OPP[i] * pl + rc + (P.nx - 1)] : src[plane * pl + r + xr];
         }
         E raw[V][NPOP];
 #pragma unroll
@@ -92,21 +87,16 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
 #pragma unroll
                 for (int k = 1; k < V; ++k) raw[k][i] = pk[i].e[k - 1];
             } else {
-                raw[V - 1][i] = dn;
+                raw[V - 1][i] = lane == 31 ? edge[i] : dn;
 #pragma unroll
                 for (int k = 0; k < V - 1; ++k) raw[k][i] = pk[i].e[k + 1];
-                // the warp's last node takes the column right of it (wrapped or bounced)
-#pragma unroll
-                for (int k = 0; k < V; ++k)
-                    if (lane == last_lane && k == last_k) raw[k][i] = edge[i];
             }
         }
         const int rowmask = (wallB ? 4 : 0) | (wallT ? 8 : 0);
         int mask[V];
 #pragma unroll
         for (int k = 0; k < V; ++k)
-            mask[k] = rowmask | ((wallL && lane == 0 && k == 0) ? 1 : 0) |
-                      ((wallR && lane == last_lane && k == last_k) ? 2 : 0);
+            mask[k] = rowmask | ((wallL && lane == 0 && k == 0) ? 1 : 0) | ((wallR && lane == 31 && k == V - 1) ? 2 : 0);
         PK out[NPOP];
         if constexpr (Storage<ST>::DEV && V % 2 == 0) {
             // FP32 arithmetic: two nodes per packed f32x2 instruction
@@ -141,17 +131,8 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
                 for (int i = 0; i < 5; ++i) out[9 + i].e[k] = from_a(g[i], (E*)nullptr);
             }
         }
-        if (x0 + V - 1 <= wx1) {
 #pragma unroll
-            for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];
-        } else {
-            // past the end of the row: store the nodes that exist, one by one
-#pragma unroll
-            for (int k = 0; k < V; ++k)
-                if (x0 + k <= wx1)
-#pragma unroll
-                    for (int i = 0; i < NPOP; ++i) dst[i * pl + rc + x0 + k] = out[i].e[k];
-        }
+        for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];
     } else {
 #pragma unroll
         for (int k = 0; k < V; ++k) {

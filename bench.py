@@ -36,6 +36,9 @@ from paper_1710_10569_gb300 import workloads as W  # noqa: E402
 
 BYTES_PER_NODE = {W.STORAGE_F64: 224, W.STORAGE_F32: 112, W.STORAGE_F16DEV: 56}  # 14 in + 14 out
 DTYPE = {W.STORAGE_F64: "f64", W.STORAGE_F32: "f32", W.STORAGE_F16DEV: "f16dev storage, f32 arithmetic"}
+# Lattice of each storage form when it runs as a variant beside the headline: FP16 storage moves
+# 56 B per node, so at 2048 x 1024 a step's 117 MB would fit the 129 MB L2; it runs at 4096 x 2048.
+VARIANT_SIZE = {W.STORAGE_F64: (2048, 1024), W.STORAGE_F32: (2048, 1024), W.STORAGE_F16DEV: (4096, 2048)}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_traffic.json")
 KERNEL_SOURCES = ["paper_1710_10569_gb300/csrc/clb_core.cuh", "paper_1710_10569_gb300/csrc/clb_kernels.cuh"]
 
@@ -71,17 +74,13 @@ def profile_counts():
     return d if d.get("kernel_source_hash") == kernel_hash() else {}
 
 
-def traffic_per_launch(storage: int):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
-    if not os.path.exists(TRAFFIC_FILE):
+def traffic_per_launch(storage: int, nx: int, ny: int):
+    """DRAM bytes per step-kernel launch on an nx x ny lattice from the committed ncu summary, if
+    it was taken on the current kernel source and that lattice (else None)."""
+    e = profile_counts().get("launches", {}).get(W.STORAGE_NAMES[storage])
+    if not e or e.get("nx") != nx or e.get("ny") != ny:
         return None
-    with open(TRAFFIC_FILE) as f:
-        d = json.load(f)
-    if d.get("kernel_source_hash") != kernel_hash():
-        return None
-    v = d.get("dram_bytes_per_launch", {}).get(W.STORAGE_NAMES[storage])
-    return float(v) if v else None
+    return float(e["dram_bytes_per_launch"])
 
 
 class ClockSampler:
@@ -189,12 +188,16 @@ def time_steps(lat, steps: int, warmup: int, world: int):
     return e0.elapsed_time(e1) / 1e3
 
 
-def cpu_baseline(storage: int, sample_steps: int = 6):
-    """The oracle, as it stands, on the full bench lattice for a few steps."""
+def cpu_baseline(storage: int, nx: int, ny: int, seconds: float = 10.0):
+    """The oracle, as it stands, on the full bench lattice for as many steps as take about
+    `seconds` (one step timed first to size the sample)."""
     import oracle
-    prob = workload(storage)
+    prob = workload(storage, nx, ny)
     o = oracle.Oracle.from_problem(prob)
+    t0 = time.perf_counter()
     o.step(1)
+    one = time.perf_counter() - t0
+    sample_steps = int(min(400, max(3, seconds / max(one, 1e-6))))
     t0 = time.perf_counter()
     o.step(sample_steps)
     dt = time.perf_counter() - t0
@@ -204,12 +207,12 @@ def cpu_baseline(storage: int, sample_steps: int = 6):
                       f"{oracle.threads()} OpenMP threads), {dt:.1f} s"}
 
 
-def e2e_run(storage: int, steps: int):
+def e2e_run(storage: int, steps: int, nx: int, ny: int):
     """The same metric through the public C ABI with host buffers: upload the initial fields from
     pinned host memory, step, and read the fields back, all inside the timed region."""
     import torch
     from paper_1710_10569_gb300 import clb
-    prob = workload(storage)
+    prob = workload(storage, nx, ny)
     n = prob.nodes
     pin = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(8)]
     for t, a in zip(pin[:4], prob.fields()):
@@ -331,9 +334,9 @@ def run_ours(args):
     storage = {"f64": W.STORAGE_F64, "f32": W.STORAGE_F32, "f16dev": W.STORAGE_F16DEV}[args.storage]
 
     # CPU baseline first (before the GPU is busy), rank 0 at N = 1 only
-    cpu = cpu_baseline(storage) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    cpu = cpu_baseline(storage, args.nx, args.ny) if (rank == 0 and world == 1 and not args.no_cpu) else None
 
-    prob = workload(storage)
+    prob = workload(storage, args.nx, args.ny)
     lat = clb.Lattice.from_problem(prob)
     if args.autotune:
         lat.autotune()
@@ -346,24 +349,27 @@ def run_ours(args):
     per_launch_s = secs / args.steps
     alg_bytes = BYTES_PER_NODE[storage] * nodes
     achieved = alg_bytes / per_launch_s / 1e9
-    traffic = traffic_per_launch(storage)
+    traffic = traffic_per_launch(storage, prob.nx, prob.ny)
 
     variants = {}
     if rank == 0 and not args.no_variants:
         for st in (W.STORAGE_F64, W.STORAGE_F16DEV, W.STORAGE_F32):
             if st == storage:
                 continue
-            p2 = workload(st)
+            vx, vy = VARIANT_SIZE[st]
+            p2 = workload(st, vx, vy)
             l2 = clb.Lattice.from_problem(p2)
             if args.autotune:
                 l2.autotune()
             k = max(200, args.steps // (8 if st == W.STORAGE_F64 else 2))
             s2 = time_steps(l2, k, max(3, args.warmup // 4), 1)
             variants[W.STORAGE_NAMES[st]] = {
+                "workload": f"rayleigh_benard_{p2.nx}x{p2.ny}_Ra1e7_Pr0.71",
                 "mlups": p2.nodes * k / s2 / 1e6,
                 "achieved_gbs": BYTES_PER_NODE[st] * p2.nodes / (s2 / k) / 1e9,
                 "hbm_frac": BYTES_PER_NODE[st] * p2.nodes / (s2 / k) / 1e9 / peak,
-                "steps": k, "dram_bytes_per_launch": traffic_per_launch(st),
+                "steps": k, "dram_bytes_per_launch": traffic_per_launch(st, p2.nx, p2.ny),
+                "working_set_mb": BYTES_PER_NODE[st] * p2.nodes / 1e6,
                 "launch": list(l2.launch())}
             ops = profile_counts().get("fp64_ops_per_node")
             if st == W.STORAGE_F64 and ops:
@@ -375,7 +381,7 @@ def run_ours(args):
                     "dp_instructions_per_node": dp,
                     "peak_kind": "derived: 152 SMs x 2 FP64 lanes/clock x 2.07 GHz"}
             l2.close()
-    e2e = e2e_run(storage, args.steps) if rank == 0 else None
+    e2e = e2e_run(storage, args.steps, args.nx, args.ny) if rank == 0 else None
     thermal = thermal_run(storage, args.steps) if (rank == 0 and not args.no_variants) else None
     batched = batched_run(storage) if (rank == 0 and not args.no_serve) else None
     served = served_run(storage) if (rank == 0 and not args.no_serve) else None
@@ -388,10 +394,10 @@ def run_ours(args):
             "config": {"workload": f"rayleigh_benard_{prob.nx}x{prob.ny}_Ra1e7_Pr0.71",
                        "nodes": nodes, "storage": W.STORAGE_NAMES[storage],
                        "launch": list(lat.launch()),
-                       "l2": "no flush: two population buffers of "
-                             f"{2 * alg_bytes / 2 / 1e6:.0f} MB each (working set "
-                             f"{alg_bytes / 1e6:.0f} MB) exceed the 129 MB L2; ncu DRAM bytes per "
-                             "launch in roofline.traffic",
+                       "l2": "no flush: each step reads one population buffer and writes the "
+                             f"other ({alg_bytes / 2 / 1e6:.0f} MB each, {alg_bytes / 1e6:.0f} MB "
+                             "per step against the 129 MB L2); roofline.traffic is the ncu DRAM "
+                             "bytes per launch",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -453,6 +459,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16dev"])
+    ap.add_argument("--nx", type=int, default=2048, help="lattice width of the timed workload")
+    ap.add_argument("--ny", type=int, default=1024, help="lattice height of the timed workload")
     ap.add_argument("--autotune", action="store_true", help="time the autotuned launch shape instead of the default")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_step_batched(const Member<typename Stor
     const int x0 = (tx * blockDim.x + threadIdx.x) * V;
     const int y = ty * blockDim.y + threadIdx.y;
     if (y >= M.P.ny || x0 - lane * V >= M.P.nx) return;
-    step_warp_nodes<ST, V>((const E*)M.buf[parity], (E*)M.buf[parity ^ 1], M.P, x0, y, lane);
+    step_warp_nodes<ST, V, false>((const E*)M.buf[parity], (E*)M.buf[parity ^ 1], M.P, x0, y, lane);
 }
 
 template <int ST>

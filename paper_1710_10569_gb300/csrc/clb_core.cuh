@@ -66,6 +66,20 @@ struct F2 {
         asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(u));
     }
 };
+// Both lanes of a packed pair to storage, each rounded to nearest even (for FP16 one conversion
+// instruction packs the two halves).
+__device__ __forceinline__ void from_a2(F2 v, float& lo, float& hi) { v.split(lo, hi); }
+__device__ __forceinline__ void from_a2(F2 v, __half& lo, __half& hi)
+{
+    float a, b;
+    v.split(a, b);
+    unsigned r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));  // b to the upper half
+    unsigned short l16, h16;
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(l16), "=h"(h16) : "r"(r));
+    lo = __ushort_as_half(l16);
+    hi = __ushort_as_half(h16);
+}
 __device__ __forceinline__ F2 operator+(F2 a, F2 b)
 {
     F2 r;

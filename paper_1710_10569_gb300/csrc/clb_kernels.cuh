@@ -30,21 +30,24 @@ __device__ __forceinline__ E lane_down(E v) { return __shfl_down_sync(0xffffffff
 // plane (no shift), and at an x wall lane 0 (lane 31) loads its node's own opposite values instead
 // of the missing neighbour; the wall terms are then added per node by finish_pull. The ragged end
 // of a row gathers node by node. Every path feeds identical values to the identical collision.
-template <int ST, int V>
-__device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* __restrict__ src,
-                                                typename Storage<ST>::T* __restrict__ dst,
-                                                const LatParams<typename Storage<ST>::A>& P, int x0,
-                                                int y, int lane)
+//
+// warp_vector is the vector body. WALLS = false is the interior of the lattice (no wall next to any node of the
+// warp), where every wall term folds away at compile time.
+template <int ST, int V, bool WALLS>
+__device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __restrict__ src,
+                                            typename Storage<ST>::T* __restrict__ dst,
+                                            const LatParams<typename Storage<ST>::A>& P, int x0, int y,
+                                            int lane)
 {
     using A = typename Storage<ST>::A;
     using E = typename Storage<ST>::T;
     using PK = Pack<E, V>;
     const int wx0 = x0 - lane * V, wx1 = wx0 + 32 * V - 1;
-    if (wx1 < P.nx && !(P.wet_y && (y == 0 || y == P.ny - 1))) {
-        const bool wallB = !P.per_y && y == 0;
-        const bool wallT = !P.per_y && y == P.ny - 1;
-        const bool wallL = !P.per_x && wx0 == 0;
-        const bool wallR = !P.per_x && wx1 == P.nx - 1;
+    {
+        const bool wallB = WALLS && !P.per_y && y == 0;
+        const bool wallT = WALLS && !P.per_y && y == P.ny - 1;
+        const bool wallL = WALLS && !P.per_x && wx0 == 0;
+        const bool wallR = WALLS && !P.per_x && wx1 == P.nx - 1;
         const int ym = y > 0 ? y - 1 : P.ny - 1;
         const int yp = y < P.ny - 1 ? y + 1 : 0;
         const int rc = y * P.pitch, rm = ym * P.pitch, rp = yp * P.pitch;
@@ -112,12 +115,7 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
                 for (int i = 0; i < 5; ++i) g[i] = F2(ga[i], gb[i]);
                 collide_dev(P, f, g);
 #pragma unroll
-                for (int i = 0; i < NPOP; ++i) {
-                    float lo, hi;
-                    (i < 9 ? f[i] : g[i - 9]).split(lo, hi);
-                    out[i].e[k] = from_a(lo, (E*)nullptr);
-                    out[i].e[k + 1] = from_a(hi, (E*)nullptr);
-                }
+                for (int i = 0; i < NPOP; ++i) from_a2(i < 9 ? f[i] : g[i - 9], out[i].e[k], out[i].e[k + 1]);
             }
         } else {
 #pragma unroll
@@ -133,6 +131,26 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
         }
 #pragma unroll
         for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];
+    }
+}
+
+// step_warp_nodes picks the path. SPLIT = true compiles the vector body twice, with and without
+// the wall terms, and interior warps take the lean copy (fewer instructions; the FP16 form is
+// issue-limited). The batched kernel keeps one copy: the second raises its register count past an
+// occupancy step.
+template <int ST, int V, bool SPLIT = true>
+__device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* __restrict__ src,
+                                                typename Storage<ST>::T* __restrict__ dst,
+                                                const LatParams<typename Storage<ST>::A>& P, int x0,
+                                                int y, int lane)
+{
+    using A = typename Storage<ST>::A;
+    const int wx0 = x0 - lane * V, wx1 = wx0 + 32 * V - 1;
+    if (wx1 < P.nx && !(P.wet_y && (y == 0 || y == P.ny - 1))) {
+        const bool walls =
+            (!P.per_y && (y == 0 || y == P.ny - 1)) || (!P.per_x && (wx0 == 0 || wx1 == P.nx - 1));
+        if (!SPLIT || walls) warp_vector<ST, V, true>(src, dst, P, x0, y, lane);
+        else warp_vector<ST, V, false>(src, dst, P, x0, y, lane);
     } else {
 #pragma unroll
         for (int k = 0; k < V; ++k) {

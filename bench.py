@@ -272,15 +272,23 @@ def batched_run(storage: int, count: int = 256, steps: int = 1000, seq_subset: i
     probs = W.batch_cavities(count, seed=0, storage=storage)
     nodes = sum(p.nodes for p in probs)
 
+    def device_seconds(stream_handle, fn):
+        """CUDA-event time of fn's work on the given stream."""
+        st = torch.cuda.ExternalStream(stream_handle) if stream_handle else torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
     def time_batch(ps, k):
         b = clb.Batch(ps)
         tile = b.autotune()
         b.step(64)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        b.step(k)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        dt = device_seconds(b.stream, lambda: b.step(k))
         b.close()
         return dt, tile
 
@@ -288,15 +296,15 @@ def batched_run(storage: int, count: int = 256, steps: int = 1000, seq_subset: i
     sub = probs[:seq_subset]
     sub_nodes = sum(p.nodes for p in sub)
     dt_sub, _ = time_batch(sub, steps)
-    lats = [clb.Lattice.from_problem(p) for p in sub]
+    lats = [clb.Lattice.from_problem(p) for p in sub]  # all on torch's current stream
     for lat in lats:
         lat.step(64)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for lat in lats:
-        lat.step(steps)
-        lat.sync()
-    dt_seq = time.perf_counter() - t0
+
+    def sequential():
+        for lat in lats:
+            lat.step(steps)
+
+    dt_seq = device_seconds(lats[0].stream, sequential)
     for lat in lats:
         lat.close()
     return {"instances": count, "nodes": nodes, "steps": steps, "storage": W.STORAGE_NAMES[storage],
@@ -465,11 +473,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched and served runs")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched workload (256 uneven cavities) and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.batched_only:
+        print(json.dumps(batched_run({"f64": W.STORAGE_F64, "f32": W.STORAGE_F32,
+                                      "f16dev": W.STORAGE_F16DEV}[args.storage], steps=args.steps)), flush=True)
     else:
         run_ours(args)
 

@@ -24,7 +24,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "clb_oracle.c")
+_SRCS = [os.path.join(_HERE, "clb_oracle.c"), os.path.join(_HERE, "clb3d_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
@@ -36,11 +36,11 @@ PERIODIC, DIRICHLET, ADIABATIC, WET = 0, 1, 2, 3
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, no FMA contraction, no host-specific flags)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(map(os.path.getmtime, _SRCS)):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
                                "-fopenmp",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -53,6 +53,17 @@ class _Params(ctypes.Structure):
                 ("lambda0", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
                 ("Fv", ctypes.c_double * 2), ("wall", ctypes.c_int * 4), ("T_wall", ctypes.c_double * 4),
                 ("thermal_only", ctypes.c_int), ("u_wall", ctypes.c_double * 8)]
+
+
+class _Params3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("nu", ctypes.c_double), ("kappa", ctypes.c_double), ("g_beta", ctypes.c_double),
+                ("T0", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("s_b", ctypes.c_double), ("s_3", ctypes.c_double), ("s_4", ctypes.c_double),
+                ("s_5", ctypes.c_double), ("s_6", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
+                ("Fv", ctypes.c_double * 3), ("g_axis", ctypes.c_int), ("wall", ctypes.c_int * 6),
+                ("T_wall", ctypes.c_double * 6)]
 
 
 def _load():
@@ -82,6 +93,19 @@ def _load():
             lib.orc_equilibrium_node.argtypes = [P(_Params), ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, d, d]
             lib.orc_matrices.argtypes = [P(_Params), ctypes.c_double, ctypes.c_double] + [d] * 11
+            vp = ctypes.c_void_p
+            lib.orc3_create.argtypes = [P(_Params3), P(vp)]
+            lib.orc3_create.restype = ctypes.c_int
+            lib.orc3_destroy.argtypes = [vp]
+            lib.orc3_init.argtypes = [vp, d, d, d, d, d]
+            lib.orc3_step.argtypes = [vp, ctypes.c_long]
+            lib.orc3_fields.argtypes = [vp, d, d, d, d, d]
+            lib.orc3_get_pops.argtypes = [vp, d, d]
+            lib.orc3_set_pops.argtypes = [vp, d, d]
+            lib.orc3_collide_node.argtypes = [P(_Params3), d, d, d, d]
+            lib.orc3_equilibrium_node.argtypes = [P(_Params3)] + [ctypes.c_double] * 5 + [d, d]
+            lib.orc3_matrices.argtypes = ([P(_Params3)] + [ctypes.c_double] * 3 + [d] * 9
+                                          + [P(ctypes.c_int)] * 2)
             _lib = lib
     return _lib
 
@@ -276,3 +300,138 @@ def run_to_steady(o: Oracle, tol: float, max_steps: int, interval: int = 100):
         if er < tol:
             break
     return o.steps, er
+
+
+# ------------------------------------------------------------------------------------------------
+# Three-dimensional form (D3Q27 flow + D3Q7 temperature, clb3d_oracle.c). Fields are (nz, ny, nx)
+# float64 arrays; params are those of the two-dimensional form plus s_5, s_6 (rates of the fifth-
+# and sixth-order moments, default 1), Fv of length 3, g_axis (buoyancy along +g_axis, default 2)
+# and six faces in wall / T_wall (-x, +x, -y, +y, -z, +z).
+
+
+def _params3(p: dict, nx: int = 1, ny: int = 1, nz: int = 1) -> _Params3:
+    s = _Params3()
+    s.nx, s.ny, s.nz = nx, ny, nz
+    for k in ("nu", "kappa", "g_beta", "T0", "rho0", "s_b", "s_3", "s_4", "lambda2", "cs2_T"):
+        setattr(s, k, float(p[k]))
+    s.s_5 = float(p.get("s_5", 1.0))
+    s.s_6 = float(p.get("s_6", 1.0))
+    s.lambda0 = float(p.get("lambda0", 1.0))
+    for i in range(3):
+        s.Fv[i] = float(p["Fv"][i])
+    s.g_axis = int(p.get("g_axis", 2))
+    for i in range(6):
+        s.wall[i] = int(p["wall"][i])
+        s.T_wall[i] = float(p["T_wall"][i])
+    return s
+
+
+class Oracle3D:
+    """One 3-D lattice stepped on the CPU in FP64."""
+
+    def __init__(self, nx: int, ny: int, nz: int, params: dict):
+        self._lib = _load()
+        self.nx, self.ny, self.nz, self.params = nx, ny, nz, dict(params)
+        self._p = _params3(params, nx, ny, nz)
+        h = ctypes.c_void_p()
+        rc = self._lib.orc3_create(ctypes.byref(self._p), ctypes.byref(h))
+        if rc != 0:
+            raise ValueError(f"oracle: invalid lattice {nx}x{ny}x{nz} (code {rc})")
+        self._h = h
+        self.steps = 0
+
+    @classmethod
+    def from_problem(cls, prob) -> "Oracle3D":
+        o = cls(prob.nx, prob.ny, prob.nz, prob.params)
+        o.init(prob.rho, prob.ux, prob.uy, prob.uz, prob.T)
+        return o
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.orc3_destroy(h)
+            self._h = None
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def init(self, rho, ux, uy, uz, T):
+        arrs = [np.ascontiguousarray(np.broadcast_to(a, self.shape), dtype=np.float64)
+                for a in (rho, ux, uy, uz, T)]
+        self._lib.orc3_init(self._h, *[_ptr(a) for a in arrs])
+        self.steps = 0
+
+    def step(self, n: int = 1):
+        self._lib.orc3_step(self._h, int(n))
+        self.steps += int(n)
+
+    def fields(self):
+        """(rho, ux, uy, uz, T), each (nz, ny, nx)."""
+        out = [np.empty(self.shape) for _ in range(5)]
+        self._lib.orc3_fields(self._h, *[_ptr(a) for a in out])
+        return tuple(out)
+
+    def populations(self):
+        f = np.empty((27,) + self.shape)
+        g = np.empty((7,) + self.shape)
+        self._lib.orc3_get_pops(self._h, _ptr(f), _ptr(g))
+        return f, g
+
+    def set_populations(self, f, g):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.shape == (27,) + self.shape and g.shape == (7,) + self.shape
+        self._lib.orc3_set_pops(self._h, _ptr(f), _ptr(g))
+
+    def nusselt(self, axis: int = 2) -> float:
+        _, ux, uy, uz, T = self.fields()
+        return nusselt3((ux, uy, uz)[axis], T, self.params, axis)
+
+
+def collide3_node(params: dict, f, g):
+    """Post-collision (f*, g*) of one D3Q27 + D3Q7 node."""
+    lib = _load()
+    p = _params3(params)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    fo, go = np.empty(27), np.empty(7)
+    lib.orc3_collide_node(ctypes.byref(p), _ptr(f), _ptr(g), _ptr(fo), _ptr(go))
+    return fo, go
+
+
+def equilibrium3_node(params: dict, rho, ux, uy, uz, T):
+    lib = _load()
+    p = _params3(params)
+    f, g = np.empty(27), np.empty(7)
+    lib.orc3_equilibrium_node(ctypes.byref(p), float(rho), float(ux), float(uy), float(uz), float(T),
+                              _ptr(f), _ptr(g))
+    return f, g
+
+
+def matrices3(params: dict, ux: float, uy: float, uz: float) -> dict:
+    """M, Minv, N, S (27 x 27), MT, MTinv, NT, ST (7 x 7), wT (7), e27 (27 x 3), e7 (7 x 3)."""
+    lib = _load()
+    p = _params3(params)
+    shapes = dict(M=(27, 27), Minv=(27, 27), N=(27, 27), S=(27, 27), MT=(7, 7), MTinv=(7, 7),
+                  NT=(7, 7), ST=(7, 7), wT=(7,))
+    out = {k: np.empty(s) for k, s in shapes.items()}
+    e27 = np.empty((27, 3), dtype=np.int32)
+    e7 = np.empty((7, 3), dtype=np.int32)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.orc3_matrices(ctypes.byref(p), float(ux), float(uy), float(uz),
+                      *[_ptr(out[k]) for k in ("M", "Minv", "N", "S", "MT", "MTinv", "NT", "ST", "wT")],
+                      e27.ctypes.data_as(ip), e7.ctypes.data_as(ip))
+    out["e27"], out["e7"] = e27, e7
+    return out
+
+
+def nusselt3(u_axis, T, params: dict, axis: int) -> float:
+    """Eq. (29) on a 3-D lattice: Nu = 1 + <u_axis (T - T0)> H / (alpha dT) over all nodes, H the
+    node count along `axis` (walls halfway between nodes), dT the difference of the wall
+    temperatures of that axis, heat from the hot wall counted positive."""
+    H = T.shape[2 - axis]
+    Tl, Th = params["T_wall"][2 * axis], params["T_wall"][2 * axis + 1]
+    dT = abs(Tl - Th) or 1.0
+    sign = 1.0 if Tl >= Th else -1.0
+    return 1.0 + sign * float(np.mean(u_axis * (T - params["T0"]))) * H / (params["kappa"] * dT)

@@ -278,3 +278,131 @@ def request_trace(count: int = 64, seed: int = 0, rate_hz: float = 50.0, lo: int
         prob.name = f"req{k}_" + prob.name
         out.append((t, prob))
     return out
+
+
+# ------------------------------------------------------------------------------------------------
+# Three-dimensional problems (D3Q27 flow + D3Q7 temperature). Fields are float64 arrays of shape
+# (nz, ny, nx), x fastest; faces in wall / T_wall are ordered -x, +x, -y, +y, -z, +z; buoyancy acts
+# along +g_axis (z by default, gravity along -z).
+
+
+def default_params3(**overrides) -> dict:
+    """Defaults of the 3-D form: those of default_params, with the rates of the fifth- and
+    sixth-order moments s_5 = s_6 = 1, a 3-vector Fv, g_axis = 2 and six faces."""
+    p = dict(
+        nu=0.02, kappa=0.02, g_beta=0.0, T0=0.0, rho0=1.0,
+        s_b=1.0, s_3=1.0, s_4=1.0, s_5=1.0, s_6=1.0, lambda0=1.0, lambda2=1.0, cs2_T=0.25,
+        Fv=(0.0, 0.0, 0.0), g_axis=2,
+        wall=(WALL_PERIODIC,) * 6, T_wall=(0.0,) * 6,
+        storage=STORAGE_F64, T_ref=0.0, u_ref=0.0, dT_ref=0.0,
+    )
+    for k, v in overrides.items():
+        if k not in p:
+            raise KeyError(f"unknown parameter {k!r}")
+        p[k] = v
+    return p
+
+
+@dataclasses.dataclass
+class Problem3D:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    params: dict
+    rho: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    uz: np.ndarray
+    T: np.ndarray
+    nu_axis: int = 2
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def fields(self):
+        return self.rho, self.ux, self.uy, self.uz, self.T
+
+    def with_storage(self, storage: int) -> "Problem3D":
+        p = dict(self.params)
+        p["storage"] = storage
+        return dataclasses.replace(self, params=p)
+
+
+def _grid3(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y, z
+
+
+def rayleigh_benard3d(nx: int, ny: int, nz: int, Ra: float, Pr: float = 0.71, u_c: float = 0.1,
+                      perturb: float = 1e-3, seed: int = 0, storage=STORAGE_F64) -> Problem3D:
+    """Rayleigh-Benard convection in a box periodic in x and y, Dirichlet walls on the z faces
+    (T = +0.5 below, -0.5 above), H = nz, fluid at rest, T on the conduction line plus seeded
+    uniform noise of amplitude `perturb`."""
+    H = float(nz)
+    nu, alpha, gb = convection_params(H, Ra, Pr, u_c)
+    rng = np.random.default_rng(seed)
+    _, _, z = _grid3(nx, ny, nz)
+    T = 0.5 - (z + 0.5) / H + rng.uniform(-perturb, perturb, (nz, ny, nx))
+    zero = np.zeros((nz, ny, nx))
+    p = default_params3(nu=nu, kappa=alpha, g_beta=gb, T0=0.0, storage=storage,
+                        wall=(WALL_PERIODIC,) * 4 + (WALL_DIRICHLET,) * 2,
+                        T_wall=(0.0,) * 4 + (0.5, -0.5), u_ref=u_c, dT_ref=1.0)
+    return Problem3D(f"rayleigh_benard3d_{nx}x{ny}x{nz}", nx, ny, nz, p, np.ones((nz, ny, nx)),
+                     zero.copy(), zero.copy(), zero.copy(), T, nu_axis=2,
+                     meta=dict(Ra=Ra, Pr=Pr, u_c=u_c, seed=seed))
+
+
+def taylor_green3d(n: int = 32, U: float = 0.01, nu: float = 0.02, kappa: float = 0.02,
+                   T_amp: float = 0.01, noise: float = 1e-4, seed: int = 0,
+                   storage=STORAGE_F64) -> Problem3D:
+    """Triply periodic Taylor-Green vortex: u_x = U sin(kx) cos(ky) cos(kz), u_y = -U cos(kx)
+    sin(ky) cos(kz), u_z = 0, T = T_amp sin(kx) sin(ky) sin(kz), rho = 1, plus seeded noise."""
+    rng = np.random.default_rng(seed)
+    x, y, z = _grid3(n, n, n)
+    k = 2 * math.pi / n
+    sh = (n, n, n)
+    ux = U * np.sin(k * x) * np.cos(k * y) * np.cos(k * z) + rng.uniform(-noise, noise, sh)
+    uy = -U * np.cos(k * x) * np.sin(k * y) * np.cos(k * z) + rng.uniform(-noise, noise, sh)
+    uz = rng.uniform(-noise, noise, sh)
+    T = T_amp * np.sin(k * x) * np.sin(k * y) * np.sin(k * z) + rng.uniform(-noise, noise, sh)
+    p = default_params3(nu=nu, kappa=kappa, storage=storage, u_ref=U, dT_ref=T_amp)
+    return Problem3D(f"taylor_green3d_{n}", n, n, n, p, np.ones(sh), ux, uy, uz, T,
+                     meta=dict(U=U, seed=seed))
+
+
+def random_problem3d(nx: int, ny: int, nz: int, seed: int = 0, storage=STORAGE_F64,
+                     walls: tuple | None = None) -> Problem3D:
+    """Seeded random parameters, faces and fields (for parity tests): rates drawn in their stable
+    ranges, buoyancy along a random axis, each axis periodic or walled (Dirichlet or adiabatic per
+    face), velocities up to 0.05, temperatures within +-0.5."""
+    rng = np.random.default_rng(seed)
+    if walls is None:
+        walls = []
+        for _ in range(3):
+            if rng.uniform() < 0.5:
+                walls += [WALL_PERIODIC, WALL_PERIODIC]
+            else:
+                walls += [int(rng.choice([WALL_DIRICHLET, WALL_ADIABATIC])) for _ in range(2)]
+    sh = (nz, ny, nx)
+    p = default_params3(nu=float(rng.uniform(0.01, 0.15)), kappa=float(rng.uniform(0.01, 0.15)),
+                        g_beta=float(rng.uniform(0, 5e-3)), T0=float(rng.uniform(-0.1, 0.1)),
+                        s_b=float(rng.uniform(0.8, 1.6)), s_3=float(rng.uniform(0.8, 1.6)),
+                        s_4=float(rng.uniform(0.8, 1.6)), s_5=float(rng.uniform(0.8, 1.6)),
+                        s_6=float(rng.uniform(0.8, 1.6)), lambda2=float(rng.uniform(0.8, 1.6)),
+                        Fv=tuple(float(v) for v in rng.uniform(-1e-4, 1e-4, 3)),
+                        g_axis=int(rng.integers(0, 3)), wall=tuple(walls),
+                        T_wall=tuple(float(v) for v in rng.uniform(-0.5, 0.5, 6)),
+                        storage=storage, T_ref=0.0, u_ref=0.05, dT_ref=0.5)
+    rho = 1.0 + rng.uniform(-1e-3, 1e-3, sh)
+    ux, uy, uz = (rng.uniform(-0.05, 0.05, sh) for _ in range(3))
+    T = rng.uniform(-0.5, 0.5, sh)
+    return Problem3D(f"random3d_{nx}x{ny}x{nz}_s{seed}", nx, ny, nz, p, rho, ux, uy, uz, T,
+                     meta=dict(seed=seed))

@@ -1,0 +1,112 @@
+/*
+ * clb3d.h -- C ABI of the three-dimensional form of the coupled central-moment lattice Boltzmann
+ * method (Fei, Luo, Lin & Li, arXiv:1710.10569): D3Q27 flow populations and D3Q7 temperature
+ * populations, stepped by one fused collide-and-stream kernel on the GPU.
+ *
+ * The paper states the method in two dimensions (D2Q9 flow, Sec. 2.1, Eqs. 4-13; D2Q5 temperature,
+ * Sec. 2.2, Eqs. 14-23) and says it extends to three dimensions directly (Sec. 4). This library
+ * applies the same definitions on the 3-D lattices:
+ *   - central moments k~_abc = sum_i (e_x-u_x)^a (e_y-u_y)^b (e_z-u_z)^c f_i, a, b, c in {0,1,2}
+ *     (Eq. 5 on D3Q27);
+ *   - equilibrium central moments rho m(a) m(b) m(c) with m(0) = 1, m(1) = 0, m(2) = 1/3 (Eq. 9);
+ *   - forcing moments F_d prod_{d' != d} m(a_d') where exactly one index a_d is 1 (Eq. 11);
+ *   - relaxation Gamma~* = Gamma~ - S (Gamma~ - Gamma~eq) + (I - S/2) C (Eq. 8): the trace of the
+ *     three normal second moments with s_b, their deviators and the off-diagonal second moments
+ *     with s_nu (nu = (1/s_nu - 1/2)/3), third- to sixth-order moments with s_3 .. s_6;
+ *   - D3Q7 moments 1, e_d, e_d^2, equilibrium (T, 0, 0, 0, cs2_T T x3), rates
+ *     (lambda0, lambda1 x3, lambda2 x3) with alpha = (1/lambda1 - 1/2) cs2_T (Eqs. 16-21);
+ *   - Boussinesq force F = Fv + rho0 g_beta (T - T0) along +g_axis (Eq. 3), u = (sum f e + F/2)/rho
+ *     (Eq. 13), T = sum g (Eq. 23);
+ *   - walls halfway between nodes on any face: f bounces back, g anti-bounces back
+ *     (g_i = -g*_opp + cs2_T T_w) on Dirichlet faces and bounces back on adiabatic faces.
+ *
+ * Status codes, clb_last_error() and the storage forms are those of clb.h.
+ *
+ * Layout. Fields passed in and out are FP64 host arrays of nz * ny * nx values, x fastest
+ * (index (z * ny + y) * nx + x). Population arrays are [27][nz][ny][nx] and [7][nz][ny][nx]:
+ * D3Q27 population i = a + 3 b + 9 c has velocity (v(a), v(b), v(c)) with v(0) = 0, v(1) = +1,
+ * v(2) = -1; D3Q7 populations are ordered rest, +x, -x, +y, -y, +z, -z.
+ *
+ * Ownership. clb3d_create allocates the lattice's device memory (two population buffers of 34
+ * planes, FP64 staging for the fields and the reduction partials) and owns it until
+ * clb3d_destroy. All work is enqueued on the stream given at creation (NULL: the legacy default
+ * stream); functions that return host data synchronise that stream.
+ */
+#ifndef CLB3D_H
+#define CLB3D_H
+
+#include <stddef.h>
+
+#include "clb.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct clb3d_lattice clb3d_lattice;
+
+typedef struct {
+    double nu;        /* kinematic viscosity, > 0 (gives s_nu; 0 < s_nu < 2) */
+    double kappa;     /* thermal diffusivity, > 0 (gives lambda1; 0 < lambda1 < 2) */
+    double g_beta;    /* |g| beta >= 0 */
+    double T0;        /* reference temperature of the Boussinesq force */
+    double rho0;      /* reference density (force, and the rest state of deviation storage) */
+    double s_b, s_3, s_4, s_5, s_6; /* rates of the bulk, 3rd-, 4th-, 5th- and 6th-order moments, in (0, 2) */
+    double lambda2;   /* rate of the second-order D3Q7 moments, in (0, 2) */
+    double cs2_T;     /* D3Q7 sound speed squared, in (0, 1/3) */
+    double Fv[3];     /* body force density */
+    int g_axis;       /* buoyancy along +g_axis: 0, 1 or 2 */
+    int wall[6];      /* clb_wall of faces -x, +x, -y, +y, -z, +z: periodic faces come in pairs;
+                         CLB_WALL_WET is not supported in 3-D */
+    double T_wall[6]; /* temperature of Dirichlet faces */
+    int storage;      /* clb_storage: CLB_F64 or CLB_F32 (FP32 deviations from the rest state) */
+    double T_ref;     /* rest temperature of FP32 deviation storage */
+} clb3d_params;
+
+/* Defaults: nu = kappa = 0.02, rho0 = 1, all rates 1, cs2_T = 1/4, g_axis = 2, periodic, FP64. */
+clb_status clb3d_params_default(clb3d_params* p);
+
+/* Device bytes clb3d_create will allocate for an nx x ny x nz lattice. */
+clb_status clb3d_footprint(int nx, int ny, int nz, const clb3d_params* p, size_t* bytes);
+
+/* Create a lattice (1 <= n <= 2^20 per axis, nx * ny * nz <= 2^30). Errors: CLB_EINVAL for bad sizes
+ * or parameters, CLB_ENOMEM, CLB_ECUDA. The populations are undefined until clb3d_init_fields. */
+clb_status clb3d_create(int nx, int ny, int nz, const clb3d_params* p, void* stream, clb3d_lattice** out);
+void clb3d_destroy(clb3d_lattice* h);
+
+/* f = f^eq(rho, u), g = g^eq(T, u) at every node from host fields (nz*ny*nx each). */
+clb_status clb3d_init_fields(clb3d_lattice* h, const double* rho, const double* ux, const double* uy,
+                             const double* uz, const double* T);
+
+/* n >= 0 time steps (collision, then pull streaming with the face rules), enqueued on the stream;
+ * returns after enqueueing. */
+clb_status clb3d_step(clb3d_lattice* h, long n);
+
+/* rho, u, T of the current (pre-collision) state into host arrays; synchronises. */
+clb_status clb3d_fields(clb3d_lattice* h, double* rho, double* ux, double* uy, double* uz, double* T);
+
+/* The current pre-collision populations, as FP64 populations (not deviations), into host arrays
+ * f[27 * n], g[7 * n]; synchronises. */
+clb_status clb3d_populations(clb3d_lattice* h, double* f, double* g);
+
+/* Nusselt number along `axis` (Eq. 29 with H the node count of that axis): 1 + <u_axis (T - T0)>
+ * H / (kappa dT), dT the difference of that axis's wall temperatures (1 if equal), heat from the
+ * hot face counted positive. FP64 sums in a fixed order. CLB_ENAN if a field is not finite. */
+clb_status clb3d_nusselt(clb3d_lattice* h, int axis, double* nu_out);
+
+/* Launch shape of the step kernel: block_x threads along x (a multiple of 32, <= 256) times block_y
+ * rows (block_x * block_y <= 256). 0 keeps a value. */
+clb_status clb3d_set_launch(clb3d_lattice* h, int block_x, int block_y);
+
+clb_status clb3d_sync(clb3d_lattice* h);
+
+/* The stream the lattice works on, and the device address of the buffer holding the current
+ * post-collision state with its plane stride in elements (for device-side consumers). */
+void* clb3d_stream(clb3d_lattice* h);
+clb_status clb3d_buffers(clb3d_lattice* h, void** current, long long* plane_elems, int* row_pitch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -20,7 +20,8 @@ from . import workloads as W
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libclb.so")
-HEADER = os.path.join(os.path.dirname(_HERE), "include", "clb.h")
+INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+HEADER = os.path.join(INCLUDE, "clb.h")
 
 CLB_OK, CLB_EINVAL, CLB_ENOMEM, CLB_ENAN, CLB_ETIMEOUT, CLB_ECUDA, CLB_EBUSY = range(7)
 STATUS_NAMES = {0: "CLB_OK", 1: "CLB_EINVAL", 2: "CLB_ENOMEM", 3: "CLB_ENAN", 4: "CLB_ETIMEOUT",
@@ -40,6 +41,15 @@ class clb_params(ctypes.Structure):
                 ("cs2_T", ctypes.c_double), ("Fv", ctypes.c_double * 2), ("wall", ctypes.c_int * 4),
                 ("T_wall", ctypes.c_double * 4), ("storage", ctypes.c_int), ("T_ref", ctypes.c_double),
                 ("u_ref", ctypes.c_double), ("dT_ref", ctypes.c_double), ("u_wall", ctypes.c_double * 8)]
+
+
+class clb3d_params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("kappa", ctypes.c_double), ("g_beta", ctypes.c_double),
+                ("T0", ctypes.c_double), ("rho0", ctypes.c_double), ("s_b", ctypes.c_double),
+                ("s_3", ctypes.c_double), ("s_4", ctypes.c_double), ("s_5", ctypes.c_double),
+                ("s_6", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
+                ("Fv", ctypes.c_double * 3), ("g_axis", ctypes.c_int), ("wall", ctypes.c_int * 6),
+                ("T_wall", ctypes.c_double * 6), ("storage", ctypes.c_int), ("T_ref", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -101,9 +111,22 @@ _SIGS = {
     "clb_serve_poll": [_VP, _L, _P(_I), _D, _P(_L), _D],
     "clb_serve_cancel": [_VP, _L],
     "clb_serve_fetch": [_VP, _L, _D, _D, _D, _D],
+    "clb3d_params_default": [_P(clb3d_params)],
+    "clb3d_footprint": [_I, _I, _I, _P(clb3d_params), _P(_S)],
+    "clb3d_create": [_I, _I, _I, _P(clb3d_params), _VP, _P(_VP)],
+    "clb3d_destroy": [_VP],
+    "clb3d_init_fields": [_VP, _D, _D, _D, _D, _D],
+    "clb3d_step": [_VP, _L],
+    "clb3d_fields": [_VP, _D, _D, _D, _D, _D],
+    "clb3d_populations": [_VP, _D, _D],
+    "clb3d_nusselt": [_VP, _I, _D],
+    "clb3d_set_launch": [_VP, _I, _I],
+    "clb3d_sync": [_VP],
+    "clb3d_stream": [_VP],
+    "clb3d_buffers": [_VP, _P(_VP), _P(ctypes.c_longlong), _P(_I)],
 }
 _RESTYPES = {"clb_destroy": None, "clb_batch_destroy": None, "clb_serve_close": None,
-             "clb_thermal_destroy": None,
+             "clb_thermal_destroy": None, "clb3d_destroy": None, "clb3d_stream": _VP,
              "clb_last_error": ctypes.c_char_p, "clb_version": ctypes.c_char_p, "clb_stream": _VP}
 
 _lock = threading.Lock()
@@ -486,9 +509,102 @@ class Server:
         return tuple(out)
 
 
-def declared_entry_points(header: str = HEADER):
-    """Names of the functions include/clb.h declares."""
+def declared_entry_points(header: str | None = None):
+    """Names of the functions the headers in include/ declare (or the one header given)."""
+    import glob
     import re
-    text = open(header).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(clb_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    for path in [header] if header else sorted(glob.glob(os.path.join(INCLUDE, "*.h"))):
+        text = open(path).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(clb(?:3d)?_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def params3(p: dict) -> clb3d_params:
+    """clb3d_params from a parameter dict (see workloads.default_params3)."""
+    s = clb3d_params()
+    for k in ("nu", "kappa", "g_beta", "T0", "rho0", "s_b", "s_3", "s_4", "s_5", "s_6", "lambda2",
+              "cs2_T", "T_ref"):
+        setattr(s, k, float(p[k]))
+    for i in range(3):
+        s.Fv[i] = float(p["Fv"][i])
+    s.g_axis = int(p["g_axis"])
+    for i in range(6):
+        s.wall[i] = int(p["wall"][i])
+        s.T_wall[i] = float(p["T_wall"][i])
+    s.storage = int(p["storage"])
+    return s
+
+
+class Lattice3D:
+    """One 3-D lattice (D3Q27 + D3Q7, include/clb3d.h). Fields are (nz, ny, nx) float64 arrays. The
+    library allocates the lattice's device memory; work goes on torch's current stream unless a
+    stream is given."""
+
+    def __init__(self, nx: int, ny: int, nz: int, p: dict, stream=None):
+        L = lib()
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.params = dict(p)
+        self._p = params3(p)
+        self.stream = _stream_handle(stream)
+        h = _VP()
+        _check(L.clb3d_create(nx, ny, nz, ctypes.byref(self._p), self.stream, ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_problem(cls, prob, stream=None) -> "Lattice3D":
+        lat = cls(prob.nx, prob.ny, prob.nz, prob.params, stream)
+        lat.init_fields(*prob.fields())
+        return lat
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().clb3d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, rho, ux, uy, uz, T):
+        n = self.nodes
+        arrs = [_host(np.broadcast_to(np.asarray(a, dtype=np.float64), self.shape), n)
+                for a in (rho, ux, uy, uz, T)]
+        _check(lib().clb3d_init_fields(self._h, *[_dptr(a) for a in arrs]))
+
+    def step(self, n: int = 1):
+        _check(lib().clb3d_step(self._h, int(n)))
+
+    def sync(self):
+        _check(lib().clb3d_sync(self._h))
+
+    def fields(self):
+        """(rho, ux, uy, uz, T), each (nz, ny, nx)."""
+        out = [np.empty(self.shape) for _ in range(5)]
+        _check(lib().clb3d_fields(self._h, *[_dptr(a) for a in out]))
+        return tuple(out)
+
+    def populations(self):
+        f = np.empty((27,) + self.shape)
+        g = np.empty((7,) + self.shape)
+        _check(lib().clb3d_populations(self._h, _dptr(f), _dptr(g)))
+        return f, g
+
+    def nusselt(self, axis: int = 2) -> float:
+        v = ctypes.c_double()
+        _check(lib().clb3d_nusselt(self._h, int(axis), ctypes.byref(v)))
+        return v.value
+
+    def set_launch(self, block_x: int = 0, block_y: int = 0):
+        _check(lib().clb3d_set_launch(self._h, int(block_x), int(block_y)))

@@ -315,6 +315,40 @@ def batched_run(storage: int, count: int = 256, steps: int = 1000, seq_subset: i
                        "speedup": dt_seq / dt_sub}}
 
 
+BYTES_PER_NODE_3D = {W.STORAGE_F64: 544, W.STORAGE_F32: 272}  # 34 populations in + 34 out
+
+
+def three_d_run(steps: int, nx: int = 256, ny: int = 256, nz: int = 128):
+    """The 3-D form (D3Q27 + D3Q7): Rayleigh-Benard on nx x ny x nz, Ra = 1e7, timed with CUDA
+    events on the lattice's stream, FP32 deviation storage (HBM roofline at 272 B/node) and FP64
+    (FP64 issue-bound; a shorter window)."""
+    import torch
+    from paper_1710_10569_gb300 import clb
+    peak, _ = measured_peaks()
+    out = {}
+    for st, k in ((W.STORAGE_F32, steps), (W.STORAGE_F64, max(32, steps // 32))):
+        prob = W.rayleigh_benard3d(nx, ny, nz, Ra=1e7, storage=st)
+        lat = clb.Lattice3D.from_problem(prob)
+        lat.step(64)
+        stream = torch.cuda.ExternalStream(lat.stream) if lat.stream else torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
+        lat.close()
+        gbs = BYTES_PER_NODE_3D[st] * prob.nodes * k / dt / 1e9
+        out[W.STORAGE_NAMES[st]] = {"mlups": prob.nodes * k / dt / 1e6, "achieved_gbs": gbs,
+                                    "hbm_frac": gbs / peak, "steps": k,
+                                    "bytes_per_node": BYTES_PER_NODE_3D[st]}
+    out["workload"] = f"rayleigh_benard3d_{nx}x{ny}x{nz}_Ra1e7_Pr0.71"
+    out["kernel"] = "k_step3"
+    return out
+
+
 def served_run(storage: int, count: int = 48, step_cap: int = 20000, tol: float = 1e-6):
     """A seeded Poisson request trace (mean 50 requests/s; periodic Taylor-Green, side-heated
     cavity and Rayleigh-Benard; edges log-uniform 64-512, aspect 1 or 2) served with continuous
@@ -391,6 +425,7 @@ def run_ours(args):
             l2.close()
     e2e = e2e_run(storage, args.steps, args.nx, args.ny) if rank == 0 else None
     thermal = thermal_run(storage, args.steps) if (rank == 0 and not args.no_variants) else None
+    three_d = three_d_run(max(200, args.steps // 20)) if (rank == 0 and not args.no_variants) else None
     batched = batched_run(storage) if (rank == 0 and not args.no_serve) else None
     served = served_run(storage) if (rank == 0 and not args.no_serve) else None
     if rank == 0:
@@ -418,6 +453,7 @@ def run_ours(args):
             "clocks": clocks.summary(),
             "variants": variants,
             "thermal_only": thermal,
+            "three_d": three_d,
             "batched": batched,
             "served": served,
         }
@@ -473,6 +509,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched and served runs")
+    ap.add_argument("--three-d-only", action="store_true",
+                    help="run only the 3-D workload (D3Q27 + D3Q7, 256 x 256 x 128) and print its JSON")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload (256 uneven cavities) and print its JSON")
     args = ap.parse_args()
@@ -480,6 +518,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.three_d_only:
+        print(json.dumps(three_d_run(args.steps)), flush=True)
     elif args.batched_only:
         print(json.dumps(batched_run({"f64": W.STORAGE_F64, "f32": W.STORAGE_F32,
                                       "f16dev": W.STORAGE_F16DEV}[args.storage], steps=args.steps)), flush=True)

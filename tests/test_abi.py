@@ -100,3 +100,40 @@ def test_binding_raises_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(c, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         c.lib()
+
+
+def footprint3(clb, nx, ny, nz, **kw):
+    p = clb.params3(W.default_params3(**kw))
+    n = ctypes.c_size_t()
+    st = clb.lib().clb3d_footprint(nx, ny, nz, ctypes.byref(p), ctypes.byref(n))
+    return st, n.value
+
+
+def test_3d_defaults_and_footprint(clb):
+    p = clb.clb3d_params()
+    assert clb.lib().clb3d_params_default(ctypes.byref(p)) == clb.CLB_OK
+    assert (p.cs2_T, p.s_3, p.s_6, p.g_axis, p.rho0) == (0.25, 1.0, 1.0, 2, 1.0)
+    st, n64 = footprint3(clb, 256, 256, 128, storage=W.STORAGE_F64)
+    st2, n32 = footprint3(clb, 256, 256, 128, storage=W.STORAGE_F32)
+    assert st == st2 == clb.CLB_OK
+    nodes = 256 * 256 * 128
+    # two buffers of 34 populations plus 5 FP64 staging fields per node
+    assert nodes * (2 * 34 * 8 + 40) <= n64 < nodes * (2 * 34 * 8 + 40) * 1.01
+    assert nodes * (2 * 34 * 4 + 40) <= n32 < nodes * (2 * 34 * 4 + 40) * 1.01
+
+
+@pytest.mark.parametrize("kw,n", [
+    (dict(nu=0.0), (8, 8, 8)),
+    (dict(storage=W.STORAGE_F16DEV), (8, 8, 8)),
+    (dict(wall=(W.WALL_PERIODIC, W.WALL_DIRICHLET) + (W.WALL_PERIODIC,) * 4), (8, 8, 8)),
+    (dict(wall=(W.WALL_WET,) * 2 + (W.WALL_PERIODIC,) * 4), (8, 8, 8)),
+    (dict(g_axis=3), (8, 8, 8)),
+    (dict(s_5=2.0), (8, 8, 8)),
+    (dict(cs2_T=0.34), (8, 8, 8)),
+    (dict(), (0, 8, 8)),
+    (dict(), (1 << 11, 1 << 11, 1 << 10)),
+])
+def test_3d_invalid_arguments_are_rejected(clb, kw, n):
+    st, _ = footprint3(clb, *n, **kw)
+    assert st == clb.CLB_EINVAL
+    assert clb.lib().clb_last_error()

@@ -41,11 +41,12 @@ DTYPE = {W.STORAGE_F64: "f64", W.STORAGE_F32: "f32", W.STORAGE_F16DEV: "f16dev s
 VARIANT_SIZE = {W.STORAGE_F64: (2048, 1024), W.STORAGE_F32: (2048, 1024), W.STORAGE_F16DEV: (4096, 2048)}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_traffic.json")
 KERNEL_SOURCES = ["paper_1710_10569_gb300/csrc/clb_core.cuh", "paper_1710_10569_gb300/csrc/clb_kernels.cuh"]
+KERNEL3D_SOURCES = ["paper_1710_10569_gb300/csrc/clb_core.cuh", "paper_1710_10569_gb300/csrc/clb3d.cu"]
 
 
-def kernel_hash() -> str:
+def kernel_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -79,6 +80,21 @@ def traffic_per_launch(storage: int, nx: int, ny: int):
     it was taken on the current kernel source and that lattice (else None)."""
     e = profile_counts().get("launches", {}).get(W.STORAGE_NAMES[storage])
     if not e or e.get("nx") != nx or e.get("ny") != ny:
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+def traffic3d_per_launch(storage: int, nx: int, ny: int, nz: int):
+    """DRAM bytes per 3-D step-kernel launch from the committed ncu summary, if it was taken on the
+    current 3-D kernel source and that lattice (else None)."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as f:
+        d = json.load(f)
+    if d.get("kernel3d_source_hash") != kernel_hash(KERNEL3D_SOURCES):
+        return None
+    e = d.get("launches3d", {}).get(W.STORAGE_NAMES[storage])
+    if not e or (e.get("nx"), e.get("ny"), e.get("nz")) != (nx, ny, nz):
         return None
     return float(e["dram_bytes_per_launch"])
 
@@ -343,7 +359,8 @@ def three_d_run(steps: int, nx: int = 256, ny: int = 256, nz: int = 128):
         gbs = BYTES_PER_NODE_3D[st] * prob.nodes * k / dt / 1e9
         out[W.STORAGE_NAMES[st]] = {"mlups": prob.nodes * k / dt / 1e6, "achieved_gbs": gbs,
                                     "hbm_frac": gbs / peak, "steps": k,
-                                    "bytes_per_node": BYTES_PER_NODE_3D[st]}
+                                    "bytes_per_node": BYTES_PER_NODE_3D[st],
+                                    "dram_bytes_per_launch": traffic3d_per_launch(st, nx, ny, nz)}
     out["workload"] = f"rayleigh_benard3d_{nx}x{ny}x{nz}_Ra1e7_Pr0.71"
     out["kernel"] = "k_step3"
     return out

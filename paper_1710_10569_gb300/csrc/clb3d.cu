@@ -153,13 +153,17 @@ struct Axis {
     }
 };
 
-// E_k of the deviation collision: rho_b (R R R - m m m) - drho m m m.
-template <typename A>
+// E_k of the deviation collision: rho_b (R R R - m m m) - drho m m m. Populations stored as
+// themselves (DEV = false, rho_b = 0) need only the last term, which is what the full expression
+// evaluates to there (fma(0, d, t) = t).
+template <bool DEV, typename A>
 __device__ __forceinline__ A e_term(const Axis<A>& X, const Axis<A>& Y, const Axis<A>& Z, int a, int b,
                                     int c, A rho_b, A drho)
 {
+    const A t = -drho * (X.m[a] * Y.m[b] * Z.m[c]);
+    if constexpr (!DEV) return t;
     const A d = X.dl[a] * Y.R[b] * Z.R[c] + X.m[a] * (Y.dl[b] * Z.R[c] + Y.m[b] * Z.dl[c]);
-    return fma_(rho_b, d, -drho * (X.m[a] * Y.m[b] * Z.m[c]));
+    return fma_(rho_b, d, t);
 }
 
 // Forcing moment C_k (Eq. 11 on D3Q27): F_d times the Maxwellian moments of the other axes where
@@ -178,7 +182,7 @@ __device__ __forceinline__ A c_term(const Axis<A>& X, const Axis<A>& Y, const Ax
 // One node: Eqs. (3), (13), (23), then the D3Q27 collision (Eq. 8 in 3-D) and the D3Q7 collision
 // (Eq. 19 in 3-D), on the stored form (deviations for FP32, populations for FP64). f and g are
 // pre-collision on entry and post-collision on return.
-template <typename A>
+template <bool DEV, typename A>
 __device__ __forceinline__ void collide3(const Lat3<A>& P, A f[NF], A g[NG])
 {
     const A cs2 = A(1.0 / 3.0);
@@ -200,9 +204,9 @@ __device__ __forceinline__ void collide3(const Lat3<A>& P, A f[NF], A g[NG])
 
     const Axis<A> X(ux, cs2), Y(uy, cs2), Z(uz, cs2);
     // normal second moments: trace with s_b, deviators with s_nu
-    const A Xx = f[2] + e_term(X, Y, Z, 2, 0, 0, P.rho_b, drho);
-    const A Xy = f[6] + e_term(X, Y, Z, 0, 2, 0, P.rho_b, drho);
-    const A Xz = f[18] + e_term(X, Y, Z, 0, 0, 2, P.rho_b, drho);
+    const A Xx = f[2] + e_term<DEV>(X, Y, Z, 2, 0, 0, P.rho_b, drho);
+    const A Xy = f[6] + e_term<DEV>(X, Y, Z, 0, 2, 0, P.rho_b, drho);
+    const A Xz = f[18] + e_term<DEV>(X, Y, Z, 0, 0, 2, P.rho_b, drho);
     const A tr = P.s_b3 * ((Xx + Xy) + Xz);
     f[2] = f[2] - fma_(P.s_nu, Xx, tr);
     f[6] = f[6] - fma_(P.s_nu, Xy, tr);
@@ -216,7 +220,7 @@ __device__ __forceinline__ void collide3(const Lat3<A>& P, A f[NF], A g[NG])
             continue;
         }
         const A s = o == 2 ? P.s_nu : o == 3 ? P.s_3 : o == 4 ? P.s_4 : o == 5 ? P.s_5 : P.s_6;
-        const A x = f[k] + e_term(X, Y, Z, a, b, c, P.rho_b, drho);
+        const A x = f[k] + e_term<DEV>(X, Y, Z, a, b, c, P.rho_b, drho);
         const A cf = c_term(X, Y, Z, a, b, c, F);
         const bool forced = ((a == 1) + (b == 1) + (c == 1)) == 1;  // C_k can be non-zero
         f[k] = forced ? fma_(fma_(A(-0.5), s, A(1)), cf, fma_(-s, x, f[k])) : fma_(-s, x, f[k]);
@@ -233,9 +237,9 @@ __device__ __forceinline__ void collide3(const Lat3<A>& P, A f[NF], A g[NG])
         kd[d] = fma_(-u[d], dT, r1);
         kdd[d] = fma_(u[d] * u[d], dT, fma_(A(-2) * u[d], r1, r2));
         // relax: first order towards 0 (deviation term -T_b u), second towards cs2_T T
-        const A e1 = -P.T_b * u[d];
-        const A e2 = fma_(P.T_b, u[d] * u[d], -P.cs2T * dT);
-        kd[d] = fma_(-P.lambda1, kd[d] + e1, kd[d]);
+        const A e1 = DEV ? -P.T_b * u[d] : A(0);
+        const A e2 = DEV ? fma_(P.T_b, u[d] * u[d], -P.cs2T * dT) : -P.cs2T * dT;
+        kd[d] = fma_(-P.lambda1, DEV ? kd[d] + e1 : kd[d], kd[d]);
         kdd[d] = fma_(-P.lambda2, kdd[d] + e2, kdd[d]);
     }
     A rest = dT;
@@ -252,14 +256,14 @@ __device__ __forceinline__ void collide3(const Lat3<A>& P, A f[NF], A g[NG])
 
 // Equilibrium of one node on the stored form: the back transform of the equilibrium central
 // moments minus those of the rest state (-E for D3Q27; (dT, T_b u, cs2_T dT - T_b u^2) for D3Q7).
-template <typename A>
+template <bool DEV, typename A>
 __device__ __forceinline__ void equilibrium3(const Lat3<A>& P, A drho, A ux, A uy, A uz, A dT, A f[NF],
                                              A g[NG])
 {
     const A cs2 = A(1.0 / 3.0);
     const Axis<A> X(ux, cs2), Y(uy, cs2), Z(uz, cs2);
 #pragma unroll
-    for (int k = 0; k < NF; ++k) f[k] = -e_term(X, Y, Z, k % 3, (k / 3) % 3, k / 9, P.rho_b, drho);
+    for (int k = 0; k < NF; ++k) f[k] = -e_term<DEV>(X, Y, Z, k % 3, (k / 3) % 3, k / 9, P.rho_b, drho);
     back27(f, ux, uy, uz);
     const A u[3] = {ux, uy, uz};
     A rest = dT;
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(256) k_step3(const typename Storage<ST>::T* __
     const int y = r % P.ny, z = r / P.ny;
     A f[NF], g[NG];
     gather3(src, P, x, y, z, f, g);
-    collide3(P, f, g);
+    collide3<Storage<ST>::DEV>(P, f, g);
     store3(dst, P, (z * P.ny + y) * P.pitch + x, f, g);
 }
 
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(256) k_init3(typename Storage<ST>::T* __restri
     const A ux = A(fields[n + k]), uy = A(fields[2 * n + k]), uz = A(fields[3 * n + k]);
     const A dT = A(fields[4 * n + k] - double(P.T_b));
     A f[NF], g[NG];
-    equilibrium3(P, drho, ux, uy, uz, dT, f, g);
+    equilibrium3<Storage<ST>::DEV>(P, drho, ux, uy, uz, dT, f, g);
     const int pl = (int)P.plane;
     const int here = (z * P.ny + y) * P.pitch + x;
     // the node's pull of population i reads the node at x - e_i; write there, or in the opposite

@@ -478,43 +478,68 @@ __device__ __forceinline__ void block_sum(double v[RS_N], double* out)
 // kReduceThreads per row y; threads stride over x in a fixed order, so the sums do not depend on
 // how the step kernel is launched. With update != 0 the snapshot (u_x, u_y, T as double
 // [3][ny][nx]) is replaced by the current fields.
+// One node's terms of the diagnostics sums (pulled populations -> u, T in FP64), added to v; with
+// update != 0 the node's snapshot entries are replaced by the current fields. wrow weights the
+// Nusselt term (wet-wall rows count half, the trapezoid rule over [0, H]).
+template <typename E, typename A>
+__device__ __forceinline__ void node_diag(const E* __restrict__ src, const LatParams<A>& P, int x, int y,
+                                          int axis, double* __restrict__ snap, int update, double wrow,
+                                          double v[RS_N])
+{
+    const long long N = (long long)P.nx * P.ny;
+    A f[9], g[5];
+    gather(src, P, x, y, f, g);
+    const Macro<A> m = macroscopic(P, f, g);
+    const double ux = double(m.ux), uy = double(m.uy), T = double(P.T_b) + double(m.dT);
+    const long long n = (long long)y * P.nx + x;
+    const double sx = snap[n], sy = snap[N + n], sT = snap[2 * N + n];
+    v[RS_UT] += wrow * ((axis == 0 ? ux : uy) * (T - double(P.T0)));
+    v[RS_DU] += (ux - sx) * (ux - sx) + (uy - sy) * (uy - sy);
+    v[RS_U] += ux * ux + uy * uy;
+    v[RS_DT] += (T - sT) * (T - sT);
+    v[RS_T] += T * T;
+    v[RS_BAD] += (isfinite(ux) && isfinite(uy) && isfinite(T) && isfinite(double(m.rho))) ? 0.0 : 1.0;
+    if (update) {
+        snap[n] = ux;
+        snap[N + n] = uy;
+        snap[2 * N + n] = T;
+    }
+}
+
+// Per-row FP64 partial sums for the diagnostics: sum u_axis (T - T0), sum |u - u_snap|^2,
+// sum |u|^2, sum (T - T_snap)^2, sum T^2 and the count of non-finite nodes. One block of
+// kReduceThreads per row y; threads stride over x in a fixed order, so the sums do not depend on
+// how the step kernel is launched. With update != 0 the snapshot (u_x, u_y, T as double
+// [3][ny][nx]) is replaced by the current fields. (The batched lattices use this form; a single
+// lattice uses the one-node-per-thread form below.)
 template <typename E, typename A>
 __device__ __forceinline__ void reduce_row(const E* __restrict__ src, const LatParams<A>& P, int y,
                                            int axis, double* __restrict__ snap, int update,
                                            double* __restrict__ partial_row)
 {
-    const long long N = (long long)P.nx * P.ny;
     // wet walls lie on the end rows: the average over [0, H] gives those rows half weight
     const double wrow = (P.wet_y && axis == 1 && (y == 0 || y == P.ny - 1)) ? 0.5 : 1.0;
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
-    for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) {
-        A f[9], g[5];
-        gather(src, P, x, y, f, g);
-        const Macro<A> m = macroscopic(P, f, g);
-        const double ux = double(m.ux), uy = double(m.uy), T = double(P.T_b) + double(m.dT);
-        const long long n = (long long)y * P.nx + x;
-        const double sx = snap[n], sy = snap[N + n], sT = snap[2 * N + n];
-        v[RS_UT] += wrow * ((axis == 0 ? ux : uy) * (T - double(P.T0)));
-        v[RS_DU] += (ux - sx) * (ux - sx) + (uy - sy) * (uy - sy);
-        v[RS_U] += ux * ux + uy * uy;
-        v[RS_DT] += (T - sT) * (T - sT);
-        v[RS_T] += T * T;
-        v[RS_BAD] += (isfinite(ux) && isfinite(uy) && isfinite(T) && isfinite(double(m.rho))) ? 0.0 : 1.0;
-        if (update) {
-            snap[n] = ux;
-            snap[N + n] = uy;
-            snap[2 * N + n] = T;
-        }
-    }
+    for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, wrow, v);
     block_sum(v, partial_row);
 }
 
+// The same sums with one node per thread: block b covers nodes seg * kReduceThreads .. + 255 of
+// row y (b = y * nseg + seg) and writes its partial sums (shuffle tree within each warp, then the
+// warps in order) to partial[b]. Every node's load is in flight at once, so the pass runs near the
+// memory bandwidth instead of waiting on one gather per thread after another; the summation order
+// depends only on nx and ny.
 template <int ST>
-__global__ void __launch_bounds__(kReduceThreads) k_reduce_rows(
+__global__ void __launch_bounds__(kReduceThreads, 4) k_reduce_nodes(
     const typename Storage<ST>::T* __restrict__ src, const LatParams<typename Storage<ST>::A> P,
-    int axis, double* __restrict__ snap, int update, double* __restrict__ partial)
+    int axis, double* __restrict__ snap, int update, double* __restrict__ partial, int nseg)
 {
-    reduce_row(src, P, blockIdx.x, axis, snap, update, partial + (long long)blockIdx.x * RS_N);
+    const int seg = blockIdx.x % nseg, y = blockIdx.x / nseg;
+    const int x = seg * kReduceThreads + threadIdx.x;
+    const double wrow = (P.wet_y && axis == 1 && (y == 0 || y == P.ny - 1)) ? 0.5 : 1.0;
+    double v[RS_N] = {0, 0, 0, 0, 0, 0};
+    if (x < P.nx) node_diag(src, P, x, y, axis, snap, update, wrow, v);
+    block_sum(v, partial + (long long)blockIdx.x * RS_N);
 }
 
 // Sum the per-row partials in row order and finish the diagnostics in FP64: out[0..RS_N-1] = the

@@ -106,6 +106,9 @@ struct DeviceGuard {
     }
 };
 
+// Blocks per row of the one-node-per-thread diagnostics pass.
+int diag_segments(int nx) { return (nx + kReduceThreads - 1) / kReduceThreads; }
+
 struct Layout {
     size_t buf[2], snap, stage, partial, diag, total;
 };
@@ -120,7 +123,7 @@ Layout layout(int nx, int ny, int storage)
     L.buf[1] = off; off += bb;
     L.snap = off; off += align256(3 * N * sizeof(double));
     L.stage = off; off += align256(4 * N * sizeof(double));
-    L.partial = off; off += align256((size_t)ny * RS_N * sizeof(double));
+    L.partial = off; off += align256((size_t)ny * diag_segments(nx) * RS_N * sizeof(double));
     L.diag = off; off += align256(16 * sizeof(double));
     L.total = off;
     return L;
@@ -302,11 +305,12 @@ clb_status launch_fields(clb_handle* h, double* rho, double* ux, double* uy, dou
 clb_status run_diagnostics(clb_handle* h, int axis, int update)
 {
     const void* s = h->buf[h->cur];
-    const int rows = h->ny;
+    const int nseg = diag_segments(h->nx);
+    const int rows = h->ny * nseg;  // partial entries
     switch (h->p.storage) {
-    case CLB_F64: k_reduce_rows<ST_F64><<<rows, kReduceThreads, 0, h->stream>>>((const double*)s, h->Pd, axis, h->snap, update, h->partial); break;
-    case CLB_F32: k_reduce_rows<ST_F32><<<rows, kReduceThreads, 0, h->stream>>>((const float*)s, h->Pf, axis, h->snap, update, h->partial); break;
-    default: k_reduce_rows<ST_F16DEV><<<rows, kReduceThreads, 0, h->stream>>>((const __half*)s, h->Pf, axis, h->snap, update, h->partial); break;
+    case CLB_F64: k_reduce_nodes<ST_F64><<<rows, kReduceThreads, 0, h->stream>>>((const double*)s, h->Pd, axis, h->snap, update, h->partial, nseg); break;
+    case CLB_F32: k_reduce_nodes<ST_F32><<<rows, kReduceThreads, 0, h->stream>>>((const float*)s, h->Pf, axis, h->snap, update, h->partial, nseg); break;
+    default: k_reduce_nodes<ST_F16DEV><<<rows, kReduceThreads, 0, h->stream>>>((const __half*)s, h->Pf, axis, h->snap, update, h->partial, nseg); break;
     }
     CLB_CUDA(cudaGetLastError());
     const NuGeom g = nu_geom(h->nx, h->ny, h->p, axis);

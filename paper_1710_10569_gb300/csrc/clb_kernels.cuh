@@ -473,14 +473,21 @@ __device__ __forceinline__ void block_sum(double v[RS_N], double* out)
         }
 }
 
-// Per-row FP64 partial sums for the diagnostics: sum u_axis (T - T0), sum |u - u_snap|^2,
-// sum |u|^2, sum (T - T_snap)^2, sum T^2 and the count of non-finite nodes. One block of
-// kReduceThreads per row y; threads stride over x in a fixed order, so the sums do not depend on
-// how the step kernel is launched. With update != 0 the snapshot (u_x, u_y, T as double
-// [3][ny][nx]) is replaced by the current fields.
-// One node's terms of the diagnostics sums (pulled populations -> u, T in FP64), added to v; with
-// update != 0 the node's snapshot entries are replaced by the current fields. wrow weights the
-// Nusselt term (wet-wall rows count half, the trapezoid rule over [0, H]).
+// The Nusselt term u_axis (T - T0) of one node (Eq. 29), in the arithmetic precision A; T is
+// returned through T_out.
+template <typename A, typename S>
+__device__ __forceinline__ A nu_term(const LatParams<S>& P, const Macro<A>& m, int axis, A& T_out)
+{
+    const A T = A(P.T_b) + m.dT;
+    T_out = T;
+    return (axis == 0 ? m.ux : m.uy) * (T - A(P.T0));
+}
+
+// One node's terms of the diagnostics sums, added to v: the fields come from the pulled populations,
+// the terms are formed in the arithmetic precision A (FP64 for FP64 storage, FP32 for the FP32 and
+// FP16 forms, whose fields carry FP32 rounding anyway; GB300 issues FP64 slowly) and accumulated in
+// FP64. With update != 0 the node's snapshot entries are replaced by the current fields. wrow
+// weights the Nusselt term (wet-wall rows count half, the trapezoid rule over [0, H]).
 template <typename E, typename A>
 __device__ __forceinline__ void node_diag(const E* __restrict__ src, const LatParams<A>& P, int x, int y,
                                           int axis, double* __restrict__ snap, int update, double wrow,
@@ -490,19 +497,20 @@ __device__ __forceinline__ void node_diag(const E* __restrict__ src, const LatPa
     A f[9], g[5];
     gather(src, P, x, y, f, g);
     const Macro<A> m = macroscopic(P, f, g);
-    const double ux = double(m.ux), uy = double(m.uy), T = double(P.T_b) + double(m.dT);
+    A T;
+    const A q = nu_term(P, m, axis, T);
     const long long n = (long long)y * P.nx + x;
-    const double sx = snap[n], sy = snap[N + n], sT = snap[2 * N + n];
-    v[RS_UT] += wrow * ((axis == 0 ? ux : uy) * (T - double(P.T0)));
-    v[RS_DU] += (ux - sx) * (ux - sx) + (uy - sy) * (uy - sy);
-    v[RS_U] += ux * ux + uy * uy;
-    v[RS_DT] += (T - sT) * (T - sT);
-    v[RS_T] += T * T;
-    v[RS_BAD] += (isfinite(ux) && isfinite(uy) && isfinite(T) && isfinite(double(m.rho))) ? 0.0 : 1.0;
+    const A dux = m.ux - A(snap[n]), duy = m.uy - A(snap[N + n]), dT = T - A(snap[2 * N + n]);
+    v[RS_UT] += wrow * double(q);
+    v[RS_DU] += double(dux * dux + duy * duy);
+    v[RS_U] += double(m.ux * m.ux + m.uy * m.uy);
+    v[RS_DT] += double(dT * dT);
+    v[RS_T] += double(T * T);
+    v[RS_BAD] += (isfinite(m.ux) && isfinite(m.uy) && isfinite(T) && isfinite(m.rho)) ? 0.0 : 1.0;
     if (update) {
-        snap[n] = ux;
-        snap[N + n] = uy;
-        snap[2 * N + n] = T;
+        snap[n] = double(m.ux);
+        snap[N + n] = double(m.uy);
+        snap[2 * N + n] = double(T);
     }
 }
 
@@ -511,7 +519,7 @@ __device__ __forceinline__ void node_diag(const E* __restrict__ src, const LatPa
 // kReduceThreads per row y; threads stride over x in a fixed order, so the sums do not depend on
 // how the step kernel is launched. With update != 0 the snapshot (u_x, u_y, T as double
 // [3][ny][nx]) is replaced by the current fields. (The batched lattices use this form; a single
-// lattice uses the one-node-per-thread form below.)
+// lattice uses the row-segment form below.)
 template <typename E, typename A>
 __device__ __forceinline__ void reduce_row(const E* __restrict__ src, const LatParams<A>& P, int y,
                                            int axis, double* __restrict__ snap, int update,
@@ -524,21 +532,24 @@ __device__ __forceinline__ void reduce_row(const E* __restrict__ src, const LatP
     block_sum(v, partial_row);
 }
 
-// The same sums with one node per thread: block b covers nodes seg * kReduceThreads .. + 255 of
-// row y (b = y * nseg + seg) and writes its partial sums (shuffle tree within each warp, then the
-// warps in order) to partial[b]. Every node's load is in flight at once, so the pass runs near the
-// memory bandwidth instead of waiting on one gather per thread after another; the summation order
-// depends only on nx and ny.
+// The same sums over row segments of kDiagNodes = kReduceThreads * 8 nodes: block b covers segment
+// seg of row y (b = y * nseg + seg), each thread sums its 8 nodes x = seg * kDiagNodes + t + 256 k in
+// order, then the shuffle tree within each warp and the warps in order give partial[b]. The per-node
+// sums are FP64 and GB300 issues FP64 slowly, so each thread takes 8 nodes (the warp tree's 30
+// FP64 adds per thread are shared by 8 nodes); the register cap keeps 4 blocks per SM so that
+// enough gathers are in flight. For nx <= kDiagNodes the order is that of reduce_row.
+constexpr int kDiagNodes = kReduceThreads * 8;
+
 template <int ST>
 __global__ void __launch_bounds__(kReduceThreads, 4) k_reduce_nodes(
     const typename Storage<ST>::T* __restrict__ src, const LatParams<typename Storage<ST>::A> P,
     int axis, double* __restrict__ snap, int update, double* __restrict__ partial, int nseg)
 {
     const int seg = blockIdx.x % nseg, y = blockIdx.x / nseg;
-    const int x = seg * kReduceThreads + threadIdx.x;
+    const int x0 = seg * kDiagNodes, x1 = min(P.nx, x0 + kDiagNodes);
     const double wrow = (P.wet_y && axis == 1 && (y == 0 || y == P.ny - 1)) ? 0.5 : 1.0;
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
-    if (x < P.nx) node_diag(src, P, x, y, axis, snap, update, wrow, v);
+    for (int x = x0 + threadIdx.x; x < x1; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, wrow, v);
     block_sum(v, partial + (long long)blockIdx.x * RS_N);
 }
 

@@ -106,8 +106,8 @@ struct DeviceGuard {
     }
 };
 
-// Blocks per row of the one-node-per-thread diagnostics pass.
-int diag_segments(int nx) { return (nx + kReduceThreads - 1) / kReduceThreads; }
+// Blocks per row of the diagnostics pass (row segments of kDiagNodes nodes).
+int diag_segments(int nx) { return (nx + kDiagNodes - 1) / kDiagNodes; }
 
 struct Layout {
     size_t buf[2], snap, stage, partial, diag, total;

@@ -52,8 +52,8 @@ clb_status scratch_address(double** out)
     return CLB_OK;
 }
 
-// Per-row sums of u_axis (T - T0) and of non-finite nodes, in the same fixed order as the
-// handle-based diagnostics (one block of kReduceThreads per row, threads striding over x).
+// Per-row sums of u_axis (T - T0) and of non-finite nodes (one block of kReduceThreads per row,
+// threads striding over x), each node's term formed as in the handle-based diagnostics.
 template <int ST>
 __global__ void __launch_bounds__(kReduceThreads) k_nusselt_rows_noalloc(
     const typename Storage<ST>::T* __restrict__ src, const LatParams<typename Storage<ST>::A> P,
@@ -67,9 +67,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_nusselt_rows_noalloc(
         A f[9], g[5];
         gather(src, P, x, y, f, g);
         const Macro<A> m = macroscopic(P, f, g);
-        const double ux = double(m.ux), uy = double(m.uy), T = double(P.T_b) + double(m.dT);
-        v[RS_UT] += wrow * ((axis == 0 ? ux : uy) * (T - double(P.T0)));
-        v[RS_BAD] += (isfinite(ux) && isfinite(uy) && isfinite(T) && isfinite(double(m.rho))) ? 0.0 : 1.0;
+        A T;
+        const A q = nu_term(P, m, axis, T);  // the same term as the handle-based diagnostics
+        v[RS_UT] += wrow * double(q);
+        v[RS_BAD] += (isfinite(m.ux) && isfinite(m.uy) && isfinite(T) && isfinite(m.rho)) ? 0.0 : 1.0;
     }
     block_sum(v, scratch + (long long)y * RS_N);
 }

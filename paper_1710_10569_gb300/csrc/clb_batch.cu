@@ -49,8 +49,11 @@ __device__ __forceinline__ void load_member(const Member<A>* __restrict__ src, M
 // One time step of every lattice: block b covers tile (b - tile_begin) of lattice owner[b]; a
 // tile is (blockDim.x * V) x blockDim.y nodes, V consecutive nodes per thread (the same
 // per-warp update as the single-lattice step).
+// Register cap: the FP32 two-nodes-per-thread form (the default tile) is held at 96 registers so
+// that five 128-thread blocks stay resident per SM; the other forms take what they need (blocks
+// have at most 256 threads).
 template <int ST, int V>
-__global__ void __launch_bounds__(256) k_step_batched(const Member<typename Storage<ST>::A>* __restrict__ mem,
+__global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(const Member<typename Storage<ST>::A>* __restrict__ mem,
                                                       const int* __restrict__ owner, int parity)
 {
     using A = typename Storage<ST>::A;
@@ -60,10 +63,20 @@ __global__ void __launch_bounds__(256) k_step_batched(const Member<typename Stor
     const int t = blockIdx.x - M.tile_begin;
     const int tx = t % M.tiles_x, ty = t / M.tiles_x;
     const int lane = threadIdx.x & 31;
-    const int x0 = (tx * blockDim.x + threadIdx.x) * V;
+    const int span = blockDim.x * V;
+    int xt = tx * span, keep = 0;
+    // The last tile of a row that would run past the row's end is moved left to end on its last
+    // node, so that its warps take the vector path (walls included) instead of node-by-node
+    // gathers; the nodes it shares with the tile before it are computed alike and stored by that
+    // tile only. The moved start stays a multiple of V (the vector loads stay aligned) when nx is.
+    if (xt + span > M.P.nx && M.P.nx > span && M.P.nx % V == 0) {
+        keep = xt;
+        xt = M.P.nx - span;
+    }
+    const int x0 = xt + threadIdx.x * V;
     const int y = ty * blockDim.y + threadIdx.y;
     if (y >= M.P.ny || x0 - lane * V >= M.P.nx) return;
-    step_warp_nodes<ST, V, false>((const E*)M.buf[parity], (E*)M.buf[parity ^ 1], M.P, x0, y, lane);
+    step_warp_nodes<ST, V, false>((const E*)M.buf[parity], (E*)M.buf[parity ^ 1], M.P, x0, y, lane, keep);
 }
 
 template <int ST>

@@ -37,7 +37,7 @@ template <int ST, int V, bool WALLS>
 __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __restrict__ src,
                                             typename Storage<ST>::T* __restrict__ dst,
                                             const LatParams<typename Storage<ST>::A>& P, int x0, int y,
-                                            int lane)
+                                            int lane, int keep)
 {
     using A = typename Storage<ST>::A;
     using E = typename Storage<ST>::T;
@@ -129,33 +129,35 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
                 for (int i = 0; i < 5; ++i) out[9 + i].e[k] = from_a(g[i], (E*)nullptr);
             }
         }
+        if (x0 >= keep)
 #pragma unroll
-        for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];
+            for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];
     }
 }
 
 // step_warp_nodes picks the path. SPLIT = true compiles the vector body twice, with and without
 // the wall terms, and interior warps take the lean copy (fewer instructions; the FP16 form is
 // issue-limited). The batched kernel keeps one copy: the second raises its register count past an
-// occupancy step.
+// occupancy step. Nodes x < keep are computed but not stored (they belong to another warp: see the
+// shifted last tile of a row in the batched kernel).
 template <int ST, int V, bool SPLIT = true>
 __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* __restrict__ src,
                                                 typename Storage<ST>::T* __restrict__ dst,
                                                 const LatParams<typename Storage<ST>::A>& P, int x0,
-                                                int y, int lane)
+                                                int y, int lane, int keep = 0)
 {
     using A = typename Storage<ST>::A;
     const int wx0 = x0 - lane * V, wx1 = wx0 + 32 * V - 1;
     if (wx1 < P.nx && !(P.wet_y && (y == 0 || y == P.ny - 1))) {
         const bool walls =
             (!P.per_y && (y == 0 || y == P.ny - 1)) || (!P.per_x && (wx0 == 0 || wx1 == P.nx - 1));
-        if (!SPLIT || walls) warp_vector<ST, V, true>(src, dst, P, x0, y, lane);
-        else warp_vector<ST, V, false>(src, dst, P, x0, y, lane);
+        if (!SPLIT || walls) warp_vector<ST, V, true>(src, dst, P, x0, y, lane, keep);
+        else warp_vector<ST, V, false>(src, dst, P, x0, y, lane, keep);
     } else {
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             const int x = x0 + k;
-            if (x < P.nx) {
+            if (x < P.nx && x >= keep) {
                 A f[9], g[5];
                 gather(src, P, x, y, f, g);
                 collide_any<Storage<ST>::DEV>(P, f, g);

@@ -504,7 +504,8 @@ def run_ours(args):
                          "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            # every step's fused kernel, plus the two reduction kernels of each check
+            "gpu_launches": args.steps + 2 * (args.steps // DIAG_INTERVAL),
             "clocks": clocks.summary(),
             "variants": variants,
             "thermal_only": thermal,

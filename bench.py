@@ -362,18 +362,18 @@ def batched_run(storage: int, count: int = 256, steps: int = 1000, seq_subset: i
                        "speedup": dt_seq / dt_sub}}
 
 
-BYTES_PER_NODE_3D = {W.STORAGE_F64: 544, W.STORAGE_F32: 272}  # 34 populations in + 34 out
+BYTES_PER_NODE_3D = {W.STORAGE_F64: 544, W.STORAGE_F32: 272, W.STORAGE_F16DEV: 136}  # 34 in + 34 out
 
 
 def three_d_run(steps: int, nx: int = 256, ny: int = 256, nz: int = 128):
     """The 3-D form (D3Q27 + D3Q7): Rayleigh-Benard on nx x ny x nz, Ra = 1e7, timed with CUDA
-    events on the lattice's stream, FP32 deviation storage (HBM roofline at 272 B/node) and FP64
-    (FP64 issue-bound; a shorter window)."""
+    events on the lattice's stream: FP32 deviation storage (HBM roofline at 272 B/node), FP16
+    deviation storage (136 B/node) and FP64 (FP64 issue-bound; a shorter window)."""
     import torch
     from paper_1710_10569_gb300 import clb
     peak, _ = measured_peaks()
     out = {}
-    for st, k in ((W.STORAGE_F32, steps), (W.STORAGE_F64, max(32, steps // 32))):
+    for st, k in ((W.STORAGE_F32, steps), (W.STORAGE_F16DEV, steps), (W.STORAGE_F64, max(32, steps // 32))):
         prob = W.rayleigh_benard3d(nx, ny, nz, Ra=1e7, storage=st)
         lat = clb.Lattice3D.from_problem(prob)
         lat.step(64)

@@ -59,8 +59,9 @@ typedef struct {
     int wall[6];      /* clb_wall of faces -x, +x, -y, +y, -z, +z: periodic faces come in pairs;
                          CLB_WALL_WET is not supported in 3-D */
     double T_wall[6]; /* temperature of Dirichlet faces */
-    int storage;      /* clb_storage: CLB_F64 or CLB_F32 (FP32 deviations from the rest state) */
-    double T_ref;     /* rest temperature of FP32 deviation storage */
+    int storage;      /* clb_storage: CLB_F64, CLB_F32 or CLB_F16DEV (FP32 or FP16 deviations from the rest
+                         state; FP32 arithmetic for both) */
+    double T_ref;     /* rest temperature of deviation storage */
 } clb3d_params;
 
 /* Defaults: nu = kappa = 0.02, rho0 = 1, all rates 1, cs2_T = 1/4, g_axis = 2, periodic, FP64. */

@@ -12,8 +12,9 @@
 // (uncentral3). About 330 flops for the transforms instead of the ~3,000 of literal 27 x 27
 // products.
 //
-// Storage. FP64 buffers hold the populations. FP32 buffers hold deviations from the rest state,
-// h_i = f_i - w_i rho0 and t_i = g_i - w^T_i T_ref (w_i = w(a) w(b) w(c), w(0) = 2/3, w(+-1) = 1/6).
+// Storage. FP64 buffers hold the populations. FP32 and FP16 buffers hold deviations from the rest
+// state, h_i = f_i - w_i rho0 and t_i = g_i - w^T_i T_ref (w_i = w(a) w(b) w(c), w(0) = 2/3,
+// w(+-1) = 1/6), and both compute in FP32.
 // The central moments of w_i rho0 about u are rho0 R(a) R(b) R(c) with R = (1, -u, 1/3 + u^2), so
 // the collision of Eq. (8) on deviations is k* = k - S (k + E) + (I - S/2) C with
 // E = rho0 (R R R - m m m) - (rho - rho0) m m m, m = (1, 0, 1/3); E is formed from per-axis
@@ -575,7 +576,7 @@ namespace {
 
 long long nodes_of(const clb3d_lattice* h) { return (long long)h->nx * h->ny * h->nz; }
 
-size_t esize(int storage) { return storage == CLB_F64 ? 8 : 4; }
+size_t esize(int storage) { return storage == CLB_F64 ? 8 : storage == CLB_F32 ? 4 : 2; }
 
 int pitch3(int nx, int storage)
 {
@@ -618,8 +619,8 @@ clb_status validate3(int nx, int ny, int nz, const clb3d_params* p)
         return set_error(CLB_EINVAL, "lattice %dx%dx%d: each extent must be in [1, %d]", nx, ny, nz, kMaxEdge);
     if ((long long)nx * ny * nz > kMaxNodes)
         return set_error(CLB_EINVAL, "lattice %dx%dx%d exceeds %lld nodes", nx, ny, nz, kMaxNodes);
-    if (p->storage != CLB_F64 && p->storage != CLB_F32)
-        return set_error(CLB_EINVAL, "3-D storage must be CLB_F64 or CLB_F32 (got %d)", p->storage);
+    if (p->storage != CLB_F64 && p->storage != CLB_F32 && p->storage != CLB_F16DEV)
+        return set_error(CLB_EINVAL, "3-D storage must be CLB_F64, CLB_F32 or CLB_F16DEV (got %d)", p->storage);
     if (NP * plane3(nx, ny, nz, p->storage) >= (1LL << 31))
         return set_error(CLB_EINVAL, "lattice %dx%dx%d: a buffer exceeds 2^31 elements", nx, ny, nz);
     for (int f = 0; f < 6; ++f) {
@@ -690,8 +691,10 @@ clb_status launch_step3(clb3d_lattice* h, int from, cudaStream_t s)
     const unsigned grid = unsigned((long long)xb * rb);
     if (h->p.storage == CLB_F64)
         k_step3<ST_F64><<<grid, block, 0, s>>>((const double*)h->buf[from], (double*)h->buf[from ^ 1], h->Pd, xb);
-    else
+    else if (h->p.storage == CLB_F32)
         k_step3<ST_F32><<<grid, block, 0, s>>>((const float*)h->buf[from], (float*)h->buf[from ^ 1], h->Pf, xb);
+    else
+        k_step3<ST_F16DEV><<<grid, block, 0, s>>>((const __half*)h->buf[from], (__half*)h->buf[from ^ 1], h->Pf, xb);
     CLB_CUDA(cudaGetLastError());
     return CLB_OK;
 }
@@ -814,8 +817,10 @@ extern "C" clb_status clb3d_init_fields(clb3d_lattice* h, const double* rho, con
     const unsigned grid = unsigned((n + 255) / 256);
     if (h->p.storage == CLB_F64)
         k_init3<ST_F64><<<grid, 256, 0, h->stream>>>((double*)h->buf[0], h->Pd, h->stage, n);
-    else
+    else if (h->p.storage == CLB_F32)
         k_init3<ST_F32><<<grid, 256, 0, h->stream>>>((float*)h->buf[0], h->Pf, h->stage, n);
+    else
+        k_init3<ST_F16DEV><<<grid, 256, 0, h->stream>>>((__half*)h->buf[0], h->Pf, h->stage, n);
     CLB_CUDA(cudaGetLastError());
     h->cur = 0;
     h->steps = 0;
@@ -850,8 +855,10 @@ clb_status extract3(clb3d_lattice* h, double* pops_dev)
     const unsigned grid = unsigned((n + 255) / 256);
     if (h->p.storage == CLB_F64)
         k_fields3<ST_F64><<<grid, 256, 0, h->stream>>>((const double*)h->buf[h->cur], h->Pd, h->stage, pops_dev, n);
-    else
+    else if (h->p.storage == CLB_F32)
         k_fields3<ST_F32><<<grid, 256, 0, h->stream>>>((const float*)h->buf[h->cur], h->Pf, h->stage, pops_dev, n);
+    else
+        k_fields3<ST_F16DEV><<<grid, 256, 0, h->stream>>>((const __half*)h->buf[h->cur], h->Pf, h->stage, pops_dev, n);
     CLB_CUDA(cudaGetLastError());
     return CLB_OK;
 }
@@ -893,8 +900,10 @@ extern "C" clb_status clb3d_nusselt(clb3d_lattice* h, int axis, double* nu_out)
     const int rows = h->ny * h->nz;
     if (h->p.storage == CLB_F64)
         k_nu_rows3<ST_F64><<<rows, kRedThreads, 0, h->stream>>>((const double*)h->buf[h->cur], h->Pd, axis, h->partial);
-    else
+    else if (h->p.storage == CLB_F32)
         k_nu_rows3<ST_F32><<<rows, kRedThreads, 0, h->stream>>>((const float*)h->buf[h->cur], h->Pf, axis, h->partial);
+    else
+        k_nu_rows3<ST_F16DEV><<<rows, kRedThreads, 0, h->stream>>>((const __half*)h->buf[h->cur], h->Pf, axis, h->partial);
     CLB_CUDA(cudaGetLastError());
     k_nu_final3<<<1, kRedThreads, 0, h->stream>>>(h->partial, rows, h->out);
     CLB_CUDA(cudaGetLastError());

@@ -124,7 +124,7 @@ def test_3d_defaults_and_footprint(clb):
 
 @pytest.mark.parametrize("kw,n", [
     (dict(nu=0.0), (8, 8, 8)),
-    (dict(storage=W.STORAGE_F16DEV), (8, 8, 8)),
+    (dict(storage=3), (8, 8, 8)),
     (dict(wall=(W.WALL_PERIODIC, W.WALL_DIRICHLET) + (W.WALL_PERIODIC,) * 4), (8, 8, 8)),
     (dict(wall=(W.WALL_WET,) * 2 + (W.WALL_PERIODIC,) * 4), (8, 8, 8)),
     (dict(g_axis=3), (8, 8, 8)),

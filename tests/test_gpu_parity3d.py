@@ -6,6 +6,9 @@ larger of max|u| and u_ref, T against the larger of max|T| and dT_ref):
   FP32 deviation storage: 3 n u32 (floor 2e-6) after n steps, u32 = 2^-24. Each step rounds every
     stored deviation once and sums 27 of them for the density and momentum; relative to the field
     scales these are a few u32 per step, adding up at worst linearly.
+  FP16 deviation storage (FP32 arithmetic): 3 sqrt(n) u16, u16 = 2^-11. The half-precision store of
+    every deviation each step dominates; the roundings of successive stores are independent and add
+    like a random walk; 27 of them enter each density and momentum sum.
 """
 import json
 import os
@@ -18,14 +21,18 @@ from paper_1710_10569_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-F64, F32 = W.STORAGE_F64, W.STORAGE_F32
+F64, F32, F16 = W.STORAGE_F64, W.STORAGE_F32, W.STORAGE_F16DEV
 P, D, A = W.WALL_PERIODIC, W.WALL_DIRICHLET, W.WALL_ADIABATIC
 NAMES = ("rho", "ux", "uy", "uz", "T")
-U32 = 2.0 ** -24
+U32, U16 = 2.0 ** -24, 2.0 ** -11
 
 
 def tol3(storage, steps):
-    return 1e-12 if storage == F64 else max(2e-6, 3 * steps * U32)
+    if storage == F64:
+        return 1e-12
+    if storage == F32:
+        return max(2e-6, 3 * steps * U32)
+    return 3 * max(steps, 1) ** 0.5 * U16
 
 
 @pytest.fixture(scope="module")
@@ -76,7 +83,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("storage", [F64, F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("storage", [F64, F32, F16], ids=["f64", "f32", "f16dev"])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_fields_match_the_oracle(clb, case, storage):
     """Fields after 1 step and after the case's step count (which includes a 32-step graph where
@@ -100,7 +107,7 @@ def test_fields_match_the_oracle(clb, case, storage):
     lat.close()
 
 
-@pytest.mark.parametrize("storage", [F64, F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("storage", [F64, F32, F16], ids=["f64", "f32", "f16dev"])
 def test_launch_shapes_are_bitwise_equal(clb, storage):
     prob = W.random_problem3d(70, 6, 5, seed=9, storage=storage)
     out = []

@@ -156,11 +156,17 @@ struct Axis {
 
 // E_k of the deviation collision: rho_b (R R R - m m m) - drho m m m. Populations stored as
 // themselves (DEV = false, rho_b = 0) need only the last term, which is what the full expression
-// evaluates to there (fma(0, d, t) = t).
+// evaluates to there (fma(0, d, t) = t). A moment with an order 1 along some axis has no
+// Maxwellian part (m(1) = 0): there E is rho_b R R R, a product without cancellation, and zero for
+// populations stored as themselves.
 template <bool DEV, typename A>
 __device__ __forceinline__ A e_term(const Axis<A>& X, const Axis<A>& Y, const Axis<A>& Z, int a, int b,
                                     int c, A rho_b, A drho)
 {
+    if (a == 1 || b == 1 || c == 1) {
+        if constexpr (!DEV) return A(0);
+        return rho_b * (X.R[a] * (Y.R[b] * Z.R[c]));
+    }
     const A t = -drho * (X.m[a] * Y.m[b] * Z.m[c]);
     if constexpr (!DEV) return t;
     const A d = X.dl[a] * Y.R[b] * Z.R[c] + X.m[a] * (Y.dl[b] * Z.R[c] + Y.m[b] * Z.dl[c]);
@@ -299,8 +305,9 @@ struct Src {
 
 // Pull of Eqs. (12), (22): population i at the node comes from the node at x - e_i; across a
 // wall face f takes the node's own opposite post-collision value, and g the anti-bounce-back
-// value on Dirichlet faces.
-template <typename T, typename A>
+// value on Dirichlet faces. NOWALL = true is for nodes none of whose pulls crosses a wall (every
+// source exists, periodic wrap included): the same loads without the wall selects.
+template <bool NOWALL = false, typename T, typename A>
 __device__ __forceinline__ void gather3(const T* __restrict__ src, const Lat3<A>& P, int x, int y, int z,
                                         A f[NF], A g[NG])
 {
@@ -317,7 +324,7 @@ __device__ __forceinline__ void gather3(const T* __restrict__ src, const Lat3<A>
             for (int a = 0; a < 3; ++a) {
                 const int i = a + 3 * b + 9 * c;
                 const int o = oppd(a) + 3 * oppd(b) + 9 * oppd(c);
-                const bool ok = okyz && sx.ok[a];
+                const bool ok = NOWALL || (okyz && sx.ok[a]);
                 const int off = ok ? i * pl + row + sx.s[a] : o * pl + here;
                 f[i] = to_a(src[off]);
             }
@@ -333,7 +340,7 @@ __device__ __forceinline__ void gather3(const T* __restrict__ src, const Lat3<A>
             const int at = d == 0 ? (z * P.ny + y) * P.pitch + S.s[digit]
                          : d == 1 ? (z * P.ny + S.s[digit]) * P.pitch + x
                                   : (S.s[digit] * P.ny + y) * P.pitch + x;
-            if (S.ok[digit]) {
+            if (NOWALL || S.ok[digit]) {
                 g[j] = to_a(src[(NF + j) * pl + at]);
             } else {
                 const int face = 2 * d + s;
@@ -368,7 +375,10 @@ __global__ void __launch_bounds__(256) k_step3(const typename Storage<ST>::T* __
     if (x >= P.nx || r >= P.ny * P.nz) return;
     const int y = r % P.ny, z = r / P.ny;
     A f[NF], g[NG];
-    gather3(src, P, x, y, z, f, g);
+    const bool nowall = (P.per[0] || (x > 0 && x < P.nx - 1)) && (P.per[1] || (y > 0 && y < P.ny - 1)) &&
+                        (P.per[2] || (z > 0 && z < P.nz - 1));
+    if (nowall) gather3<true>(src, P, x, y, z, f, g);
+    else gather3(src, P, x, y, z, f, g);
     collide3<Storage<ST>::DEV>(P, f, g);
     store3(dst, P, (z * P.ny + y) * P.pitch + x, f, g);
 }
@@ -787,8 +797,8 @@ extern "C" clb_status clb3d_create(int nx, int ny, int nz, const clb3d_params* p
     h->Pf = make_lat3<float>(nx, ny, nz, *p);
     h->plane = plane3(nx, ny, nz, p->storage);
     h->pitch = pitch3(nx, p->storage);
-    h->bx = nx > 64 ? 128 : (nx > 32 ? 64 : 32);
-    h->by = 128 / h->bx;
+    h->bx = nx > 128 ? 256 : (nx > 64 ? 128 : (nx > 32 ? 64 : 32));
+    h->by = h->bx >= 128 ? 1 : 128 / h->bx;
     *out = h;
     return CLB_OK;
 }

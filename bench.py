@@ -279,12 +279,14 @@ def e2e_run(storage: int, steps: int, nx: int, ny: int):
                     f"{DIAG_INTERVAL} steps) -> clb_fields -> pinned host"}
 
 
-def thermal_run(storage: int, steps: int):
-    """The D2Q5-only step with a prescribed velocity (a cellular flow of amplitude 0.1) on the bench
-    lattice's temperature field: 5 populations in and out plus the node's velocity."""
+def thermal_run(storage: int, steps: int, nx: int = 4096, ny: int = 4096):
+    """The D2Q5-only step with a prescribed velocity (a cellular flow of amplitude 0.1) on a
+    Rayleigh-Benard temperature field: 5 populations in and out plus the node's velocity. The
+    lattice is 4096 x 4096 so that a step's working set (two 336 MB FP32 buffers and 134 MB of
+    velocities) is several times the 129 MB L2; at 2048 x 1024 it would fit."""
     import torch
     from paper_1710_10569_gb300 import clb
-    prob = workload(storage)
+    prob = workload(storage, nx, ny)
     nx, ny = prob.nx, prob.ny
     x, y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)
     kx, ky = 2 * math.pi / nx, 2 * math.pi / ny
@@ -305,8 +307,9 @@ def thermal_run(storage: int, steps: int):
     per_node = {W.STORAGE_F64: 96, W.STORAGE_F32: 48, W.STORAGE_F16DEV: 28}[storage]
     peak, _ = measured_peaks()
     gbs = per_node * nx * ny * steps / dt / 1e9
-    return {"mlups": nx * ny * steps / dt / 1e6, "bytes_per_node": per_node, "achieved_gbs": gbs,
-            "hbm_frac": gbs / peak, "steps": steps, "storage": W.STORAGE_NAMES[storage]}
+    return {"workload": f"thermal_only_{nx}x{ny}_cellular_flow", "mlups": nx * ny * steps / dt / 1e6,
+            "bytes_per_node": per_node, "achieved_gbs": gbs, "hbm_frac": gbs / peak, "steps": steps,
+            "storage": W.STORAGE_NAMES[storage]}
 
 
 def batched_run(storage: int, count: int = 256, steps: int = 1000, seq_subset: int = 32):
@@ -475,7 +478,7 @@ def run_ours(args):
                     "peak_kind": "derived: 152 SMs x 2 FP64 lanes/clock x 2.07 GHz"}
             l2.close()
     e2e = e2e_run(storage, args.steps, args.nx, args.ny) if rank == 0 else None
-    thermal = thermal_run(storage, args.steps) if (rank == 0 and not args.no_variants) else None
+    thermal = thermal_run(storage, max(200, args.steps // 8)) if (rank == 0 and not args.no_variants) else None
     three_d = three_d_run(max(200, args.steps // 20)) if (rank == 0 and not args.no_variants) else None
     batched = batched_run(storage) if (rank == 0 and not args.no_serve) else None
     served = served_run(storage) if (rank == 0 and not args.no_serve) else None
@@ -565,6 +568,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched and served runs")
+    ap.add_argument("--thermal-only", action="store_true",
+                    help="run only the D2Q5 thermal-only step (4096 x 4096) and print its JSON")
     ap.add_argument("--three-d-only", action="store_true",
                     help="run only the 3-D workload (D3Q27 + D3Q7, 256 x 256 x 128) and print its JSON")
     ap.add_argument("--batched-only", action="store_true",
@@ -574,6 +579,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.thermal_only:
+        st = {"f64": W.STORAGE_F64, "f32": W.STORAGE_F32, "f16dev": W.STORAGE_F16DEV}[args.storage]
+        print(json.dumps(thermal_run(st, args.steps)), flush=True)
     elif args.three_d_only:
         print(json.dumps(three_d_run(args.steps)), flush=True)
     elif args.batched_only:

@@ -16,6 +16,12 @@ namespace {
 
 constexpr int NT = 5;  // planes per buffer
 
+// Two consecutive elements loaded or stored as one aligned access.
+template <typename E>
+struct alignas(2 * sizeof(E)) Pair {
+    E e[2];
+};
+
 // Velocity storage of the thermal handle: the arithmetic type of the storage.
 template <int ST>
 using VelT = typename Storage<ST>::A;
@@ -58,6 +64,24 @@ __device__ __forceinline__ void thermal_gather(const E* __restrict__ src, const 
     }
 }
 
+// One node's collision (Eqs. 16-21) with its prescribed velocity.
+template <int ST>
+__device__ __forceinline__ void thermal_collide(const LatParams<typename Storage<ST>::A>& P,
+                                                typename Storage<ST>::A u, typename Storage<ST>::A v,
+                                                typename Storage<ST>::A g[NT])
+{
+    using A = typename Storage<ST>::A;
+    const A dT = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    if constexpr (Storage<ST>::DEV) collide_d2q5_dev(P, P.T_b + dT, dT, u, v, g);
+    else collide_d2q5(P, P.T_b + dT, u, v, g);
+}
+
+// One time step, two neighbouring nodes x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x) and x0 + 1
+// of row y = blockIdx.y per thread. A pair whose pulls all stay inside the lattice without wrapping
+// reads the planes pulled along y (and the rest plane) as aligned pairs and stores every plane as
+// an aligned pair; other pairs (next to a wall or a periodic seam, or the single node at the end of
+// an odd row) gather node by node with the wall rules. The values are those of the node-by-node
+// path.
 template <int ST>
 __global__ void __launch_bounds__(256) k_thermal_step(const typename Storage<ST>::T* __restrict__ src,
                                                       typename Storage<ST>::T* __restrict__ dst,
@@ -67,19 +91,47 @@ __global__ void __launch_bounds__(256) k_thermal_step(const typename Storage<ST>
 {
     using A = typename Storage<ST>::A;
     using E = typename Storage<ST>::T;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    A g[NT];
-    thermal_gather(src, P, x, y, g);
-    const long long n = (long long)y * P.nx + x;
-    const A u = ux[n], v = uy[n];
-    const A dT = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
-    if constexpr (Storage<ST>::DEV) collide_d2q5_dev(P, P.T_b + dT, dT, u, v, g);
-    else collide_d2q5(P, P.T_b + dT, u, v, g);
-    const long long here = (long long)y * P.pitch + x;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y;
+    if (x0 >= P.nx) return;
+    const bool two = x0 + 1 < P.nx;
+    const long long pl = P.plane;
+    const long long here = (long long)y * P.pitch + x0;
+    const long long n = (long long)y * P.nx + x0;
+    A ga[NT], gb[NT];
+    if (two && x0 > 0 && x0 + 2 < P.nx && y > 0 && y + 1 < P.ny) {
+        const Pair<E> c0 = *reinterpret_cast<const Pair<E>*>(src + here);
+        const Pair<E> c2 = *reinterpret_cast<const Pair<E>*>(src + 2 * pl + here - P.pitch);
+        const Pair<E> c4 = *reinterpret_cast<const Pair<E>*>(src + 4 * pl + here + P.pitch);
+        ga[0] = to_a(c0.e[0]);
+        gb[0] = to_a(c0.e[1]);
+        ga[1] = to_a(src[pl + here - 1]);
+        gb[1] = to_a(src[pl + here]);
+        ga[2] = to_a(c2.e[0]);
+        gb[2] = to_a(c2.e[1]);
+        ga[3] = to_a(src[3 * pl + here + 1]);
+        gb[3] = to_a(src[3 * pl + here + 2]);
+        ga[4] = to_a(c4.e[0]);
+        gb[4] = to_a(c4.e[1]);
+    } else {
+        thermal_gather(src, P, x0, y, ga);
+        if (two) thermal_gather(src, P, x0 + 1, y, gb);
+    }
+    thermal_collide<ST>(P, A(ux[n]), A(uy[n]), ga);
+    if (two) {
+        thermal_collide<ST>(P, A(ux[n + 1]), A(uy[n + 1]), gb);
+        // here is even (x0 and the row pitch are): one aligned pair per plane
 #pragma unroll
-    for (int i = 0; i < NT; ++i) dst[i * P.plane + here] = from_a(g[i], (E*)nullptr);
+        for (int i = 0; i < NT; ++i) {
+            Pair<E> o;
+            o.e[0] = from_a(ga[i], (E*)nullptr);
+            o.e[1] = from_a(gb[i], (E*)nullptr);
+            *reinterpret_cast<Pair<E>*>(dst + i * pl + here) = o;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NT; ++i) dst[i * pl + here] = from_a(ga[i], (E*)nullptr);
+    }
 }
 
 // g^eq(T, u) written to the slots the next pull reads (as k_init does for the coupled step), and
@@ -186,7 +238,7 @@ size_t thermal_footprint(int nx, int ny, int storage)
 
 clb_status thermal_launch(clb_thermal* h, int from, cudaStream_t s)
 {
-    const dim3 block(128, 1), grid((h->nx + 127) / 128, h->ny);
+    const dim3 block(128, 1), grid((h->nx + 255) / 256, h->ny);  // two nodes per thread
     const void* a = h->buf[from];
     void* b = h->buf[from ^ 1];
     switch (h->p.storage) {
@@ -206,7 +258,7 @@ clb_status thermal_launch(clb_thermal* h, int from, cudaStream_t s)
 
 clb_status thermal_out(clb_thermal* h, double* T, double* pops)
 {
-    const dim3 block(128, 1), grid((h->nx + 127) / 128, h->ny);
+    const dim3 block(128, 1), grid((h->nx + 255) / 256, h->ny);  // two nodes per thread
     const void* a = h->buf[h->cur];
     switch (h->p.storage) {
     case CLB_F64: k_thermal_out<ST_F64><<<grid, block, 0, h->stream>>>((const double*)a, h->Pd, T, pops); break;
@@ -283,7 +335,7 @@ extern "C" clb_status clb_thermal_init(clb_thermal* h, const double* T, const do
             CLB_CUDA(cudaMemcpyAsync(h->stage + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
             dev[k] = h->stage + k * N;
         }
-    const dim3 block(128, 1), grid((h->nx + 127) / 128, h->ny);
+    const dim3 block(128, 1), grid((h->nx + 255) / 256, h->ny);  // two nodes per thread
     void* d = h->buf[h->cur];
     switch (h->p.storage) {
     case CLB_F64: k_thermal_init<ST_F64><<<grid, block, 0, h->stream>>>((double*)d, (double*)h->vel[0], (double*)h->vel[1], h->Pd, dev[0], dev[1], dev[2]); break;

@@ -137,3 +137,10 @@ def test_3d_invalid_arguments_are_rejected(clb, kw, n):
     st, _ = footprint3(clb, *n, **kw)
     assert st == clb.CLB_EINVAL
     assert clb.lib().clb_last_error()
+
+
+def test_3d_largest_lattice_in_32_bit_offsets(clb):
+    """A 3-D buffer must stay below 2^31 elements (offsets within it are 32-bit): 384 x 384 x 428
+    in FP32 (34 planes of 63.1 M elements) is accepted, one more layer is refused."""
+    assert footprint3(clb, 384, 384, 428, storage=W.STORAGE_F32)[0] == clb.CLB_OK
+    assert footprint3(clb, 384, 384, 429, storage=W.STORAGE_F32)[0] == clb.CLB_EINVAL

@@ -63,7 +63,7 @@ class _Params3(ctypes.Structure):
                 ("s_5", ctypes.c_double), ("s_6", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
                 ("Fv", ctypes.c_double * 3), ("g_axis", ctypes.c_int), ("wall", ctypes.c_int * 6),
-                ("T_wall", ctypes.c_double * 6)]
+                ("T_wall", ctypes.c_double * 6), ("u_wall", ctypes.c_double * 18)]
 
 
 def _load():
@@ -306,7 +306,7 @@ def run_to_steady(o: Oracle, tol: float, max_steps: int, interval: int = 100):
 # Three-dimensional form (D3Q27 flow + D3Q7 temperature, clb3d_oracle.c). Fields are (nz, ny, nx)
 # float64 arrays; params are those of the two-dimensional form plus s_5, s_6 (rates of the fifth-
 # and sixth-order moments, default 1), Fv of length 3, g_axis (buoyancy along +g_axis, default 2)
-# and six faces in wall / T_wall (-x, +x, -y, +y, -z, +z).
+# and six faces in wall / T_wall / u_wall (-x, +x, -y, +y, -z, +z).
 
 
 def _params3(p: dict, nx: int = 1, ny: int = 1, nz: int = 1) -> _Params3:
@@ -323,6 +323,10 @@ def _params3(p: dict, nx: int = 1, ny: int = 1, nz: int = 1) -> _Params3:
     for i in range(6):
         s.wall[i] = int(p["wall"][i])
         s.T_wall[i] = float(p["T_wall"][i])
+    uw = p.get("u_wall", ((0.0, 0.0, 0.0),) * 6)
+    for face in range(6):
+        for d in range(3):
+            s.u_wall[3 * face + d] = float(uw[face][d])
     return s
 
 

@@ -26,7 +26,12 @@
  *   - Boussinesq force along +axis g_axis: F = Fv + rho0 g_beta (T - T0) e_g (Eq. 3); u = (sum f e +
  *     F/2) / rho with the local rho (Eq. 13); T = sum g (Eq. 23).
  *   - Walls halfway between nodes on any face: f bounces back; g anti-bounces back,
- *     g_i = -g*_opp + 2 w^T_i T_w, on Dirichlet faces and bounces back on adiabatic faces.
+ *     g_i = -g*_opp + 2 w^T_i T_w, on Dirichlet faces and bounces back on adiabatic faces. A wall
+ *     face may move with velocity u_w (tangential motion and normal injection alike): then
+ *     f_i = f*_opp + [f^eq_i - f^eq_opp](rho0, u_w) and, on Dirichlet faces,
+ *     g_i = -g*_opp + [g^eq_i + g^eq_opp](T_w, u_w) (the 2-D moving-wall rule on each face); a
+ *     diagonal that crosses several faces at an edge or corner takes the velocity of the face of the
+ *     highest axis (z before y before x).
  * M^-1 and M_T^-1 are computed numerically (Gauss-Jordan); N^-1 is applied by solving the unit
  * lower-triangular system. Nothing is fused or reordered: collide every node, then stream.
  *
@@ -60,6 +65,7 @@ typedef struct {
     int g_axis;       /* buoyancy acts along +g_axis (0: x, 1: y, 2: z) */
     int wall[6];      /* faces -x, +x, -y, +y, -z, +z */
     double T_wall[6];
+    double u_wall[6][3]; /* velocity of each wall face */
 } orc3_params;
 
 /* Velocity component of index digit 0, 1, 2: 0, +1, -1. Population i has digits (i%3, i/3%3, i/9). */
@@ -80,6 +86,8 @@ typedef struct {
     double MT[Q7][Q7], MTinv[Q7][Q7], ST[Q7][Q7];
     int opp[Q27], oppT[Q7];
     double wT[Q7];
+    double fwall[6][Q27];   /* f^eq(rho0, u_wall) of each face */
+    double gwall[6][Q7];    /* g^eq(T_wall, u_wall) of each face */
     double *f, *g, *fs, *gs; /* [q][z][y][x] */
     long steps;
 } orc3_sim;
@@ -371,18 +379,19 @@ static void stream(orc3_sim *s)
                 for (int i = 0; i < Q27; ++i) {
                     int c[3] = {x - ex27(i), y - ey27(i), z - ez27(i)};
                     const int len[3] = {nx, ny, nz};
-                    int crossed = 0;
+                    int face = -1; /* the face crossed; of several, that of the highest axis */
                     for (int d = 0; d < 3; ++d) {
                         if (c[d] < 0) {
-                            if (p->wall[2 * d] == ORC3_PERIODIC) c[d] += len[d]; else crossed = 1;
+                            if (p->wall[2 * d] == ORC3_PERIODIC) c[d] += len[d]; else face = 2 * d;
                         } else if (c[d] >= len[d]) {
-                            if (p->wall[2 * d + 1] == ORC3_PERIODIC) c[d] -= len[d]; else crossed = 1;
+                            if (p->wall[2 * d + 1] == ORC3_PERIODIC) c[d] -= len[d]; else face = 2 * d + 1;
                         }
                     }
-                    if (!crossed)
+                    const int o = s->opp[i];
+                    if (face < 0)
                         s->f[i * n + here] = s->fs[i * n + ((size_t)c[2] * ny + c[1]) * nx + c[0]];
                     else
-                        s->f[i * n + here] = s->fs[s->opp[i] * n + here];
+                        s->f[i * n + here] = s->fs[o * n + here] + (s->fwall[face][i] - s->fwall[face][o]);
                 }
                 for (int i = 0; i < Q7; ++i) {
                     int c[3] = {x - EX7[i], y - EY7[i], z - EZ7[i]};
@@ -399,7 +408,7 @@ static void stream(orc3_sim *s)
                     if (face < 0)
                         s->g[i * n + here] = s->gs[i * n + ((size_t)c[2] * ny + c[1]) * nx + c[0]];
                     else if (p->wall[face] == ORC3_DIRICHLET)
-                        s->g[i * n + here] = -s->gs[o * n + here] + 2.0 * s->wT[i] * p->T_wall[face];
+                        s->g[i * n + here] = -s->gs[o * n + here] + (s->gwall[face][i] + s->gwall[face][o]);
                     else
                         s->g[i * n + here] = s->gs[o * n + here];
                 }
@@ -432,6 +441,8 @@ int orc3_create(const orc3_params *p, orc3_sim **out)
     if (!s) return -2;
     s->p = *p;
     build_constants(s);
+    for (int face = 0; face < 6; ++face)
+        equilibrium(s, p->rho0, p->u_wall[face], p->T_wall[face], s->fwall[face], s->gwall[face]);
     const size_t n = nodes(s);
     s->f = (double *)calloc(Q27 * n, sizeof(double));
     s->fs = (double *)calloc(Q27 * n, sizeof(double));

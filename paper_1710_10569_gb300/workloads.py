@@ -293,7 +293,7 @@ def default_params3(**overrides) -> dict:
         nu=0.02, kappa=0.02, g_beta=0.0, T0=0.0, rho0=1.0,
         s_b=1.0, s_3=1.0, s_4=1.0, s_5=1.0, s_6=1.0, lambda0=1.0, lambda2=1.0, cs2_T=0.25,
         Fv=(0.0, 0.0, 0.0), g_axis=2,
-        wall=(WALL_PERIODIC,) * 6, T_wall=(0.0,) * 6,
+        wall=(WALL_PERIODIC,) * 6, T_wall=(0.0,) * 6, u_wall=((0.0, 0.0, 0.0),) * 6,
         storage=STORAGE_F64, T_ref=0.0, u_ref=0.0, dT_ref=0.0,
     )
     for k, v in overrides.items():
@@ -379,10 +379,11 @@ def taylor_green3d(n: int = 32, U: float = 0.01, nu: float = 0.02, kappa: float 
 
 
 def random_problem3d(nx: int, ny: int, nz: int, seed: int = 0, storage=STORAGE_F64,
-                     walls: tuple | None = None) -> Problem3D:
+                     walls: tuple | None = None, moving: bool = False) -> Problem3D:
     """Seeded random parameters, faces and fields (for parity tests): rates drawn in their stable
     ranges, buoyancy along a random axis, each axis periodic or walled (Dirichlet or adiabatic per
-    face), velocities up to 0.05, temperatures within +-0.5."""
+    face), velocities up to 0.05, temperatures within +-0.5; with moving=True every wall face moves
+    with a random velocity of up to 0.05 per component (tangential and normal)."""
     rng = np.random.default_rng(seed)
     if walls is None:
         walls = []
@@ -401,6 +402,9 @@ def random_problem3d(nx: int, ny: int, nz: int, seed: int = 0, storage=STORAGE_F
                         g_axis=int(rng.integers(0, 3)), wall=tuple(walls),
                         T_wall=tuple(float(v) for v in rng.uniform(-0.5, 0.5, 6)),
                         storage=storage, T_ref=0.0, u_ref=0.05, dT_ref=0.5)
+    if moving:
+        p["u_wall"] = tuple((0.0, 0.0, 0.0) if walls[f] == WALL_PERIODIC else
+                            tuple(float(v) for v in rng.uniform(-0.05, 0.05, 3)) for f in range(6))
     rho = 1.0 + rng.uniform(-1e-3, 1e-3, sh)
     ux, uy, uz = (rng.uniform(-0.05, 0.05, sh) for _ in range(3))
     T = rng.uniform(-0.5, 0.5, sh)

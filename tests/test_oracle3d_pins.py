@@ -372,3 +372,64 @@ def test_closed_box_conserves_mass_and_heat():
     f1, g1 = o.populations()
     assert f1.sum() == pytest.approx(f0.sum(), rel=1e-13)
     assert g1.sum() == pytest.approx(g0.sum(), rel=1e-12, abs=1e-12)
+
+
+# ----------------------------------------------------------------------------- moving wall faces
+
+
+@pytest.mark.parametrize("lid_face,axis", [(5, 2), (3, 1), (1, 0)])
+def test_couette_flow_between_a_moving_and_a_resting_face_is_linear(lid_face, axis):
+    """A channel with walls on the faces of one axis, the upper one moving tangentially with
+    (U, V) in the two other directions: the steady velocity is linear from 0 at the resting wall
+    to the lid velocity at the moving one, both walls halfway between nodes, exact to 1e-12
+    (as in 2-D, halfway bounce-back with the wall's equilibrium is exact for Couette flow)."""
+    n = 12
+    shape = [1, 1, 1]
+    shape[axis] = n
+    walls = [P] * 6
+    walls[2 * axis], walls[2 * axis + 1] = A, A
+    uw = [[0.0, 0.0, 0.0] for _ in range(6)]
+    tang = [d for d in range(3) if d != axis]
+    uw[lid_face][tang[0]], uw[lid_face][tang[1]] = 0.02, -0.013
+    p = W.default_params3(nu=0.1, kappa=0.1, wall=tuple(walls), u_wall=tuple(map(tuple, uw)))
+    o = oracle.Oracle3D(*shape, p)
+    o.init(1.0, 0.0, 0.0, 0.0, 0.0)
+    o.step(int(12 * n * n / 0.1))
+    u = o.fields()[1:4]
+    c = np.arange(n)
+    line = (c + 0.5) / n
+    for d, U in ((tang[0], 0.02), (tang[1], -0.013)):
+        np.testing.assert_allclose(u[d].reshape(-1), U * line, atol=1e-12 * abs(U) + 1e-15)
+    np.testing.assert_allclose(u[axis], 0.0, atol=1e-14)
+
+
+def test_moving_faces_uniform_along_an_axis_reproduce_the_2d_oracle():
+    """Moving walls with tangential motion and normal injection, fields uniform along z: the 3-D
+    oracle steps like the 2-D one with the same moving y walls (pinned in test_oracle_pins.py)."""
+    rng = np.random.default_rng(21)
+    nx, ny = 6, 5
+    nu = 0.06
+    s_nu = 1.0 / (3 * nu + 0.5)
+    uw2 = ((0.0, 0.0), (0.0, 0.0), (0.02, 0.01), (-0.015, -0.005))
+    p2 = W.default_params(nu=nu, kappa=0.04, g_beta=4e-3, T0=0.05, s_b=s_nu, s_3=1.3, s_4=0.9,
+                          lambda2=1.2, Fv=(1e-4, -5e-5), wall=(P, P, D, A), T_wall=(0, 0, 0.4, -0.3),
+                          u_wall=uw2)
+    rho = 1.0 + rng.uniform(-1e-3, 1e-3, (ny, nx))
+    ux, uy = rng.uniform(-0.05, 0.05, (ny, nx)), rng.uniform(-0.05, 0.05, (ny, nx))
+    T = rng.uniform(-0.4, 0.4, (ny, nx))
+    o2 = oracle.Oracle(nx, ny, p2)
+    o2.init(rho, ux, uy, T)
+    uw3 = tuple((u[0], u[1], 0.0) for u in uw2) + ((0.0, 0.0, 0.0),) * 2
+    p3 = W.default_params3(nu=nu, kappa=0.04, g_beta=4e-3, T0=0.05, s_b=s_nu, s_3=1.3, s_4=0.9,
+                           s_5=1.7, s_6=0.6, lambda2=1.2, Fv=(1e-4, -5e-5, 0.0), g_axis=1,
+                           wall=(P, P, D, A, P, P), T_wall=(0, 0, 0.4, -0.3, 0, 0), u_wall=uw3)
+    o3 = oracle.Oracle3D(nx, ny, 2, p3)
+    lift = lambda a: np.broadcast_to(a, (2, ny, nx))
+    o3.init(lift(rho), lift(ux), lift(uy), 0.0, lift(T))
+    o2.step(25)
+    o3.step(25)
+    r2, ux2, uy2, T2 = o2.fields()
+    r3, ux3, uy3, uz3, T3 = o3.fields()
+    for a3, a2 in ((r3, r2), (ux3, ux2), (uy3, uy2), (T3, T2)):
+        np.testing.assert_allclose(a3, lift(a2), atol=1e-13)
+    np.testing.assert_allclose(uz3, 0.0, atol=1e-15)

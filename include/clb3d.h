@@ -18,7 +18,9 @@
  *   - Boussinesq force F = Fv + rho0 g_beta (T - T0) along +g_axis (Eq. 3), u = (sum f e + F/2)/rho
  *     (Eq. 13), T = sum g (Eq. 23);
  *   - walls halfway between nodes on any face: f bounces back, g anti-bounces back
- *     (g_i = -g*_opp + cs2_T T_w) on Dirichlet faces and bounces back on adiabatic faces.
+ *     (g_i = -g*_opp + cs2_T T_w) on Dirichlet faces and bounces back on adiabatic faces; wall
+ *     faces may move (tangential motion and normal injection), with the wall's equilibrium added
+ *     as in the 2-D moving-wall rule.
  *
  * Status codes, clb_last_error() and the storage forms are those of clb.h.
  *
@@ -62,6 +64,10 @@ typedef struct {
     int storage;      /* clb_storage: CLB_F64, CLB_F32 or CLB_F16DEV (FP32 or FP16 deviations from the rest
                          state; FP32 arithmetic for both) */
     double T_ref;     /* rest temperature of deviation storage */
+    double u_wall[6][3]; /* velocity of each wall face, |component| <= 0.4 (ignored on periodic faces):
+                            f_i = f*_opp + [f^eq_i - f^eq_opp](rho0, u_w) across the face and, on a
+                            Dirichlet face, g_i = -g*_opp + T_w (cs2_T + u_wn^2); a link across an
+                            edge or corner takes the velocity of the face of the highest axis */
 } clb3d_params;
 
 /* Defaults: nu = kappa = 0.02, rho0 = 1, all rates 1, cs2_T = 1/4, g_axis = 2, periodic, FP64. */

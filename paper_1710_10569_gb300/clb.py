@@ -49,7 +49,8 @@ class clb3d_params(ctypes.Structure):
                 ("s_3", ctypes.c_double), ("s_4", ctypes.c_double), ("s_5", ctypes.c_double),
                 ("s_6", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
                 ("Fv", ctypes.c_double * 3), ("g_axis", ctypes.c_int), ("wall", ctypes.c_int * 6),
-                ("T_wall", ctypes.c_double * 6), ("storage", ctypes.c_int), ("T_ref", ctypes.c_double)]
+                ("T_wall", ctypes.c_double * 6), ("storage", ctypes.c_int), ("T_ref", ctypes.c_double),
+                ("u_wall", ctypes.c_double * 18)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -533,6 +534,10 @@ def params3(p: dict) -> clb3d_params:
     for i in range(6):
         s.wall[i] = int(p["wall"][i])
         s.T_wall[i] = float(p["T_wall"][i])
+    uw = p.get("u_wall", ((0.0, 0.0, 0.0),) * 6)
+    for face in range(6):
+        for d in range(3):
+            s.u_wall[3 * face + d] = float(uw[face][d])
     s.storage = int(p["storage"])
     return s
 

@@ -44,7 +44,9 @@ struct Lat3 {
     long long plane;       // elements between planes (< 2^31: 32-bit offsets within a plane)
     int per[3];            // periodic flag per axis
     int kind[6];           // clb_wall per face -x, +x, -y, +y, -z, +z
-    A Tw[6];               // anti-bounce-back constant of a Dirichlet face: cs2_T (T_w - T_b)
+    A Tw[6];               // anti-bounce-back constant of a Dirichlet face: T_w (cs2_T + u_wn^2) - cs2_T T_b
+    int moving;            // some wall face moves: fbb holds its momentum terms
+    A fbb[6][27];          // [f^eq_i - f^eq_opp](rho0, u_w) of each face, added on bounce-back
     A s_nu, s_b3, s_3, s_4, s_5, s_6;  // s_b3 = (s_b - s_nu) / 3
     A lambda1, lambda2, cs2T;
     A Fv[3];
@@ -327,6 +329,11 @@ __device__ __forceinline__ void gather3(const T* __restrict__ src, const Lat3<A>
                 const bool ok = NOWALL || (okyz && sx.ok[a]);
                 const int off = ok ? i * pl + row + sx.s[a] : o * pl + here;
                 f[i] = to_a(src[off]);
+                if (!NOWALL && !ok && P.moving) {
+                    // the face crossed; of several (edge, corner), that of the highest axis
+                    const int face = !sz.ok[c] ? (c == 1 ? 4 : 5) : !sy.ok[b] ? (b == 1 ? 2 : 3) : (a == 1 ? 0 : 1);
+                    f[i] = f[i] + P.fbb[face][i];
+                }
             }
         }
     g[0] = to_a(src[NF * pl + here]);
@@ -422,7 +429,17 @@ __global__ void __launch_bounds__(256) k_init3(typename Storage<ST>::T* __restri
         }
         const int o = oppd(dg[0]) + 3 * oppd(dg[1]) + 9 * oppd(dg[2]);
         const int off = ok ? i * pl + (s[2] * P.ny + s[1]) * P.pitch + s[0] : o * pl + here;
-        dst[off] = from_a(f[i], (T*)nullptr);
+        A v = f[i];
+        if (!ok && P.moving) {
+            // the pull adds the crossed face's wall term: store the value without it
+            int face = -1;
+            for (int d = 0; d < 3; ++d) {
+                const int sd = c3[d] - vel(dg[d]);
+                if (!P.per[d] && (sd < 0 || sd >= n3[d])) face = 2 * d + (sd < 0 ? 0 : 1);
+            }
+            v = v - P.fbb[face][i];
+        }
+        dst[off] = from_a(v, (T*)nullptr);
     }
     dst[NF * pl + here] = from_a(g[0], (T*)nullptr);
 #pragma unroll
@@ -650,6 +667,10 @@ clb_status validate3(int nx, int ny, int nz, const clb3d_params* p)
     if (!(p->rho0 > 0)) return set_error(CLB_EINVAL, "rho0 must be > 0");
     if (!(p->g_beta >= 0)) return set_error(CLB_EINVAL, "g_beta must be >= 0");
     if (p->g_axis < 0 || p->g_axis > 2) return set_error(CLB_EINVAL, "g_axis must be 0, 1 or 2");
+    for (int f = 0; f < 6; ++f)
+        for (int d = 0; d < 3; ++d)
+            if (!(std::fabs(p->u_wall[f][d]) <= 0.4))
+                return set_error(CLB_EINVAL, "face %d: wall velocity components must lie in [-0.4, 0.4]", f);
     return CLB_OK;
 }
 
@@ -667,9 +688,27 @@ Lat3<A> make_lat3(int nx, int ny, int nz, const clb3d_params& p)
     P.rho_b = dev ? A(p.rho0) : A(0);
     P.T_b = dev ? A(p.T_ref) : A(0);
     for (int d = 0; d < 3; ++d) P.per[d] = p.wall[2 * d] == CLB_PERIODIC;
+    // Wall terms from the equilibria of the wall state, f^eq_i(rho0, u_w) = rho0 prod_d p1(e_d; u_d)
+    // with the 1-D lattice Maxwellian p1(0; u) = 2/3 - u^2, p1(+-1; u) = (1/3 + u^2 +- u)/2, and
+    // g^eq_i + g^eq_opp = T_w (cs2_T + u_wn^2) for the pair along the face normal.
+    auto p1 = [](int e, double u) { return e == 0 ? 2.0 / 3.0 - u * u : 0.5 * (1.0 / 3.0 + u * u + e * u); };
+    P.moving = 0;
     for (int f = 0; f < 6; ++f) {
         P.kind[f] = p.wall[f];
-        P.Tw[f] = A(p.cs2_T * p.T_wall[f] - p.cs2_T * (dev ? p.T_ref : 0.0));
+        const bool wall = p.wall[f] != CLB_PERIODIC;
+        const double* u = p.u_wall[f];
+        const double un = wall ? u[f / 2] : 0.0;
+        P.Tw[f] = A(p.T_wall[f] * (p.cs2_T + un * un) - p.cs2_T * (dev ? p.T_ref : 0.0));
+        for (int i = 0; i < NF; ++i) {
+            const int e[3] = {vel(i % 3), vel((i / 3) % 3), vel(i / 9)};
+            double fi = 1.0, fo = 1.0;
+            for (int d = 0; d < 3; ++d) {
+                fi *= p1(e[d], wall ? u[d] : 0.0);
+                fo *= p1(-e[d], wall ? u[d] : 0.0);
+            }
+            P.fbb[f][i] = A(p.rho0 * (fi - fo));
+        }
+        if (wall && (u[0] != 0.0 || u[1] != 0.0 || u[2] != 0.0)) P.moving = 1;
     }
     const double s_nu = rate_nu(p.nu);
     P.s_nu = A(s_nu);

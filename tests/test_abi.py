@@ -129,6 +129,8 @@ def test_3d_defaults_and_footprint(clb):
     (dict(wall=(W.WALL_WET,) * 2 + (W.WALL_PERIODIC,) * 4), (8, 8, 8)),
     (dict(g_axis=3), (8, 8, 8)),
     (dict(s_5=2.0), (8, 8, 8)),
+    (dict(wall=(W.WALL_PERIODIC,) * 4 + (W.WALL_ADIABATIC,) * 2,
+          u_wall=((0.0, 0.0, 0.0),) * 5 + ((0.5, 0.0, 0.0),)), (8, 8, 8)),
     (dict(cs2_T=0.34), (8, 8, 8)),
     (dict(), (0, 8, 8)),
     (dict(), (1 << 11, 1 << 11, 1 << 10)),

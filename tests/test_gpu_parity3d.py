@@ -80,6 +80,10 @@ CASES = {
                                                   walls=(P, P, P, P, D, D)), 40),
     "slab_6x5x1": (lambda st: W.random_problem3d(6, 5, 1, seed=5, storage=st,
                                                walls=(A, D, P, P, P, P)), 30),
+    "moving_faces_33x6x7": (lambda st: W.random_problem3d(33, 6, 7, seed=6, storage=st, moving=True,
+                                                        walls=(D, A, P, P, A, D)), 35),
+    "moving_box_9x8x7": (lambda st: W.random_problem3d(9, 8, 7, seed=7, storage=st, moving=True,
+                                                     walls=(D, A, A, D, A, D)), 35),
 }
 
 

@@ -30,7 +30,8 @@
  * v(2) = -1; D3Q7 populations are ordered rest, +x, -x, +y, -y, +z, -z.
  *
  * Ownership. clb3d_create allocates the lattice's device memory (two population buffers of 34
- * planes, FP64 staging for the fields and the reduction partials) and owns it until
+ * planes, FP64 staging for the fields, the residual's FP64 snapshot and the reduction partials) and
+ * owns it until
  * clb3d_destroy. All work is enqueued on the stream given at creation (NULL: the legacy default
  * stream); functions that return host data synchronise that stream.
  */
@@ -68,6 +69,8 @@ typedef struct {
                             f_i = f*_opp + [f^eq_i - f^eq_opp](rho0, u_w) across the face and, on a
                             Dirichlet face, g_i = -g*_opp + T_w (cs2_T + u_wn^2); a link across an
                             edge or corner takes the velocity of the face of the highest axis */
+    double u_ref;     /* velocity scale of the residual's floor (0: no floor) */
+    double dT_ref;    /* temperature scale of the residual's floor (0: no floor) */
 } clb3d_params;
 
 /* Defaults: nu = kappa = 0.02, rho0 = 1, all rates 1, cs2_T = 1/4, g_axis = 2, periodic, FP64. */
@@ -100,6 +103,17 @@ clb_status clb3d_populations(clb3d_lattice* h, double* f, double* g);
  * H / (kappa dT), dT the difference of that axis's wall temperatures (1 if equal), heat from the
  * hot face counted positive. FP64 sums in a fixed order. CLB_ENAN if a field is not finite. */
 clb_status clb3d_nusselt(clb3d_lattice* h, int axis, double* nu_out);
+
+/* Steady-state residual since the previous call (or since clb3d_init_fields), the 2-D form's E_R
+ * with u a 3-vector: max over X in {u, T} of sqrt(sum |X(t) - X(t')|^2 / max(sum |X(t)|^2,
+ * N (1e-3 X_ref)^2)), X_ref = u_ref, dT_ref; FP64 sums in a fixed order over an FP64 snapshot of
+ * u and T that the call then replaces. Synchronises; CLB_ENAN if a field is not finite. */
+clb_status clb3d_residual(clb3d_lattice* h, double* er_out);
+
+/* Step in chunks of `interval` until clb3d_residual < tol after a chunk or max_steps steps are
+ * done; the steps taken and the last residual are returned. */
+clb_status clb3d_run(clb3d_lattice* h, double tol, long max_steps, long interval, long* steps_out,
+                     double* er_out);
 
 /* Launch shape of the step kernel: block_x threads along x (a multiple of 32, <= 256) times block_y
  * rows (block_x * block_y <= 256). 0 keeps a value. */

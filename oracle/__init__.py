@@ -439,3 +439,22 @@ def nusselt3(u_axis, T, params: dict, axis: int) -> float:
     dT = abs(Tl - Th) or 1.0
     sign = 1.0 if Tl >= Th else -1.0
     return 1.0 + sign * float(np.mean(u_axis * (T - params["T0"]))) * H / (params["kappa"] * dT)
+
+
+def residual3(prev, cur, u_ref: float, dT_ref: float) -> float:
+    """E_R of the 3-D form between field snapshots (ux, uy, uz, T) taken some steps apart: the 2-D
+    reading with u a 3-vector."""
+    pux, puy, puz, pT = prev
+    cux, cuy, cuz, cT = cur
+    n = cT.size
+
+    def ratio(num, den, ref):
+        den = max(den, n * (1e-3 * ref) ** 2)
+        if num == 0.0:
+            return 0.0
+        return float(np.sqrt(num / den)) if den > 0 else float("inf")
+
+    ru = ratio(float(np.sum((cux - pux) ** 2 + (cuy - puy) ** 2 + (cuz - puz) ** 2)),
+               float(np.sum(cux ** 2 + cuy ** 2 + cuz ** 2)), u_ref)
+    rT = ratio(float(np.sum((cT - pT) ** 2)), float(np.sum(cT ** 2)), dT_ref)
+    return max(ru, rT)

@@ -50,7 +50,7 @@ class clb3d_params(ctypes.Structure):
                 ("s_6", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
                 ("Fv", ctypes.c_double * 3), ("g_axis", ctypes.c_int), ("wall", ctypes.c_int * 6),
                 ("T_wall", ctypes.c_double * 6), ("storage", ctypes.c_int), ("T_ref", ctypes.c_double),
-                ("u_wall", ctypes.c_double * 18)]
+                ("u_wall", ctypes.c_double * 18), ("u_ref", ctypes.c_double), ("dT_ref", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -122,6 +122,8 @@ _SIGS = {
     "clb3d_populations": [_VP, _D, _D],
     "clb3d_nusselt": [_VP, _I, _D],
     "clb3d_set_launch": [_VP, _I, _I],
+    "clb3d_residual": [_VP, _D],
+    "clb3d_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D],
     "clb3d_sync": [_VP],
     "clb3d_stream": [_VP],
     "clb3d_buffers": [_VP, _P(_VP), _P(ctypes.c_longlong), _P(_I)],
@@ -526,7 +528,7 @@ def params3(p: dict) -> clb3d_params:
     """clb3d_params from a parameter dict (see workloads.default_params3)."""
     s = clb3d_params()
     for k in ("nu", "kappa", "g_beta", "T0", "rho0", "s_b", "s_3", "s_4", "s_5", "s_6", "lambda2",
-              "cs2_T", "T_ref"):
+              "cs2_T", "T_ref", "u_ref", "dT_ref"):
         setattr(s, k, float(p[k]))
     for i in range(3):
         s.Fv[i] = float(p["Fv"][i])
@@ -613,3 +615,14 @@ class Lattice3D:
 
     def set_launch(self, block_x: int = 0, block_y: int = 0):
         _check(lib().clb3d_set_launch(self._h, int(block_x), int(block_y)))
+
+    def residual(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().clb3d_residual(self._h, ctypes.byref(v)))
+        return v.value
+
+    def run(self, tol: float, max_steps: int, interval: int = 100):
+        st, er = _L(), ctypes.c_double()
+        _check(lib().clb3d_run(self._h, float(tol), int(max_steps), int(interval), ctypes.byref(st),
+                               ctypes.byref(er)))
+        return st.value, er.value

@@ -22,6 +22,7 @@
 // FP64 collision on the populations themselves.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -573,6 +574,87 @@ __global__ void __launch_bounds__(kRedThreads) k_nu_final3(const double* __restr
     }
 }
 
+// Per-row FP64 sums for the steady-state residual: sum |u - u_snap|^2, sum |u|^2,
+// sum (T - T_snap)^2, sum T^2 and the count of non-finite nodes (block per row (y, z), threads
+// striding over x, a fixed order); with update != 0 the snapshot (u_x, u_y, u_z, T as double
+// [4][n]) is replaced by the current fields.
+constexpr int kResN = 5;
+
+template <int ST>
+__global__ void __launch_bounds__(kRedThreads) k_resid_rows3(const typename Storage<ST>::T* __restrict__ src,
+                                                             const Lat3<typename Storage<ST>::A> P,
+                                                             double* __restrict__ snap, int update,
+                                                             double* __restrict__ partial)
+{
+    using A = typename Storage<ST>::A;
+    const int r = blockIdx.x;
+    const int y = r % P.ny, z = r / P.ny;
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    double v[kResN] = {0, 0, 0, 0, 0};
+    for (int x = threadIdx.x; x < P.nx; x += kRedThreads) {
+        A f[NF], g[NG];
+        gather3(src, P, x, y, z, f, g);
+        double drho = 0, j[3] = {0, 0, 0}, dT = 0;
+        for (int i = 0; i < NF; ++i) {
+            const double w = double(f[i]);
+            drho += w;
+            j[0] += vel(i % 3) * w;
+            j[1] += vel((i / 3) % 3) * w;
+            j[2] += vel(i / 9) * w;
+        }
+        for (int q = 0; q < NG; ++q) dT += double(g[q]);
+        const double rho = double(P.rho_b) + drho, T = double(P.T_b) + dT;
+        const double buoy = double(P.gb) * (T - double(P.T0));
+        double u[3];
+        for (int d = 0; d < 3; ++d) u[d] = (j[d] + 0.5 * (double(P.Fv[d]) + (P.g_axis == d ? buoy : 0.0))) / rho;
+        const long long k = ((long long)z * P.ny + y) * P.nx + x;
+        double du = 0.0, uu = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double e = u[d] - snap[d * n + k];
+            du += e * e;
+            uu += u[d] * u[d];
+        }
+        const double eT = T - snap[3 * n + k];
+        v[0] += du;
+        v[1] += uu;
+        v[2] += eT * eT;
+        v[3] += T * T;
+        v[4] += (isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(T)) ? 0.0 : 1.0;
+        if (update) {
+            for (int d = 0; d < 3; ++d) snap[d * n + k] = u[d];
+            snap[3 * n + k] = T;
+        }
+    }
+    __shared__ double sh[kResN][kRedThreads];
+    for (int q = 0; q < kResN; ++q) sh[q][threadIdx.x] = v[q];
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < kResN; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < kResN; ++q) partial[(long long)kResN * r + q] = sh[q][0];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_resid_final3(const double* __restrict__ partial, int rows,
+                                                              double* __restrict__ out)
+{
+    double v[kResN] = {0, 0, 0, 0, 0};
+    for (int r = threadIdx.x; r < rows; r += kRedThreads)
+        for (int q = 0; q < kResN; ++q) v[q] += partial[(long long)kResN * r + q];
+    __shared__ double sh[kResN][kRedThreads];
+    for (int q = 0; q < kResN; ++q) sh[q][threadIdx.x] = v[q];
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < kResN; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < kResN; ++q) out[q] = sh[q][0];
+}
+
 }  // namespace clb3
 
 using namespace clb3;
@@ -586,9 +668,10 @@ struct clb3d_lattice {
     void* buf[2] = {nullptr, nullptr};
     double* stage = nullptr;    // 5 fields (init and extraction)
     double* popst = nullptr;    // populations (allocated on first use)
-    double* partial = nullptr;  // 2 per row
-    double* out = nullptr;      // 2
-    double* host_out = nullptr; // pinned
+    double* snap = nullptr;     // u_x, u_y, u_z, T at the last residual check (FP64)
+    double* partial = nullptr;  // kResN per row
+    double* out = nullptr;      // kResN
+    double* host_out = nullptr; // pinned, kResN
     int cur = 0;
     long steps = 0;
     int bx = 128, by = 1;
@@ -624,7 +707,7 @@ size_t buf_bytes(int nx, int ny, int nz, int storage)
 }
 
 struct Layout3 {
-    size_t buf, stage, partial, out, total;
+    size_t buf, stage, snap, partial, out, total;
 };
 
 Layout3 layout3(int nx, int ny, int nz, int storage)
@@ -633,9 +716,10 @@ Layout3 layout3(int nx, int ny, int nz, int storage)
     const size_t n = (size_t)nx * ny * nz;
     L.buf = buf_bytes(nx, ny, nz, storage);
     L.stage = align256(5 * n * sizeof(double));
-    L.partial = align256(2 * (size_t)ny * nz * sizeof(double));
+    L.snap = align256(4 * n * sizeof(double));
+    L.partial = align256((size_t)kResN * ny * nz * sizeof(double));
     L.out = 256;
-    L.total = 2 * L.buf + L.stage + L.partial + L.out;
+    L.total = 2 * L.buf + L.stage + L.snap + L.partial + L.out;
     return L;
 }
 
@@ -824,9 +908,10 @@ extern "C" clb_status clb3d_create(int nx, int ny, int nz, const clb3d_params* p
     h->buf[0] = m;
     h->buf[1] = m + L.buf;
     h->stage = (double*)(m + 2 * L.buf);
-    h->partial = (double*)(m + 2 * L.buf + L.stage);
-    h->out = (double*)(m + 2 * L.buf + L.stage + L.partial);
-    e = cudaMallocHost((void**)&h->host_out, 2 * sizeof(double));
+    h->snap = (double*)(m + 2 * L.buf + L.stage);
+    h->partial = (double*)(m + 2 * L.buf + L.stage + L.snap);
+    h->out = (double*)(m + 2 * L.buf + L.stage + L.snap + L.partial);
+    e = cudaMallocHost((void**)&h->host_out, kResN * sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         clb3d_destroy(h);
@@ -854,6 +939,66 @@ extern "C" void clb3d_destroy(clb3d_lattice* h)
     delete h;
 }
 
+namespace {
+
+// The residual E_R since the last snapshot, with the snapshot replaced by the current fields:
+// E_R = max over u (all three components) and T of sqrt(sum |X - X_snap|^2 / max(sum |X|^2,
+// N (1e-3 X_ref)^2)) with X_ref = u_ref, dT_ref (the reading of the 2-D form). Synchronises.
+clb_status residual3(clb3d_lattice* h, double* er)
+{
+    const int rows = h->ny * h->nz;
+    if (h->p.storage == CLB_F64)
+        k_resid_rows3<ST_F64><<<rows, kRedThreads, 0, h->stream>>>((const double*)h->buf[h->cur], h->Pd, h->snap, 1, h->partial);
+    else if (h->p.storage == CLB_F32)
+        k_resid_rows3<ST_F32><<<rows, kRedThreads, 0, h->stream>>>((const float*)h->buf[h->cur], h->Pf, h->snap, 1, h->partial);
+    else
+        k_resid_rows3<ST_F16DEV><<<rows, kRedThreads, 0, h->stream>>>((const __half*)h->buf[h->cur], h->Pf, h->snap, 1, h->partial);
+    CLB_CUDA(cudaGetLastError());
+    k_resid_final3<<<1, kRedThreads, 0, h->stream>>>(h->partial, rows, h->out);
+    CLB_CUDA(cudaGetLastError());
+    CLB_CUDA(cudaMemcpyAsync(h->host_out, h->out, kResN * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CLB_CUDA(cudaStreamSynchronize(h->stream));
+    const double* v = h->host_out;
+    if (v[4] > 0) return set_error(CLB_ENAN, "%.0f nodes have non-finite fields after %ld steps", v[4], h->steps);
+    const double N = double(nodes_of(h));
+    const double fu = N * (1e-3 * h->p.u_ref) * (1e-3 * h->p.u_ref);
+    const double fT = N * (1e-3 * h->p.dT_ref) * (1e-3 * h->p.dT_ref);
+    const double du = v[1] > fu ? v[1] : fu, dt = v[3] > fT ? v[3] : fT;
+    const double ru = v[0] == 0.0 ? 0.0 : (du > 0 ? std::sqrt(v[0] / du) : INFINITY);
+    const double rt = v[2] == 0.0 ? 0.0 : (dt > 0 ? std::sqrt(v[2] / dt) : INFINITY);
+    *er = ru > rt ? ru : rt;
+    return CLB_OK;
+}
+
+}  // namespace
+
+extern "C" clb_status clb3d_residual(clb3d_lattice* h, double* er_out)
+{
+    CHECK_H3(h);
+    if (!er_out) return set_error(CLB_EINVAL, "er_out must not be NULL");
+    return residual3(h, er_out);
+}
+
+extern "C" clb_status clb3d_run(clb3d_lattice* h, double tol, long max_steps, long interval, long* steps_out,
+                                double* er_out)
+{
+    CHECK_H3(h);
+    if (interval <= 0 || max_steps < 0) return set_error(CLB_EINVAL, "interval must be > 0 and max_steps >= 0");
+    long done = 0;
+    double er = INFINITY;
+    clb_status st = CLB_OK;
+    while (done < max_steps) {
+        const long n = std::min(interval, max_steps - done);
+        CLB_TRY(clb3d_step(h, n));
+        done += n;
+        st = residual3(h, &er);
+        if (st != CLB_OK || er < tol) break;
+    }
+    if (steps_out) *steps_out = done;
+    if (er_out) *er_out = er;
+    return st;
+}
+
 extern "C" clb_status clb3d_init_fields(clb3d_lattice* h, const double* rho, const double* ux, const double* uy,
                                         const double* uz, const double* T)
 {
@@ -873,8 +1018,9 @@ extern "C" clb_status clb3d_init_fields(clb3d_lattice* h, const double* rho, con
     CLB_CUDA(cudaGetLastError());
     h->cur = 0;
     h->steps = 0;
-    // the host arrays may be reused by the caller as soon as this returns
-    CLB_CUDA(cudaStreamSynchronize(h->stream));
+    // the residual's first snapshot: the initial fields
+    double er = 0.0;
+    CLB_TRY(residual3(h, &er));
     return CLB_OK;
 }
 

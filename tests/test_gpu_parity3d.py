@@ -237,3 +237,33 @@ def test_largest_lattice_steps_and_conserves_mass(clb):
     assert all(np.isfinite(a).all() for a in (rho, ux, uy, uz, T))
     assert float(np.sum(rho)) == pytest.approx(m0, rel=1e-6)
     assert float(np.max(np.abs(T))) <= 0.5 + 1e-2
+
+
+@pytest.mark.parametrize("storage", [F64, F32], ids=["f64", "f32"])
+def test_residual_and_run_match_the_oracle(clb, storage):
+    """clb3d_residual against the residual of the oracle's fields at the same two times (FP64 to
+    1e-9 relative, FP32 to 1e-3), twice in a row so the snapshot is replaced; clb3d_run stops a
+    conduction problem at the residual tolerance with the linear temperature profile."""
+    prob = W.rayleigh_benard3d(10, 8, 9, Ra=5e4, perturb=1e-2, storage=storage)
+    o = oracle.Oracle3D.from_problem(prob)
+    lat = clb.Lattice3D.from_problem(prob)
+    p = prob.params
+    prev = o.fields()[1:]
+    for k in (40, 25):
+        o.step(k)
+        lat.step(k)
+        cur = o.fields()[1:]
+        exp = oracle.residual3(prev, cur, p["u_ref"], p["dT_ref"])
+        assert lat.residual() == pytest.approx(exp, rel=1e-9 if storage == F64 else 1e-3)
+        prev = cur
+    lat.close()
+    cond = W.default_params3(nu=0.1, kappa=0.1, wall=(P, P, P, P, D, D), T_wall=(0, 0, 0, 0, 0.7, -0.3),
+                             storage=storage, dT_ref=1.0)
+    lat = clb.Lattice3D(2, 2, 12, cond)
+    lat.init_fields(1.0, 0.0, 0.0, 0.0, 0.0)
+    steps, er = lat.run(1e-9 if storage == F64 else 1e-6, 40000, 100)
+    assert er < (1e-9 if storage == F64 else 1e-6) and steps < 40000
+    T = lat.fields()[4][:, 0, 0]
+    zc = np.arange(12)
+    np.testing.assert_allclose(T, 0.7 - (zc + 0.5) / 12, atol=1e-7 if storage == F64 else 1e-4)
+    lat.close()

@@ -433,3 +433,14 @@ def test_moving_faces_uniform_along_an_axis_reproduce_the_2d_oracle():
     for a3, a2 in ((r3, r2), (ux3, ux2), (uy3, uy2), (T3, T2)):
         np.testing.assert_allclose(a3, lift(a2), atol=1e-13)
     np.testing.assert_allclose(uz3, 0.0, atol=1e-15)
+
+
+def test_residual3_reduces_to_the_2d_residual():
+    """With no z velocity the 3-D residual is the 2-D one of the same (ux, uy, T) fields."""
+    rng = np.random.default_rng(31)
+    prev = [rng.normal(size=(4, 5, 6)) * s for s in (0.01, 0.02, 0.0, 0.3)]
+    cur = [p + rng.normal(size=p.shape) * 1e-4 for p in prev]
+    cur[2] = np.zeros_like(cur[2])
+    e3 = oracle.residual3(prev, cur, 0.05, 1.0)
+    e2 = oracle.residual((prev[0], prev[1], prev[3]), (cur[0], cur[1], cur[3]), 0.05, 1.0)
+    assert e3 == pytest.approx(e2, rel=1e-14)

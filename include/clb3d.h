@@ -115,6 +115,14 @@ clb_status clb3d_residual(clb3d_lattice* h, double* er_out);
 clb_status clb3d_run(clb3d_lattice* h, double tol, long max_steps, long interval, long* steps_out,
                      double* er_out);
 
+/* Checkpoint: the current post-collision buffer as stored (populations or deviations) and the step
+ * count, after a small header. With buf == NULL, *bytes receives the size; otherwise *bytes is the
+ * buffer's capacity on entry and the bytes written on return. clb3d_load restores a checkpoint of a
+ * lattice with the same extents and storage (CLB_EINVAL otherwise) and restarts the residual's
+ * snapshot from the restored state. Both synchronise. */
+clb_status clb3d_save(clb3d_lattice* h, void* buf, size_t* bytes);
+clb_status clb3d_load(clb3d_lattice* h, const void* buf, size_t bytes);
+
 /* Launch shape of the step kernel: block_x threads along x (a multiple of 32, <= 256) times block_y
  * rows (block_x * block_y <= 256). 0 keeps a value. */
 clb_status clb3d_set_launch(clb3d_lattice* h, int block_x, int block_y);

@@ -123,6 +123,8 @@ _SIGS = {
     "clb3d_nusselt": [_VP, _I, _D],
     "clb3d_set_launch": [_VP, _I, _I],
     "clb3d_residual": [_VP, _D],
+    "clb3d_save": [_VP, _VP, _P(_S)],
+    "clb3d_load": [_VP, _VP, _S],
     "clb3d_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D],
     "clb3d_sync": [_VP],
     "clb3d_stream": [_VP],
@@ -620,6 +622,16 @@ class Lattice3D:
         v = ctypes.c_double()
         _check(lib().clb3d_residual(self._h, ctypes.byref(v)))
         return v.value
+
+    def save(self) -> bytes:
+        n = _S()
+        _check(lib().clb3d_save(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().clb3d_save(self._h, buf, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def load(self, data: bytes):
+        _check(lib().clb3d_load(self._h, data, len(data)))
 
     def run(self, tol: float, max_steps: int, interval: int = 100):
         st, er = _L(), ctypes.c_double()

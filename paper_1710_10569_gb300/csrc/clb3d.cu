@@ -1136,6 +1136,65 @@ extern "C" clb_status clb3d_sync(clb3d_lattice* h)
     return CLB_OK;
 }
 
+namespace {
+
+struct Ckpt3Header {
+    char magic[8];
+    int nx, ny, nz, storage;
+    long long steps;
+    unsigned long long bytes;
+};
+
+size_t ckpt3_payload(const clb3d_lattice* h)
+{
+    return (size_t)NP * (size_t)h->plane * esize(h->p.storage);
+}
+
+}  // namespace
+
+extern "C" clb_status clb3d_save(clb3d_lattice* h, void* buf, size_t* bytes)
+{
+    CHECK_H3(h);
+    if (!bytes) return set_error(CLB_EINVAL, "bytes must not be NULL");
+    const size_t bb = ckpt3_payload(h), need = sizeof(Ckpt3Header) + bb;
+    if (!buf) {
+        *bytes = need;
+        return CLB_OK;
+    }
+    if (*bytes < need) return set_error(CLB_EINVAL, "checkpoint buffer %zu < %zu bytes", *bytes, need);
+    Ckpt3Header hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "CLB3CKP1", 8);
+    hd.nx = h->nx;
+    hd.ny = h->ny;
+    hd.nz = h->nz;
+    hd.storage = h->p.storage;
+    hd.steps = h->steps;
+    hd.bytes = bb;
+    std::memcpy(buf, &hd, sizeof(hd));
+    CLB_CUDA(cudaMemcpyAsync((char*)buf + sizeof(hd), h->buf[h->cur], bb, cudaMemcpyDeviceToHost, h->stream));
+    CLB_CUDA(cudaStreamSynchronize(h->stream));
+    *bytes = need;
+    return CLB_OK;
+}
+
+extern "C" clb_status clb3d_load(clb3d_lattice* h, const void* buf, size_t bytes)
+{
+    CHECK_H3(h);
+    if (!buf || bytes < sizeof(Ckpt3Header)) return set_error(CLB_EINVAL, "checkpoint too small");
+    Ckpt3Header hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    const size_t bb = ckpt3_payload(h);
+    if (std::memcmp(hd.magic, "CLB3CKP1", 8) != 0 || hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz ||
+        hd.storage != h->p.storage || hd.bytes != bb || bytes < sizeof(hd) + bb)
+        return set_error(CLB_EINVAL, "checkpoint does not match this lattice");
+    CLB_CUDA(cudaMemcpyAsync(h->buf[h->cur], (const char*)buf + sizeof(hd), bb, cudaMemcpyHostToDevice, h->stream));
+    h->steps = hd.steps;
+    // the residual's snapshot restarts from the restored state
+    double er = 0.0;
+    return residual3(h, &er);
+}
+
 extern "C" void* clb3d_stream(clb3d_lattice* h) { return h ? (void*)h->stream : nullptr; }
 
 extern "C" clb_status clb3d_buffers(clb3d_lattice* h, void** current, long long* plane_elems, int* row_pitch)

@@ -267,3 +267,40 @@ def test_residual_and_run_match_the_oracle(clb, storage):
     zc = np.arange(12)
     np.testing.assert_allclose(T, 0.7 - (zc + 0.5) / 12, atol=1e-7 if storage == F64 else 1e-4)
     lat.close()
+
+
+@pytest.mark.parametrize("storage", [F64, F16], ids=["f64", "f16dev"])
+def test_checkpoint_restores_the_run_bit_for_bit(clb, storage):
+    """clb3d_save after 37 steps, 20 more steps, clb3d_load, the same 20 steps again: the same
+    populations bit for bit; a checkpoint of another lattice is refused."""
+    prob = W.random_problem3d(13, 7, 6, seed=15, storage=storage, moving=True, walls=(P, P, D, A, A, D))
+    lat = clb.Lattice3D.from_problem(prob)
+    lat.step(37)
+    ck = lat.save()
+    lat.step(20)
+    a = lat.populations()
+    lat.load(ck)
+    lat.step(20)
+    b = lat.populations()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    other = clb.Lattice3D(13, 7, 5, prob.params)
+    with pytest.raises(clb.CLBError):
+        other.load(ck)
+    other.close()
+    lat.close()
+
+
+def test_non_finite_fields_are_reported(clb):
+    """A NaN in the initial temperature reaches CLB_ENAN in the Nusselt number and the residual."""
+    prob = W.rayleigh_benard3d(8, 6, 5, Ra=1e4)
+    prob.T[2, 3, 4] = float("nan")
+    lat = clb.Lattice3D(prob.nx, prob.ny, prob.nz, prob.params)
+    with pytest.raises(clb.CLBError) as e:
+        lat.init_fields(*prob.fields())
+    assert e.value.status == clb.CLB_ENAN
+    lat.step(3)
+    for call in (lambda: lat.nusselt(2), lat.residual):
+        with pytest.raises(clb.CLBError) as e:
+            call()
+        assert e.value.status == clb.CLB_ENAN
+    lat.close()

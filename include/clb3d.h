@@ -84,7 +84,9 @@ clb_status clb3d_footprint(int nx, int ny, int nz, const clb3d_params* p, size_t
 clb_status clb3d_create(int nx, int ny, int nz, const clb3d_params* p, void* stream, clb3d_lattice** out);
 void clb3d_destroy(clb3d_lattice* h);
 
-/* f = f^eq(rho, u), g = g^eq(T, u) at every node from host fields (nz*ny*nx each). */
+/* f = f^eq(rho, u), g = g^eq(T, u) at every node from host fields (nz*ny*nx each); also takes the
+ * residual's first snapshot. Synchronises. CLB_ENAN if a resulting field is not finite (the state
+ * is set all the same). */
 clb_status clb3d_init_fields(clb3d_lattice* h, const double* rho, const double* ux, const double* uy,
                              const double* uz, const double* T);
 

@@ -191,8 +191,11 @@ __device__ __forceinline__ A c_term(const Axis<A>& X, const Axis<A>& Y, const Ax
 
 // One node: Eqs. (3), (13), (23), then the D3Q27 collision (Eq. 8 in 3-D) and the D3Q7 collision
 // (Eq. 19 in 3-D), on the stored form (deviations for FP32, populations for FP64). f and g are
-// pre-collision on entry and post-collision on return.
-template <bool DEV, typename A>
+// pre-collision on entry and post-collision on return. HIGH1 = true is for s_3 = s_4 = s_5 = s_6 = 1
+// (the paper's setting of the high-order rates): there every moment of order 3 or more relaxes to
+// its equilibrium plus half its forcing term, k* = -E + C/2, whatever its pre-collision value, so
+// those moments need not be formed at all.
+template <bool DEV, bool HIGH1 = false, typename A>
 __device__ __forceinline__ void collide3(const Lat3<A>& P, A f[NF], A g[NG])
 {
     const A cs2 = A(1.0 / 3.0);
@@ -229,10 +232,15 @@ __device__ __forceinline__ void collide3(const Lat3<A>& P, A f[NF], A g[NG])
             f[k] = f[k] + (a == 1 ? F[0] : b == 1 ? F[1] : F[2]);
             continue;
         }
+        const bool forced = ((a == 1) + (b == 1) + (c == 1)) == 1;  // C_k can be non-zero
+        if (HIGH1 && o >= 3) {
+            const A E = e_term<DEV>(X, Y, Z, a, b, c, P.rho_b, drho);
+            f[k] = forced ? fma_(A(0.5), c_term(X, Y, Z, a, b, c, F), -E) : -E;
+            continue;
+        }
         const A s = o == 2 ? P.s_nu : o == 3 ? P.s_3 : o == 4 ? P.s_4 : o == 5 ? P.s_5 : P.s_6;
         const A x = f[k] + e_term<DEV>(X, Y, Z, a, b, c, P.rho_b, drho);
         const A cf = c_term(X, Y, Z, a, b, c, F);
-        const bool forced = ((a == 1) + (b == 1) + (c == 1)) == 1;  // C_k can be non-zero
         f[k] = forced ? fma_(fma_(A(-0.5), s, A(1)), cf, fma_(-s, x, f[k])) : fma_(-s, x, f[k]);
     }
     back27(f, ux, uy, uz);
@@ -371,7 +379,7 @@ __device__ __forceinline__ void store3(T* __restrict__ dst, const Lat3<A>& P, in
 
 // One time step: thread (tx, ty) of block b updates node x = (b % xblocks) * blockDim.x + tx of
 // row r = (b / xblocks) * blockDim.y + ty, row r being (y, z) = (r % ny, r / ny).
-template <int ST>
+template <int ST, bool HIGH1>
 __global__ void __launch_bounds__(256) k_step3(const typename Storage<ST>::T* __restrict__ src,
                                                typename Storage<ST>::T* __restrict__ dst,
                                                const Lat3<typename Storage<ST>::A> P, int xblocks)
@@ -387,7 +395,7 @@ __global__ void __launch_bounds__(256) k_step3(const typename Storage<ST>::T* __
                         (P.per[2] || (z > 0 && z < P.nz - 1));
     if (nowall) gather3<true>(src, P, x, y, z, f, g);
     else gather3(src, P, x, y, z, f, g);
-    collide3<Storage<ST>::DEV>(P, f, g);
+    collide3<Storage<ST>::DEV, HIGH1>(P, f, g);
     store3(dst, P, (z * P.ny + y) * P.pitch + x, f, g);
 }
 
@@ -816,18 +824,34 @@ Lat3<A> make_lat3(int nx, int ny, int nz, const clb3d_params& p)
 
 int xblocks_of(const clb3d_lattice* h) { return (h->nx + h->bx - 1) / h->bx; }
 
+template <int ST, bool HIGH1>
+void launch3(const clb3d_lattice* h, int from, cudaStream_t s, unsigned grid, dim3 block, int xb)
+{
+    using T = typename Storage<ST>::T;
+    if constexpr (ST == ST_F64)
+        k_step3<ST, HIGH1><<<grid, block, 0, s>>>((const T*)h->buf[from], (T*)h->buf[from ^ 1], h->Pd, xb);
+    else
+        k_step3<ST, HIGH1><<<grid, block, 0, s>>>((const T*)h->buf[from], (T*)h->buf[from ^ 1], h->Pf, xb);
+}
+
+template <int ST>
+void launch3_rates(const clb3d_lattice* h, int from, cudaStream_t s, unsigned grid, dim3 block, int xb)
+{
+    // the high-order rates all 1 (the paper's setting): the form that skips those moments
+    const bool high1 = h->p.s_3 == 1.0 && h->p.s_4 == 1.0 && h->p.s_5 == 1.0 && h->p.s_6 == 1.0;
+    if (high1) launch3<ST, true>(h, from, s, grid, block, xb);
+    else launch3<ST, false>(h, from, s, grid, block, xb);
+}
+
 clb_status launch_step3(clb3d_lattice* h, int from, cudaStream_t s)
 {
     const int xb = xblocks_of(h);
     const long long rb = ((long long)h->ny * h->nz + h->by - 1) / h->by;
     const dim3 block(h->bx, h->by);
     const unsigned grid = unsigned((long long)xb * rb);
-    if (h->p.storage == CLB_F64)
-        k_step3<ST_F64><<<grid, block, 0, s>>>((const double*)h->buf[from], (double*)h->buf[from ^ 1], h->Pd, xb);
-    else if (h->p.storage == CLB_F32)
-        k_step3<ST_F32><<<grid, block, 0, s>>>((const float*)h->buf[from], (float*)h->buf[from ^ 1], h->Pf, xb);
-    else
-        k_step3<ST_F16DEV><<<grid, block, 0, s>>>((const __half*)h->buf[from], (__half*)h->buf[from ^ 1], h->Pf, xb);
+    if (h->p.storage == CLB_F64) launch3_rates<ST_F64>(h, from, s, grid, block, xb);
+    else if (h->p.storage == CLB_F32) launch3_rates<ST_F32>(h, from, s, grid, block, xb);
+    else launch3_rates<ST_F16DEV>(h, from, s, grid, block, xb);
     CLB_CUDA(cudaGetLastError());
     return CLB_OK;
 }

@@ -75,6 +75,11 @@ inline size_t buffer_slot_bytes(int nx, int ny, int storage)
 
 clb_status validate(int nx, int ny, const clb_params* p);
 
+// One step of the staged-rows kernel (k_step_pipe, clb_pipe_*.cu) from buffer a into buffer b:
+// V nodes per thread, S stages, R rows per warp; Pd or Pf by the storage form.
+cudaError_t enqueue_pipe_any(int storage, const LatParams<double>& Pd, const LatParams<float>& Pf, int device,
+                             int nx, int ny, const void* a, void* b, cudaStream_t s, int V, int S, int R);
+
 // s_nu from nu = (1/s_nu - 1/2) c_s^2 with c_s^2 = 1/3 (Sec. 2.1).
 inline double rate_nu(double nu) { return 1.0 / (3.0 * nu + 0.5); }
 // lambda1 from alpha = (1/lambda1 - 1/2) c_T,s^2 (Sec. 2.2).

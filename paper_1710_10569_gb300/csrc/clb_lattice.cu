@@ -191,41 +191,6 @@ void enqueue_step_npt(const clb_handle* h, const void* a, void* b, cudaStream_t 
     else enqueue_step<ST, 1>(h, a, b, s, bx, by);
 }
 
-template <int ST, int V, int S>
-cudaError_t enqueue_pipe(const clb_handle* h, const void* a, void* b, cudaStream_t s, int R)
-{
-    using E = typename Storage<ST>::T;
-    using A = typename Storage<ST>::A;
-    constexpr size_t smem = pipe_smem_bytes<ST, V, S>();
-    static bool attr_set[64] = {false};  // per instantiation and device
-    const int dev = h->device >= 0 && h->device < 64 ? h->device : 0;
-    if (!attr_set[dev]) {
-        const cudaError_t e = cudaFuncSetAttribute(k_step_pipe<ST, V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
-    }
-    const int cols = kPipeWarps * 32 * V;
-    const dim3 grid((h->nx + cols - 1) / cols, (h->ny + R - 1) / R);
-    const LatParams<A>& P = *reinterpret_cast<const LatParams<A>*>(ST == ST_F64 ? (const void*)&h->Pd : (const void*)&h->Pf);
-    k_step_pipe<ST, V, S><<<grid, kPipeWarps * 32, smem, s>>>((const E*)a, (E*)b, P, R);
-    return cudaSuccess;
-}
-
-template <int ST, int V>
-cudaError_t enqueue_pipe_s(const clb_handle* h, const void* a, void* b, cudaStream_t s, int S, int R)
-{
-    if (S == 2) return enqueue_pipe<ST, V, 2>(h, a, b, s, R);
-    if (S == 3) return enqueue_pipe<ST, V, 3>(h, a, b, s, R);
-    return enqueue_pipe<ST, V, 4>(h, a, b, s, R);
-}
-
-template <int ST>
-cudaError_t enqueue_pipe_v(const clb_handle* h, const void* a, void* b, cudaStream_t s, int V, int S, int R)
-{
-    if (V == 4) return enqueue_pipe_s<ST, 4>(h, a, b, s, S, R);
-    return enqueue_pipe_s<ST, 2>(h, a, b, s, S, R);
-}
-
 struct Launch {
     int bx, by, npt, stages, rows;
 };
@@ -238,12 +203,8 @@ clb_status launch_step(clb_handle* h, int from, cudaStream_t s, const Launch& L)
     void* a = h->buf[from];
     void* b = h->buf[from ^ 1];
     if (L.stages > 0) {
-        cudaError_t e;
-        switch (h->p.storage) {
-        case CLB_F64: e = enqueue_pipe_v<ST_F64>(h, a, b, s, L.npt, L.stages, L.rows); break;
-        case CLB_F32: e = enqueue_pipe_v<ST_F32>(h, a, b, s, L.npt, L.stages, L.rows); break;
-        default: e = enqueue_pipe_v<ST_F16DEV>(h, a, b, s, L.npt, L.stages, L.rows); break;
-        }
+        const cudaError_t e = enqueue_pipe_any(h->p.storage, h->Pd, h->Pf, h->device, h->nx, h->ny, a, b, s, L.npt,
+                                               L.stages, L.rows);
         if (e != cudaSuccess) return set_error(CLB_ECUDA, "pipelined step: %s", cudaGetErrorString(e));
     } else {
         switch (h->p.storage) {

@@ -63,7 +63,8 @@ class _Params3(ctypes.Structure):
                 ("s_5", ctypes.c_double), ("s_6", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("lambda2", ctypes.c_double), ("cs2_T", ctypes.c_double),
                 ("Fv", ctypes.c_double * 3), ("g_axis", ctypes.c_int), ("wall", ctypes.c_int * 6),
-                ("T_wall", ctypes.c_double * 6), ("u_wall", ctypes.c_double * 18)]
+                ("T_wall", ctypes.c_double * 6), ("u_wall", ctypes.c_double * 18),
+                ("thermal_only", ctypes.c_int)]
 
 
 def _load():
@@ -104,6 +105,7 @@ def _load():
             lib.orc3_set_pops.argtypes = [vp, d, d]
             lib.orc3_collide_node.argtypes = [P(_Params3), d, d, d, d]
             lib.orc3_equilibrium_node.argtypes = [P(_Params3)] + [ctypes.c_double] * 5 + [d, d]
+            lib.orc3_collide_thermal_node.argtypes = [P(_Params3), d] + [ctypes.c_double] * 3 + [d]
             lib.orc3_matrices.argtypes = ([P(_Params3)] + [ctypes.c_double] * 3 + [d] * 9
                                           + [P(ctypes.c_int)] * 2)
             _lib = lib
@@ -327,6 +329,7 @@ def _params3(p: dict, nx: int = 1, ny: int = 1, nz: int = 1) -> _Params3:
     for face in range(6):
         for d in range(3):
             s.u_wall[3 * face + d] = float(uw[face][d])
+    s.thermal_only = int(p.get("thermal_only", 0))
     return s
 
 
@@ -458,3 +461,13 @@ def residual3(prev, cur, u_ref: float, dT_ref: float) -> float:
                float(np.sum(cux ** 2 + cuy ** 2 + cuz ** 2)), u_ref)
     rT = ratio(float(np.sum((cT - pT) ** 2)), float(np.sum(cT ** 2)), dT_ref)
     return max(ru, rT)
+
+
+def collide3_thermal_node(params: dict, g, ux, uy, uz):
+    """Post-collision D3Q7 populations of one node for a prescribed velocity."""
+    lib = _load()
+    p = _params3(params)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    go = np.empty(7)
+    lib.orc3_collide_thermal_node(ctypes.byref(p), _ptr(g), float(ux), float(uy), float(uz), _ptr(go))
+    return go

@@ -38,6 +38,9 @@
  * Only the test-suite, the package smoke check and the benchmark's CPU-baseline leg load this file.
  * It shares no code, header, table or constant with the CUDA library.
  *
+ * With thermal_only set only the D3Q7 equation is stepped, with the velocity given to orc3_init
+ * held fixed (the 3-D form of the Sec. 3.1 set-up).
+ *
  * Pins (tests/test_oracle3d_pins.py): moments against brute-force sums, N(u) N(-u) = I,
  * conservation, the equilibrium as a fixed point, a field uniform along one axis reproducing the
  * two-dimensional oracle step for step (all three axis orientations), axis permutation symmetry,
@@ -66,6 +69,7 @@ typedef struct {
     int wall[6];      /* faces -x, +x, -y, +y, -z, +z */
     double T_wall[6];
     double u_wall[6][3]; /* velocity of each wall face */
+    int thermal_only;    /* 1: only the D3Q7 equation, with the velocity given to orc3_init held fixed */
 } orc3_params;
 
 /* Velocity component of index digit 0, 1, 2: 0, +1, -1. Population i has digits (i%3, i/3%3, i/9). */
@@ -89,6 +93,7 @@ typedef struct {
     double fwall[6][Q27];   /* f^eq(rho0, u_wall) of each face */
     double gwall[6][Q7];    /* g^eq(T_wall, u_wall) of each face */
     double *f, *g, *fs, *gs; /* [q][z][y][x] */
+    double *up[3];           /* prescribed velocity of the thermal-only mode, [z][y][x] */
     long steps;
 } orc3_sim;
 
@@ -308,6 +313,24 @@ static void macroscopic(const orc3_sim *s, const double f[Q27], const double g[Q
     for (int d = 0; d < 3; ++d) u[d] = (j[d] + 0.5 * F[d]) / r;
 }
 
+/* D3Q7 collision (Eqs. 16-21 in 3-D) with the velocity u; T = sum g. */
+static void collide_d3q7(const orc3_sim *s, const double g[Q7], const double u[3], double go[Q7])
+{
+    double T = 0.0;
+    for (int i = 0; i < Q7; ++i) T += g[i];
+    double NT[Q7][Q7], gamT[Q7], gtT[Q7], dT[Q7], SdT[Q7], gtsT[Q7], gamsT[Q7];
+    build_NT(u[0], u[1], u[2], NT);
+    matvec(Q7, &s->MT[0][0], g, gamT);
+    matvec(Q7, &NT[0][0], gamT, gtT);
+    const double c2 = s->p.cs2_T;
+    const double geqT[Q7] = {T, 0, 0, 0, T * c2, T * c2, T * c2};
+    for (int k = 0; k < Q7; ++k) dT[k] = gtT[k] - geqT[k];
+    matvec(Q7, &s->ST[0][0], dT, SdT);
+    for (int k = 0; k < Q7; ++k) gtsT[k] = gtT[k] - SdT[k];
+    solve_unit_lower(Q7, &NT[0][0], gtsT, gamsT);
+    matvec(Q7, &s->MTinv[0][0], gamsT, go);
+}
+
 static void collide(const orc3_sim *s, const double f[Q27], const double g[Q7], double fo[Q27],
                     double go[Q7])
 {
@@ -330,18 +353,7 @@ static void collide(const orc3_sim *s, const double f[Q27], const double g[Q7], 
     solve_unit_lower(Q27, &Nl[0][0], gts, gams);
     matvec(Q27, &s->Minv[0][0], gams, fo);
 
-    /* ---- D3Q7 ---- */
-    double NT[Q7][Q7], gamT[Q7], gtT[Q7], dT[Q7], SdT[Q7], gtsT[Q7], gamsT[Q7];
-    build_NT(u[0], u[1], u[2], NT);
-    matvec(Q7, &s->MT[0][0], g, gamT);
-    matvec(Q7, &NT[0][0], gamT, gtT);
-    const double c2 = p->cs2_T;
-    const double geqT[Q7] = {T, 0, 0, 0, T * c2, T * c2, T * c2};
-    for (int k = 0; k < Q7; ++k) dT[k] = gtT[k] - geqT[k];
-    matvec(Q7, &s->ST[0][0], dT, SdT);
-    for (int k = 0; k < Q7; ++k) gtsT[k] = gtT[k] - SdT[k];
-    solve_unit_lower(Q7, &NT[0][0], gtsT, gamsT);
-    matvec(Q7, &s->MTinv[0][0], gamsT, go);
+    collide_d3q7(s, g, u, go);
 }
 
 static void equilibrium(const orc3_sim *s, double rho, const double u[3], double T, double f[Q27],
@@ -423,7 +435,13 @@ static void collide_all(orc3_sim *s)
         double f[Q27], g[Q7], fo[Q27], go[Q7];
         for (int i = 0; i < Q27; ++i) f[i] = s->f[i * n + k];
         for (int i = 0; i < Q7; ++i) g[i] = s->g[i * n + k];
-        collide(s, f, g, fo, go);
+        if (s->p.thermal_only) {
+            const double u[3] = {s->up[0][k], s->up[1][k], s->up[2][k]};
+            for (int i = 0; i < Q27; ++i) fo[i] = f[i];
+            collide_d3q7(s, g, u, go);
+        } else {
+            collide(s, f, g, fo, go);
+        }
         for (int i = 0; i < Q27; ++i) s->fs[i * n + k] = fo[i];
         for (int i = 0; i < Q7; ++i) s->gs[i * n + k] = go[i];
     }
@@ -448,8 +466,11 @@ int orc3_create(const orc3_params *p, orc3_sim **out)
     s->fs = (double *)calloc(Q27 * n, sizeof(double));
     s->g = (double *)calloc(Q7 * n, sizeof(double));
     s->gs = (double *)calloc(Q7 * n, sizeof(double));
-    if (!s->f || !s->fs || !s->g || !s->gs) {
-        free(s->f); free(s->fs); free(s->g); free(s->gs); free(s);
+    for (int d = 0; d < 3; ++d) s->up[d] = (double *)calloc(n, sizeof(double));
+    if (!s->f || !s->fs || !s->g || !s->gs || !s->up[0] || !s->up[1] || !s->up[2]) {
+        free(s->f); free(s->fs); free(s->g); free(s->gs);
+        for (int d = 0; d < 3; ++d) free(s->up[d]);
+        free(s);
         return -2;
     }
     *out = s;
@@ -460,14 +481,21 @@ void orc3_destroy(orc3_sim *s)
 {
     if (!s) return;
     free(s->f); free(s->fs); free(s->g); free(s->gs);
+    for (int d = 0; d < 3; ++d) free(s->up[d]);
     free(s);
 }
 
-/* f = f^eq(rho, u), g = g^eq(T, u) from [nz][ny][nx] fields. */
+/* f = f^eq(rho, u), g = g^eq(T, u) from [nz][ny][nx] fields (in the thermal-only mode u is also
+ * kept as the prescribed velocity). */
 void orc3_init(orc3_sim *s, const double *rho, const double *ux, const double *uy, const double *uz,
                const double *T)
 {
     const size_t n = nodes(s);
+    if (s->p.thermal_only) {
+        memcpy(s->up[0], ux, n * sizeof(double));
+        memcpy(s->up[1], uy, n * sizeof(double));
+        memcpy(s->up[2], uz, n * sizeof(double));
+    }
     for (size_t k = 0; k < n; ++k) {
         double f[Q27], g[Q7];
         const double u[3] = {ux[k], uy[k], uz[k]};
@@ -495,6 +523,8 @@ void orc3_fields(const orc3_sim *s, double *rho, double *ux, double *uy, double 
         for (int i = 0; i < Q27; ++i) f[i] = s->f[i * n + k];
         for (int i = 0; i < Q7; ++i) g[i] = s->g[i * n + k];
         macroscopic(s, f, g, &rho[k], u, &T[k], F);
+        if (s->p.thermal_only)
+            for (int d = 0; d < 3; ++d) u[d] = s->up[d][k];
         ux[k] = u[0];
         uy[k] = u[1];
         uz[k] = u[2];
@@ -572,4 +602,17 @@ void orc3_matrices(const orc3_params *p, double ux, double uy, double uz, double
         e7[3 * i + 2] = EZ7[i];
     }
     free(s);
+}
+
+/* D3Q7 collision of one node with a prescribed velocity (the thermal-only mode). */
+int orc3_collide_thermal_node(const orc3_params *p, const double *g, double ux, double uy, double uz, double *go)
+{
+    orc3_sim *s = (orc3_sim *)calloc(1, sizeof(orc3_sim));
+    if (!s) return -2;
+    s->p = *p;
+    build_constants(s);
+    const double u[3] = {ux, uy, uz};
+    collide_d3q7(s, g, u, go);
+    free(s);
+    return 0;
 }

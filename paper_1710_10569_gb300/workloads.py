@@ -294,7 +294,7 @@ def default_params3(**overrides) -> dict:
         s_b=1.0, s_3=1.0, s_4=1.0, s_5=1.0, s_6=1.0, lambda0=1.0, lambda2=1.0, cs2_T=0.25,
         Fv=(0.0, 0.0, 0.0), g_axis=2,
         wall=(WALL_PERIODIC,) * 6, T_wall=(0.0,) * 6, u_wall=((0.0, 0.0, 0.0),) * 6,
-        storage=STORAGE_F64, T_ref=0.0, u_ref=0.0, dT_ref=0.0,
+        storage=STORAGE_F64, T_ref=0.0, u_ref=0.0, dT_ref=0.0, thermal_only=0,
     )
     for k, v in overrides.items():
         if k not in p:

@@ -444,3 +444,59 @@ def test_residual3_reduces_to_the_2d_residual():
     e3 = oracle.residual3(prev, cur, 0.05, 1.0)
     e2 = oracle.residual((prev[0], prev[1], prev[3]), (cur[0], cur[1], cur[3]), 0.05, 1.0)
     assert e3 == pytest.approx(e2, rel=1e-14)
+
+
+# ----------------------------------------------------------------------------- thermal-only mode
+
+
+def test_thermal_only_collision_equals_the_coupled_d3q7_part():
+    """The D3Q7 collision with a prescribed velocity equals the coupled step's D3Q7 part when the
+    prescribed velocity is the flow's (no force, so u = sum f e / rho)."""
+    rng = np.random.default_rng(41)
+    for _ in range(20):
+        p = rand_params3(rng, g_beta=0.0, Fv=(0.0, 0.0, 0.0))
+        f = rng.uniform(0.005, 0.1, 27)
+        g = rng.uniform(-0.1, 0.2, 7)
+        u = (f @ E27) / f.sum()
+        _, go = oracle.collide3_node(p, f, g)
+        np.testing.assert_allclose(oracle.collide3_thermal_node(p, g, *u), go, atol=1e-16)
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_thermal_only_moving_frame_diffusivity(axis):
+    """Sec. 3.1 in 3-D with the D3Q7 equation alone: a temperature wave along `axis` in a prescribed
+    uniform flow (0.1, 0.12, -0.08) keeps alpha within 0.1% and travels at u_axis."""
+    L, alpha, B = 60, 0.05, 0.01
+    n3 = [1, 1, 1]
+    n3[axis] = L
+    adv = (0.1, 0.12, -0.08)
+    p = W.default_params3(nu=0.05, kappa=alpha, T0=1.0, thermal_only=1)
+    c = np.arange(L, dtype=np.float64)
+    T = (1.0 + B * np.sin(2 * math.pi * c / L)).reshape([L if (2 - i) == axis else 1 for i in range(3)])
+    o = oracle.Oracle3D(*n3, p)
+    o.init(1.0, adv[0], adv[1], adv[2], np.broadcast_to(T, n3[::-1]))
+    k = 2 * math.pi / L
+    o.step(300)
+    z1 = _mode(o.fields()[4].reshape(-1) - 1.0, k, L)
+    o.step(1500)
+    z2 = _mode(o.fields()[4].reshape(-1) - 1.0, k, L)
+    assert -math.log(abs(z2) / abs(z1)) / (k * k * 1500) == pytest.approx(alpha, rel=1e-3)
+    dphase = np.angle(z2 / z1)
+    assert abs((dphase + k * adv[axis] * 1500 + math.pi) % (2 * math.pi) - math.pi) < 2e-3
+    np.testing.assert_allclose(o.fields()[1], adv[0], atol=0)
+
+
+def test_thermal_only_closed_box_conserves_heat():
+    """Adiabatic faces all round and a divergence-free cellular velocity: sum g is conserved."""
+    n = 8
+    z, y, x = np.meshgrid(*(np.arange(n) + 0.5,) * 3, indexing="ij")
+    k = math.pi / n
+    ux = 0.05 * np.sin(k * x) * np.cos(k * y)
+    uy = -0.05 * np.cos(k * x) * np.sin(k * y)
+    p = W.default_params3(kappa=0.03, wall=(A,) * 6, thermal_only=1)
+    o = oracle.Oracle3D(n, n, n, p)
+    rng = np.random.default_rng(3)
+    o.init(1.0, ux, uy, 0.0, rng.uniform(-0.5, 0.5, (n, n, n)))
+    g0 = o.populations()[1].sum()
+    o.step(40)
+    assert o.populations()[1].sum() == pytest.approx(g0, rel=1e-13, abs=1e-13)

@@ -397,7 +397,36 @@ def three_d_run(steps: int, nx: int = 256, ny: int = 256, nz: int = 128):
                                     "dram_bytes_per_launch": traffic3d_per_launch(st, nx, ny, nz)}
     out["workload"] = f"rayleigh_benard3d_{nx}x{ny}x{nz}_Ra1e7_Pr0.71"
     out["kernel"] = "k_step3"
+    out["thermal_only"] = thermal3d_run(steps)
     return out
+
+
+def thermal3d_run(steps: int, n: int = 256):
+    """The 3-D thermal-only step (D3Q7 with a prescribed cellular velocity) on n^3 nodes, FP32
+    deviation storage: 7 populations in and out plus 3 velocity components in = 68 B/node."""
+    import torch
+    from paper_1710_10569_gb300 import clb
+    p = W.default_params3(kappa=0.02, storage=W.STORAGE_F32, thermal_only=1,
+                          wall=(W.WALL_PERIODIC,) * 4 + (W.WALL_DIRICHLET,) * 2, T_wall=(0.0,) * 4 + (0.5, -0.5))
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=np.float64) + 0.5,) * 3, indexing="ij")
+    k = 2 * math.pi / n
+    th = clb.Thermal3D(n, n, n, p)
+    th.init(0.5 - z / n, 0.1 * np.sin(k * x) * np.cos(k * y), -0.1 * np.cos(k * x) * np.sin(k * y), 0.0)
+    th.step(64)
+    stream = torch.cuda.ExternalStream(th.stream) if th.stream else torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    th.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    th.close()
+    peak, _ = measured_peaks()
+    nodes = n ** 3
+    gbs = 68 * nodes * steps / dt / 1e9
+    return {"workload": f"thermal_only3d_{n}^3_cellular_flow", "mlups": nodes * steps / dt / 1e6,
+            "bytes_per_node": 68, "achieved_gbs": gbs, "hbm_frac": gbs / peak, "steps": steps, "storage": "f32"}
 
 
 def served_run(storage: int, count: int = 48, step_cap: int = 20000, tol: float = 1e-6):

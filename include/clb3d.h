@@ -136,6 +136,25 @@ clb_status clb3d_sync(clb3d_lattice* h);
 void* clb3d_stream(clb3d_lattice* h);
 clb_status clb3d_buffers(clb3d_lattice* h, void** current, long long* plane_elems, int* row_pitch);
 
+/* Thermal-only mode: the D3Q7 equation alone with a prescribed velocity field (the 3-D form of
+ * the paper's Sec. 3.1 set-up, where only the temperature equation is solved for a given flow).
+ * The same pull, face rules, collision and equilibrium as the coupled step's D3Q7 part; the flow
+ * parameters of clb3d_params are not used (they are still validated). Device memory: two buffers
+ * of 7 planes, the velocity (3 values per node in the arithmetic precision) and FP64 staging. */
+typedef struct clb3d_thermal clb3d_thermal;
+clb_status clb3d_thermal_create(int nx, int ny, int nz, const clb3d_params* p, void* stream,
+                                clb3d_thermal** out);
+void clb3d_thermal_destroy(clb3d_thermal* h);
+/* g = g^eq(T, u) and the prescribed velocity u from host fields (nz*ny*nx each); synchronises. */
+clb_status clb3d_thermal_init(clb3d_thermal* h, const double* T, const double* ux, const double* uy,
+                              const double* uz);
+clb_status clb3d_thermal_step(clb3d_thermal* h, long n);
+/* T of the current state into a host array; synchronises. */
+clb_status clb3d_thermal_fields(clb3d_thermal* h, double* T);
+/* The current pre-collision D3Q7 populations (FP64, not deviations), [7][nz][ny][nx]; synchronises. */
+clb_status clb3d_thermal_populations(clb3d_thermal* h, double* g);
+clb_status clb3d_thermal_sync(clb3d_thermal* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -123,6 +123,13 @@ _SIGS = {
     "clb3d_nusselt": [_VP, _I, _D],
     "clb3d_set_launch": [_VP, _I, _I],
     "clb3d_residual": [_VP, _D],
+    "clb3d_thermal_create": [_I, _I, _I, _P(clb3d_params), _VP, _P(_VP)],
+    "clb3d_thermal_destroy": [_VP],
+    "clb3d_thermal_init": [_VP, _D, _D, _D, _D],
+    "clb3d_thermal_step": [_VP, _L],
+    "clb3d_thermal_fields": [_VP, _D],
+    "clb3d_thermal_populations": [_VP, _D],
+    "clb3d_thermal_sync": [_VP],
     "clb3d_save": [_VP, _VP, _P(_S)],
     "clb3d_load": [_VP, _VP, _S],
     "clb3d_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D],
@@ -132,6 +139,7 @@ _SIGS = {
 }
 _RESTYPES = {"clb_destroy": None, "clb_batch_destroy": None, "clb_serve_close": None,
              "clb_thermal_destroy": None, "clb3d_destroy": None, "clb3d_stream": _VP,
+             "clb3d_thermal_destroy": None,
              "clb_last_error": ctypes.c_char_p, "clb_version": ctypes.c_char_p, "clb_stream": _VP}
 
 _lock = threading.Lock()
@@ -638,3 +646,53 @@ class Lattice3D:
         _check(lib().clb3d_run(self._h, float(tol), int(max_steps), int(interval), ctypes.byref(st),
                                ctypes.byref(er)))
         return st.value, er.value
+
+
+class Thermal3D:
+    """The D3Q7 equation alone with a prescribed velocity (include/clb3d.h, clb3d_thermal_*).
+    Fields are (nz, ny, nx) float64 arrays."""
+
+    def __init__(self, nx: int, ny: int, nz: int, p: dict, stream=None):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.params = dict(p)
+        self._p = params3(p)
+        self.stream = _stream_handle(stream)
+        h = _VP()
+        _check(lib().clb3d_thermal_create(nx, ny, nz, ctypes.byref(self._p), self.stream, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().clb3d_thermal_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, T, ux, uy, uz):
+        n = self.nx * self.ny * self.nz
+        arrs = [_host(np.broadcast_to(np.asarray(a, dtype=np.float64), self.shape), n) for a in (T, ux, uy, uz)]
+        _check(lib().clb3d_thermal_init(self._h, *[_dptr(a) for a in arrs]))
+
+    def step(self, n: int = 1):
+        _check(lib().clb3d_thermal_step(self._h, int(n)))
+
+    def sync(self):
+        _check(lib().clb3d_thermal_sync(self._h))
+
+    def temperature(self):
+        T = np.empty(self.shape)
+        _check(lib().clb3d_thermal_fields(self._h, _dptr(T)))
+        return T
+
+    def populations(self):
+        g = np.empty((7,) + self.shape)
+        _check(lib().clb3d_thermal_populations(self._h, _dptr(g)))
+        return g

@@ -189,6 +189,9 @@ __device__ __forceinline__ A c_term(const Axis<A>& X, const Axis<A>& Y, const Ax
     return v;
 }
 
+template <bool DEV, typename A>
+__device__ __forceinline__ void collide_d3q7(const Lat3<A>& P, const A u[3], A dT, A g[NG]);
+
 // One node: Eqs. (3), (13), (23), then the D3Q27 collision (Eq. 8 in 3-D) and the D3Q7 collision
 // (Eq. 19 in 3-D), on the stored form (deviations for FP32, populations for FP64). f and g are
 // pre-collision on entry and post-collision on return. HIGH1 = true is for s_3 = s_4 = s_5 = s_6 = 1
@@ -245,8 +248,15 @@ __device__ __forceinline__ void collide3(const Lat3<A>& P, A f[NF], A g[NG])
     }
     back27(f, ux, uy, uz);
 
-    // D3Q7: central moments of the deviations about u, relaxation, back transform
     const A u[3] = {ux, uy, uz};
+    collide_d3q7<DEV>(P, u, dT, g);
+}
+
+// D3Q7 collision (Eqs. 16-21 in 3-D) on the stored form with velocity u; dT = sum of the stored
+// values (T - T_b). Central moments about u, relaxation, back transform.
+template <bool DEV, typename A>
+__device__ __forceinline__ void collide_d3q7(const Lat3<A>& P, const A u[3], A dT, A g[NG])
+{
     A kd[3], kdd[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -272,6 +282,9 @@ __device__ __forceinline__ void collide3(const Lat3<A>& P, A f[NF], A g[NG])
     g[0] = rest;
 }
 
+template <typename A>
+__device__ __forceinline__ void equilibrium_d3q7(const Lat3<A>& P, const A u[3], A dT, A g[NG]);
+
 // Equilibrium of one node on the stored form: the back transform of the equilibrium central
 // moments minus those of the rest state (-E for D3Q27; (dT, T_b u, cs2_T dT - T_b u^2) for D3Q7).
 template <bool DEV, typename A>
@@ -284,6 +297,13 @@ __device__ __forceinline__ void equilibrium3(const Lat3<A>& P, A drho, A ux, A u
     for (int k = 0; k < NF; ++k) f[k] = -e_term<DEV>(X, Y, Z, k % 3, (k / 3) % 3, k / 9, P.rho_b, drho);
     back27(f, ux, uy, uz);
     const A u[3] = {ux, uy, uz};
+    equilibrium_d3q7(P, u, dT, g);
+}
+
+// D3Q7 equilibrium on the stored form: the back transform of (dT, T_b u, cs2_T dT - T_b u^2).
+template <typename A>
+__device__ __forceinline__ void equilibrium_d3q7(const Lat3<A>& P, const A u[3], A dT, A g[NG])
+{
     A rest = dT;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -313,6 +333,35 @@ struct Src {
         s[2] = c < n - 1 ? c + 1 : (per ? 0 : c);
     }
 };
+
+// Pull of Eq. (22) for the D3Q7 populations held in planes base .. base + 6 of the buffer.
+template <bool NOWALL = false, typename T, typename A>
+__device__ __forceinline__ void gather_d3q7(const T* __restrict__ src, const Lat3<A>& P, int x, int y, int z,
+                                            int base, A g[NG])
+{
+    const Src sx(x, P.nx, P.per[0]), sy(y, P.ny, P.per[1]), sz(z, P.nz, P.per[2]);
+    const int pl = (int)P.plane;
+    const int here = (z * P.ny + y) * P.pitch + x;
+    g[0] = to_a(src[base * pl + here]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int j = 1 + 2 * d + s, jo = 1 + 2 * d + (1 - s);
+            const Src& S = d == 0 ? sx : (d == 1 ? sy : sz);
+            const int digit = 1 + s;
+            const int at = d == 0 ? (z * P.ny + y) * P.pitch + S.s[digit]
+                         : d == 1 ? (z * P.ny + S.s[digit]) * P.pitch + x
+                                  : (S.s[digit] * P.ny + y) * P.pitch + x;
+            if (NOWALL || S.ok[digit]) {
+                g[j] = to_a(src[(base + j) * pl + at]);
+            } else {
+                const int face = 2 * d + s;
+                const A bb = to_a(src[(base + jo) * pl + here]);
+                g[j] = P.kind[face] == CLB_WALL_DIRICHLET_T ? P.Tw[face] - bb : bb;
+            }
+        }
+}
 
 // Pull of Eqs. (12), (22): population i at the node comes from the node at x - e_i; across a
 // wall face f takes the node's own opposite post-collision value, and g the anti-bounce-back
@@ -345,25 +394,7 @@ __device__ __forceinline__ void gather3(const T* __restrict__ src, const Lat3<A>
                 }
             }
         }
-    g[0] = to_a(src[NF * pl + here]);
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int j = 1 + 2 * d + s, jo = 1 + 2 * d + (1 - s);
-            const Src& S = d == 0 ? sx : (d == 1 ? sy : sz);
-            const int digit = 1 + s;
-            const int at = d == 0 ? (z * P.ny + y) * P.pitch + S.s[digit]
-                         : d == 1 ? (z * P.ny + S.s[digit]) * P.pitch + x
-                                  : (S.s[digit] * P.ny + y) * P.pitch + x;
-            if (NOWALL || S.ok[digit]) {
-                g[j] = to_a(src[(NF + j) * pl + at]);
-            } else {
-                const int face = 2 * d + s;
-                const A bb = to_a(src[(NF + jo) * pl + here]);
-                g[j] = P.kind[face] == CLB_WALL_DIRICHLET_T ? P.Tw[face] - bb : bb;
-            }
-        }
+    gather_d3q7<NOWALL>(src, P, x, y, z, NF, g);
 }
 
 template <typename T, typename A>
@@ -397,6 +428,38 @@ __global__ void __launch_bounds__(256) k_step3(const typename Storage<ST>::T* __
     else gather3(src, P, x, y, z, f, g);
     collide3<Storage<ST>::DEV, HIGH1>(P, f, g);
     store3(dst, P, (z * P.ny + y) * P.pitch + x, f, g);
+}
+
+// The D3Q7 populations of node (x, y, z) written into the slots the next pull reads (planes base ..
+// base + 6): across a wall face into the node's own opposite slot, as Tw - value on Dirichlet faces.
+template <typename T, typename A>
+__device__ __forceinline__ void scatter_d3q7(T* __restrict__ dst, const Lat3<A>& P, int x, int y, int z, int base,
+                                             const A g[NG])
+{
+    const int pl = (int)P.plane;
+    const int here = (z * P.ny + y) * P.pitch + x;
+    const int n3[3] = {P.nx, P.ny, P.nz};
+    dst[base * pl + here] = from_a(g[0], (T*)nullptr);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const int j = 1 + 2 * d + sgn, jo = 1 + 2 * d + (1 - sgn);
+            int s[3] = {x, y, z};
+            s[d] -= sgn == 0 ? 1 : -1;
+            bool ok = true;
+            if (s[d] < 0 || s[d] >= n3[d]) {
+                if (P.per[d]) s[d] = (s[d] + n3[d]) % n3[d];
+                else ok = false;
+            }
+            if (ok) {
+                dst[(base + j) * pl + (s[2] * P.ny + s[1]) * P.pitch + s[0]] = from_a(g[j], (T*)nullptr);
+            } else {
+                const int face = 2 * d + sgn;
+                const A v = P.kind[face] == CLB_WALL_DIRICHLET_T ? P.Tw[face] - g[j] : g[j];
+                dst[(base + jo) * pl + here] = from_a(v, (T*)nullptr);
+            }
+        }
 }
 
 // Initial state f = f^eq(rho, u), g = g^eq(T, u), written into the slots the first step's pull
@@ -450,27 +513,7 @@ __global__ void __launch_bounds__(256) k_init3(typename Storage<ST>::T* __restri
         }
         dst[off] = from_a(v, (T*)nullptr);
     }
-    dst[NF * pl + here] = from_a(g[0], (T*)nullptr);
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int sgn = 0; sgn < 2; ++sgn) {
-            const int j = 1 + 2 * d + sgn, jo = 1 + 2 * d + (1 - sgn);
-            int s[3] = {x, y, z};
-            s[d] -= sgn == 0 ? 1 : -1;
-            bool ok = true;
-            if (s[d] < 0 || s[d] >= n3[d]) {
-                if (P.per[d]) s[d] = (s[d] + n3[d]) % n3[d];
-                else ok = false;
-            }
-            if (ok) {
-                dst[(NF + j) * pl + (s[2] * P.ny + s[1]) * P.pitch + s[0]] = from_a(g[j], (T*)nullptr);
-            } else {
-                const int face = 2 * d + sgn;
-                const A v = P.kind[face] == CLB_WALL_DIRICHLET_T ? P.Tw[face] - g[j] : g[j];
-                dst[(NF + jo) * pl + here] = from_a(v, (T*)nullptr);
-            }
-        }
+    scatter_d3q7(dst, P, x, y, z, NF, g);
 }
 
 // Macroscopic fields (FP64) of the current pre-collision state; with pops != nullptr also the
@@ -661,6 +704,80 @@ __global__ void __launch_bounds__(kRedThreads) k_resid_final3(const double* __re
     }
     if (threadIdx.x == 0)
         for (int q = 0; q < kResN; ++q) out[q] = sh[q][0];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Thermal-only mode: the D3Q7 equation alone with a prescribed velocity (the 3-D form of the
+// Sec. 3.1 set-up). Buffers hold the 7 D3Q7 planes; the velocity is a dense [3][nz][ny][nx] array
+// in the arithmetic precision. The pull, collision, equilibrium and initial scatter are the coupled
+// step's D3Q7 functions.
+
+template <int ST>
+__global__ void __launch_bounds__(256) k_thermal3_step(const typename Storage<ST>::T* __restrict__ src,
+                                                       typename Storage<ST>::T* __restrict__ dst,
+                                                       const typename Storage<ST>::A* __restrict__ vel,
+                                                       const Lat3<typename Storage<ST>::A> P, int xblocks)
+{
+    using A = typename Storage<ST>::A;
+    using T = typename Storage<ST>::T;
+    const int xb = blockIdx.x % xblocks, rb = blockIdx.x / xblocks;
+    const int x = xb * blockDim.x + threadIdx.x;
+    const int r = rb * blockDim.y + threadIdx.y;
+    if (x >= P.nx || r >= P.ny * P.nz) return;
+    const int y = r % P.ny, z = r / P.ny;
+    A g[NG];
+    const bool nowall = (P.per[0] || (x > 0 && x < P.nx - 1)) && (P.per[1] || (y > 0 && y < P.ny - 1)) &&
+                        (P.per[2] || (z > 0 && z < P.nz - 1));
+    if (nowall) gather_d3q7<true>(src, P, x, y, z, 0, g);
+    else gather_d3q7(src, P, x, y, z, 0, g);
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    const long long k = ((long long)z * P.ny + y) * P.nx + x;
+    const A u[3] = {vel[k], vel[n + k], vel[2 * n + k]};
+    const A dT = (g[0] + (g[1] + g[2])) + ((g[3] + g[4]) + (g[5] + g[6]));
+    collide_d3q7<Storage<ST>::DEV>(P, u, dT, g);
+    const int pl = (int)P.plane;
+    const int here = (z * P.ny + y) * P.pitch + x;
+#pragma unroll
+    for (int j = 0; j < NG; ++j) dst[j * pl + here] = from_a(g[j], (T*)nullptr);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256) k_thermal3_init(typename Storage<ST>::T* __restrict__ dst,
+                                                       typename Storage<ST>::A* __restrict__ vel,
+                                                       const Lat3<typename Storage<ST>::A> P,
+                                                       const double* __restrict__ fields, long long n)
+{
+    using A = typename Storage<ST>::A;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int x = int(k % P.nx), y = int((k / P.nx) % P.ny), z = int(k / ((long long)P.nx * P.ny));
+    const A u[3] = {A(fields[n + k]), A(fields[2 * n + k]), A(fields[3 * n + k])};
+    const A dT = A(fields[k] - double(P.T_b));
+    A g[NG];
+    equilibrium_d3q7(P, u, dT, g);
+    scatter_d3q7(dst, P, x, y, z, 0, g);
+    for (int d = 0; d < 3; ++d) vel[d * n + k] = u[d];
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256) k_thermal3_out(const typename Storage<ST>::T* __restrict__ src,
+                                                      const Lat3<typename Storage<ST>::A> P,
+                                                      double* __restrict__ T, double* __restrict__ pops,
+                                                      long long n)
+{
+    using A = typename Storage<ST>::A;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int x = int(k % P.nx), y = int((k / P.nx) % P.ny), z = int(k / ((long long)P.nx * P.ny));
+    A g[NG];
+    gather_d3q7(src, P, x, y, z, 0, g);
+    double dT = 0.0;
+    for (int j = 0; j < NG; ++j) dT += double(g[j]);
+    if (T) T[k] = double(P.T_b) + dT;
+    if (pops) {
+        const double c2 = double(P.cs2T);
+        for (int j = 0; j < NG; ++j) pops[j * n + k] = double(g[j]) + double(P.T_b) * (j == 0 ? 1.0 - 3.0 * c2 : 0.5 * c2);
+    }
 }
 
 }  // namespace clb3
@@ -1227,5 +1344,216 @@ extern "C" clb_status clb3d_buffers(clb3d_lattice* h, void** current, long long*
     if (current) *current = h->buf[h->cur];
     if (plane_elems) *plane_elems = h->plane;
     if (row_pitch) *row_pitch = h->pitch;
+    return CLB_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Thermal-only handle.
+
+struct clb3d_thermal {
+    int nx = 0, ny = 0, nz = 0;
+    clb3d_params p{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    char* mem = nullptr;
+    void* buf[2] = {nullptr, nullptr};
+    void* vel = nullptr;
+    double* stage = nullptr;  // T, ux, uy, uz (init) and T (out)
+    double* pops = nullptr;   // populations on demand
+    int cur = 0;
+    long steps = 0;
+    int bx = 128, by = 1;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    Lat3<double> Pd{};
+    Lat3<float> Pf{};
+};
+
+namespace {
+
+size_t thermal3_buf_bytes(int nx, int ny, int nz, int storage)
+{
+    return align256((size_t)NG * (size_t)plane3(nx, ny, nz, storage) * esize(storage)) + 1024;
+}
+
+size_t thermal3_vel_bytes(long long n, int storage)
+{
+    return align256((size_t)3 * n * (storage == CLB_F64 ? 8 : 4));
+}
+
+clb_status thermal3_launch(clb3d_thermal* h, int from, cudaStream_t s)
+{
+    const int xb = (h->nx + h->bx - 1) / h->bx;
+    const long long rb = ((long long)h->ny * h->nz + h->by - 1) / h->by;
+    const dim3 block(h->bx, h->by);
+    const unsigned grid = unsigned((long long)xb * rb);
+    if (h->p.storage == CLB_F64)
+        k_thermal3_step<ST_F64><<<grid, block, 0, s>>>((const double*)h->buf[from], (double*)h->buf[from ^ 1],
+                                                       (const double*)h->vel, h->Pd, xb);
+    else if (h->p.storage == CLB_F32)
+        k_thermal3_step<ST_F32><<<grid, block, 0, s>>>((const float*)h->buf[from], (float*)h->buf[from ^ 1],
+                                                       (const float*)h->vel, h->Pf, xb);
+    else
+        k_thermal3_step<ST_F16DEV><<<grid, block, 0, s>>>((const __half*)h->buf[from], (__half*)h->buf[from ^ 1],
+                                                          (const float*)h->vel, h->Pf, xb);
+    CLB_CUDA(cudaGetLastError());
+    return CLB_OK;
+}
+
+#define CHECK_T3(h) \
+    if (!(h)) return set_error(CLB_EINVAL, "thermal handle is NULL")
+
+}  // namespace
+
+extern "C" clb_status clb3d_thermal_create(int nx, int ny, int nz, const clb3d_params* p, void* stream,
+                                           clb3d_thermal** out)
+{
+    if (!out) return set_error(CLB_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    CLB_TRY(validate3(nx, ny, nz, p));
+    clb3d_thermal* h = new (std::nothrow) clb3d_thermal();
+    if (!h) return set_error(CLB_ENOMEM, "host allocation failed");
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->p = *p;
+    h->stream = (cudaStream_t)stream;
+    const long long n = (long long)nx * ny * nz;
+    const size_t bb = thermal3_buf_bytes(nx, ny, nz, p->storage), vb = thermal3_vel_bytes(n, p->storage);
+    const size_t sb = align256(4 * (size_t)n * sizeof(double));
+    cudaError_t e = cudaMalloc((void**)&h->mem, 2 * bb + vb + sb);
+    if (e != cudaSuccess) {
+        delete h;
+        return set_error(e == cudaErrorMemoryAllocation ? CLB_ENOMEM : CLB_ECUDA, "cudaMalloc: %s",
+                         cudaGetErrorString(e));
+    }
+    h->buf[0] = h->mem;
+    h->buf[1] = h->mem + bb;
+    h->vel = h->mem + 2 * bb;
+    h->stage = (double*)(h->mem + 2 * bb + vb);
+    e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        clb3d_thermal_destroy(h);
+        return set_error(CLB_ECUDA, "thermal set-up: %s", cudaGetErrorString(e));
+    }
+    h->Pd = make_lat3<double>(nx, ny, nz, *p);
+    h->Pf = make_lat3<float>(nx, ny, nz, *p);
+    h->bx = nx > 128 ? 256 : (nx > 64 ? 128 : (nx > 32 ? 64 : 32));
+    h->by = h->bx >= 128 ? 1 : 128 / h->bx;
+    *out = h;
+    return CLB_OK;
+}
+
+extern "C" void clb3d_thermal_destroy(clb3d_thermal* h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto& g : h->graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->pops) cudaFree(h->pops);
+    if (h->mem) cudaFree(h->mem);
+    delete h;
+}
+
+extern "C" clb_status clb3d_thermal_init(clb3d_thermal* h, const double* T, const double* ux, const double* uy,
+                                         const double* uz)
+{
+    CHECK_T3(h);
+    if (!T || !ux || !uy || !uz) return set_error(CLB_EINVAL, "field pointers must not be NULL");
+    const long long n = (long long)h->nx * h->ny * h->nz;
+    const double* src[4] = {T, ux, uy, uz};
+    for (int q = 0; q < 4; ++q)
+        CLB_CUDA(cudaMemcpyAsync(h->stage + q * n, src[q], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const unsigned grid = unsigned((n + 255) / 256);
+    if (h->p.storage == CLB_F64)
+        k_thermal3_init<ST_F64><<<grid, 256, 0, h->stream>>>((double*)h->buf[0], (double*)h->vel, h->Pd, h->stage, n);
+    else if (h->p.storage == CLB_F32)
+        k_thermal3_init<ST_F32><<<grid, 256, 0, h->stream>>>((float*)h->buf[0], (float*)h->vel, h->Pf, h->stage, n);
+    else
+        k_thermal3_init<ST_F16DEV><<<grid, 256, 0, h->stream>>>((__half*)h->buf[0], (float*)h->vel, h->Pf, h->stage, n);
+    CLB_CUDA(cudaGetLastError());
+    h->cur = 0;
+    h->steps = 0;
+    CLB_CUDA(cudaStreamSynchronize(h->stream));
+    return CLB_OK;
+}
+
+extern "C" clb_status clb3d_thermal_step(clb3d_thermal* h, long n)
+{
+    CHECK_T3(h);
+    if (n < 0) return set_error(CLB_EINVAL, "n = %ld < 0", n);
+    while (n >= kChunk) {
+        if (!h->graph[h->cur]) {
+            CLB_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+            clb_status st = CLB_OK;
+            for (int k = 0; k < kChunk && st == CLB_OK; ++k) st = thermal3_launch(h, h->cur ^ (k & 1), h->cap);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+            if (st != CLB_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return set_error(CLB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+            const cudaError_t e2 = cudaGraphInstantiate(&h->graph[h->cur], g, 0);
+            cudaGraphDestroy(g);
+            if (e2 != cudaSuccess) return set_error(CLB_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+        }
+        CLB_CUDA(cudaGraphLaunch(h->graph[h->cur], h->stream));
+        n -= kChunk;
+        h->steps += kChunk;
+    }
+    for (; n > 0; --n) {
+        CLB_TRY(thermal3_launch(h, h->cur, h->stream));
+        h->cur ^= 1;
+        h->steps += 1;
+    }
+    return CLB_OK;
+}
+
+namespace {
+
+clb_status thermal3_out(clb3d_thermal* h, double* T_dev, double* pops_dev)
+{
+    const long long n = (long long)h->nx * h->ny * h->nz;
+    const unsigned grid = unsigned((n + 255) / 256);
+    if (h->p.storage == CLB_F64)
+        k_thermal3_out<ST_F64><<<grid, 256, 0, h->stream>>>((const double*)h->buf[h->cur], h->Pd, T_dev, pops_dev, n);
+    else if (h->p.storage == CLB_F32)
+        k_thermal3_out<ST_F32><<<grid, 256, 0, h->stream>>>((const float*)h->buf[h->cur], h->Pf, T_dev, pops_dev, n);
+    else
+        k_thermal3_out<ST_F16DEV><<<grid, 256, 0, h->stream>>>((const __half*)h->buf[h->cur], h->Pf, T_dev, pops_dev, n);
+    CLB_CUDA(cudaGetLastError());
+    return CLB_OK;
+}
+
+}  // namespace
+
+extern "C" clb_status clb3d_thermal_fields(clb3d_thermal* h, double* T)
+{
+    CHECK_T3(h);
+    if (!T) return set_error(CLB_EINVAL, "T must not be NULL");
+    const long long n = (long long)h->nx * h->ny * h->nz;
+    CLB_TRY(thermal3_out(h, h->stage, nullptr));
+    CLB_CUDA(cudaMemcpyAsync(T, h->stage, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CLB_CUDA(cudaStreamSynchronize(h->stream));
+    return CLB_OK;
+}
+
+extern "C" clb_status clb3d_thermal_populations(clb3d_thermal* h, double* g)
+{
+    CHECK_T3(h);
+    if (!g) return set_error(CLB_EINVAL, "g must not be NULL");
+    const long long n = (long long)h->nx * h->ny * h->nz;
+    if (!h->pops) CLB_CUDA(cudaMalloc((void**)&h->pops, (size_t)NG * n * sizeof(double)));
+    CLB_TRY(thermal3_out(h, nullptr, h->pops));
+    CLB_CUDA(cudaMemcpyAsync(g, h->pops, (size_t)NG * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CLB_CUDA(cudaStreamSynchronize(h->stream));
+    return CLB_OK;
+}
+
+extern "C" clb_status clb3d_thermal_sync(clb3d_thermal* h)
+{
+    CHECK_T3(h);
+    CLB_CUDA(cudaStreamSynchronize(h->stream));
     return CLB_OK;
 }

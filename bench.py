@@ -336,13 +336,15 @@ def batched_run(storage: int, count: int = 256, steps: int = 1000, seq_subset: i
 
     def time_batch(ps, k):
         b = clb.Batch(ps)
-        tile = b.autotune()
+        b.autotune()
+        launch = b.launch()
         b.step(64)
         dt = device_seconds(b.stream, lambda: b.step(k))
         b.close()
-        return dt, tile
+        return dt, launch
 
-    dt_all, tile = time_batch(probs, steps)
+    dt_all, launch = time_batch(probs, steps)
+    peak, _ = measured_peaks()
     sub = probs[:seq_subset]
     sub_nodes = sum(p.nodes for p in sub)
     dt_sub, _ = time_batch(sub, steps)
@@ -358,7 +360,9 @@ def batched_run(storage: int, count: int = 256, steps: int = 1000, seq_subset: i
     for lat in lats:
         lat.close()
     return {"instances": count, "nodes": nodes, "steps": steps, "storage": W.STORAGE_NAMES[storage],
-            "tile": list(tile), "mlups": nodes * steps / dt_all / 1e6,
+            "tile": list(launch["tile"]), "row_groups_per_block": launch["groups"],
+            "blocks_per_launch": launch["blocks"], "mlups": nodes * steps / dt_all / 1e6,
+            "hbm_frac": nodes * steps * BYTES_PER_NODE[storage] / dt_all / 1e9 / peak,
             "instance_steps_per_s": count * steps / dt_all,
             "subset": {"instances": seq_subset, "batched_mlups": sub_nodes * steps / dt_sub / 1e6,
                        "sequential_mlups": sub_nodes * steps / dt_seq / 1e6,

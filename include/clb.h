@@ -248,10 +248,17 @@ clb_status clb_batch_diagnostics(clb_batch *b, const int *axis, double *nu, doub
 clb_status clb_batch_run(clb_batch *b, double tol, long max_steps, long interval, long *steps,
                          double *er, int *status);
 /* Tile shape of the batched launch: threads along x (32..256), rows (block_x * rows <= 256) and
- * nodes per thread (1, 2, 4). clb_batch_autotune times candidates over the whole batch (the
- * populations are restored afterwards) and keeps the fastest. Results do not depend on it. */
+ * nodes per thread (1, 2, 4). Each block steps 1, 2, 4, ... such groups of rows one after another
+ * (it fetches its lattice's descriptor once): as many as keep a block at 2048 nodes or fewer and
+ * the launch at 8 or more rounds of the blocks the device holds at once. clb_batch_autotune times
+ * candidates over the whole batch (the populations are restored afterwards) and keeps the
+ * fastest. Results do not depend on it. */
 clb_status clb_batch_set_tile(clb_batch *b, int tile_x, int tile_y, int nodes_per_thread);
 clb_status clb_batch_autotune(clb_batch *b, int *tile_x, int *tile_y, int *nodes_per_thread);
+/* Launch geometry of the next batched step over the active instances: tile shape, groups of rows
+ * per block and blocks per launch. Any pointer may be NULL. */
+clb_status clb_batch_get_launch(clb_batch *b, int *tile_x, int *tile_y, int *nodes_per_thread,
+                                int *groups, long *blocks);
 
 /* ---------------------------------------------------------------------------------------------
  * Serving: requests arrive over time; each is admitted when a slot and enough of the HBM budget

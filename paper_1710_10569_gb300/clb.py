@@ -105,6 +105,7 @@ _SIGS = {
     "clb_batch_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D, _P(_I)],
     "clb_batch_set_tile": [_VP, _I, _I, _I],
     "clb_batch_autotune": [_VP, _P(_I), _P(_I), _P(_I)],
+    "clb_batch_get_launch": [_VP, _P(_I), _P(_I), _P(_I), _P(_I), _P(ctypes.c_long)],
     "clb_serve_open": [_S, _I, _I, _VP, _P(_VP)],
     "clb_serve_close": [_VP],
     "clb_serve_submit": [_VP, _I, _I, _P(clb_params), _D, _D, _D, _D, _I, _L, ctypes.c_double, _P(_L)],
@@ -468,6 +469,14 @@ class Batch:
         tx, ty, npt = _I(), _I(), _I()
         _check(lib().clb_batch_autotune(self._h, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(npt)))
         return tx.value, ty.value, npt.value
+
+    def launch(self) -> dict:
+        """Geometry of the next batched step: tile (threads x, threads y, nodes per thread), groups
+        of rows each block steps, and blocks per launch."""
+        tx, ty, npt, groups, blocks = _I(), _I(), _I(), _I(), ctypes.c_long()
+        _check(lib().clb_batch_get_launch(self._h, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(npt),
+                                          ctypes.byref(groups), ctypes.byref(blocks)))
+        return dict(tile=(tx.value, ty.value, npt.value), groups=groups.value, blocks=blocks.value)
 
 
 class Server:

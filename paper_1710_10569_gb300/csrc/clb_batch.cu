@@ -47,14 +47,14 @@ __device__ __forceinline__ void load_member(const Member<A>* __restrict__ src, M
 }
 
 // One time step of every lattice: block b covers tile (b - tile_begin) of lattice owner[b]; a
-// tile is (blockDim.x * V) x blockDim.y nodes, V consecutive nodes per thread (the same
-// per-warp update as the single-lattice step).
+// tile is (blockDim.x * V) x (blockDim.y * groups) nodes, V consecutive nodes per thread (the
+// same per-warp update as the single-lattice step), each warp stepping `groups` rows.
 // Register cap: the FP32 two-nodes-per-thread form (the default tile) is held at 96 registers so
 // that five 128-thread blocks stay resident per SM; the other forms take what they need (blocks
 // have at most 256 threads).
 template <int ST, int V>
 __global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(const Member<typename Storage<ST>::A>* __restrict__ mem,
-                                                      const int* __restrict__ owner, int parity)
+                                                      const int* __restrict__ owner, int parity, int groups)
 {
     using A = typename Storage<ST>::A;
     using E = typename Storage<ST>::T;
@@ -65,18 +65,57 @@ __global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(
     const int lane = threadIdx.x & 31;
     const int span = blockDim.x * V;
     int xt = tx * span, keep = 0;
-    // The last tile of a row that would run past the row's end is moved left to end on its last
-    // node, so that its warps take the vector path (walls included) instead of node-by-node
-    // gathers; the nodes it shares with the tile before it are computed alike and stored by that
-    // tile only. The moved start stays a multiple of V (the vector loads stay aligned) when nx is.
-    if (xt + span > M.P.nx && M.P.nx > span && M.P.nx % V == 0) {
+    // The last tile of a row that would run past the row's end is moved left to end on the last
+    // multiple of V below nx (tail), so that its warps take the vector path (walls included)
+    // instead of node-by-node gathers; the nodes it shares with the tile before it are computed
+    // alike and stored by that tile only, and the nx % V nodes from tail on are updated node by
+    // node by the thread holding the tile's last vector. The moved start stays a multiple of V, so the vector loads stay aligned.
+    // A tile that would store no vector node (xt == tail) is not moved.
+    const int tail = M.P.nx - M.P.nx % V;
+    const bool moved = xt + span > M.P.nx && xt < tail && tail >= span;
+    if (moved) {
         keep = xt;
-        xt = M.P.nx - span;
+        xt = tail - span;
     }
     const int x0 = xt + threadIdx.x * V;
-    const int y = ty * blockDim.y + threadIdx.y;
-    if (y >= M.P.ny || x0 - lane * V >= M.P.nx) return;
-    step_warp_nodes<ST, V, false>((const E*)M.buf[parity], (E*)M.buf[parity ^ 1], M.P, x0, y, lane, keep);
+    if (x0 - lane * V >= M.P.nx) return;  // whole warps only
+    const E* src = (const E*)M.buf[parity];
+    E* dst = (E*)M.buf[parity ^ 1];
+    // The tile's rows: `groups` groups of blockDim.y rows, one group after another, so that the
+    // descriptor fetched above serves several rows per warp.
+    const int rows = blockDim.y * groups;
+    const int y_end = min(M.P.ny, (ty + 1) * rows);
+    for (int y = ty * rows + threadIdx.y; y < y_end; y += blockDim.y) {
+        step_warp_nodes<ST, V, false>(src, dst, M.P, x0, y, lane, keep);
+        if (moved && x0 + V == tail)
+            for (int x = tail; x < M.P.nx; ++x) {
+                A f[9], g[5];
+                gather(src, M.P, x, y, f, g);
+                collide_any<Storage<ST>::DEV>(M.P, f, g);
+                store_node(dst, M.P, x, y, f, g);
+            }
+    }
+}
+
+// Blocks of k_step_batched<ST, V> resident on the whole device at once.
+template <int ST, int V>
+long resident_blocks_of(int threads)
+{
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batched<ST, V>, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return (long)std::max(1, sms) * std::max(1, per_sm);
+}
+
+template <int ST>
+long resident_blocks_npt(int npt, int threads)
+{
+    return npt == 4 ? resident_blocks_of<ST, 4>(threads)
+                    : npt == 2 ? resident_blocks_of<ST, 2>(threads) : resident_blocks_of<ST, 1>(threads);
 }
 
 template <int ST>
@@ -165,6 +204,15 @@ Member<A> make_member(const Lattice& L, int tile_x, int npt, int tile_begin, int
 
 constexpr int kChunk = 32;  // steps per captured graph (even, so the buffers return)
 
+// Nodes a block of the batched step covers at most: each block first fetches its lattice's
+// descriptor (two dependent loads and a barrier), so a block that steps only one group of rows
+// spends a large part of its short life waiting on that fetch. On 256 uneven cavities (FP32,
+// 32 x 4 threads x 2 nodes) 1, 2, 4, 8 and 16 groups of rows per block gave 42.9, 46.9, 49.2,
+// 49.6 and 48.3 GLUPS. Fewer, longer blocks leave a longer tail at the end of the launch, so the
+// number of groups is also held where the launch still has kMinWaves rounds of resident blocks.
+constexpr int kBlockNodes = 2048;
+constexpr int kMinWaves = 8;
+
 // The set of resident lattices and the device tables of the batched launch.
 class Ensemble {
 public:
@@ -172,6 +220,7 @@ public:
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
     int tile_x = 128, tile_y = 1, npt = 1;
+    int groups = 1;  // row groups per block (kBlockNodes): a tile is (tile_x * npt) x (tile_y * groups) nodes
     int parity = 0;  // every resident lattice holds its current data in buf[parity]
     std::vector<Lattice*> members;  // launch order
 
@@ -203,6 +252,27 @@ public:
 
     void mark_dirty() { dirty = true; }
 
+    // Tiles of the active members when each block steps g groups of tile_y rows.
+    long tiles_with(int g) const
+    {
+        long t = 0;
+        for (const Lattice* L : active)
+            t += (long)((L->nx + tile_x * npt - 1) / (tile_x * npt)) * ((L->ny + tile_y * g - 1) / (tile_y * g));
+        return t;
+    }
+
+    // Groups of rows per block: doubled while a block covers at most kBlockNodes nodes and the
+    // launch keeps kMinWaves rounds of resident blocks.
+    void choose_groups()
+    {
+        const int threads = tile_x * tile_y;
+        const long resident = storage == CLB_F64 ? resident_blocks_npt<ST_F64>(npt, threads)
+                              : storage == CLB_F32 ? resident_blocks_npt<ST_F32>(npt, threads)
+                                                   : resident_blocks_npt<ST_F16DEV>(npt, threads);
+        groups = 1;
+        for (int g = 2; g * threads * npt <= kBlockNodes && tiles_with(g) >= kMinWaves * resident; g *= 2) groups = g;
+    }
+
     // Rebuild the tile and row tables for the active members.
     clb_status rebuild()
     {
@@ -214,13 +284,14 @@ public:
         active.clear();
         for (Lattice* L : members)
             if (L->active) active.push_back(L);
+        choose_groups();
         std::vector<int> owner, row_owner;
         const size_t msz = storage == CLB_F64 ? sizeof(Member<double>) : sizeof(Member<float>);
         std::vector<char> host(msz * std::max<size_t>(1, active.size()));
         int tiles = 0, rows = 0;
         for (size_t k = 0; k < active.size(); ++k) {
             const Lattice& L = *active[k];
-            const int tx = (L.nx + tile_x * npt - 1) / (tile_x * npt), ty = (L.ny + tile_y - 1) / tile_y;
+            const int tx = (L.nx + tile_x * npt - 1) / (tile_x * npt), ty = (L.ny + tile_y * groups - 1) / (tile_y * groups);
             if (storage == CLB_F64) {
                 Member<double> m = make_member<double>(L, tile_x, npt, tiles, rows);
                 std::memcpy(host.data() + k * msz, &m, msz);
@@ -261,9 +332,9 @@ public:
         using A = typename Storage<ST>::A;
         const dim3 block(tile_x, tile_y);
         const Member<A>* m = (const Member<A>*)d_members;
-        if (npt == 4) k_step_batched<ST, 4><<<ntiles, block, 0, s>>>(m, d_owner, par);
-        else if (npt == 2) k_step_batched<ST, 2><<<ntiles, block, 0, s>>>(m, d_owner, par);
-        else k_step_batched<ST, 1><<<ntiles, block, 0, s>>>(m, d_owner, par);
+        if (npt == 4) k_step_batched<ST, 4><<<ntiles, block, 0, s>>>(m, d_owner, par, groups);
+        else if (npt == 2) k_step_batched<ST, 2><<<ntiles, block, 0, s>>>(m, d_owner, par, groups);
+        else k_step_batched<ST, 1><<<ntiles, block, 0, s>>>(m, d_owner, par, groups);
     }
 
     clb_status launch_step(cudaStream_t s, int par)
@@ -685,6 +756,19 @@ extern "C" clb_status clb_batch_autotune(clb_batch* b, int* tile_x, int* tile_y,
     if (tile_x) *tile_x = bt[0];
     if (tile_y) *tile_y = bt[1];
     if (nodes_per_thread) *nodes_per_thread = bt[2];
+    return CLB_OK;
+}
+
+extern "C" clb_status clb_batch_get_launch(clb_batch* b, int* tile_x, int* tile_y, int* nodes_per_thread,
+                                           int* groups, long* blocks)
+{
+    if (!b) return set_error(CLB_EINVAL, "batch is NULL");
+    CLB_TRY(b->E.rebuild());
+    if (tile_x) *tile_x = b->E.tile_x;
+    if (tile_y) *tile_y = b->E.tile_y;
+    if (nodes_per_thread) *nodes_per_thread = b->E.npt;
+    if (groups) *groups = b->E.groups;
+    if (blocks) *blocks = b->E.ntiles;
     return CLB_OK;
 }
 

@@ -53,6 +53,49 @@ def test_tile_shape_does_not_change_results(clb, tile):
             assert np.array_equal(x, y)
 
 
+# Rows one to four tiles long, ending at every residue modulo V = 1, 2, 4 and modulo the tile width;
+# short lattices, and tall ones that take several tiles (of several groups of rows) along y.
+WIDE = [(nx, 5 + k % 3) for k, nx in enumerate([63, 64, 65, 66, 67, 97, 127, 128, 129, 130, 131, 133,
+                                                191, 193, 258])] + [(97, 70), (133, 33), (64, 129)]
+
+
+@pytest.mark.parametrize("storage", [F32, F16, F64])
+@pytest.mark.parametrize("tile", [(32, 4, 2), (32, 4, 4), (64, 2, 2), (32, 1, 1)])
+def test_rows_wider_than_a_tile_equal_single_lattice(clb, storage, tile):
+    """The last tile of a row that runs past the row's end is moved left to end on the last
+    multiple of V below nx, and the nx % V nodes after it are updated one by one; every node must
+    come out exactly as the single-lattice step computes it (walls on x, some of them moving)."""
+    probs = [W.random_problem(nx, ny, seed=1 + k % 3, storage=storage, moving=k % 2 == 1)
+             for k, (nx, ny) in enumerate(WIDE)]
+    b = clb.Batch(probs)
+    b.set_tile(*tile)
+    b.step(12)
+    for k, prob in enumerate(probs):
+        single = clb.Lattice.from_problem(prob)
+        single.step(12)
+        for x, y in zip(b.fields(k), single.fields()):
+            assert np.array_equal(x, y), (prob.name, tile)
+
+
+def test_row_groups_per_block_equal_single_lattice(clb):
+    """A batch large enough (3.7 M nodes) that each block steps several groups of rows, with odd and
+    even widths and walls on x: sampled instances equal the single-lattice step bitwise. A small
+    batch keeps one group per block (the launch keeps enough blocks to fill the device)."""
+    sizes = [(256 + 3 * (k % 5), 200 + 17 * (k % 7)) for k in range(56)]
+    probs = [W.random_problem(nx, ny, seed=1 + k % 3, storage=F32, moving=k % 2 == 1)
+             for k, (nx, ny) in enumerate(sizes)]
+    b = clb.Batch(probs)
+    launch = b.launch()
+    assert launch["tile"] == (32, 4, 2) and launch["groups"] >= 2, launch
+    b.step(6)
+    for k in (0, 1, 2, 3, 4, 9, 27, 55):
+        single = clb.Lattice.from_problem(probs[k])
+        single.step(6)
+        for x, y in zip(b.fields(k), single.fields()):
+            assert np.array_equal(x, y), probs[k].name
+    assert clb.Batch(probs[:2]).launch()["groups"] == 1
+
+
 def test_batch_autotune_keeps_state_and_results(clb):
     probs = mixed_problems(F32)
     ref = clb.Batch(probs)

@@ -247,6 +247,32 @@ def test_nusselt_and_residual_match_oracle(clb):
         assert er_gpu == pytest.approx(er_ref, rel=1e-9)
 
 
+@pytest.mark.parametrize("storage", [F32, F16])
+def test_reduced_precision_diagnostics_match_oracle(clb, storage):
+    """FP32 and FP16 storage: the node terms of the diagnostics are formed in FP32 (FP64 sums). E_R
+    of a random problem's first 100 steps and Nu of a Rayleigh-Benard cell agree with the FP64
+    oracle to the fields' precision, and a second pass gives the same Nu."""
+    prob = W.random_problem(300, 37, seed=5, storage=storage)
+    lat = clb.Lattice.from_problem(prob)
+    o = oracle.Oracle.from_problem(prob.with_storage(F64))
+    prev = o.fields()[1:]
+    lat.step(100)
+    o.step(100)
+    er_ref = oracle.residual(prev, o.fields()[1:], prob.params["u_ref"], prob.params["dT_ref"])
+    assert lat.residual() == pytest.approx(er_ref, rel=1e-2 if storage == F16 else 1e-4)
+
+    prob = W.rayleigh_benard(256, 128, Ra=1e5, storage=storage)
+    lat = clb.Lattice.from_problem(prob)
+    o = oracle.Oracle.from_problem(prob.with_storage(F64))
+    lat.step(100)
+    o.step(100)
+    cur = o.fields()
+    nu_ref = oracle.nusselt(cur[1], cur[2], cur[3], prob.params, prob.nu_axis)
+    nu_gpu = lat.nusselt(prob.nu_axis)
+    assert nu_gpu == pytest.approx(nu_ref, rel=2e-3 if storage == F16 else 1e-4)
+    assert lat.nusselt(prob.nu_axis) == nu_gpu
+
+
 def test_run_to_steady_conduction(clb):
     """clb_run stops at the residual tolerance; the steady state is the conduction line."""
     ny = 16

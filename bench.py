@@ -433,16 +433,19 @@ def thermal3d_run(steps: int, n: int = 256):
             "bytes_per_node": 68, "achieved_gbs": gbs, "hbm_frac": gbs / peak, "steps": steps, "storage": "f32"}
 
 
-def served_run(storage: int, count: int = 48, step_cap: int = 20000, tol: float = 1e-6):
+def served_run(storage: int, count: int = 48, step_cap: int = 20000, tol: float = 1e-6, hi: int = 512,
+               hbm_budget_gb: int = 32):
     """A seeded Poisson request trace (mean 50 requests/s; periodic Taylor-Green, side-heated
-    cavity and Rayleigh-Benard; edges log-uniform 64-512, aspect 1 or 2) served with continuous
+    cavity and Rayleigh-Benard; edges log-uniform 64-hi, aspect 1 or 2) served with continuous
     batching in `storage`, against the plain FP64 one-at-a-time path on the same trace."""
     from paper_1710_10569_gb300 import serve
-    trace = W.request_trace(count=count, seed=0, rate_hz=50.0, lo=64, hi=512, storage=storage)
-    s_sum, s_rec = serve.serve_trace(trace, storage, hbm_budget_bytes=32 << 30, max_slots=256,
+    trace = W.request_trace(count=count, seed=0, rate_hz=50.0, lo=64, hi=hi, storage=storage)
+    s_sum, s_rec = serve.serve_trace(trace, storage, hbm_budget_bytes=hbm_budget_gb << 30, max_slots=256,
                                      chunk=100, step_cap=step_cap, tol=tol)
     p_sum, p_rec = serve.plain_trace(trace, step_cap=step_cap, tol=tol)
-    return {"requests": count, "step_cap": step_cap, "tol": tol, "storage": W.STORAGE_NAMES[storage],
+    return {"requests": count, "edges": [64, hi], "step_cap": step_cap, "tol": tol,
+            "node_updates": float(sum(r["nodes"] * r["steps"] for r in s_rec)),
+            "storage": W.STORAGE_NAMES[storage],
             "served": s_sum, "plain_f64": p_sum,
             "speedup_solves_per_s": s_sum["solves_per_s"] / p_sum["solves_per_s"],
             "p99_ratio_plain_over_served": p_sum["p99_s"] / s_sum["p99_s"],
@@ -607,6 +610,9 @@ def main():
                     help="run only the 3-D workload (D3Q27 + D3Q7, 256 x 256 x 128) and print its JSON")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload (256 uneven cavities) and print its JSON")
+    ap.add_argument("--served-large", action="store_true",
+                    help="run only a served trace over the full edge range (32 requests, edges "
+                         "64-4096, cap 4,000 steps, tol 1e-8) against plain FP64, and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -617,6 +623,10 @@ def main():
         print(json.dumps(thermal_run(st, args.steps)), flush=True)
     elif args.three_d_only:
         print(json.dumps(three_d_run(args.steps)), flush=True)
+    elif args.served_large:
+        st = {"f64": W.STORAGE_F64, "f32": W.STORAGE_F32, "f16dev": W.STORAGE_F16DEV}[args.storage]
+        print(json.dumps(served_run(st, count=32, step_cap=4000, tol=1e-8, hi=4096, hbm_budget_gb=96)),
+              flush=True)
     elif args.batched_only:
         print(json.dumps(batched_run({"f64": W.STORAGE_F64, "f32": W.STORAGE_F32,
                                       "f16dev": W.STORAGE_F16DEV}[args.storage], steps=args.steps)), flush=True)

@@ -402,7 +402,61 @@ def three_d_run(steps: int, nx: int = 256, ny: int = 256, nz: int = 128):
     out["workload"] = f"rayleigh_benard3d_{nx}x{ny}x{nz}_Ra1e7_Pr0.71"
     out["kernel"] = "k_step3"
     out["thermal_only"] = thermal3d_run(steps)
+    out["batched"] = batched3d_run(steps)
     return out
+
+
+def batched3d_run(steps: int, count: int = 48, seq_subset: int = 12):
+    """A 3-D batch: 48 Rayleigh-Benard boxes with extents log-uniform in 24-128 (each axis drawn
+    separately), FP32, one k_step3_batched launch per step, against a seeded subset stepped one
+    lattice after another through single-lattice launches; CUDA events on the batch's stream."""
+    import torch
+    from paper_1710_10569_gb300 import clb
+    peak, _ = measured_peaks()
+    st = W.STORAGE_F32
+    probs = W.batch_boxes3d(count, seed=0, storage=st)
+
+    def timed(stream_handle, fn):
+        s = torch.cuda.ExternalStream(stream_handle) if stream_handle else torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def batch_time(ps):
+        b = clb.Batch3D(ps)
+        b.step(64)
+        dt = timed(b.stream, lambda: b.step(steps))
+        launch = b.launch()
+        b.close()
+        return dt, launch
+
+    nodes = sum(p.nodes for p in probs)
+    dt, launch = batch_time(probs)
+    sub = probs[:seq_subset]
+    sub_nodes = sum(p.nodes for p in sub)
+    dt_sub, _ = batch_time(sub)
+    lats = [clb.Lattice3D.from_problem(p) for p in sub]
+    for lat in lats:
+        lat.step(64)
+
+    def sequential():
+        for lat in lats:
+            lat.step(steps)
+
+    dt_seq = timed(lats[0].stream, sequential)
+    for lat in lats:
+        lat.close()
+    gbs = BYTES_PER_NODE_3D[st] * nodes * steps / dt / 1e9
+    return {"instances": count, "nodes": nodes, "steps": steps, "storage": W.STORAGE_NAMES[st],
+            "block": list(launch["block"]), "row_groups_per_block": launch["groups"],
+            "blocks_per_launch": launch["blocks"], "mlups": nodes * steps / dt / 1e6,
+            "achieved_gbs": gbs, "hbm_frac": gbs / peak,
+            "subset": {"instances": seq_subset, "batched_mlups": sub_nodes * steps / dt_sub / 1e6,
+                       "sequential_mlups": sub_nodes * steps / dt_seq / 1e6, "speedup": dt_seq / dt_sub}}
 
 
 def thermal3d_run(steps: int, n: int = 256):

@@ -136,6 +136,37 @@ clb_status clb3d_sync(clb3d_lattice* h);
 void* clb3d_stream(clb3d_lattice* h);
 clb_status clb3d_buffers(clb3d_lattice* h, void** current, long long* plane_elems, int* row_pitch);
 
+/* Batches: n independent lattices of different extents and parameters (all with the same storage)
+ * stepped together by one launch per time step over their concatenated tiles (replayed from CUDA
+ * graphs), each lattice computing exactly what it computes alone (bitwise the same). The paper
+ * has no counterpart; this is the 3-D form of the clb_batch_* interface of clb.h.
+ * Every lattice is an ordinary clb3d_lattice owned by the batch: clb3d_batch_lattice gives its
+ * handle for clb3d_fields, clb3d_populations, clb3d_nusselt, clb3d_residual and clb3d_save; its
+ * state changes only through clb3d_batch_init_fields and clb3d_batch_step (stepping, initialising
+ * or loading it through its own handle breaks the batch's bookkeeping of which buffer is current).
+ * Device memory: each lattice's own (clb3d_footprint), two small tables, and the graphs. */
+typedef struct clb3d_batch clb3d_batch;
+/* n >= 1 lattices nx[k] x ny[k] x nz[k] with parameters p[k]; CLB_EINVAL if any lattice is invalid
+ * or the storages differ. The populations are undefined until clb3d_batch_init_fields. */
+clb_status clb3d_batch_create(int n, const int* nx, const int* ny, const int* nz, const clb3d_params* p,
+                              void* stream, clb3d_batch** out);
+void clb3d_batch_destroy(clb3d_batch* b);
+/* The handle of lattice k (0 <= k < n), owned by the batch. */
+clb_status clb3d_batch_lattice(clb3d_batch* b, int k, clb3d_lattice** out);
+/* clb3d_init_fields for lattice k (steps since init restart at 0); synchronises. */
+clb_status clb3d_batch_init_fields(clb3d_batch* b, int k, const double* rho, const double* ux,
+                                   const double* uy, const double* uz, const double* T);
+/* n >= 0 time steps of every lattice, enqueued on the stream. */
+clb_status clb3d_batch_step(clb3d_batch* b, long n);
+/* Thread block of the batched step: block_x threads along x (a multiple of 32, <= 256) times block_y
+ * rows (block_x * block_y <= 256). Each block steps 1, 2, 4, ... groups of block_y rows one after
+ * another: as many as keep a block at 2048 nodes or fewer and the launch at 8 or more rounds of the
+ * blocks the device holds at once. Results do not depend on it. */
+clb_status clb3d_batch_set_tile(clb3d_batch* b, int block_x, int block_y);
+/* The thread block, groups of rows per block and blocks per launch of the batched step. */
+clb_status clb3d_batch_get_launch(clb3d_batch* b, int* block_x, int* block_y, int* groups,
+                                  long long* blocks);
+
 /* Thermal-only mode: the D3Q7 equation alone with a prescribed velocity field (the 3-D form of
  * the paper's Sec. 3.1 set-up, where only the temperature equation is solved for a given flow).
  * The same pull, face rules, collision and equilibrium as the coupled step's D3Q7 part; the flow

@@ -137,10 +137,17 @@ _SIGS = {
     "clb3d_sync": [_VP],
     "clb3d_stream": [_VP],
     "clb3d_buffers": [_VP, _P(_VP), _P(ctypes.c_longlong), _P(_I)],
+    "clb3d_batch_create": [_I, _P(_I), _P(_I), _P(_I), _P(clb3d_params), _VP, _P(_VP)],
+    "clb3d_batch_destroy": [_VP],
+    "clb3d_batch_lattice": [_VP, _I, _P(_VP)],
+    "clb3d_batch_init_fields": [_VP, _I, _D, _D, _D, _D, _D],
+    "clb3d_batch_step": [_VP, _L],
+    "clb3d_batch_set_tile": [_VP, _I, _I],
+    "clb3d_batch_get_launch": [_VP, _P(_I), _P(_I), _P(_I), _P(ctypes.c_longlong)],
 }
 _RESTYPES = {"clb_destroy": None, "clb_batch_destroy": None, "clb_serve_close": None,
              "clb_thermal_destroy": None, "clb3d_destroy": None, "clb3d_stream": _VP,
-             "clb3d_thermal_destroy": None,
+             "clb3d_thermal_destroy": None, "clb3d_batch_destroy": None,
              "clb_last_error": ctypes.c_char_p, "clb_version": ctypes.c_char_p, "clb_stream": _VP}
 
 _lock = threading.Lock()
@@ -655,6 +662,87 @@ class Lattice3D:
         _check(lib().clb3d_run(self._h, float(tol), int(max_steps), int(interval), ctypes.byref(st),
                                ctypes.byref(er)))
         return st.value, er.value
+
+
+class _Member3D(Lattice3D):
+    """A lattice owned by a Batch3D: read access through the single-lattice calls; its state changes
+    only through the batch."""
+
+    def __init__(self, batch, k: int, prob):
+        self.nx, self.ny, self.nz = prob.nx, prob.ny, prob.nz
+        self.params = dict(prob.params)
+        self.stream = batch.stream
+        h = _VP()
+        _check(lib().clb3d_batch_lattice(batch._h, int(k), ctypes.byref(h)))
+        self._h = h
+        self._batch = batch  # the batch owns and destroys the handle
+
+    def close(self):
+        self._h = None
+
+    def step(self, n: int = 1):
+        raise RuntimeError("a batch member is stepped by its batch (Batch3D.step)")
+
+    def init_fields(self, *a):
+        raise RuntimeError("a batch member is initialised by its batch (Batch3D.init_fields)")
+
+
+class Batch3D:
+    """Many 3-D lattices (clb3d_batch_*) stepped by one launch per time step. `member(k)` gives a
+    Lattice3D view of lattice k for fields, populations, Nusselt number and residual."""
+
+    def __init__(self, problems, stream=None):
+        L = lib()
+        self.problems = list(problems)
+        n = len(self.problems)
+        self.stream = _stream_handle(stream)
+        nx = (_I * n)(*[p.nx for p in self.problems])
+        ny = (_I * n)(*[p.ny for p in self.problems])
+        nz = (_I * n)(*[p.nz for p in self.problems])
+        ps = (clb3d_params * n)(*[params3(p.params) for p in self.problems])
+        h = _VP()
+        _check(L.clb3d_batch_create(n, nx, ny, nz, ps, self.stream, ctypes.byref(h)))
+        self._h = h
+        self.members = [_Member3D(self, k, p) for k, p in enumerate(self.problems)]
+        for k, p in enumerate(self.problems):
+            self.init_fields(k, *p.fields())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m.close()
+            lib().clb3d_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def member(self, k: int) -> Lattice3D:
+        return self.members[k]
+
+    def init_fields(self, k: int, rho, ux, uy, uz, T):
+        m = self.members[k]
+        arrs = [_host(np.broadcast_to(np.asarray(a, dtype=np.float64), m.shape), m.nodes)
+                for a in (rho, ux, uy, uz, T)]
+        _check(lib().clb3d_batch_init_fields(self._h, int(k), *[_dptr(a) for a in arrs]))
+
+    def step(self, n: int = 1):
+        _check(lib().clb3d_batch_step(self._h, int(n)))
+
+    def fields(self, k: int):
+        return self.members[k].fields()
+
+    def set_tile(self, block_x: int, block_y: int = 1):
+        _check(lib().clb3d_batch_set_tile(self._h, int(block_x), int(block_y)))
+
+    def launch(self) -> dict:
+        bx, by, groups, blocks = _I(), _I(), _I(), ctypes.c_longlong()
+        _check(lib().clb3d_batch_get_launch(self._h, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(groups),
+                                            ctypes.byref(blocks)))
+        return dict(block=(bx.value, by.value), groups=groups.value, blocks=blocks.value)
 
 
 class Thermal3D:

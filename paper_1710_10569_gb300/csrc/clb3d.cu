@@ -26,6 +26,8 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
+#include <cstddef>
 
 #include "../../include/clb3d.h"
 #include "clb_core.cuh"
@@ -408,19 +410,13 @@ __device__ __forceinline__ void store3(T* __restrict__ dst, const Lat3<A>& P, in
     for (int j = 0; j < NG; ++j) dst[(NF + j) * pl + here] = from_a(g[j], (T*)nullptr);
 }
 
-// One time step: thread (tx, ty) of block b updates node x = (b % xblocks) * blockDim.x + tx of
-// row r = (b / xblocks) * blockDim.y + ty, row r being (y, z) = (r % ny, r / ny).
-template <int ST, bool HIGH1>
-__global__ void __launch_bounds__(256) k_step3(const typename Storage<ST>::T* __restrict__ src,
-                                               typename Storage<ST>::T* __restrict__ dst,
-                                               const Lat3<typename Storage<ST>::A> P, int xblocks)
+// One node's time step: pull (with the face rules where the node touches a wall face), collision,
+// store into the other buffer.
+template <int ST, bool HIGH1, typename A>
+__device__ __forceinline__ void step3_node(const typename Storage<ST>::T* __restrict__ src,
+                                           typename Storage<ST>::T* __restrict__ dst, const Lat3<A>& P,
+                                           int x, int y, int z)
 {
-    using A = typename Storage<ST>::A;
-    const int xb = blockIdx.x % xblocks, rb = blockIdx.x / xblocks;
-    const int x = xb * blockDim.x + threadIdx.x;
-    const int r = rb * blockDim.y + threadIdx.y;
-    if (x >= P.nx || r >= P.ny * P.nz) return;
-    const int y = r % P.ny, z = r / P.ny;
     A f[NF], g[NG];
     const bool nowall = (P.per[0] || (x > 0 && x < P.nx - 1)) && (P.per[1] || (y > 0 && y < P.ny - 1)) &&
                         (P.per[2] || (z > 0 && z < P.nz - 1));
@@ -428,6 +424,69 @@ __global__ void __launch_bounds__(256) k_step3(const typename Storage<ST>::T* __
     else gather3(src, P, x, y, z, f, g);
     collide3<Storage<ST>::DEV, HIGH1>(P, f, g);
     store3(dst, P, (z * P.ny + y) * P.pitch + x, f, g);
+}
+
+// One time step: thread (tx, ty) of block b updates node x = (b % xblocks) * blockDim.x + tx of
+// row r = (b / xblocks) * blockDim.y + ty, row r being (y, z) = (r % ny, r / ny).
+template <int ST, bool HIGH1>
+__global__ void __launch_bounds__(256) k_step3(const typename Storage<ST>::T* __restrict__ src,
+                                               typename Storage<ST>::T* __restrict__ dst,
+                                               const Lat3<typename Storage<ST>::A> P, int xblocks)
+{
+    const int xb = blockIdx.x % xblocks, rb = blockIdx.x / xblocks;
+    const int x = xb * blockDim.x + threadIdx.x;
+    const int r = rb * blockDim.y + threadIdx.y;
+    if (x >= P.nx || r >= P.ny * P.nz) return;
+    step3_node<ST, HIGH1>(src, dst, P, x, r % P.ny, r / P.ny);
+}
+
+// A lattice of a 3-D batch as the blocks of the batched step see it (each block copies it to
+// shared memory).
+template <typename A>
+struct Member3 {
+    Lat3<A> P;
+    void* buf[2];
+    int xblocks;     // blocks along x
+    int tile_begin;  // the lattice's first block
+    int flip;        // the lattice's current state is in buf[parity ^ flip]
+    int high1;       // s_3 = s_4 = s_5 = s_6 = 1: the collision form that skips those moments
+};
+
+// One time step of every lattice of a batch: block b covers tile t = b - tile_begin of lattice
+// owner[b], nodes x = (t % xblocks) * blockDim.x + tx of rows (y, z) = (r % ny, r / ny) for
+// r = (t / xblocks) * blockDim.y * groups + ty + k blockDim.y, k < groups. The per-node update is
+// step3_node, the single-lattice step's. Register cap: the lattice's parameters come from shared
+// memory rather than the constant bank, and uncapped the FP32 form takes 128 registers (two
+// 256-thread blocks per SM); at 64 it keeps the single-lattice step's four blocks (4 bytes of
+// spills), the FP16 form three at 80. FP64 is bound by its arithmetic and takes what it needs.
+template <int ST>
+__global__ void __maxnreg__(ST == ST_F32 ? 64 : ST == ST_F16DEV ? 80 : 255) k_step3_batched(const Member3<typename Storage<ST>::A>* __restrict__ mem,
+                                                       const int* __restrict__ owner, int parity, int groups)
+{
+    using A = typename Storage<ST>::A;
+    using T = typename Storage<ST>::T;
+    __shared__ Member3<A> M;
+    {
+        static_assert(sizeof(Member3<A>) % 4 == 0, "member size");
+        const int* s = reinterpret_cast<const int*>(mem + owner[blockIdx.x]);
+        int* d = reinterpret_cast<int*>(&M);
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        for (int w = tid; w < (int)(sizeof(Member3<A>) / 4); w += blockDim.x * blockDim.y) d[w] = s[w];
+        __syncthreads();
+    }
+    const int t = blockIdx.x - M.tile_begin;
+    const int xb = t % M.xblocks, rb = t / M.xblocks;
+    const int x = xb * blockDim.x + threadIdx.x;
+    if (x >= M.P.nx) return;
+    const int rows = blockDim.y * groups;
+    const int r_end = min(M.P.ny * M.P.nz, (rb + 1) * rows);
+    const int cur = parity ^ M.flip;
+    const T* src = (const T*)M.buf[cur];
+    T* dst = (T*)M.buf[cur ^ 1];
+    for (int r = rb * rows + threadIdx.y; r < r_end; r += blockDim.y) {
+        if (M.high1) step3_node<ST, true>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
+        else step3_node<ST, false>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
+    }
 }
 
 // The D3Q7 populations of node (x, y, z) written into the slots the next pull reads (planes base ..
@@ -1344,6 +1403,282 @@ extern "C" clb_status clb3d_buffers(clb3d_lattice* h, void** current, long long*
     if (current) *current = h->buf[h->cur];
     if (plane_elems) *plane_elems = h->plane;
     if (row_pitch) *row_pitch = h->pitch;
+    return CLB_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batches of 3-D lattices: every lattice is an ordinary handle (its own memory, fields, Nusselt
+// number, residual); the time steps of all of them go through one k_step3_batched launch per step
+// over their concatenated tiles, replayed from CUDA graphs of kChunk steps.
+
+struct clb3d_batch {
+    int storage = CLB_F64;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only to capture graphs
+    std::vector<clb3d_lattice*> lat;
+    std::vector<int> flip;       // lattice k's current state is in buf[parity ^ flip[k]]
+    std::vector<char> host_members;
+    void* d_members = nullptr;
+    int* d_owner = nullptr;
+    long long ntiles = 0;
+    int bx = 128, by = 2, groups = 1;
+    int parity = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+// Nodes a block of the batched 3-D step covers at most, and the rounds of resident blocks a
+// launch keeps at least (fewer groups of rows per block where the batch is small): the same
+// policy as the 2-D batch.
+constexpr int kBlockNodes3 = 2048;
+constexpr int kMinWaves3 = 8;
+
+template <int ST>
+long long resident_blocks3(int threads)
+{
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step3_batched<ST>, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return (long long)std::max(1, sms) * std::max(1, per_sm);
+}
+
+long long batch3_tiles(const clb3d_batch* b, int g)
+{
+    long long t = 0;
+    for (const clb3d_lattice* h : b->lat)
+        t += (long long)((h->nx + b->bx - 1) / b->bx) *
+             (((long long)h->ny * h->nz + (long long)b->by * g - 1) / ((long long)b->by * g));
+    return t;
+}
+
+void drop_batch3_graphs(clb3d_batch* b)
+{
+    for (auto& g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+template <typename A>
+Member3<A> member3(const clb3d_batch* b, const clb3d_lattice* h, int flip, int tile_begin, const Lat3<A>& P)
+{
+    Member3<A> m;
+    std::memset(&m, 0, sizeof(m));
+    m.P = P;
+    m.buf[0] = h->buf[0];
+    m.buf[1] = h->buf[1];
+    m.xblocks = (h->nx + b->bx - 1) / b->bx;
+    m.tile_begin = tile_begin;
+    m.flip = flip;
+    m.high1 = h->p.s_3 == 1.0 && h->p.s_4 == 1.0 && h->p.s_5 == 1.0 && h->p.s_6 == 1.0;
+    return m;
+}
+
+// Groups of rows per block and the member and owner tables for the current tile shape; uploads
+// them and synchronises the stream.
+clb_status batch3_tables(clb3d_batch* b)
+{
+    drop_batch3_graphs(b);
+    const int threads = b->bx * b->by;
+    const long long resident = b->storage == CLB_F64   ? resident_blocks3<ST_F64>(threads)
+                               : b->storage == CLB_F32 ? resident_blocks3<ST_F32>(threads)
+                                                       : resident_blocks3<ST_F16DEV>(threads);
+    b->groups = 1;
+    for (int g = 2; g * threads <= kBlockNodes3 && batch3_tiles(b, g) >= kMinWaves3 * resident; g *= 2) b->groups = g;
+    const long long tiles = batch3_tiles(b, b->groups);
+    if (tiles > 0x7fffffffLL) return set_error(CLB_EINVAL, "batch of %lld blocks per step is too large", tiles);
+    const size_t msz = b->storage == CLB_F64 ? sizeof(Member3<double>) : sizeof(Member3<float>);
+    b->host_members.assign(msz * b->lat.size(), 0);
+    std::vector<int> owner((size_t)tiles);
+    long long t0 = 0;
+    for (size_t k = 0; k < b->lat.size(); ++k) {
+        const clb3d_lattice* h = b->lat[k];
+        if (b->storage == CLB_F64) {
+            const Member3<double> m = member3<double>(b, h, b->flip[k], (int)t0, h->Pd);
+            std::memcpy(b->host_members.data() + k * msz, &m, msz);
+        } else {
+            const Member3<float> m = member3<float>(b, h, b->flip[k], (int)t0, h->Pf);
+            std::memcpy(b->host_members.data() + k * msz, &m, msz);
+        }
+        const long long n = (long long)((h->nx + b->bx - 1) / b->bx) *
+                            (((long long)h->ny * h->nz + (long long)b->by * b->groups - 1) / ((long long)b->by * b->groups));
+        std::fill(owner.begin() + t0, owner.begin() + t0 + n, (int)k);
+        t0 += n;
+    }
+    cudaFree(b->d_members);
+    cudaFree(b->d_owner);
+    b->d_members = nullptr;
+    b->d_owner = nullptr;
+    CLB_CUDA(cudaMalloc(&b->d_members, b->host_members.size()));
+    CLB_CUDA(cudaMalloc((void**)&b->d_owner, std::max<size_t>(1, owner.size()) * sizeof(int)));
+    CLB_CUDA(cudaMemcpyAsync(b->d_members, b->host_members.data(), b->host_members.size(), cudaMemcpyHostToDevice, b->stream));
+    CLB_CUDA(cudaMemcpyAsync(b->d_owner, owner.data(), owner.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    CLB_CUDA(cudaStreamSynchronize(b->stream));  // the host vectors are reused or die
+    b->ntiles = tiles;
+    return CLB_OK;
+}
+
+clb_status batch3_launch(clb3d_batch* b, int par, cudaStream_t s)
+{
+    if (b->ntiles == 0) return CLB_OK;
+    const dim3 block(b->bx, b->by);
+    const unsigned grid = (unsigned)b->ntiles;
+    if (b->storage == CLB_F64)
+        k_step3_batched<ST_F64><<<grid, block, 0, s>>>((const Member3<double>*)b->d_members, b->d_owner, par, b->groups);
+    else if (b->storage == CLB_F32)
+        k_step3_batched<ST_F32><<<grid, block, 0, s>>>((const Member3<float>*)b->d_members, b->d_owner, par, b->groups);
+    else
+        k_step3_batched<ST_F16DEV><<<grid, block, 0, s>>>((const Member3<float>*)b->d_members, b->d_owner, par, b->groups);
+    CLB_CUDA(cudaGetLastError());
+    return CLB_OK;
+}
+
+clb_status batch3_graph(clb3d_batch* b, int start)
+{
+    CLB_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    clb_status st = CLB_OK;
+    for (int k = 0; k < kChunk && st == CLB_OK; ++k) st = batch3_launch(b, start ^ (k & 1), b->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (st != CLB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return set_error(CLB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&b->graph[start], g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return set_error(CLB_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+    return CLB_OK;
+}
+
+#define CHECK_B3(b) \
+    if (!(b)) return set_error(CLB_EINVAL, "batch handle is NULL")
+#define CHECK_K3(b, k) \
+    if ((k) < 0 || (k) >= (int)(b)->lat.size()) return set_error(CLB_EINVAL, "lattice %d of a batch of %zu", (k), (b)->lat.size())
+
+}  // namespace
+
+extern "C" clb_status clb3d_batch_create(int n, const int* nx, const int* ny, const int* nz, const clb3d_params* p,
+                                         void* stream, clb3d_batch** out)
+{
+    if (!out) return set_error(CLB_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    if (n < 1 || !nx || !ny || !nz || !p) return set_error(CLB_EINVAL, "a batch needs n >= 1 lattices and their extents and parameters");
+    for (int k = 0; k < n; ++k) {
+        CLB_TRY(validate3(nx[k], ny[k], nz[k], &p[k]));
+        if (p[k].storage != p[0].storage)
+            return set_error(CLB_EINVAL, "lattice %d: every lattice of a batch has the same storage", k);
+    }
+    clb3d_batch* b = new (std::nothrow) clb3d_batch();
+    if (!b) return set_error(CLB_ENOMEM, "host allocation failed");
+    b->storage = p[0].storage;
+    b->stream = (cudaStream_t)stream;
+    clb_status st = CLB_OK;
+    for (int k = 0; k < n && st == CLB_OK; ++k) {
+        clb3d_lattice* h = nullptr;
+        st = clb3d_create(nx[k], ny[k], nz[k], &p[k], stream, &h);
+        if (st == CLB_OK) {
+            b->lat.push_back(h);
+            b->flip.push_back(0);
+        }
+    }
+    if (st == CLB_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+        st = set_error(CLB_ECUDA, "batch set-up: %s", cudaGetErrorString(cudaGetLastError()));
+    if (st == CLB_OK) st = batch3_tables(b);
+    if (st != CLB_OK) {
+        clb3d_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return CLB_OK;
+}
+
+extern "C" void clb3d_batch_destroy(clb3d_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    drop_batch3_graphs(b);
+    for (clb3d_lattice* h : b->lat) clb3d_destroy(h);
+    cudaFree(b->d_members);
+    cudaFree(b->d_owner);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+extern "C" clb_status clb3d_batch_lattice(clb3d_batch* b, int k, clb3d_lattice** out)
+{
+    CHECK_B3(b);
+    CHECK_K3(b, k);
+    if (!out) return set_error(CLB_EINVAL, "out must not be NULL");
+    *out = b->lat[k];
+    return CLB_OK;
+}
+
+extern "C" clb_status clb3d_batch_init_fields(clb3d_batch* b, int k, const double* rho, const double* ux,
+                                              const double* uy, const double* uz, const double* T)
+{
+    CHECK_B3(b);
+    CHECK_K3(b, k);
+    const clb_status st = clb3d_init_fields(b->lat[k], rho, ux, uy, uz, T);
+    if (st != CLB_OK && st != CLB_ENAN) return st;
+    // the lattice's state is now in buf[0]: buf[parity ^ flip] with flip = parity
+    b->flip[k] = b->parity;
+    const size_t msz = b->storage == CLB_F64 ? sizeof(Member3<double>) : sizeof(Member3<float>);
+    const size_t off = msz * k + (b->storage == CLB_F64 ? offsetof(Member3<double>, flip) : offsetof(Member3<float>, flip));
+    std::memcpy(b->host_members.data() + off, &b->flip[k], sizeof(int));
+    CLB_CUDA(cudaMemcpyAsync((char*)b->d_members + off, b->host_members.data() + off, sizeof(int),
+                             cudaMemcpyHostToDevice, b->stream));
+    CLB_CUDA(cudaStreamSynchronize(b->stream));
+    return st;
+}
+
+extern "C" clb_status clb3d_batch_step(clb3d_batch* b, long n)
+{
+    CHECK_B3(b);
+    if (n < 0) return set_error(CLB_EINVAL, "n = %ld < 0", n);
+    const long total = n;
+    while (n >= kChunk) {
+        if (!b->graph[b->parity]) CLB_TRY(batch3_graph(b, b->parity));
+        CLB_CUDA(cudaGraphLaunch(b->graph[b->parity], b->stream));
+        n -= kChunk;
+    }
+    for (; n > 0; --n) {
+        CLB_TRY(batch3_launch(b, b->parity, b->stream));
+        b->parity ^= 1;
+    }
+    for (size_t k = 0; k < b->lat.size(); ++k) {
+        b->lat[k]->cur = b->parity ^ b->flip[k];
+        b->lat[k]->steps += total;
+    }
+    return CLB_OK;
+}
+
+extern "C" clb_status clb3d_batch_set_tile(clb3d_batch* b, int block_x, int block_y)
+{
+    CHECK_B3(b);
+    if (block_x < 32 || block_x > 256 || block_x % 32 || block_y < 1 || block_x * block_y > 256)
+        return set_error(CLB_EINVAL, "tile %d x %d: block_x in [32, 256] multiple of 32, block_x * block_y <= 256",
+                         block_x, block_y);
+    CLB_CUDA(cudaStreamSynchronize(b->stream));
+    b->bx = block_x;
+    b->by = block_y;
+    return batch3_tables(b);
+}
+
+extern "C" clb_status clb3d_batch_get_launch(clb3d_batch* b, int* block_x, int* block_y, int* groups,
+                                             long long* blocks)
+{
+    CHECK_B3(b);
+    if (block_x) *block_x = b->bx;
+    if (block_y) *block_y = b->by;
+    if (groups) *groups = b->groups;
+    if (blocks) *blocks = b->ntiles;
     return CLB_OK;
 }
 

@@ -360,6 +360,28 @@ def rayleigh_benard3d(nx: int, ny: int, nz: int, Ra: float, Pr: float = 0.71, u_
                      meta=dict(Ra=Ra, Pr=Pr, u_c=u_c, seed=seed))
 
 
+def batch_boxes3d(count: int = 48, seed: int = 0, lo: int = 24, hi: int = 128,
+                  Ra_range=(1e3, 1e6), Pr_range=(0.71, 7.0), u_c: float = 0.1,
+                  nu_cap: float = 0.1, storage=STORAGE_F32) -> list[Problem3D]:
+    """Independent Rayleigh-Benard boxes for the 3-D batch: each extent log-uniform in [lo, hi]
+    (drawn separately), Ra log-uniform, Pr uniform; u_c is lowered where needed so that
+    nu <= nu_cap."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        nx, ny, nz = (int(round(math.exp(rng.uniform(math.log(lo), math.log(hi))))) for _ in range(3))
+        Ra = math.exp(rng.uniform(math.log(Ra_range[0]), math.log(Ra_range[1])))
+        Pr = float(rng.uniform(*Pr_range))
+        uc = u_c
+        nu = uc * nz * math.sqrt(Pr / Ra)
+        if nu > nu_cap:
+            uc *= nu_cap / nu
+        prob = rayleigh_benard3d(nx, ny, nz, Ra=Ra, Pr=Pr, u_c=uc, seed=seed * 100003 + k, storage=storage)
+        prob.name = f"box{k}_" + prob.name
+        out.append(prob)
+    return out
+
+
 def taylor_green3d(n: int = 32, U: float = 0.01, nu: float = 0.02, kappa: float = 0.02,
                    T_amp: float = 0.01, noise: float = 1e-4, seed: int = 0,
                    storage=STORAGE_F64) -> Problem3D:

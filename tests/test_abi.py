@@ -146,3 +146,19 @@ def test_3d_largest_lattice_in_32_bit_offsets(clb):
     in FP32 (34 planes of 63.1 M elements) is accepted, one more layer is refused."""
     assert footprint3(clb, 384, 384, 428, storage=W.STORAGE_F32)[0] == clb.CLB_OK
     assert footprint3(clb, 384, 384, 429, storage=W.STORAGE_F32)[0] == clb.CLB_EINVAL
+
+
+def test_3d_batch_invalid_arguments_are_rejected(clb):
+    """clb3d_batch_create checks its arguments before touching the device: no lattices, a bad
+    lattice, or storages that differ."""
+    L = clb.lib()
+    out = ctypes.c_void_p()
+    n3 = (ctypes.c_int * 2)(8, 8)
+    good = clb.params3(W.default_params3(storage=W.STORAGE_F32))
+    other = clb.params3(W.default_params3(storage=W.STORAGE_F64))
+    bad = clb.params3(W.default_params3(nu=0.0, storage=W.STORAGE_F32))
+    assert L.clb3d_batch_create(0, n3, n3, n3, ctypes.byref(good), None, ctypes.byref(out)) == clb.CLB_EINVAL
+    for second in (other, bad):
+        ps = (clb.clb3d_params * 2)(good, second)
+        assert L.clb3d_batch_create(2, n3, n3, n3, ps, None, ctypes.byref(out)) == clb.CLB_EINVAL
+        assert not out.value

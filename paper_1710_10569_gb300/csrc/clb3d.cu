@@ -477,15 +477,28 @@ __global__ void __maxnreg__(ST == ST_F32 ? 64 : ST == ST_F16DEV ? 80 : 255) k_st
     const int t = blockIdx.x - M.tile_begin;
     const int xb = t % M.xblocks, rb = t / M.xblocks;
     const int x = xb * blockDim.x + threadIdx.x;
-    if (x >= M.P.nx) return;
+    // Threads just past a row's end fill the rest of its last 32-byte sector (row padding, never
+    // read) so that every sector of the row is written whole: a partly written sector is read back
+    // from DRAM when it is written out, and the rows of small lattices end mid-sector.
+    constexpr int kSector = 32 / (int)sizeof(T);
+    const int x_pad = min(M.P.pitch, (M.P.nx + kSector - 1) / kSector * kSector);
+    if (x >= x_pad) return;
     const int rows = blockDim.y * groups;
     const int r_end = min(M.P.ny * M.P.nz, (rb + 1) * rows);
     const int cur = parity ^ M.flip;
     const T* src = (const T*)M.buf[cur];
     T* dst = (T*)M.buf[cur ^ 1];
     for (int r = rb * rows + threadIdx.y; r < r_end; r += blockDim.y) {
-        if (M.high1) step3_node<ST, true>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
-        else step3_node<ST, false>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
+        if (x >= M.P.nx) {
+            const T zero = from_a(A(0), (T*)nullptr);
+            const int here = r * M.P.pitch + x;  // row r = (y, z) with r = z * ny + y
+#pragma unroll
+            for (int i = 0; i < NF + NG; ++i) dst[i * (int)M.P.plane + here] = zero;
+        } else if (M.high1) {
+            step3_node<ST, true>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
+        } else {
+            step3_node<ST, false>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
+        }
     }
 }
 

@@ -477,28 +477,15 @@ __global__ void __maxnreg__(ST == ST_F32 ? 64 : ST == ST_F16DEV ? 80 : 255) k_st
     const int t = blockIdx.x - M.tile_begin;
     const int xb = t % M.xblocks, rb = t / M.xblocks;
     const int x = xb * blockDim.x + threadIdx.x;
-    // Threads just past a row's end fill the rest of its last 32-byte sector (row padding, never
-    // read) so that every sector of the row is written whole: a partly written sector is read back
-    // from DRAM when it is written out, and the rows of small lattices end mid-sector.
-    constexpr int kSector = 32 / (int)sizeof(T);
-    const int x_pad = min(M.P.pitch, (M.P.nx + kSector - 1) / kSector * kSector);
-    if (x >= x_pad) return;
+    if (x >= M.P.nx) return;
     const int rows = blockDim.y * groups;
     const int r_end = min(M.P.ny * M.P.nz, (rb + 1) * rows);
     const int cur = parity ^ M.flip;
     const T* src = (const T*)M.buf[cur];
     T* dst = (T*)M.buf[cur ^ 1];
     for (int r = rb * rows + threadIdx.y; r < r_end; r += blockDim.y) {
-        if (x >= M.P.nx) {
-            const T zero = from_a(A(0), (T*)nullptr);
-            const int here = r * M.P.pitch + x;  // row r = (y, z) with r = z * ny + y
-#pragma unroll
-            for (int i = 0; i < NF + NG; ++i) dst[i * (int)M.P.plane + here] = zero;
-        } else if (M.high1) {
-            step3_node<ST, true>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
-        } else {
-            step3_node<ST, false>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
-        }
+        if (M.high1) step3_node<ST, true>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
+        else step3_node<ST, false>(src, dst, M.P, x, r % M.P.ny, r / M.P.ny);
     }
 }
 
@@ -885,10 +872,15 @@ long long nodes_of(const clb3d_lattice* h) { return (long long)h->nx * h->ny * h
 
 size_t esize(int storage) { return storage == CLB_F64 ? 8 : storage == CLB_F32 ? 4 : 2; }
 
+// Row pitch: rows follow one another without padding (each node is one thread and no access is
+// vectorised, so rows need no alignment). A padded row would end mid-sector: the pulls would read
+// its padding, and a sector written in part is read back from DRAM when it is written out; for
+// short rows (small lattices, batches) that cost a quarter of the read traffic. Planes start on
+// 256-byte boundaries.
 int pitch3(int nx, int storage)
 {
-    const int per = int(128 / esize(storage));
-    return (nx + per - 1) / per * per;
+    (void)storage;
+    return nx;
 }
 
 long long plane3(int nx, int ny, int nz, int storage)

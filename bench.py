@@ -75,6 +75,16 @@ def profile_counts():
     return d if d.get("kernel_source_hash") == kernel_hash() else {}
 
 
+def flops_per_node():
+    """Floating-point operations per node update (an FMA counted as two), from the FP64 step's
+    committed ncu instruction counts (the FP32 and FP16 forms evaluate the same expressions), if
+    they were taken on the current kernel source (else None)."""
+    ops = profile_counts().get("fp64_ops_per_node")
+    if not ops:
+        return None
+    return 2 * ops["dfma"] + ops["dadd"] + ops["dmul"]
+
+
 def traffic_per_launch(storage: int, nx: int, ny: int):
     """DRAM bytes per step-kernel launch on an nx x ny lattice from the committed ncu summary, if
     it was taken on the current kernel source and that lattice (else None)."""
@@ -594,6 +604,7 @@ def run_ours(args):
                          "kernel_us_per_launch": per_launch_s * 1e6,
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "kernel": f"k_step<{W.STORAGE_NAMES[storage]}>",
+                         "flops_per_node": flops_per_node(),
                          "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
             "cpu_baseline": cpu,
             "e2e": e2e,

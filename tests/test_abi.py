@@ -162,3 +162,18 @@ def test_3d_batch_invalid_arguments_are_rejected(clb):
         ps = (clb.clb3d_params * 2)(good, second)
         assert L.clb3d_batch_create(2, n3, n3, n3, ps, None, ctypes.byref(out)) == clb.CLB_EINVAL
         assert not out.value
+
+
+@pytest.mark.parametrize("header", ["clb.h", "clb3d.h"])
+def test_headers_are_plain_c(header):
+    """The ABI headers compile as C99 (no C++ in the declarations a C caller sees)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    path = os.path.join(os.path.dirname(__file__), "..", "include", header)
+    r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Werror", "-x", "c", "-std=c99", path],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

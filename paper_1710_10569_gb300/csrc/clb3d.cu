@@ -1585,17 +1585,23 @@ extern "C" clb_status clb3d_batch_create(int n, const int* nx, const int* ny, co
     b->storage = p[0].storage;
     b->stream = (cudaStream_t)stream;
     clb_status st = CLB_OK;
-    for (int k = 0; k < n && st == CLB_OK; ++k) {
-        clb3d_lattice* h = nullptr;
-        st = clb3d_create(nx[k], ny[k], nz[k], &p[k], stream, &h);
-        if (st == CLB_OK) {
-            b->lat.push_back(h);
-            b->flip.push_back(0);
+    try {
+        b->lat.reserve(n);
+        b->flip.reserve(n);
+        for (int k = 0; k < n && st == CLB_OK; ++k) {
+            clb3d_lattice* h = nullptr;
+            st = clb3d_create(nx[k], ny[k], nz[k], &p[k], stream, &h);
+            if (st == CLB_OK) {
+                b->lat.push_back(h);
+                b->flip.push_back(0);
+            }
         }
+        if (st == CLB_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+            st = set_error(CLB_ECUDA, "batch set-up: %s", cudaGetErrorString(cudaGetLastError()));
+        if (st == CLB_OK) st = batch3_tables(b);
+    } catch (const std::bad_alloc&) {
+        st = set_error(CLB_ENOMEM, "host allocation failed");
     }
-    if (st == CLB_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
-        st = set_error(CLB_ECUDA, "batch set-up: %s", cudaGetErrorString(cudaGetLastError()));
-    if (st == CLB_OK) st = batch3_tables(b);
     if (st != CLB_OK) {
         clb3d_batch_destroy(b);
         return st;
@@ -1673,7 +1679,11 @@ extern "C" clb_status clb3d_batch_set_tile(clb3d_batch* b, int block_x, int bloc
     CLB_CUDA(cudaStreamSynchronize(b->stream));
     b->bx = block_x;
     b->by = block_y;
-    return batch3_tables(b);
+    try {
+        return batch3_tables(b);
+    } catch (const std::bad_alloc&) {
+        return set_error(CLB_ENOMEM, "host allocation failed");
+    }
 }
 
 extern "C" clb_status clb3d_batch_get_launch(clb3d_batch* b, int* block_x, int* block_y, int* groups,

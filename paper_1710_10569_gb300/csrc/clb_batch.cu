@@ -521,40 +521,44 @@ struct clb_batch {
 extern "C" clb_status clb_batch_create(int n, const int* nx, const int* ny, const clb_params* p,
                                        void* stream, clb_batch** out)
 {
-    if (!out) return set_error(CLB_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (n <= 0 || !nx || !ny || !p) return set_error(CLB_EINVAL, "need n > 0 and nx, ny, p arrays");
-    const int storage = p[0].storage;
-    size_t total = 0, max_nodes = 0;
-    for (int k = 0; k < n; ++k) {
-        CLB_TRY(validate(nx[k], ny[k], &p[k]));
-        if (p[k].storage != storage) return set_error(CLB_EINVAL, "instance %d: all instances need the same storage", k);
-        total += lattice_bytes(nx[k], ny[k], storage);
-        max_nodes = std::max(max_nodes, (size_t)nx[k] * ny[k]);
+    try {
+        if (!out) return set_error(CLB_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (n <= 0 || !nx || !ny || !p) return set_error(CLB_EINVAL, "need n > 0 and nx, ny, p arrays");
+        const int storage = p[0].storage;
+        size_t total = 0, max_nodes = 0;
+        for (int k = 0; k < n; ++k) {
+            CLB_TRY(validate(nx[k], ny[k], &p[k]));
+            if (p[k].storage != storage) return set_error(CLB_EINVAL, "instance %d: all instances need the same storage", k);
+            total += lattice_bytes(nx[k], ny[k], storage);
+            max_nodes = std::max(max_nodes, (size_t)nx[k] * ny[k]);
+        }
+        auto b = std::make_unique<clb_batch>();
+        cudaGetDevice(&b->device);
+        CLB_TRY(b->E.init(storage, (cudaStream_t)stream));
+        const size_t stage_bytes = align256(4 * max_nodes * sizeof(double));
+        CLB_CUDA(cudaMalloc((void**)&b->mem, total + stage_bytes));
+        b->stage = (double*)(b->mem + total);
+        CLB_CUDA(cudaMemsetAsync(b->mem, 0, total, b->E.stream));
+        size_t off = 0;
+        for (int k = 0; k < n; ++k) {
+            auto L = std::make_unique<Lattice>();
+            L->nx = nx[k];
+            L->ny = ny[k];
+            L->p = p[k];
+            L->axis = p[k].wall[0] != CLB_PERIODIC ? 0 : 1;
+            carve(*L, b->mem + off);
+            off += lattice_bytes(nx[k], ny[k], storage);
+            CLB_TRY(b->E.init_member(L.get(), nullptr, nullptr, nullptr, nullptr));
+            b->E.members.push_back(L.get());
+            b->lat.push_back(std::move(L));
+        }
+        CLB_CUDA(cudaStreamSynchronize(b->E.stream));
+        *out = b.release();
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    auto b = std::make_unique<clb_batch>();
-    cudaGetDevice(&b->device);
-    CLB_TRY(b->E.init(storage, (cudaStream_t)stream));
-    const size_t stage_bytes = align256(4 * max_nodes * sizeof(double));
-    CLB_CUDA(cudaMalloc((void**)&b->mem, total + stage_bytes));
-    b->stage = (double*)(b->mem + total);
-    CLB_CUDA(cudaMemsetAsync(b->mem, 0, total, b->E.stream));
-    size_t off = 0;
-    for (int k = 0; k < n; ++k) {
-        auto L = std::make_unique<Lattice>();
-        L->nx = nx[k];
-        L->ny = ny[k];
-        L->p = p[k];
-        L->axis = p[k].wall[0] != CLB_PERIODIC ? 0 : 1;
-        carve(*L, b->mem + off);
-        off += lattice_bytes(nx[k], ny[k], storage);
-        CLB_TRY(b->E.init_member(L.get(), nullptr, nullptr, nullptr, nullptr));
-        b->E.members.push_back(L.get());
-        b->lat.push_back(std::move(L));
-    }
-    CLB_CUDA(cudaStreamSynchronize(b->E.stream));
-    *out = b.release();
-    return CLB_OK;
 }
 
 extern "C" void clb_batch_destroy(clb_batch* b)
@@ -575,201 +579,233 @@ extern "C" void clb_batch_destroy(clb_batch* b)
 extern "C" clb_status clb_batch_init_fields(clb_batch* b, int k, const double* rho, const double* ux,
                                             const double* uy, const double* T)
 {
-    CHECK_B(b, k);
-    Lattice* L = b->lat[k].get();
-    if (!L->active) {
-        L->active = true;
-        b->E.mark_dirty();
+    try {
+        CHECK_B(b, k);
+        Lattice* L = b->lat[k].get();
+        if (!L->active) {
+            L->active = true;
+            b->E.mark_dirty();
+        }
+        L->status = CLB_OK;
+        L->er = INFINITY;
+        return init_from_host(b->E, L, b->stage, rho, ux, uy, T);
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    L->status = CLB_OK;
-    L->er = INFINITY;
-    return init_from_host(b->E, L, b->stage, rho, ux, uy, T);
 }
 
 extern "C" clb_status clb_batch_step(clb_batch* b, long n)
 {
-    if (!b) return set_error(CLB_EINVAL, "batch is NULL");
-    if (n < 0) return set_error(CLB_EINVAL, "n < 0");
-    return b->E.step(n);
+    try {
+        if (!b) return set_error(CLB_EINVAL, "batch is NULL");
+        if (n < 0) return set_error(CLB_EINVAL, "n < 0");
+        return b->E.step(n);
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
+    }
 }
 
 extern "C" clb_status clb_batch_fields(clb_batch* b, int k, double* rho, double* ux, double* uy, double* T)
 {
-    CHECK_B(b, k);
-    Lattice* L = b->lat[k].get();
-    const size_t N = (size_t)L->nx * L->ny;
-    double* host[4] = {rho, ux, uy, T};
-    double* dev[4];
-    for (int i = 0; i < 4; ++i) dev[i] = host[i] ? b->stage + i * N : nullptr;
-    CLB_TRY(b->E.fields(L, dev[0], dev[1], dev[2], dev[3]));
-    for (int i = 0; i < 4; ++i)
-        if (host[i]) CLB_CUDA(cudaMemcpyAsync(host[i], dev[i], N * sizeof(double), cudaMemcpyDeviceToHost, b->E.stream));
-    CLB_CUDA(cudaStreamSynchronize(b->E.stream));
-    return CLB_OK;
+    try {
+        CHECK_B(b, k);
+        Lattice* L = b->lat[k].get();
+        const size_t N = (size_t)L->nx * L->ny;
+        double* host[4] = {rho, ux, uy, T};
+        double* dev[4];
+        for (int i = 0; i < 4; ++i) dev[i] = host[i] ? b->stage + i * N : nullptr;
+        CLB_TRY(b->E.fields(L, dev[0], dev[1], dev[2], dev[3]));
+        for (int i = 0; i < 4; ++i)
+            if (host[i]) CLB_CUDA(cudaMemcpyAsync(host[i], dev[i], N * sizeof(double), cudaMemcpyDeviceToHost, b->E.stream));
+        CLB_CUDA(cudaStreamSynchronize(b->E.stream));
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
+    }
 }
 
 extern "C" clb_status clb_batch_diagnostics(clb_batch* b, const int* axis, double* nu, double* er)
 {
-    if (!b) return set_error(CLB_EINVAL, "batch is NULL");
-    bool changed = false;
-    for (size_t k = 0; k < b->lat.size(); ++k) {
-        const int a = axis ? axis[k] : b->lat[k]->axis;
-        if (a != 0 && a != 1) return set_error(CLB_EINVAL, "axis[%zu] must be 0 or 1", k);
-        if (a != b->lat[k]->axis) {
-            b->lat[k]->axis = a;
-            changed = true;
+    try {
+        if (!b) return set_error(CLB_EINVAL, "batch is NULL");
+        bool changed = false;
+        for (size_t k = 0; k < b->lat.size(); ++k) {
+            const int a = axis ? axis[k] : b->lat[k]->axis;
+            if (a != 0 && a != 1) return set_error(CLB_EINVAL, "axis[%zu] must be 0 or 1", k);
+            if (a != b->lat[k]->axis) {
+                b->lat[k]->axis = a;
+                changed = true;
+            }
         }
+        if (changed) b->E.mark_dirty();
+        CLB_TRY(b->E.diagnostics(1));
+        clb_status st = CLB_OK;
+        for (size_t k = 0; k < b->lat.size(); ++k) {
+            const Lattice* L = b->lat[k].get();
+            if (nu) nu[k] = L->nu;
+            if (er) er[k] = L->er;
+            if (L->status == CLB_ENAN) st = set_error(CLB_ENAN, "instance %zu has non-finite fields", k);
+        }
+        return st;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    if (changed) b->E.mark_dirty();
-    CLB_TRY(b->E.diagnostics(1));
-    clb_status st = CLB_OK;
-    for (size_t k = 0; k < b->lat.size(); ++k) {
-        const Lattice* L = b->lat[k].get();
-        if (nu) nu[k] = L->nu;
-        if (er) er[k] = L->er;
-        if (L->status == CLB_ENAN) st = set_error(CLB_ENAN, "instance %zu has non-finite fields", k);
-    }
-    return st;
 }
 
 extern "C" clb_status clb_batch_run(clb_batch* b, double tol, long max_steps, long interval,
                                     long* steps, double* er, int* status)
 {
-    if (!b) return set_error(CLB_EINVAL, "batch is NULL");
-    if (interval <= 0 || interval % 2 || max_steps < 0)
-        return set_error(CLB_EINVAL, "interval must be even and > 0, max_steps >= 0");
-    for (auto& L : b->lat)
-        if (L->status != CLB_OK || L->steps >= max_steps) {
-            L->active = false;
-            b->E.mark_dirty();
-        }
-    for (;;) {
-        bool any = false;
-        long n = interval;
+    try {
+        if (!b) return set_error(CLB_EINVAL, "batch is NULL");
+        if (interval <= 0 || interval % 2 || max_steps < 0)
+            return set_error(CLB_EINVAL, "interval must be even and > 0, max_steps >= 0");
         for (auto& L : b->lat)
-            if (L->active) {
-                any = true;
-                n = std::min(n, max_steps - L->steps);
-            }
-        if (!any) break;
-        CLB_TRY(b->E.step(n));
-        CLB_TRY(b->E.diagnostics(1));
-        for (auto& L : b->lat)
-            if (L->active && (L->status != CLB_OK || L->er < tol || L->steps >= max_steps)) {
+            if (L->status != CLB_OK || L->steps >= max_steps) {
                 L->active = false;
                 b->E.mark_dirty();
             }
+        for (;;) {
+            bool any = false;
+            long n = interval;
+            for (auto& L : b->lat)
+                if (L->active) {
+                    any = true;
+                    n = std::min(n, max_steps - L->steps);
+                }
+            if (!any) break;
+            CLB_TRY(b->E.step(n));
+            CLB_TRY(b->E.diagnostics(1));
+            for (auto& L : b->lat)
+                if (L->active && (L->status != CLB_OK || L->er < tol || L->steps >= max_steps)) {
+                    L->active = false;
+                    b->E.mark_dirty();
+                }
+        }
+        for (size_t k = 0; k < b->lat.size(); ++k) {
+            if (steps) steps[k] = b->lat[k]->steps;
+            if (er) er[k] = b->lat[k]->er;
+            if (status) status[k] = b->lat[k]->status;
+        }
+        // instances stay retired until re-initialised; re-activate them for further stepping
+        for (auto& L : b->lat) L->active = true;
+        b->E.mark_dirty();
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    for (size_t k = 0; k < b->lat.size(); ++k) {
-        if (steps) steps[k] = b->lat[k]->steps;
-        if (er) er[k] = b->lat[k]->er;
-        if (status) status[k] = b->lat[k]->status;
-    }
-    // instances stay retired until re-initialised; re-activate them for further stepping
-    for (auto& L : b->lat) L->active = true;
-    b->E.mark_dirty();
-    return CLB_OK;
 }
 
 extern "C" clb_status clb_batch_set_tile(clb_batch* b, int tile_x, int tile_y, int nodes_per_thread)
 {
-    if (!b) return set_error(CLB_EINVAL, "batch is NULL");
-    if (tile_x < 32 || tile_x > 256 || tile_x % 32 || tile_y < 1 || tile_x * tile_y > 256 ||
-        (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4))
-        return set_error(CLB_EINVAL, "tile %d x %d x %d: tile_x in [32, 256] multiple of 32, "
-                                     "tile_x * tile_y <= 256, nodes per thread 1, 2 or 4",
-                         tile_x, tile_y, nodes_per_thread);
-    cudaStreamSynchronize(b->E.stream);
-    b->E.tile_x = tile_x;
-    b->E.tile_y = tile_y;
-    b->E.npt = nodes_per_thread;
-    b->E.mark_dirty();
-    return CLB_OK;
+    try {
+        if (!b) return set_error(CLB_EINVAL, "batch is NULL");
+        if (tile_x < 32 || tile_x > 256 || tile_x % 32 || tile_y < 1 || tile_x * tile_y > 256 ||
+            (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4))
+            return set_error(CLB_EINVAL, "tile %d x %d x %d: tile_x in [32, 256] multiple of 32, "
+                                         "tile_x * tile_y <= 256, nodes per thread 1, 2 or 4",
+                             tile_x, tile_y, nodes_per_thread);
+        cudaStreamSynchronize(b->E.stream);
+        b->E.tile_x = tile_x;
+        b->E.tile_y = tile_y;
+        b->E.npt = nodes_per_thread;
+        b->E.mark_dirty();
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
+    }
 }
 
 // Times candidate tile shapes over the whole batch (10 steps each after 4 warm-up steps) and keeps
 // the fastest; the populations of every instance are saved first and restored afterwards.
 extern "C" clb_status clb_batch_autotune(clb_batch* b, int* tile_x, int* tile_y, int* nodes_per_thread)
 {
-    if (!b) return set_error(CLB_EINVAL, "batch is NULL");
-    Ensemble& E = b->E;
-    CLB_TRY(E.rebuild());
-    size_t total = 0;
-    for (auto& L : b->lat) total += align256(buffer_bytes(L->nx, L->ny, L->p.storage));
-    char* save = nullptr;
-    CLB_CUDA(cudaMallocAsync((void**)&save, total, E.stream));
-    size_t off = 0;
-    for (auto& L : b->lat) {
-        const size_t bb = buffer_bytes(L->nx, L->ny, L->p.storage);
-        CLB_CUDA(cudaMemcpyAsync(save + off, L->buf[E.parity], bb, cudaMemcpyDeviceToDevice, E.stream));
-        off += align256(bb);
-    }
-    std::vector<long> steps0;
-    for (auto& L : b->lat) steps0.push_back(L->steps);
-    const int shapes[][3] = {{64, 1, 1}, {128, 1, 1}, {256, 1, 1}, {64, 1, 2}, {128, 1, 2}, {64, 2, 2},
-                             {64, 1, 4}, {128, 1, 4}, {32, 4, 2}, {32, 2, 4}};
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
-    int bt[3] = {E.tile_x, E.tile_y, E.npt};
-    clb_status st = CLB_OK;
-    for (auto& sh : shapes) {
-        E.tile_x = sh[0];
-        E.tile_y = sh[1];
-        E.npt = sh[2];
-        E.mark_dirty();
-        st = E.rebuild();
-        for (int k = 0; k < 4 && st == CLB_OK; ++k) st = E.launch_step(E.stream, (E.parity + k) & 1);
-        cudaEventRecord(e0, E.stream);
-        for (int k = 0; k < 10 && st == CLB_OK; ++k) st = E.launch_step(E.stream, (E.parity + k) & 1);
-        cudaEventRecord(e1, E.stream);
-        if (st != CLB_OK) break;
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            bt[0] = sh[0];
-            bt[1] = sh[1];
-            bt[2] = sh[2];
+    try {
+        if (!b) return set_error(CLB_EINVAL, "batch is NULL");
+        Ensemble& E = b->E;
+        CLB_TRY(E.rebuild());
+        size_t total = 0;
+        for (auto& L : b->lat) total += align256(buffer_bytes(L->nx, L->ny, L->p.storage));
+        char* save = nullptr;
+        CLB_CUDA(cudaMallocAsync((void**)&save, total, E.stream));
+        size_t off = 0;
+        for (auto& L : b->lat) {
+            const size_t bb = buffer_bytes(L->nx, L->ny, L->p.storage);
+            CLB_CUDA(cudaMemcpyAsync(save + off, L->buf[E.parity], bb, cudaMemcpyDeviceToDevice, E.stream));
+            off += align256(bb);
         }
+        std::vector<long> steps0;
+        for (auto& L : b->lat) steps0.push_back(L->steps);
+        const int shapes[][3] = {{64, 1, 1}, {128, 1, 1}, {256, 1, 1}, {64, 1, 2}, {128, 1, 2}, {64, 2, 2},
+                                 {64, 1, 4}, {128, 1, 4}, {32, 4, 2}, {32, 2, 4}};
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        int bt[3] = {E.tile_x, E.tile_y, E.npt};
+        clb_status st = CLB_OK;
+        for (auto& sh : shapes) {
+            E.tile_x = sh[0];
+            E.tile_y = sh[1];
+            E.npt = sh[2];
+            E.mark_dirty();
+            st = E.rebuild();
+            for (int k = 0; k < 4 && st == CLB_OK; ++k) st = E.launch_step(E.stream, (E.parity + k) & 1);
+            cudaEventRecord(e0, E.stream);
+            for (int k = 0; k < 10 && st == CLB_OK; ++k) st = E.launch_step(E.stream, (E.parity + k) & 1);
+            cudaEventRecord(e1, E.stream);
+            if (st != CLB_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt[0] = sh[0];
+                bt[1] = sh[1];
+                bt[2] = sh[2];
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        off = 0;
+        cudaError_t e = cudaSuccess;
+        for (auto& L : b->lat) {
+            const size_t bb = buffer_bytes(L->nx, L->ny, L->p.storage);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(L->buf[E.parity], save + off, bb, cudaMemcpyDeviceToDevice, E.stream);
+            off += align256(bb);
+        }
+        cudaFreeAsync(save, E.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
+        for (size_t k = 0; k < b->lat.size(); ++k) b->lat[k]->steps = steps0[k];
+        E.tile_x = bt[0];
+        E.tile_y = bt[1];
+        E.npt = bt[2];
+        E.mark_dirty();
+        if (st != CLB_OK) return st;
+        if (e != cudaSuccess) return set_error(CLB_ECUDA, "batch autotune restore: %s", cudaGetErrorString(e));
+        if (tile_x) *tile_x = bt[0];
+        if (tile_y) *tile_y = bt[1];
+        if (nodes_per_thread) *nodes_per_thread = bt[2];
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    off = 0;
-    cudaError_t e = cudaSuccess;
-    for (auto& L : b->lat) {
-        const size_t bb = buffer_bytes(L->nx, L->ny, L->p.storage);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(L->buf[E.parity], save + off, bb, cudaMemcpyDeviceToDevice, E.stream);
-        off += align256(bb);
-    }
-    cudaFreeAsync(save, E.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
-    for (size_t k = 0; k < b->lat.size(); ++k) b->lat[k]->steps = steps0[k];
-    E.tile_x = bt[0];
-    E.tile_y = bt[1];
-    E.npt = bt[2];
-    E.mark_dirty();
-    if (st != CLB_OK) return st;
-    if (e != cudaSuccess) return set_error(CLB_ECUDA, "batch autotune restore: %s", cudaGetErrorString(e));
-    if (tile_x) *tile_x = bt[0];
-    if (tile_y) *tile_y = bt[1];
-    if (nodes_per_thread) *nodes_per_thread = bt[2];
-    return CLB_OK;
 }
 
 extern "C" clb_status clb_batch_get_launch(clb_batch* b, int* tile_x, int* tile_y, int* nodes_per_thread,
                                            int* groups, long* blocks)
 {
-    if (!b) return set_error(CLB_EINVAL, "batch is NULL");
-    CLB_TRY(b->E.rebuild());
-    if (tile_x) *tile_x = b->E.tile_x;
-    if (tile_y) *tile_y = b->E.tile_y;
-    if (nodes_per_thread) *nodes_per_thread = b->E.npt;
-    if (groups) *groups = b->E.groups;
-    if (blocks) *blocks = b->E.ntiles;
-    return CLB_OK;
+    try {
+        if (!b) return set_error(CLB_EINVAL, "batch is NULL");
+        CLB_TRY(b->E.rebuild());
+        if (tile_x) *tile_x = b->E.tile_x;
+        if (tile_y) *tile_y = b->E.tile_y;
+        if (nodes_per_thread) *nodes_per_thread = b->E.npt;
+        if (groups) *groups = b->E.groups;
+        if (blocks) *blocks = b->E.ntiles;
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
+    }
 }
 
 // ------------------------------------------------------------------------------------ serving
@@ -801,16 +837,20 @@ struct clb_server {
 extern "C" clb_status clb_serve_open(size_t hbm_budget_bytes, int max_slots, int storage, void* stream,
                                      clb_server** out)
 {
-    if (!out) return set_error(CLB_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (max_slots <= 0 || hbm_budget_bytes == 0) return set_error(CLB_EINVAL, "need max_slots > 0 and a budget");
-    if (storage < CLB_F64 || storage > CLB_F16DEV) return set_error(CLB_EINVAL, "bad storage");
-    auto s = std::make_unique<clb_server>();
-    s->budget = hbm_budget_bytes;
-    s->max_slots = max_slots;
-    CLB_TRY(s->E.init(storage, (cudaStream_t)stream));
-    *out = s.release();
-    return CLB_OK;
+    try {
+        if (!out) return set_error(CLB_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (max_slots <= 0 || hbm_budget_bytes == 0) return set_error(CLB_EINVAL, "need max_slots > 0 and a budget");
+        if (storage < CLB_F64 || storage > CLB_F16DEV) return set_error(CLB_EINVAL, "bad storage");
+        auto s = std::make_unique<clb_server>();
+        s->budget = hbm_budget_bytes;
+        s->max_slots = max_slots;
+        CLB_TRY(s->E.init(storage, (cudaStream_t)stream));
+        *out = s.release();
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
+    }
 }
 
 extern "C" void clb_serve_close(clb_server* s)
@@ -826,154 +866,174 @@ extern "C" clb_status clb_serve_submit(clb_server* s, int nx, int ny, const clb_
                                        const double* ux, const double* uy, const double* T, int nu_axis,
                                        long step_cap, double tol, long* req_id)
 {
-    if (!s) return set_error(CLB_EINVAL, "server is NULL");
-    CLB_TRY(validate(nx, ny, p));
-    if (p->storage != s->E.storage) return set_error(CLB_EINVAL, "request storage differs from the server's");
-    if (nu_axis != 0 && nu_axis != 1) return set_error(CLB_EINVAL, "nu_axis must be 0 or 1");
-    if (step_cap < 0) return set_error(CLB_EINVAL, "step_cap < 0");
-    const size_t need = lattice_bytes(nx, ny, p->storage);
-    if (need > s->budget) return set_error(CLB_ENOMEM, "request needs %zu bytes > budget %zu", need, s->budget);
-    auto r = std::make_unique<Request>();
-    r->id = s->next_id++;
-    r->L = std::make_unique<Lattice>();
-    r->L->nx = nx;
-    r->L->ny = ny;
-    r->L->p = *p;
-    r->L->axis = nu_axis;
-    r->L->bytes = need;
-    r->cap = step_cap;
-    r->tol = tol;
-    const size_t N = (size_t)nx * ny;
-    r->init.assign(4 * N, 0.0);
-    const double* src[4] = {rho, ux, uy, T};
-    const double dflt[4] = {1.0, 0.0, 0.0, p->T0};
-    for (int k = 0; k < 4; ++k) {
-        if (src[k]) std::memcpy(r->init.data() + k * N, src[k], N * sizeof(double));
-        else std::fill(r->init.begin() + k * N, r->init.begin() + (k + 1) * N, dflt[k]);
+    try {
+        if (!s) return set_error(CLB_EINVAL, "server is NULL");
+        CLB_TRY(validate(nx, ny, p));
+        if (p->storage != s->E.storage) return set_error(CLB_EINVAL, "request storage differs from the server's");
+        if (nu_axis != 0 && nu_axis != 1) return set_error(CLB_EINVAL, "nu_axis must be 0 or 1");
+        if (step_cap < 0) return set_error(CLB_EINVAL, "step_cap < 0");
+        const size_t need = lattice_bytes(nx, ny, p->storage);
+        if (need > s->budget) return set_error(CLB_ENOMEM, "request needs %zu bytes > budget %zu", need, s->budget);
+        auto r = std::make_unique<Request>();
+        r->id = s->next_id++;
+        r->L = std::make_unique<Lattice>();
+        r->L->nx = nx;
+        r->L->ny = ny;
+        r->L->p = *p;
+        r->L->axis = nu_axis;
+        r->L->bytes = need;
+        r->cap = step_cap;
+        r->tol = tol;
+        const size_t N = (size_t)nx * ny;
+        r->init.assign(4 * N, 0.0);
+        const double* src[4] = {rho, ux, uy, T};
+        const double dflt[4] = {1.0, 0.0, 0.0, p->T0};
+        for (int k = 0; k < 4; ++k) {
+            if (src[k]) std::memcpy(r->init.data() + k * N, src[k], N * sizeof(double));
+            else std::fill(r->init.begin() + k * N, r->init.begin() + (k + 1) * N, dflt[k]);
+        }
+        if (req_id) *req_id = r->id;
+        s->queue.push_back(r.get());
+        s->all[r->id] = std::move(r);
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    if (req_id) *req_id = r->id;
-    s->queue.push_back(r.get());
-    s->all[r->id] = std::move(r);
-    return CLB_OK;
 }
 
 extern "C" clb_status clb_serve_progress(clb_server* s, long chunk, int* active, int* queued)
 {
-    if (!s) return set_error(CLB_EINVAL, "server is NULL");
-    if (chunk <= 0 || chunk % 2) return set_error(CLB_EINVAL, "chunk must be even and > 0");
-    // admission: first fit over the queue in arrival order
-    for (auto it = s->queue.begin(); it != s->queue.end();) {
-        Request* r = *it;
-        if ((int)s->running.size() >= s->max_slots) break;
-        if (s->used + r->L->bytes > s->budget) {
-            ++it;
-            continue;
-        }
-        char* mem = nullptr;
-        cudaError_t e = cudaMalloc((void**)&mem, r->L->bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            break;  // device memory is short of the budget; retry next round
-        }
-        r->L->mem = mem;
-        carve(*r->L, mem);
-        const size_t N = (size_t)r->L->nx * r->L->ny;
-        if (s->stage_nodes < N) {
-            cudaStreamSynchronize(s->E.stream);
-            cudaFree(s->stage);
-            s->stage = nullptr;
-            CLB_CUDA(cudaMalloc((void**)&s->stage, 4 * N * sizeof(double)));
-            s->stage_nodes = N;
-        }
-        const double* h = r->init.data();
-        CLB_TRY(init_from_host(s->E, r->L.get(), s->stage, h, h + N, h + 2 * N, h + 3 * N));
-        std::vector<double>().swap(r->init);
-        s->used += r->L->bytes;
-        s->running.push_back(r);
-        s->E.members.push_back(r->L.get());
-        s->E.mark_dirty();
-        it = s->queue.erase(it);
-    }
-    if (!s->running.empty()) {
-        CLB_TRY(s->E.step(chunk));
-        CLB_TRY(s->E.diagnostics(1));
-        std::vector<Request*> keep;
-        for (Request* r : s->running) {
-            Lattice* L = r->L.get();
-            if (L->status != CLB_OK || L->er < r->tol || L->steps >= r->cap) {
-                const size_t N = (size_t)L->nx * L->ny;
-                r->result.assign(4 * N, 0.0);
-                double* dev = nullptr;
-                if (s->stage_nodes < N) return set_error(CLB_ECUDA, "staging buffer too small");
-                dev = s->stage;
-                CLB_TRY(s->E.fields(L, dev, dev + N, dev + 2 * N, dev + 3 * N));
-                CLB_CUDA(cudaMemcpyAsync(r->result.data(), dev, 4 * N * sizeof(double), cudaMemcpyDeviceToHost, s->E.stream));
-                CLB_CUDA(cudaStreamSynchronize(s->E.stream));
-                cudaFree(L->mem);
-                L->mem = nullptr;
-                s->used -= L->bytes;
-                r->done = 1;
-                s->E.members.erase(std::find(s->E.members.begin(), s->E.members.end(), L));
-                s->E.mark_dirty();
-            } else {
-                keep.push_back(r);
+    try {
+        if (!s) return set_error(CLB_EINVAL, "server is NULL");
+        if (chunk <= 0 || chunk % 2) return set_error(CLB_EINVAL, "chunk must be even and > 0");
+        // admission: first fit over the queue in arrival order
+        for (auto it = s->queue.begin(); it != s->queue.end();) {
+            Request* r = *it;
+            if ((int)s->running.size() >= s->max_slots) break;
+            if (s->used + r->L->bytes > s->budget) {
+                ++it;
+                continue;
             }
+            char* mem = nullptr;
+            cudaError_t e = cudaMalloc((void**)&mem, r->L->bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                break;  // device memory is short of the budget; retry next round
+            }
+            r->L->mem = mem;
+            carve(*r->L, mem);
+            const size_t N = (size_t)r->L->nx * r->L->ny;
+            if (s->stage_nodes < N) {
+                cudaStreamSynchronize(s->E.stream);
+                cudaFree(s->stage);
+                s->stage = nullptr;
+                CLB_CUDA(cudaMalloc((void**)&s->stage, 4 * N * sizeof(double)));
+                s->stage_nodes = N;
+            }
+            const double* h = r->init.data();
+            CLB_TRY(init_from_host(s->E, r->L.get(), s->stage, h, h + N, h + 2 * N, h + 3 * N));
+            std::vector<double>().swap(r->init);
+            s->used += r->L->bytes;
+            s->running.push_back(r);
+            s->E.members.push_back(r->L.get());
+            s->E.mark_dirty();
+            it = s->queue.erase(it);
         }
-        s->running.swap(keep);
+        if (!s->running.empty()) {
+            CLB_TRY(s->E.step(chunk));
+            CLB_TRY(s->E.diagnostics(1));
+            std::vector<Request*> keep;
+            for (Request* r : s->running) {
+                Lattice* L = r->L.get();
+                if (L->status != CLB_OK || L->er < r->tol || L->steps >= r->cap) {
+                    const size_t N = (size_t)L->nx * L->ny;
+                    r->result.assign(4 * N, 0.0);
+                    double* dev = nullptr;
+                    if (s->stage_nodes < N) return set_error(CLB_ECUDA, "staging buffer too small");
+                    dev = s->stage;
+                    CLB_TRY(s->E.fields(L, dev, dev + N, dev + 2 * N, dev + 3 * N));
+                    CLB_CUDA(cudaMemcpyAsync(r->result.data(), dev, 4 * N * sizeof(double), cudaMemcpyDeviceToHost, s->E.stream));
+                    CLB_CUDA(cudaStreamSynchronize(s->E.stream));
+                    cudaFree(L->mem);
+                    L->mem = nullptr;
+                    s->used -= L->bytes;
+                    r->done = 1;
+                    s->E.members.erase(std::find(s->E.members.begin(), s->E.members.end(), L));
+                    s->E.mark_dirty();
+                } else {
+                    keep.push_back(r);
+                }
+            }
+            s->running.swap(keep);
+        }
+        if (active) *active = (int)s->running.size();
+        if (queued) *queued = (int)s->queue.size();
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    if (active) *active = (int)s->running.size();
-    if (queued) *queued = (int)s->queue.size();
-    return CLB_OK;
 }
 
 extern "C" clb_status clb_serve_cancel(clb_server* s, long req_id)
 {
-    if (!s) return set_error(CLB_EINVAL, "server is NULL");
-    auto it = s->all.find(req_id);
-    if (it == s->all.end()) return set_error(CLB_EINVAL, "unknown request %ld", req_id);
-    Request* r = it->second.get();
-    auto q = std::find(s->queue.begin(), s->queue.end(), r);
-    if (q != s->queue.end()) s->queue.erase(q);
-    auto run = std::find(s->running.begin(), s->running.end(), r);
-    if (run != s->running.end()) {
-        // no kernel of this server is in flight between calls; release the slot and its memory
-        CLB_CUDA(cudaStreamSynchronize(s->E.stream));
-        Lattice* L = r->L.get();
-        s->E.members.erase(std::find(s->E.members.begin(), s->E.members.end(), L));
-        s->E.mark_dirty();
-        cudaFree(L->mem);
-        L->mem = nullptr;
-        s->used -= L->bytes;
-        s->running.erase(run);
+    try {
+        if (!s) return set_error(CLB_EINVAL, "server is NULL");
+        auto it = s->all.find(req_id);
+        if (it == s->all.end()) return set_error(CLB_EINVAL, "unknown request %ld", req_id);
+        Request* r = it->second.get();
+        auto q = std::find(s->queue.begin(), s->queue.end(), r);
+        if (q != s->queue.end()) s->queue.erase(q);
+        auto run = std::find(s->running.begin(), s->running.end(), r);
+        if (run != s->running.end()) {
+            // no kernel of this server is in flight between calls; release the slot and its memory
+            CLB_CUDA(cudaStreamSynchronize(s->E.stream));
+            Lattice* L = r->L.get();
+            s->E.members.erase(std::find(s->E.members.begin(), s->E.members.end(), L));
+            s->E.mark_dirty();
+            cudaFree(L->mem);
+            L->mem = nullptr;
+            s->used -= L->bytes;
+            s->running.erase(run);
+        }
+        s->all.erase(it);
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    s->all.erase(it);
-    return CLB_OK;
 }
 
 extern "C" clb_status clb_serve_poll(clb_server* s, long req_id, int* done, double* nu, long* steps, double* er)
 {
-    if (!s) return set_error(CLB_EINVAL, "server is NULL");
-    auto it = s->all.find(req_id);
-    if (it == s->all.end()) return set_error(CLB_EINVAL, "unknown request %ld", req_id);
-    const Request* r = it->second.get();
-    if (done) *done = r->done;
-    if (nu) *nu = r->L->nu;
-    if (steps) *steps = r->L->steps;
-    if (er) *er = r->L->er;
-    return r->L->status == CLB_ENAN ? set_error(CLB_ENAN, "request %ld blew up", req_id) : CLB_OK;
+    try {
+        if (!s) return set_error(CLB_EINVAL, "server is NULL");
+        auto it = s->all.find(req_id);
+        if (it == s->all.end()) return set_error(CLB_EINVAL, "unknown request %ld", req_id);
+        const Request* r = it->second.get();
+        if (done) *done = r->done;
+        if (nu) *nu = r->L->nu;
+        if (steps) *steps = r->L->steps;
+        if (er) *er = r->L->er;
+        return r->L->status == CLB_ENAN ? set_error(CLB_ENAN, "request %ld blew up", req_id) : CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
+    }
 }
 
 extern "C" clb_status clb_serve_fetch(clb_server* s, long req_id, double* rho, double* ux, double* uy, double* T)
 {
-    if (!s) return set_error(CLB_EINVAL, "server is NULL");
-    auto it = s->all.find(req_id);
-    if (it == s->all.end()) return set_error(CLB_EINVAL, "unknown request %ld", req_id);
-    Request* r = it->second.get();
-    if (!r->done) return set_error(CLB_EBUSY, "request %ld is still running", req_id);
-    const size_t N = (size_t)r->L->nx * r->L->ny;
-    double* out[4] = {rho, ux, uy, T};
-    for (int k = 0; k < 4; ++k)
-        if (out[k]) std::memcpy(out[k], r->result.data() + k * N, N * sizeof(double));
-    s->all.erase(it);
-    return CLB_OK;
+    try {
+        if (!s) return set_error(CLB_EINVAL, "server is NULL");
+        auto it = s->all.find(req_id);
+        if (it == s->all.end()) return set_error(CLB_EINVAL, "unknown request %ld", req_id);
+        Request* r = it->second.get();
+        if (!r->done) return set_error(CLB_EBUSY, "request %ld is still running", req_id);
+        const size_t N = (size_t)r->L->nx * r->L->ny;
+        double* out[4] = {rho, ux, uy, T};
+        for (int k = 0; k < 4; ++k)
+            if (out[k]) std::memcpy(out[k], r->result.data() + k * N, N * sizeof(double));
+        s->all.erase(it);
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
+    }
 }

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 
 #include "../../include/clb.h"
@@ -17,6 +18,10 @@
 namespace clb {
 
 clb_status set_error(clb_status st, const char* fmt, ...);
+
+// An entry point's host allocation (a container, a handle) that fails: CLB_ENOMEM instead of an
+// exception crossing the C boundary.
+inline clb_status host_alloc_failed() { return set_error(CLB_ENOMEM, "host allocation failed"); }
 void clear_error();
 
 #define CLB_CUDA(call)                                                                          \

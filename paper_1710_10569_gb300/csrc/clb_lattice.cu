@@ -311,70 +311,74 @@ extern "C" clb_status clb_footprint(int nx, int ny, const clb_params* p, size_t*
 extern "C" clb_status clb_create(int nx, int ny, const clb_params* p, void* stream, void* dev_mem,
                                  size_t dev_bytes, clb_handle** out)
 {
-    if (!out) return set_error(CLB_EINVAL, "out is NULL");
-    *out = nullptr;
-    CLB_TRY(validate(nx, ny, p));
-    const Layout L = layout(nx, ny, p->storage);
-    if (dev_mem && dev_bytes < L.total)
-        return set_error(CLB_EINVAL, "dev_bytes %zu < footprint %zu", dev_bytes, L.total);
-    if (dev_mem && ((uintptr_t)dev_mem & 255))
-        return set_error(CLB_EINVAL, "dev_mem must be 256-byte aligned");
-    clb_handle* h = new clb_handle;
-    h->nx = nx;
-    h->ny = ny;
-    h->p = *p;
-    h->L = L;
-    h->stream = (cudaStream_t)stream;
-    cudaGetDevice(&h->device);
-    auto fail = [&](clb_status st) {
-        clb_destroy(h);
-        return st;
-    };
-    cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return fail(set_error(CLB_ECUDA, "stream: %s", cudaGetErrorString(e)));
-    if (dev_mem) {
-        h->mem = (char*)dev_mem;
-    } else {
-        e = cudaMalloc((void**)&h->mem, L.total);
-        if (e != cudaSuccess)
-            return fail(set_error(e == cudaErrorMemoryAllocation ? CLB_ENOMEM : CLB_ECUDA,
-                                  "cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e)));
-        h->own_mem = true;
-    }
-    e = cudaMallocHost((void**)&h->host_diag, 16 * sizeof(double));
-    if (e != cudaSuccess) return fail(set_error(CLB_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(e)));
-    h->buf[0] = h->mem + L.buf[0];
-    h->buf[1] = h->mem + L.buf[1];
-    h->snap = (double*)(h->mem + L.snap);
-    h->stage = (double*)(h->mem + L.stage);
-    h->partial = (double*)(h->mem + L.partial);
-    h->diag = (double*)(h->mem + L.diag);
-    h->Pd = make_lat_params<double>(nx, ny, *p);
-    h->Pf = make_lat_params<float>(nx, ny, *p);
-    h->npt = p->storage == CLB_F32 ? 2 : 4;
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(std::make_tuple(p->storage, nx, ny));
-        if (it != g_tune_cache.end()) {
-            h->bx = it->second[0];
-            h->by = it->second[1];
-            h->npt = it->second[2];
-            h->pipe_stages = it->second[3];
-            h->pipe_rows = it->second[4];
+    try {
+        if (!out) return set_error(CLB_EINVAL, "out is NULL");
+        *out = nullptr;
+        CLB_TRY(validate(nx, ny, p));
+        const Layout L = layout(nx, ny, p->storage);
+        if (dev_mem && dev_bytes < L.total)
+            return set_error(CLB_EINVAL, "dev_bytes %zu < footprint %zu", dev_bytes, L.total);
+        if (dev_mem && ((uintptr_t)dev_mem & 255))
+            return set_error(CLB_EINVAL, "dev_mem must be 256-byte aligned");
+        clb_handle* h = new clb_handle;
+        h->nx = nx;
+        h->ny = ny;
+        h->p = *p;
+        h->L = L;
+        h->stream = (cudaStream_t)stream;
+        cudaGetDevice(&h->device);
+        auto fail = [&](clb_status st) {
+            clb_destroy(h);
+            return st;
+        };
+        cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(set_error(CLB_ECUDA, "stream: %s", cudaGetErrorString(e)));
+        if (dev_mem) {
+            h->mem = (char*)dev_mem;
+        } else {
+            e = cudaMalloc((void**)&h->mem, L.total);
+            if (e != cudaSuccess)
+                return fail(set_error(e == cudaErrorMemoryAllocation ? CLB_ENOMEM : CLB_ECUDA,
+                                      "cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e)));
+            h->own_mem = true;
         }
+        e = cudaMallocHost((void**)&h->host_diag, 16 * sizeof(double));
+        if (e != cudaSuccess) return fail(set_error(CLB_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(e)));
+        h->buf[0] = h->mem + L.buf[0];
+        h->buf[1] = h->mem + L.buf[1];
+        h->snap = (double*)(h->mem + L.snap);
+        h->stage = (double*)(h->mem + L.stage);
+        h->partial = (double*)(h->mem + L.partial);
+        h->diag = (double*)(h->mem + L.diag);
+        h->Pd = make_lat_params<double>(nx, ny, *p);
+        h->Pf = make_lat_params<float>(nx, ny, *p);
+        h->npt = p->storage == CLB_F32 ? 2 : 4;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(std::make_tuple(p->storage, nx, ny));
+            if (it != g_tune_cache.end()) {
+                h->bx = it->second[0];
+                h->by = it->second[1];
+                h->npt = it->second[2];
+                h->pipe_stages = it->second[3];
+                h->pipe_rows = it->second[4];
+            }
+        }
+        // the padding between rows and planes is never read, but keep it defined
+        e = cudaMemsetAsync(h->mem, 0, L.snap, h->stream);
+        if (e != cudaSuccess) return fail(set_error(CLB_ECUDA, "memset: %s", cudaGetErrorString(e)));
+        clb_status st = launch_init(h, nullptr, nullptr, nullptr, nullptr);
+        if (st == CLB_OK) st = take_snapshot(h);
+        if (st == CLB_OK) {
+            e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) st = set_error(CLB_ECUDA, "init: %s", cudaGetErrorString(e));
+        }
+        if (st != CLB_OK) return fail(st);
+        *out = h;
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    // the padding between rows and planes is never read, but keep it defined
-    e = cudaMemsetAsync(h->mem, 0, L.snap, h->stream);
-    if (e != cudaSuccess) return fail(set_error(CLB_ECUDA, "memset: %s", cudaGetErrorString(e)));
-    clb_status st = launch_init(h, nullptr, nullptr, nullptr, nullptr);
-    if (st == CLB_OK) st = take_snapshot(h);
-    if (st == CLB_OK) {
-        e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) st = set_error(CLB_ECUDA, "init: %s", cudaGetErrorString(e));
-    }
-    if (st != CLB_OK) return fail(st);
-    *out = h;
-    return CLB_OK;
 }
 
 extern "C" void clb_destroy(clb_handle* h)
@@ -672,58 +676,62 @@ extern "C" clb_status clb_get_pipeline(clb_handle* h, int* stages, int* rows)
 
 extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y, int* nodes_per_thread)
 {
-    CHECK_H(h);
-    DeviceGuard dg(h->device);
-    const size_t bb = buffer_bytes(h->nx, h->ny, h->p.storage);
-    void* save = nullptr;
-    CLB_CUDA(cudaMallocAsync(&save, bb, h->stream));
-    CLB_CUDA(cudaMemcpyAsync(save, h->buf[h->cur], bb, cudaMemcpyDeviceToDevice, h->stream));
-    std::vector<Launch> cands;
-    const int shapes[][2] = {{64, 1}, {128, 1}, {256, 1}, {32, 4}, {64, 2}, {128, 2}};
-    for (int npt : {1, 2, 4})
-        for (auto& sh : shapes) cands.push_back({sh[0], sh[1], npt, 0, 8});
-    for (int npt : {2, 4})
-        for (int st : {2, 3, 4})
-            for (int rows : {4, 8, 16}) cands.push_back({128, 1, npt, st, rows});
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
-    Launch bl = current_launch(h);
-    const int reps = 10;
-    clb_status st = CLB_OK;
-    for (const Launch& c : cands) {
-        if (c.bx * c.npt > 2 * h->nx + 64 && c.bx * c.npt > 64) continue;  // far wider than the lattice
-        if (c.stages > 0 && check_launch(h, c) != CLB_OK) continue;
-        for (int k = 0; k < 4 && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, c);
-        cudaEventRecord(e0, h->stream);
-        for (int k = 0; k < reps && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, c);
-        cudaEventRecord(e1, h->stream);
-        if (st != CLB_OK) break;
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            bl = c;
+    try {
+        CHECK_H(h);
+        DeviceGuard dg(h->device);
+        const size_t bb = buffer_bytes(h->nx, h->ny, h->p.storage);
+        void* save = nullptr;
+        CLB_CUDA(cudaMallocAsync(&save, bb, h->stream));
+        CLB_CUDA(cudaMemcpyAsync(save, h->buf[h->cur], bb, cudaMemcpyDeviceToDevice, h->stream));
+        std::vector<Launch> cands;
+        const int shapes[][2] = {{64, 1}, {128, 1}, {256, 1}, {32, 4}, {64, 2}, {128, 2}};
+        for (int npt : {1, 2, 4})
+            for (auto& sh : shapes) cands.push_back({sh[0], sh[1], npt, 0, 8});
+        for (int npt : {2, 4})
+            for (int st : {2, 3, 4})
+                for (int rows : {4, 8, 16}) cands.push_back({128, 1, npt, st, rows});
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        Launch bl = current_launch(h);
+        const int reps = 10;
+        clb_status st = CLB_OK;
+        for (const Launch& c : cands) {
+            if (c.bx * c.npt > 2 * h->nx + 64 && c.bx * c.npt > 64) continue;  // far wider than the lattice
+            if (c.stages > 0 && check_launch(h, c) != CLB_OK) continue;
+            for (int k = 0; k < 4 && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, c);
+            cudaEventRecord(e0, h->stream);
+            for (int k = 0; k < reps && st == CLB_OK; ++k) st = launch_step(h, (h->cur + k) & 1, h->stream, c);
+            cudaEventRecord(e1, h->stream);
+            if (st != CLB_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bl = c;
+            }
         }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaError_t e = cudaMemcpyAsync(h->buf[h->cur], save, bb, cudaMemcpyDeviceToDevice, h->stream);
+        cudaFreeAsync(save, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (st != CLB_OK) return st;
+        if (e != cudaSuccess) return set_error(CLB_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
+        CLB_TRY(apply_launch(h, bl));
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[std::make_tuple(h->p.storage, h->nx, h->ny)] = {bl.bx, bl.by, bl.npt, bl.stages, bl.rows};
+        }
+        if (block_x) *block_x = bl.bx;
+        if (block_y) *block_y = bl.by;
+        if (nodes_per_thread) *nodes_per_thread = bl.npt;
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaError_t e = cudaMemcpyAsync(h->buf[h->cur], save, bb, cudaMemcpyDeviceToDevice, h->stream);
-    cudaFreeAsync(save, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (st != CLB_OK) return st;
-    if (e != cudaSuccess) return set_error(CLB_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
-    CLB_TRY(apply_launch(h, bl));
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[std::make_tuple(h->p.storage, h->nx, h->ny)] = {bl.bx, bl.by, bl.npt, bl.stages, bl.rows};
-    }
-    if (block_x) *block_x = bl.bx;
-    if (block_y) *block_y = bl.by;
-    if (nodes_per_thread) *nodes_per_thread = bl.npt;
-    return CLB_OK;
 }
 
 extern "C" void* clb_stream(clb_handle* h) { return h ? (void*)h->stream : nullptr; }

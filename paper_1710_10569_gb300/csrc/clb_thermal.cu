@@ -277,7 +277,8 @@ extern "C" clb_status clb_thermal_create(int nx, int ny, const clb_params* p, vo
     *out = nullptr;
     CLB_TRY(validate(nx, ny, p));
     if (p->wall[2] == CLB_WALL_WET) return set_error(CLB_EINVAL, "wet walls are not available in the thermal-only mode");
-    auto* h = new clb_thermal;
+    auto* h = new (std::nothrow) clb_thermal;
+    if (!h) return host_alloc_failed();
     h->nx = nx;
     h->ny = ny;
     h->p = *p;

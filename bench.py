@@ -14,6 +14,14 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 For N > 1 (torchrun) every rank steps its own replica of the lattice (replicas only: the
 workload is one lattice per GPU and no data crosses GPUs); value = all ranks' node updates / the
 slowest rank's time.
+
+Beside the headline the JSON line carries (rank 0, N = 1): `e2e` (the same run through the C ABI
+from pinned host fields), `cpu_baseline` (the FP64 oracle on the host cores), `variants` (FP16
+deviation storage on 4096 x 2048, FP64), `thermal_only` (D2Q5 alone, 4096 x 4096), `three_d`
+(D3Q27 + D3Q7 on 256 x 256 x 128 in three storage forms, a batch of 48 uneven boxes, the D3Q7
+thermal-only step on 256^3), `batched` (256 uneven cavities in one launch per step) and `served`
+(a Poisson request trace against the plain FP64 path). `--served-large` runs a served trace over
+edges 64-4096 instead; `--thermal-only`, `--three-d-only` and `--batched-only` run one part alone.
 """
 from __future__ import annotations
 

@@ -596,6 +596,7 @@ extern "C" clb_status clb_batch_init_fields(clb_batch* b, int k, const double* r
 
 extern "C" clb_status clb_batch_step(clb_batch* b, long n)
 {
+    TraceRange trace("clb_batch_step");
     try {
         if (!b) return set_error(CLB_EINVAL, "batch is NULL");
         if (n < 0) return set_error(CLB_EINVAL, "n < 0");
@@ -626,6 +627,7 @@ extern "C" clb_status clb_batch_fields(clb_batch* b, int k, double* rho, double*
 
 extern "C" clb_status clb_batch_diagnostics(clb_batch* b, const int* axis, double* nu, double* er)
 {
+    TraceRange trace("clb_batch_diagnostics");
     try {
         if (!b) return set_error(CLB_EINVAL, "batch is NULL");
         bool changed = false;
@@ -655,6 +657,7 @@ extern "C" clb_status clb_batch_diagnostics(clb_batch* b, const int* axis, doubl
 extern "C" clb_status clb_batch_run(clb_batch* b, double tol, long max_steps, long interval,
                                     long* steps, double* er, int* status)
 {
+    TraceRange trace("clb_batch_run");
     try {
         if (!b) return set_error(CLB_EINVAL, "batch is NULL");
         if (interval <= 0 || interval % 2 || max_steps < 0)
@@ -719,6 +722,7 @@ extern "C" clb_status clb_batch_set_tile(clb_batch* b, int tile_x, int tile_y, i
 // the fastest; the populations of every instance are saved first and restored afterwards.
 extern "C" clb_status clb_batch_autotune(clb_batch* b, int* tile_x, int* tile_y, int* nodes_per_thread)
 {
+    TraceRange trace("clb_batch_autotune");
     try {
         if (!b) return set_error(CLB_EINVAL, "batch is NULL");
         Ensemble& E = b->E;
@@ -866,6 +870,7 @@ extern "C" clb_status clb_serve_submit(clb_server* s, int nx, int ny, const clb_
                                        const double* ux, const double* uy, const double* T, int nu_axis,
                                        long step_cap, double tol, long* req_id)
 {
+    TraceRange trace("clb_serve_submit");
     try {
         if (!s) return set_error(CLB_EINVAL, "server is NULL");
         CLB_TRY(validate(nx, ny, p));
@@ -903,6 +908,7 @@ extern "C" clb_status clb_serve_submit(clb_server* s, int nx, int ny, const clb_
 
 extern "C" clb_status clb_serve_progress(clb_server* s, long chunk, int* active, int* queued)
 {
+    TraceRange trace("clb_serve_progress");
     try {
         if (!s) return set_error(CLB_EINVAL, "server is NULL");
         if (chunk <= 0 || chunk % 2) return set_error(CLB_EINVAL, "chunk must be even and > 0");

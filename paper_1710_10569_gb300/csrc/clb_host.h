@@ -12,12 +12,23 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/clb.h"
 #include "clb_core.cuh"
 
 namespace clb {
 
 clb_status set_error(clb_status st, const char* fmt, ...);
+
+// An NVTX range over the rest of an entry point (shown by nsys/ncu timelines when a tool is
+// attached; a no-op otherwise).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // An entry point's host allocation (a container, a handle) that fails: CLB_ENOMEM instead of an
 // exception crossing the C boundary.

@@ -406,6 +406,7 @@ extern "C" clb_status clb_init_fields_device(clb_handle* h, const double* rho, c
 extern "C" clb_status clb_init_fields(clb_handle* h, const double* rho, const double* ux,
                                       const double* uy, const double* T)
 {
+    TraceRange trace("clb_init_fields");
     CHECK_H(h);
     DeviceGuard dg(h->device);
     const size_t N = (size_t)h->nx * h->ny;
@@ -423,6 +424,7 @@ extern "C" clb_status clb_init_fields(clb_handle* h, const double* rho, const do
 
 extern "C" clb_status clb_step(clb_handle* h, long n)
 {
+    TraceRange trace("clb_step");
     CHECK_H(h);
     if (n < 0) return set_error(CLB_EINVAL, "n = %ld < 0", n);
     DeviceGuard dg(h->device);
@@ -449,6 +451,7 @@ extern "C" clb_status clb_fields_device(clb_handle* h, double* rho, double* ux, 
 
 extern "C" clb_status clb_fields(clb_handle* h, double* rho, double* ux, double* uy, double* T)
 {
+    TraceRange trace("clb_fields");
     CHECK_H(h);
     DeviceGuard dg(h->device);
     const size_t N = (size_t)h->nx * h->ny;
@@ -488,6 +491,7 @@ extern "C" clb_status clb_populations(clb_handle* h, double* f, double* g)
 
 extern "C" clb_status clb_nusselt(clb_handle* h, int axis, double* nu_out)
 {
+    TraceRange trace("clb_nusselt");
     CHECK_H(h);
     if (axis != 0 && axis != 1) return set_error(CLB_EINVAL, "axis must be 0 or 1");
     if (!nu_out) return set_error(CLB_EINVAL, "nu_out is NULL");
@@ -499,6 +503,7 @@ extern "C" clb_status clb_nusselt(clb_handle* h, int axis, double* nu_out)
 
 extern "C" clb_status clb_residual(clb_handle* h, double* er_out)
 {
+    TraceRange trace("clb_residual");
     CHECK_H(h);
     if (!er_out) return set_error(CLB_EINVAL, "er_out is NULL");
     DeviceGuard dg(h->device);
@@ -510,6 +515,7 @@ extern "C" clb_status clb_residual(clb_handle* h, double* er_out)
 extern "C" clb_status clb_run(clb_handle* h, double tol, long max_steps, long interval,
                               long* steps_out, double* er_out)
 {
+    TraceRange trace("clb_run");
     CHECK_H(h);
     if (interval <= 0 || max_steps < 0) return set_error(CLB_EINVAL, "interval must be > 0 and max_steps >= 0");
     DeviceGuard dg(h->device);
@@ -676,6 +682,7 @@ extern "C" clb_status clb_get_pipeline(clb_handle* h, int* stages, int* rows)
 
 extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y, int* nodes_per_thread)
 {
+    TraceRange trace("clb_autotune");
     try {
         CHECK_H(h);
         DeviceGuard dg(h->device);

@@ -146,13 +146,17 @@ clb_status clb_nusselt(clb_handle *h, int axis, double *nu_out);
  * counterpart; this is a service of the library.)
  * populations: device pointer to a population buffer in this library's layout for (nx, ny,
  * p->storage), e.g. the current buffer that clb_buffers returns; p: that lattice's parameters;
- * stream: the CUDA stream to run on; nu_out: host double, written on success. Synchronous.
+ * stream: the CUDA stream to run on; nu_out: host double, written on success. Synchronous: it
+ * returns after the result has been copied back to the host and the stream has been synchronised.
  * Scratch is a fixed array of CLB_NOALLOC_MAX_ROWS rows of FP64 partial sums that the library keeps
  * in device memory on every device it is used on until the process exits; ny above that limit
  * returns CLB_EINVAL. The first call on a device looks up that array's address (with the device
- * current); make that first call before any stream capture. All calls share the one array, so
- * calls whose kernels overlap on the GPU race: serialise them. Returns CLB_ENAN when the fields are
- * not finite. The result equals clb_nusselt on the same populations. */
+ * current) and keeps it for later calls on that device; make that first call before any stream
+ * capture. A cudaDeviceReset invalidates the kept address: do not call this entry point on a
+ * device again after resetting it. All calls share the one array, so calls whose kernels overlap
+ * on the GPU race: serialise them. Returns CLB_ENAN when the fields are not finite. The result
+ * equals clb_nusselt on the same populations within rounding (bitwise for nx <= 2048; wider rows
+ * are summed in one partial per row here and in several row segments by clb_nusselt). */
 #define CLB_NOALLOC_MAX_ROWS 8192
 clb_status clb_nusselt_noalloc(const void *populations, int nx, int ny, const clb_params *p, int axis,
                                void *stream, double *nu_out);
@@ -247,6 +251,11 @@ clb_status clb_batch_diagnostics(clb_batch *b, const int *axis, double *nu, doub
  * (their tiles leave the launch). steps[k], er[k], status[k] (clb_status) per instance. */
 clb_status clb_batch_run(clb_batch *b, double tol, long max_steps, long interval, long *steps,
                          double *er, int *status);
+/* State of every instance as of the last clb_batch_run or clb_batch_diagnostics: status[k]
+ * (clb_status; CLB_ENAN for an instance whose fields blew up), the residual E_R and the Nusselt
+ * number of its last check, and its steps since init. Host arrays of n entries, any may be NULL.
+ * Reads host bookkeeping only (no device work). */
+clb_status clb_batch_status(clb_batch *b, int *status, double *er, long *steps, double *nu);
 /* Tile shape of the batched launch: threads along x (32..256), rows (block_x * rows <= 256) and
  * nodes per thread (1, 2, 4). Each block steps 1, 2, 4, ... such groups of rows one after another
  * (it fetches its lattice's descriptor once): as many as keep a block at 2048 nodes or fewer and
@@ -264,6 +273,11 @@ clb_status clb_batch_get_launch(clb_batch *b, int *tile_x, int *tile_y, int *nod
  * Serving: requests arrive over time; each is admitted when a slot and enough of the HBM budget
  * are free, stepped together with the other resident requests (one batched launch per step), and
  * retired when E_R < tol or its step cap is reached. Results stay until fetched.
+ * clb_serve_open reserves all the device memory the server uses: the whole budget as one pool
+ * (a request takes the smallest free block that holds its lattice and gives it back at
+ * retirement or cancellation, so fragmentation can delay an admission) and the batched launch's
+ * tables at fixed capacities. Submitting, admitting, stepping, retiring and cancelling then
+ * allocate no device memory.
  */
 typedef struct clb_server clb_server;
 

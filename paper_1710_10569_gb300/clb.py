@@ -103,6 +103,7 @@ _SIGS = {
     "clb_batch_fields": [_VP, _I, _D, _D, _D, _D],
     "clb_batch_diagnostics": [_VP, _P(_I), _D, _D],
     "clb_batch_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D, _P(_I)],
+    "clb_batch_status": [_VP, _P(_I), _D, _P(_L), _D],
     "clb_batch_set_tile": [_VP, _I, _I, _I],
     "clb_batch_autotune": [_VP, _P(_I), _P(_I), _P(_I)],
     "clb_batch_get_launch": [_VP, _P(_I), _P(_I), _P(_I), _P(_I), _P(ctypes.c_long)],
@@ -468,6 +469,15 @@ class Batch:
         _check(lib().clb_batch_run(self._h, float(tol), int(max_steps), int(interval), steps,
                                    _dptr(er), status))
         return np.array(steps[:], dtype=np.int64), er, np.array(status[:], dtype=np.int32)
+
+    def status(self):
+        """(status, residual, steps, Nusselt number) of every instance as of its last check."""
+        n = len(self.problems)
+        status = (ctypes.c_int * n)()
+        steps = (ctypes.c_long * n)()
+        er, nu = np.empty(n), np.empty(n)
+        _check(lib().clb_batch_status(self._h, status, _dptr(er), steps, _dptr(nu)))
+        return (np.array(status[:], dtype=np.int32), er, np.array(steps[:], dtype=np.int64), nu)
 
     def set_tile(self, tile_x: int, tile_y: int = 1, nodes_per_thread: int = 1):
         _check(lib().clb_batch_set_tile(self._h, int(tile_x), int(tile_y), int(nodes_per_thread)))

@@ -1233,8 +1233,11 @@ extern "C" clb_status clb3d_step(clb3d_lattice* h, long n)
 {
     CHECK_H3(h);
     if (n < 0) return set_error(CLB_EINVAL, "n = %ld < 0", n);
+    // both parities are captured on the first chunk (no capture later, mid-stepping)
+    if (n >= kChunk)
+        for (int par = 0; par < 2; ++par)
+            if (!h->graph[par]) CLB_TRY(build_graph3(h, par));
     while (n >= kChunk) {
-        if (!h->graph[h->cur]) CLB_TRY(build_graph3(h, h->cur));
         CLB_CUDA(cudaGraphLaunch(h->graph[h->cur], h->stream));
         n -= kChunk;
         h->steps += kChunk;
@@ -1654,8 +1657,10 @@ extern "C" clb_status clb3d_batch_step(clb3d_batch* b, long n)
     CHECK_B3(b);
     if (n < 0) return set_error(CLB_EINVAL, "n = %ld < 0", n);
     const long total = n;
+    if (n >= kChunk)
+        for (int par = 0; par < 2; ++par)
+            if (!b->graph[par]) CLB_TRY(batch3_graph(b, par));
     while (n >= kChunk) {
-        if (!b->graph[b->parity]) CLB_TRY(batch3_graph(b, b->parity));
         CLB_CUDA(cudaGraphLaunch(b->graph[b->parity], b->stream));
         n -= kChunk;
     }
@@ -1832,22 +1837,23 @@ extern "C" clb_status clb3d_thermal_step(clb3d_thermal* h, long n)
 {
     CHECK_T3(h);
     if (n < 0) return set_error(CLB_EINVAL, "n = %ld < 0", n);
-    while (n >= kChunk) {
-        if (!h->graph[h->cur]) {
-            CLB_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-            clb_status st = CLB_OK;
-            for (int k = 0; k < kChunk && st == CLB_OK; ++k) st = thermal3_launch(h, h->cur ^ (k & 1), h->cap);
-            cudaGraph_t g = nullptr;
-            const cudaError_t e = cudaStreamEndCapture(h->cap, &g);
-            if (st != CLB_OK) {
-                if (g) cudaGraphDestroy(g);
-                return st;
-            }
-            if (e != cudaSuccess) return set_error(CLB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-            const cudaError_t e2 = cudaGraphInstantiate(&h->graph[h->cur], g, 0);
-            cudaGraphDestroy(g);
-            if (e2 != cudaSuccess) return set_error(CLB_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+    for (int par = 0; n >= kChunk && par < 2; ++par) {
+        if (h->graph[par]) continue;
+        CLB_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        clb_status st = CLB_OK;
+        for (int k = 0; k < kChunk && st == CLB_OK; ++k) st = thermal3_launch(h, par ^ (k & 1), h->cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+        if (st != CLB_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
         }
+        if (e != cudaSuccess) return set_error(CLB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        const cudaError_t e2 = cudaGraphInstantiate(&h->graph[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) return set_error(CLB_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+    }
+    while (n >= kChunk) {
         CLB_CUDA(cudaGraphLaunch(h->graph[h->cur], h->stream));
         n -= kChunk;
         h->steps += kChunk;

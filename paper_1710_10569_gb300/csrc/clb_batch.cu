@@ -176,7 +176,7 @@ void carve(Lattice& L, char* base)
 }
 
 template <typename A>
-Member<A> make_member(const Lattice& L, int tile_x, int npt, int tile_begin, int row_begin)
+Member<A> make_member(const Lattice& L, int tile_x, int npt, int tile_begin, int row_begin, double* diag)
 {
     Member<A> m;
     std::memset(&m, 0, sizeof(m));
@@ -185,7 +185,7 @@ Member<A> make_member(const Lattice& L, int tile_x, int npt, int tile_begin, int
     m.buf[1] = L.buf[1];
     m.snap = L.snap;
     m.partial = L.partial;
-    m.diag = L.diag;
+    m.diag = diag;
     m.tiles_x = (L.nx + tile_x * npt - 1) / (tile_x * npt);
     m.tile_begin = tile_begin;
     m.row_begin = row_begin;
@@ -213,7 +213,19 @@ constexpr int kChunk = 32;  // steps per captured graph (even, so the buffers re
 constexpr int kBlockNodes = 2048;
 constexpr int kMinWaves = 8;
 
-// The set of resident lattices and the device tables of the batched launch.
+// Entries of the tile-owner and row-owner tables a lattice adds to the batched launch at most:
+// tiles of one group of rows (more groups per block only merge tiles).
+long tiles_of(int nx, int ny, int tile_x, int tile_y, int npt)
+{
+    return (long)((nx + tile_x * npt - 1) / (tile_x * npt)) * ((ny + tile_y - 1) / tile_y);
+}
+
+constexpr int kDiagStride = 16;  // doubles of diagnostics output per member
+
+// The set of resident lattices and the device tables of the batched launch. Every table is
+// reserved once (reserve) with a fixed capacity, together with pinned host mirrors; a change of
+// membership rewrites the mirrors and copies them to the device in stream order, with no device
+// allocation and no synchronisation of the stream.
 class Ensemble {
 public:
     int storage = CLB_F32;
@@ -226,11 +238,10 @@ public:
 
     ~Ensemble()
     {
-        if (graph) cudaGraphExecDestroy(graph);
-        cudaFree(d_members);
-        cudaFree(d_owner);
-        cudaFree(d_row_owner);
-        if (h_diag) cudaFreeHost(h_diag);
+        drop_graphs();
+        cudaFree(d_tables);
+        if (h_tables) cudaFreeHost(h_tables);
+        if (copied) cudaEventDestroy(copied);
         if (cap) cudaStreamDestroy(cap);
     }
 
@@ -247,8 +258,34 @@ public:
             npt = 2;
         }
         CLB_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        CLB_CUDA(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
         return CLB_OK;
     }
+
+    // One device allocation (and one pinned host mirror) for the member descriptors, the
+    // diagnostics outputs and the tile- and row-owner tables, at the given capacities.
+    clb_status reserve(size_t max_members, size_t max_tiles, size_t max_rows)
+    {
+        cap_members = std::max<size_t>(1, max_members);
+        cap_tiles = std::max<size_t>(1, max_tiles);
+        cap_rows = std::max<size_t>(1, max_rows);
+        const size_t msz = std::max(sizeof(Member<double>), sizeof(Member<float>));
+        off_members = 0;
+        off_diag = align256(cap_members * msz);
+        off_owner = off_diag + align256(cap_members * kDiagStride * sizeof(double));
+        off_rows = off_owner + align256(cap_tiles * sizeof(int));
+        table_bytes = off_rows + align256(cap_rows * sizeof(int));
+        cudaError_t e = cudaMalloc(&d_tables, table_bytes);
+        if (e != cudaSuccess)
+            return set_error(e == cudaErrorMemoryAllocation ? CLB_ENOMEM : CLB_ECUDA, "launch tables (%zu bytes): %s",
+                             table_bytes, cudaGetErrorString(e));
+        e = cudaMallocHost(&h_tables, table_bytes);
+        if (e != cudaSuccess) return set_error(CLB_ENOMEM, "pinned launch tables (%zu bytes): %s", table_bytes, cudaGetErrorString(e));
+        return CLB_OK;
+    }
+
+    size_t capacity_tiles() const { return cap_tiles; }
+    size_t capacity_rows() const { return cap_rows; }
 
     void mark_dirty() { dirty = true; }
 
@@ -273,54 +310,51 @@ public:
         for (int g = 2; g * threads * npt <= kBlockNodes && tiles_with(g) >= kMinWaves * resident; g *= 2) groups = g;
     }
 
-    // Rebuild the tile and row tables for the active members.
+    // Rebuild the tile and row tables for the active members (no allocation, no stream sync).
     clb_status rebuild()
     {
         if (!dirty) return CLB_OK;
-        if (graph) {
-            cudaGraphExecDestroy(graph);
-            graph = nullptr;
-        }
+        drop_graphs();
         active.clear();
         for (Lattice* L : members)
             if (L->active) active.push_back(L);
         choose_groups();
-        std::vector<int> owner, row_owner;
+        const long tiles = tiles_with(groups);
+        long rows = 0;
+        for (const Lattice* L : active) rows += L->ny;
+        if (active.size() > cap_members || (size_t)tiles > cap_tiles || (size_t)rows > cap_rows)
+            return set_error(CLB_ENOMEM, "batched launch tables: %zu members, %ld tiles, %ld rows exceed the reserved "
+                                         "%zu, %zu, %zu", active.size(), tiles, rows, cap_members, cap_tiles, cap_rows);
+        // the mirrors of the previous rebuild may still be in flight to the device
+        CLB_CUDA(cudaEventSynchronize(copied));
         const size_t msz = storage == CLB_F64 ? sizeof(Member<double>) : sizeof(Member<float>);
-        std::vector<char> host(msz * std::max<size_t>(1, active.size()));
-        int tiles = 0, rows = 0;
+        char* hm = (char*)h_tables + off_members;
+        int* owner = (int*)((char*)h_tables + off_owner);
+        int* row_owner = (int*)((char*)h_tables + off_rows);
+        double* ddiag = (double*)((char*)d_tables + off_diag);
+        int t = 0, r = 0;
         for (size_t k = 0; k < active.size(); ++k) {
             const Lattice& L = *active[k];
             const int tx = (L.nx + tile_x * npt - 1) / (tile_x * npt), ty = (L.ny + tile_y * groups - 1) / (tile_y * groups);
             if (storage == CLB_F64) {
-                Member<double> m = make_member<double>(L, tile_x, npt, tiles, rows);
-                std::memcpy(host.data() + k * msz, &m, msz);
+                Member<double> m = make_member<double>(L, tile_x, npt, t, r, ddiag + kDiagStride * k);
+                std::memcpy(hm + k * msz, &m, msz);
             } else {
-                Member<float> m = make_member<float>(L, tile_x, npt, tiles, rows);
-                std::memcpy(host.data() + k * msz, &m, msz);
+                Member<float> m = make_member<float>(L, tile_x, npt, t, r, ddiag + kDiagStride * k);
+                std::memcpy(hm + k * msz, &m, msz);
             }
-            owner.insert(owner.end(), (size_t)tx * ty, int(k));
-            row_owner.insert(row_owner.end(), (size_t)L.ny, int(k));
-            tiles += tx * ty;
-            rows += L.ny;
+            std::fill(owner + t, owner + t + tx * ty, int(k));
+            std::fill(row_owner + r, row_owner + r + L.ny, int(k));
+            t += tx * ty;
+            r += L.ny;
         }
-        ntiles = tiles;
-        nrows = rows;
-        CLB_TRY(ensure(d_members, members_cap, host.size()));
-        CLB_TRY(ensure(d_owner, owner_cap, std::max<size_t>(1, owner.size()) * sizeof(int)));
-        CLB_TRY(ensure(d_row_owner, row_cap, std::max<size_t>(1, row_owner.size()) * sizeof(int)));
+        ntiles = t;
+        nrows = r;
         if (!active.empty()) {
-            CLB_CUDA(cudaMemcpyAsync(d_members, host.data(), host.size(), cudaMemcpyHostToDevice, stream));
-            CLB_CUDA(cudaMemcpyAsync(d_owner, owner.data(), owner.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
-            CLB_CUDA(cudaMemcpyAsync(d_row_owner, row_owner.data(), row_owner.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
-            // the host vectors die at return: wait for the copies
-            CLB_CUDA(cudaStreamSynchronize(stream));
-        }
-        if (h_diag_cap < active.size()) {
-            if (h_diag) cudaFreeHost(h_diag);
-            h_diag = nullptr;
-            CLB_CUDA(cudaMallocHost((void**)&h_diag, std::max<size_t>(1, active.size()) * 16 * sizeof(double)));
-            h_diag_cap = active.size();
+            CLB_CUDA(cudaMemcpyAsync((char*)d_tables + off_members, hm, active.size() * msz, cudaMemcpyHostToDevice, stream));
+            CLB_CUDA(cudaMemcpyAsync((char*)d_tables + off_owner, owner, (size_t)t * sizeof(int), cudaMemcpyHostToDevice, stream));
+            CLB_CUDA(cudaMemcpyAsync((char*)d_tables + off_rows, row_owner, (size_t)r * sizeof(int), cudaMemcpyHostToDevice, stream));
+            CLB_CUDA(cudaEventRecord(copied, stream));
         }
         dirty = false;
         return CLB_OK;
@@ -331,10 +365,11 @@ public:
     {
         using A = typename Storage<ST>::A;
         const dim3 block(tile_x, tile_y);
-        const Member<A>* m = (const Member<A>*)d_members;
-        if (npt == 4) k_step_batched<ST, 4><<<ntiles, block, 0, s>>>(m, d_owner, par, groups);
-        else if (npt == 2) k_step_batched<ST, 2><<<ntiles, block, 0, s>>>(m, d_owner, par, groups);
-        else k_step_batched<ST, 1><<<ntiles, block, 0, s>>>(m, d_owner, par, groups);
+        const Member<A>* m = (const Member<A>*)((char*)d_tables + off_members);
+        const int* owner = (const int*)((char*)d_tables + off_owner);
+        if (npt == 4) k_step_batched<ST, 4><<<ntiles, block, 0, s>>>(m, owner, par, groups);
+        else if (npt == 2) k_step_batched<ST, 2><<<ntiles, block, 0, s>>>(m, owner, par, groups);
+        else k_step_batched<ST, 1><<<ntiles, block, 0, s>>>(m, owner, par, groups);
     }
 
     clb_status launch_step(cudaStream_t s, int par)
@@ -353,26 +388,25 @@ public:
     {
         CLB_TRY(rebuild());
         if (active.empty() || n <= 0) return CLB_OK;
-        while (n >= kChunk) {
-            if (!graph || graph_parity != parity) {
-                if (graph) cudaGraphExecDestroy(graph);
-                graph = nullptr;
-                CLB_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-                clb_status st = CLB_OK;
-                for (int k = 0; k < kChunk && st == CLB_OK; ++k) st = launch_step(cap, parity ^ (k & 1));
-                cudaGraph_t g = nullptr;
-                cudaError_t e = cudaStreamEndCapture(cap, &g);
-                if (st != CLB_OK) {
-                    if (g) cudaGraphDestroy(g);
-                    return st;
-                }
-                if (e != cudaSuccess) return set_error(CLB_ECUDA, "capture: %s", cudaGetErrorString(e));
-                e = cudaGraphInstantiate(&graph, g, 0);
-                cudaGraphDestroy(g);
-                if (e != cudaSuccess) return set_error(CLB_ECUDA, "instantiate: %s", cudaGetErrorString(e));
-                graph_parity = parity;
+        // both parities are captured on the first chunk after a membership change
+        for (int par = 0; n >= kChunk && par < 2; ++par) {
+            if (graph[par]) continue;
+            CLB_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            clb_status st = CLB_OK;
+            for (int k = 0; k < kChunk && st == CLB_OK; ++k) st = launch_step(cap, par ^ (k & 1));
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(cap, &g);
+            if (st != CLB_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
             }
-            CLB_CUDA(cudaGraphLaunch(graph, stream));
+            if (e != cudaSuccess) return set_error(CLB_ECUDA, "capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&graph[par], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return set_error(CLB_ECUDA, "instantiate: %s", cudaGetErrorString(e));
+        }
+        while (n >= kChunk) {
+            CLB_CUDA(cudaGraphLaunch(graph[parity], stream));
             for (Lattice* L : active) L->steps += kChunk;
             n -= kChunk;
         }
@@ -385,27 +419,31 @@ public:
     }
 
     // Nu and E_R (snapshot retaken when update) of every active member; sets L->nu, L->er, status.
+    // The outputs of all members come back in one copy.
     clb_status diagnostics(int update)
     {
         CLB_TRY(rebuild());
         if (active.empty()) return CLB_OK;
+        const int* row_owner = (const int*)((char*)d_tables + off_rows);
+        const void* m = (char*)d_tables + off_members;
         switch (storage) {
-        case CLB_F64: k_reduce_rows_batched<ST_F64><<<nrows, kReduceThreads, 0, stream>>>((const Member<double>*)d_members, d_row_owner, parity, update); break;
-        case CLB_F32: k_reduce_rows_batched<ST_F32><<<nrows, kReduceThreads, 0, stream>>>((const Member<float>*)d_members, d_row_owner, parity, update); break;
-        default: k_reduce_rows_batched<ST_F16DEV><<<nrows, kReduceThreads, 0, stream>>>((const Member<float>*)d_members, d_row_owner, parity, update); break;
+        case CLB_F64: k_reduce_rows_batched<ST_F64><<<nrows, kReduceThreads, 0, stream>>>((const Member<double>*)m, row_owner, parity, update); break;
+        case CLB_F32: k_reduce_rows_batched<ST_F32><<<nrows, kReduceThreads, 0, stream>>>((const Member<float>*)m, row_owner, parity, update); break;
+        default: k_reduce_rows_batched<ST_F16DEV><<<nrows, kReduceThreads, 0, stream>>>((const Member<float>*)m, row_owner, parity, update); break;
         }
         CLB_CUDA(cudaGetLastError());
         if (storage == CLB_F64)
-            k_reduce_final_batched<double><<<(int)active.size(), kReduceThreads, 0, stream>>>((const Member<double>*)d_members);
+            k_reduce_final_batched<double><<<(int)active.size(), kReduceThreads, 0, stream>>>((const Member<double>*)m);
         else
-            k_reduce_final_batched<float><<<(int)active.size(), kReduceThreads, 0, stream>>>((const Member<float>*)d_members);
+            k_reduce_final_batched<float><<<(int)active.size(), kReduceThreads, 0, stream>>>((const Member<float>*)m);
         CLB_CUDA(cudaGetLastError());
-        for (size_t k = 0; k < active.size(); ++k)
-            CLB_CUDA(cudaMemcpyAsync(h_diag + 16 * k, active[k]->diag, (RS_N + 2) * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        double* hd = (double*)((char*)h_tables + off_diag);
+        CLB_CUDA(cudaMemcpyAsync(hd, (char*)d_tables + off_diag, active.size() * kDiagStride * sizeof(double),
+                                 cudaMemcpyDeviceToHost, stream));
         CLB_CUDA(cudaStreamSynchronize(stream));
         for (size_t k = 0; k < active.size(); ++k) {
             Lattice* L = active[k];
-            const double* d = h_diag + 16 * k;
+            const double* d = hd + kDiagStride * k;
             L->nu = d[RS_N];
             L->er = d[RS_N + 1];
             if (d[RS_BAD] > 0) L->status = CLB_ENAN;
@@ -456,53 +494,58 @@ public:
     int ntiles = 0, nrows = 0;
 
 private:
-    clb_status ensure(void*& p, size_t& cap_bytes, size_t need)
-    {
-        if (cap_bytes >= need) return CLB_OK;
-        CLB_CUDA(cudaStreamSynchronize(stream));
-        cudaFree(p);
-        p = nullptr;
-        CLB_CUDA(cudaMalloc(&p, need));
-        cap_bytes = need;
-        return CLB_OK;
-    }
-    template <typename P>
-    clb_status ensure(P*& p, size_t& cap_bytes, size_t need)
-    {
-        void* v = p;
-        clb_status st = ensure(v, cap_bytes, need);
-        p = (P*)v;
-        return st;
-    }
-
     bool dirty = true;
     std::vector<Lattice*> active;
-    void* d_members = nullptr;
-    size_t members_cap = 0;
-    int* d_owner = nullptr;
-    size_t owner_cap = 0;
-    int* d_row_owner = nullptr;
-    size_t row_cap = 0;
-    double* h_diag = nullptr;
-    size_t h_diag_cap = 0;
-    cudaGraphExec_t graph = nullptr;
-    int graph_parity = 0;
+    void* d_tables = nullptr;  // members | diagnostics outputs | tile owners | row owners
+    void* h_tables = nullptr;  // pinned mirror of the same layout
+    size_t off_members = 0, off_diag = 0, off_owner = 0, off_rows = 0, table_bytes = 0;
+    size_t cap_members = 0, cap_tiles = 0, cap_rows = 0;
+    cudaEvent_t copied = nullptr;  // recorded after the last copy of the mirrors
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+    void drop_graphs()
+    {
+        for (auto& g : graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
 };
 
-// Stage host fields into device memory (double [4][N]) and initialise a member.
-clb_status init_from_host(Ensemble& E, Lattice* L, double* stage, const double* rho, const double* ux,
-                          const double* uy, const double* T)
+// Device addresses where the four host fields of a member are staged for its initialisation, and
+// where its fields are written for the host at retirement: rho, u_x, u_y in the population buffer
+// that the next step would write (at least 28 bytes per node in every storage form, 24 needed)
+// and T in the T slot of the residual snapshot, which k_fields rewrites only after k_init has read
+// it (stream order). No extra device memory is needed.
+void own_stage(const Lattice* L, int parity, double* dev[4])
+{
+    const size_t N = (size_t)L->nx * L->ny;
+    double* spare = (double*)L->buf[parity ^ 1];
+    dev[0] = spare;
+    dev[1] = spare + N;
+    dev[2] = spare + 2 * N;
+    dev[3] = L->snap + 2 * N;
+}
+
+// Copy host fields (any may be NULL) into the member's own staging addresses and initialise it.
+// With `wait`, returns after the copies are done (the caller may then reuse its host arrays even
+// when they are pinned); otherwise the copies are only ordered on the stream.
+clb_status init_from_host(Ensemble& E, Lattice* L, const double* rho, const double* ux, const double* uy,
+                          const double* T, bool wait)
 {
     const size_t N = (size_t)L->nx * L->ny;
     const double* src[4] = {rho, ux, uy, T};
+    double* stage[4];
+    own_stage(L, E.parity, stage);
     const double* dev[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int k = 0; k < 4; ++k)
         if (src[k]) {
-            CLB_CUDA(cudaMemcpyAsync(stage + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, E.stream));
-            dev[k] = stage + k * N;
+            CLB_CUDA(cudaMemcpyAsync(stage[k], src[k], N * sizeof(double), cudaMemcpyHostToDevice, E.stream));
+            dev[k] = stage[k];
         }
     CLB_TRY(E.init_member(L, dev[0], dev[1], dev[2], dev[3]));
-    CLB_CUDA(cudaStreamSynchronize(E.stream));
+    if (wait) CLB_CUDA(cudaStreamSynchronize(E.stream));
     return CLB_OK;
 }
 
@@ -514,7 +557,6 @@ struct clb_batch {
     Ensemble E;
     std::vector<std::unique_ptr<Lattice>> lat;
     char* mem = nullptr;
-    double* stage = nullptr;
     int device = 0;
 };
 
@@ -526,19 +568,19 @@ extern "C" clb_status clb_batch_create(int n, const int* nx, const int* ny, cons
         *out = nullptr;
         if (n <= 0 || !nx || !ny || !p) return set_error(CLB_EINVAL, "need n > 0 and nx, ny, p arrays");
         const int storage = p[0].storage;
-        size_t total = 0, max_nodes = 0;
+        size_t total = 0, max_tiles = 0, rows = 0;
         for (int k = 0; k < n; ++k) {
             CLB_TRY(validate(nx[k], ny[k], &p[k]));
             if (p[k].storage != storage) return set_error(CLB_EINVAL, "instance %d: all instances need the same storage", k);
             total += lattice_bytes(nx[k], ny[k], storage);
-            max_nodes = std::max(max_nodes, (size_t)nx[k] * ny[k]);
+            max_tiles += tiles_of(nx[k], ny[k], 32, 1, 1);  // the smallest tile clb_batch_set_tile accepts
+            rows += ny[k];
         }
         auto b = std::make_unique<clb_batch>();
         cudaGetDevice(&b->device);
         CLB_TRY(b->E.init(storage, (cudaStream_t)stream));
-        const size_t stage_bytes = align256(4 * max_nodes * sizeof(double));
-        CLB_CUDA(cudaMalloc((void**)&b->mem, total + stage_bytes));
-        b->stage = (double*)(b->mem + total);
+        CLB_TRY(b->E.reserve(n, max_tiles, rows));
+        CLB_CUDA(cudaMalloc((void**)&b->mem, total));
         CLB_CUDA(cudaMemsetAsync(b->mem, 0, total, b->E.stream));
         size_t off = 0;
         for (int k = 0; k < n; ++k) {
@@ -588,7 +630,7 @@ extern "C" clb_status clb_batch_init_fields(clb_batch* b, int k, const double* r
         }
         L->status = CLB_OK;
         L->er = INFINITY;
-        return init_from_host(b->E, L, b->stage, rho, ux, uy, T);
+        return init_from_host(b->E, L, rho, ux, uy, T, true);
     } catch (const std::bad_alloc&) {
         return host_alloc_failed();
     }
@@ -613,8 +655,23 @@ extern "C" clb_status clb_batch_fields(clb_batch* b, int k, double* rho, double*
         Lattice* L = b->lat[k].get();
         const size_t N = (size_t)L->nx * L->ny;
         double* host[4] = {rho, ux, uy, T};
+        // the fields go through the spare population buffer only (the snapshot stays intact)
+        double* spare = (double*)L->buf[b->E.parity ^ 1];
         double* dev[4];
-        for (int i = 0; i < 4; ++i) dev[i] = host[i] ? b->stage + i * N : nullptr;
+        for (int i = 0; i < 4; ++i) dev[i] = nullptr;
+        for (int i = 0, slot = 0; i < 4; ++i)
+            if (host[i]) dev[i] = spare + (slot++ % 3) * N;
+        // at most three fields fit the spare buffer at once: fetch in two rounds when all four are asked
+        const int n_asked = (rho != nullptr) + (ux != nullptr) + (uy != nullptr) + (T != nullptr);
+        if (n_asked == 4) {
+            CLB_TRY(b->E.fields(L, dev[0], dev[1], dev[2], nullptr));
+            for (int i = 0; i < 3; ++i)
+                CLB_CUDA(cudaMemcpyAsync(host[i], dev[i], N * sizeof(double), cudaMemcpyDeviceToHost, b->E.stream));
+            CLB_TRY(b->E.fields(L, nullptr, nullptr, nullptr, spare));
+            CLB_CUDA(cudaMemcpyAsync(host[3], spare, N * sizeof(double), cudaMemcpyDeviceToHost, b->E.stream));
+            CLB_CUDA(cudaStreamSynchronize(b->E.stream));
+            return CLB_OK;
+        }
         CLB_TRY(b->E.fields(L, dev[0], dev[1], dev[2], dev[3]));
         for (int i = 0; i < 4; ++i)
             if (host[i]) CLB_CUDA(cudaMemcpyAsync(host[i], dev[i], N * sizeof(double), cudaMemcpyDeviceToHost, b->E.stream));
@@ -696,6 +753,19 @@ extern "C" clb_status clb_batch_run(clb_batch* b, double tol, long max_steps, lo
     } catch (const std::bad_alloc&) {
         return host_alloc_failed();
     }
+}
+
+extern "C" clb_status clb_batch_status(clb_batch* b, int* status, double* er, long* steps, double* nu)
+{
+    if (!b) return set_error(CLB_EINVAL, "batch is NULL");
+    for (size_t k = 0; k < b->lat.size(); ++k) {
+        const Lattice* L = b->lat[k].get();
+        if (status) status[k] = L->status;
+        if (er) er[k] = L->er;
+        if (steps) steps[k] = L->steps;
+        if (nu) nu[k] = L->nu;
+    }
+    return CLB_OK;
 }
 
 extern "C" clb_status clb_batch_set_tile(clb_batch* b, int tile_x, int tile_y, int nodes_per_thread)
@@ -821,21 +891,84 @@ struct Request {
     std::vector<double> init;  // 4 * N host copy, released at admission
     long cap;
     double tol;
+    long tiles = 0;  // entries of the tile-owner table at one group of rows per block
     int done = 0;
     std::vector<double> result;  // 4 * N after retirement
 };
+
+// Best-fit sub-allocation of one device reservation in 256-byte blocks; a released block merges
+// with its free neighbours. Host bookkeeping only: taking and giving blocks never calls CUDA.
+class Pool {
+public:
+    ~Pool() { cudaFree(base); }
+
+    clb_status open(size_t bytes)
+    {
+        size = bytes / 256 * 256;
+        const cudaError_t e = cudaMalloc((void**)&base, size);
+        if (e != cudaSuccess)
+            return set_error(e == cudaErrorMemoryAllocation ? CLB_ENOMEM : CLB_ECUDA, "HBM budget of %zu bytes: %s",
+                             size, cudaGetErrorString(e));
+        free_[0] = size;
+        return CLB_OK;
+    }
+
+    // The smallest free block that holds `bytes` (rounded up to 256), or NULL.
+    char* take(size_t bytes)
+    {
+        bytes = align256(bytes);
+        auto best = free_.end();
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= bytes && (best == free_.end() || it->second < best->second)) best = it;
+        if (best == free_.end()) return nullptr;
+        const size_t off = best->first, have = best->second;
+        free_.erase(best);
+        if (have > bytes) free_[off + bytes] = have - bytes;
+        used_[off] = bytes;
+        return base + off;
+    }
+
+    void give(char* p)
+    {
+        auto u = used_.find((size_t)(p - base));
+        if (u == used_.end()) return;
+        size_t off = u->first, bytes = u->second;
+        used_.erase(u);
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && next->first == off + bytes) {
+            bytes += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+
+private:
+    char* base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_, used_;  // offset -> bytes
+};
 }  // namespace
 
+// The server's device memory is reserved once at clb_serve_open: the whole HBM budget as a pool
+// that resident lattices are carved from, and the launch tables at fixed capacities. Admission,
+// stepping and retirement then allocate nothing on the device.
 struct clb_server {
     Ensemble E;
+    Pool pool;
     size_t budget = 0, used = 0;
+    long tiles_used = 0, rows_used = 0;
     int max_slots = 0;
     long next_id = 1;
     std::deque<Request*> queue;
     std::map<long, std::unique_ptr<Request>> all;
     std::vector<Request*> running;
-    double* stage = nullptr;
-    size_t stage_nodes = 0;
 };
 
 extern "C" clb_status clb_serve_open(size_t hbm_budget_bytes, int max_slots, int storage, void* stream,
@@ -844,12 +977,18 @@ extern "C" clb_status clb_serve_open(size_t hbm_budget_bytes, int max_slots, int
     try {
         if (!out) return set_error(CLB_EINVAL, "out is NULL");
         *out = nullptr;
-        if (max_slots <= 0 || hbm_budget_bytes == 0) return set_error(CLB_EINVAL, "need max_slots > 0 and a budget");
+        if (max_slots <= 0 || hbm_budget_bytes < 256) return set_error(CLB_EINVAL, "need max_slots > 0 and a budget");
         if (storage < CLB_F64 || storage > CLB_F16DEV) return set_error(CLB_EINVAL, "bad storage");
         auto s = std::make_unique<clb_server>();
         s->budget = hbm_budget_bytes;
         s->max_slots = max_slots;
         CLB_TRY(s->E.init(storage, (cudaStream_t)stream));
+        // Table capacities: a resident set this large in tiles or rows is far beyond what the
+        // budget holds in lattices of ordinary shape; a request that would overflow them waits.
+        const size_t tiles_cap = std::max<size_t>(size_t(1) << 20, hbm_budget_bytes / 16384);
+        const size_t rows_cap = std::max<size_t>(size_t(1) << 18, hbm_budget_bytes / 65536);
+        CLB_TRY(s->E.reserve(max_slots, tiles_cap, rows_cap));
+        CLB_TRY(s->pool.open(hbm_budget_bytes));
         *out = s.release();
         return CLB_OK;
     } catch (const std::bad_alloc&) {
@@ -861,8 +1000,6 @@ extern "C" void clb_serve_close(clb_server* s)
 {
     if (!s) return;
     cudaStreamSynchronize(s->E.stream);
-    for (Request* r : s->running) cudaFree(r->L->mem);
-    if (s->stage) cudaFree(s->stage);
     delete s;
 }
 
@@ -879,6 +1016,9 @@ extern "C" clb_status clb_serve_submit(clb_server* s, int nx, int ny, const clb_
         if (step_cap < 0) return set_error(CLB_EINVAL, "step_cap < 0");
         const size_t need = lattice_bytes(nx, ny, p->storage);
         if (need > s->budget) return set_error(CLB_ENOMEM, "request needs %zu bytes > budget %zu", need, s->budget);
+        const long tiles = tiles_of(nx, ny, s->E.tile_x, s->E.tile_y, s->E.npt);
+        if ((size_t)tiles > s->E.capacity_tiles() || (size_t)ny > s->E.capacity_rows())
+            return set_error(CLB_ENOMEM, "request of %d x %d exceeds the server's launch tables", nx, ny);
         auto r = std::make_unique<Request>();
         r->id = s->next_id++;
         r->L = std::make_unique<Lattice>();
@@ -889,6 +1029,7 @@ extern "C" clb_status clb_serve_submit(clb_server* s, int nx, int ny, const clb_
         r->L->bytes = need;
         r->cap = step_cap;
         r->tol = tol;
+        r->tiles = tiles;
         const size_t N = (size_t)nx * ny;
         r->init.assign(4 * N, 0.0);
         const double* src[4] = {rho, ux, uy, T};
@@ -906,40 +1047,53 @@ extern "C" clb_status clb_serve_submit(clb_server* s, int nx, int ny, const clb_
     }
 }
 
+namespace {
+// Return a resident request's memory and table entries to the server.
+void release(clb_server* s, Request* r)
+{
+    Lattice* L = r->L.get();
+    s->E.members.erase(std::find(s->E.members.begin(), s->E.members.end(), L));
+    s->E.mark_dirty();
+    s->pool.give(L->mem);
+    L->mem = nullptr;
+    s->used -= L->bytes;
+    s->tiles_used -= r->tiles;
+    s->rows_used -= L->ny;
+}
+}  // namespace
+
 extern "C" clb_status clb_serve_progress(clb_server* s, long chunk, int* active, int* queued)
 {
     TraceRange trace("clb_serve_progress");
     try {
         if (!s) return set_error(CLB_EINVAL, "server is NULL");
         if (chunk <= 0 || chunk % 2) return set_error(CLB_EINVAL, "chunk must be even and > 0");
-        // admission: first fit over the queue in arrival order
+        // admission: first fit over the queue in arrival order, into the pool and the tables
         for (auto it = s->queue.begin(); it != s->queue.end();) {
             Request* r = *it;
             if ((int)s->running.size() >= s->max_slots) break;
-            if (s->used + r->L->bytes > s->budget) {
+            if ((size_t)(s->tiles_used + r->tiles) > s->E.capacity_tiles() ||
+                (size_t)(s->rows_used + r->L->ny) > s->E.capacity_rows()) {
                 ++it;
                 continue;
             }
-            char* mem = nullptr;
-            cudaError_t e = cudaMalloc((void**)&mem, r->L->bytes);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                break;  // device memory is short of the budget; retry next round
+            char* mem = s->pool.take(r->L->bytes);
+            if (!mem) {
+                ++it;
+                continue;
             }
             r->L->mem = mem;
             carve(*r->L, mem);
             const size_t N = (size_t)r->L->nx * r->L->ny;
-            if (s->stage_nodes < N) {
-                cudaStreamSynchronize(s->E.stream);
-                cudaFree(s->stage);
-                s->stage = nullptr;
-                CLB_CUDA(cudaMalloc((void**)&s->stage, 4 * N * sizeof(double)));
-                s->stage_nodes = N;
-            }
+            // keep the padding between rows and planes defined (it is never read)
+            CLB_CUDA(cudaMemsetAsync(mem, 0, 2 * buffer_slot_bytes(r->L->nx, r->L->ny, r->L->p.storage), s->E.stream));
             const double* h = r->init.data();
-            CLB_TRY(init_from_host(s->E, r->L.get(), s->stage, h, h + N, h + 2 * N, h + 3 * N));
+            // pageable source: the copies have left the host array when they return
+            CLB_TRY(init_from_host(s->E, r->L.get(), h, h + N, h + 2 * N, h + 3 * N, false));
             std::vector<double>().swap(r->init);
             s->used += r->L->bytes;
+            s->tiles_used += r->tiles;
+            s->rows_used += r->L->ny;
             s->running.push_back(r);
             s->E.members.push_back(r->L.get());
             s->E.mark_dirty();
@@ -948,27 +1102,28 @@ extern "C" clb_status clb_serve_progress(clb_server* s, long chunk, int* active,
         if (!s->running.empty()) {
             CLB_TRY(s->E.step(chunk));
             CLB_TRY(s->E.diagnostics(1));
-            std::vector<Request*> keep;
+            std::vector<Request*> keep, leaving;
             for (Request* r : s->running) {
                 Lattice* L = r->L.get();
-                if (L->status != CLB_OK || L->er < r->tol || L->steps >= r->cap) {
-                    const size_t N = (size_t)L->nx * L->ny;
-                    r->result.assign(4 * N, 0.0);
-                    double* dev = nullptr;
-                    if (s->stage_nodes < N) return set_error(CLB_ECUDA, "staging buffer too small");
-                    dev = s->stage;
-                    CLB_TRY(s->E.fields(L, dev, dev + N, dev + 2 * N, dev + 3 * N));
-                    CLB_CUDA(cudaMemcpyAsync(r->result.data(), dev, 4 * N * sizeof(double), cudaMemcpyDeviceToHost, s->E.stream));
-                    CLB_CUDA(cudaStreamSynchronize(s->E.stream));
-                    cudaFree(L->mem);
-                    L->mem = nullptr;
-                    s->used -= L->bytes;
-                    r->done = 1;
-                    s->E.members.erase(std::find(s->E.members.begin(), s->E.members.end(), L));
-                    s->E.mark_dirty();
-                } else {
-                    keep.push_back(r);
-                }
+                if (L->status != CLB_OK || L->er < r->tol || L->steps >= r->cap) leaving.push_back(r);
+                else keep.push_back(r);
+            }
+            // fields of every retiring request through its own spare regions, one sync for all
+            for (Request* r : leaving) {
+                Lattice* L = r->L.get();
+                const size_t N = (size_t)L->nx * L->ny;
+                double* dev[4];
+                own_stage(L, s->E.parity, dev);
+                r->result.assign(4 * N, 0.0);
+                CLB_TRY(s->E.fields(L, dev[0], dev[1], dev[2], dev[3]));
+                for (int k = 0; k < 4; ++k)
+                    CLB_CUDA(cudaMemcpyAsync(r->result.data() + k * N, dev[k], N * sizeof(double), cudaMemcpyDeviceToHost,
+                                             s->E.stream));
+            }
+            if (!leaving.empty()) CLB_CUDA(cudaStreamSynchronize(s->E.stream));
+            for (Request* r : leaving) {
+                release(s, r);
+                r->done = 1;
             }
             s->running.swap(keep);
         }
@@ -991,14 +1146,9 @@ extern "C" clb_status clb_serve_cancel(clb_server* s, long req_id)
         if (q != s->queue.end()) s->queue.erase(q);
         auto run = std::find(s->running.begin(), s->running.end(), r);
         if (run != s->running.end()) {
-            // no kernel of this server is in flight between calls; release the slot and its memory
-            CLB_CUDA(cudaStreamSynchronize(s->E.stream));
-            Lattice* L = r->L.get();
-            s->E.members.erase(std::find(s->E.members.begin(), s->E.members.end(), L));
-            s->E.mark_dirty();
-            cudaFree(L->mem);
-            L->mem = nullptr;
-            s->used -= L->bytes;
+            // the slot and its memory return to the server at once; work enqueued later on the
+            // server's stream runs after everything that used them
+            release(s, r);
             s->running.erase(run);
         }
         s->all.erase(it);

@@ -428,8 +428,13 @@ extern "C" clb_status clb_step(clb_handle* h, long n)
     CHECK_H(h);
     if (n < 0) return set_error(CLB_EINVAL, "n = %ld < 0", n);
     DeviceGuard dg(h->device);
+    // Both parities are captured on the first chunk: a later odd number of single launches then
+    // switches to the other graph without a capture in the middle of the caller's stepping.
+    if (n >= kGraphChunk && (!h->graph[0] || !h->graph[1])) {
+        for (int par = 0; par < 2; ++par)
+            if (!h->graph[par]) CLB_TRY(build_graph(h, par));
+    }
     while (n >= kGraphChunk) {
-        if (!h->graph[h->cur]) CLB_TRY(build_graph(h, h->cur));
         CLB_CUDA(cudaGraphLaunch(h->graph[h->cur], h->stream));
         n -= kGraphChunk;
         h->steps += kGraphChunk;

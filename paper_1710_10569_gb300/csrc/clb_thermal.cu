@@ -353,22 +353,24 @@ extern "C" clb_status clb_thermal_step(clb_thermal* h, long n)
 {
     if (!h) return set_error(CLB_EINVAL, "handle is NULL");
     if (n < 0) return set_error(CLB_EINVAL, "n < 0");
-    while (n >= kChunkT) {
-        if (!h->graph[h->cur]) {
-            CLB_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-            clb_status st = CLB_OK;
-            for (int k = 0; k < kChunkT && st == CLB_OK; ++k) st = thermal_launch(h, h->cur ^ (k & 1), h->cap);
-            cudaGraph_t g = nullptr;
-            cudaError_t e = cudaStreamEndCapture(h->cap, &g);
-            if (st != CLB_OK) {
-                if (g) cudaGraphDestroy(g);
-                return st;
-            }
-            if (e != cudaSuccess) return set_error(CLB_ECUDA, "capture: %s", cudaGetErrorString(e));
-            e = cudaGraphInstantiate(&h->graph[h->cur], g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return set_error(CLB_ECUDA, "instantiate: %s", cudaGetErrorString(e));
+    // both parities are captured on the first chunk (no capture later, mid-stepping)
+    for (int par = 0; n >= kChunkT && par < 2; ++par) {
+        if (h->graph[par]) continue;
+        CLB_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        clb_status st = CLB_OK;
+        for (int k = 0; k < kChunkT && st == CLB_OK; ++k) st = thermal_launch(h, par ^ (k & 1), h->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+        if (st != CLB_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
         }
+        if (e != cudaSuccess) return set_error(CLB_ECUDA, "capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&h->graph[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return set_error(CLB_ECUDA, "instantiate: %s", cudaGetErrorString(e));
+    }
+    while (n >= kChunkT) {
         CLB_CUDA(cudaGraphLaunch(h->graph[h->cur], h->stream));
         n -= kChunkT;
         h->steps += kChunkT;

@@ -120,7 +120,7 @@ def test_batch_matches_oracle_and_single_lattice(clb):
         o.step(50)
         exp = o.fields()
         got = b.fields(k)
-        for a, e in zip(got[1:], exp[1:]):
+        for a, e in zip(got, exp):
             assert np.max(np.abs(a - e)) <= 1e-12 * max(np.max(np.abs(e)), 1e-300)
         single = clb.Lattice.from_problem(prob)
         single.step(50)
@@ -231,3 +231,41 @@ def test_widest_lattice(clb, storage):
     exp = o.fields()
     for a, e in zip(got[1:], exp[1:]):
         assert np.max(np.abs(a - e)) <= (1e-12 if storage == F64 else 1e-5) * max(np.max(np.abs(e)), 0.05)
+
+
+def test_serve_pool_reuses_memory_one_at_a_time(clb):
+    """A budget that holds one of these lattices but not two: requests are admitted one after
+    another into the same pool memory, and each result still equals the problem alone (nothing of
+    a retired request leaks into the next one's state)."""
+    # 128 x 96 in FP32: two population buffers of 14 planes x 96 rows x 512 bytes (1.38 MB) and a
+    # 0.3 MB snapshot, about 1.7 MB in all; the 2.5 MB budget holds one such lattice
+    probs = [W.cavity(128, Ra=1e4, ny=96, seed=k, storage=F32) for k in range(4)]
+    srv = clb.Server(hbm_budget_bytes=5 << 19, max_slots=4, storage=F32)
+    ids = [srv.submit(p, step_cap=96, tol=0.0) for p in probs]
+    most = 0
+    for _ in range(40):
+        active, queued = srv.progress(32)
+        most = max(most, active)
+        if not active and not queued:
+            break
+    assert most == 1
+    for rid, prob in zip(ids, probs):
+        done, nu, steps, er = srv.poll(rid)
+        assert done and steps == 96
+        alone = clb.Batch([prob])
+        alone.step(96)
+        for a, b in zip(srv.fetch(rid, prob.ny, prob.nx), alone.fields(0)):
+            assert np.array_equal(a, b), prob.name
+
+
+def test_batch_status_reports_the_last_check(clb):
+    probs = mixed_problems(F64, count=3)
+    b = clb.Batch(probs)
+    steps, er, status = b.run(0.0, 300, 100)
+    st, er2, steps2, nu2 = b.status()
+    assert (st == status).all() and (steps2 == steps).all()
+    np.testing.assert_array_equal(er2, er)
+    for k, prob in enumerate(probs):
+        single = clb.Lattice.from_problem(prob)
+        single.step(300)
+        assert nu2[k] == pytest.approx(single.nusselt(prob.nu_axis), rel=1e-12, abs=1e-14)

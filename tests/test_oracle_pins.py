@@ -434,6 +434,31 @@ def test_nusselt_and_residual_definitions():
     assert r1 == pytest.approx(0.1 / 1.1, rel=1e-12)
 
 
+def test_residual_floor_branch_by_hand():
+    """The floor N (1e-3 X_ref)^2 of the residual's denominator, worked by hand on a 2 x 2 lattice
+    (N = 4) with u_ref = 0.1 and dT_ref = 1, so that a wrong factor, exponent or node count fails.
+    Velocities of 1e-6 (sum |u|^2 = 8e-12) sit below the velocity floor 4 (1e-4)^2 = 4e-8; one u_x
+    changing by 1e-6 gives sqrt(1e-12 / 4e-8) = 5e-3. T = 1e-4 everywhere (sum T^2 = 4e-8) sits
+    below the temperature floor 4 (1e-3)^2 = 4e-6; one T changing by 2e-4 gives
+    sqrt(4e-8 / 4e-6) = 0.1. With T = 1 (sum 4, above its floor) the same change gives
+    sqrt(4e-8 / 4) = 1e-4 and the velocity's 5e-3 is the larger."""
+    u = np.full((2, 2), 1e-6)
+    u2 = u.copy()
+    u2[0, 1] += 1e-6
+    for T_level, expect in ((1e-4, 0.1), (1.0, 5e-3)):
+        T = np.full((2, 2), T_level)
+        T2 = T.copy()
+        T2[1, 0] += 2e-4
+        got = oracle.residual((u, u, T), (u2, u, T2), 0.1, 1.0)
+        assert got == pytest.approx(expect, rel=1e-9)
+    # the floor does not apply when X_ref = 0: the ratio is then relative to the fields alone
+    T = np.full((2, 2), 1e-4)
+    T2 = T.copy()
+    T2[1, 0] += 2e-4
+    got = oracle.residual((u, u, T), (u, u, T2), 0.0, 0.0)
+    assert got == pytest.approx(math.sqrt(4e-8 / (3 * 1e-8 + 9e-8)), rel=1e-9)
+
+
 # ----------------------------------------------------------------------------- thermal-only mode
 
 

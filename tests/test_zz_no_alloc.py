@@ -3,7 +3,9 @@ example a monitor in a server whose HBM is already committed to resident lattice
 must not let cudaMalloc/cudaFree synchronise the device). It uses a fixed scratch array that the
 library keeps in device memory, and must agree with clb_nusselt, which works through a handle and
 its own scratch. Called through the C ABI, twice in a row on the same state and once more after
-stepping, so that a stale result left in the shared array would show."""
+stepping, so that a stale result left in the shared array would show; on halfway and wet walls and
+on rows wider than the handle's 2048-node diagnostics segments; and once directly against the
+oracle."""
 import ctypes
 
 import pytest
@@ -35,13 +37,23 @@ def noalloc_nusselt(clb, lat, prob):
     return out.value
 
 
-@pytest.mark.parametrize("storage", [F64, F32, F16])
-@pytest.mark.parametrize("kind", ["cavity", "rb"])
-def test_noalloc_nusselt_equals_handle_nusselt(clb, storage, kind):
+def problem(kind, storage):
     if kind == "cavity":
-        prob = W.cavity(96, Ra=1e4, ny=80, storage=storage)
-    else:
-        prob = W.rayleigh_benard(130, 61, Ra=5e3, storage=storage)
+        return W.cavity(96, Ra=1e4, ny=80, storage=storage)
+    if kind == "rb":
+        return W.rayleigh_benard(130, 61, Ra=5e3, storage=storage)
+    if kind == "wet":
+        # the paper's own walls: wall rows at half weight in the average, H = ny - 1
+        return W.rayleigh_benard_table1(5000.0, storage=storage, wet=True)
+    # rows wider than one 2048-node segment of the handle's diagnostics pass, which then sums
+    # each row in several partials: equal within rounding, not bitwise
+    return W.rayleigh_benard(4100, 8, Ra=2e3, storage=storage)
+
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+@pytest.mark.parametrize("kind", ["cavity", "rb", "wet", "wide"])
+def test_noalloc_nusselt_equals_handle_nusselt(clb, storage, kind):
+    prob = problem(kind, storage)
     lat = clb.Lattice.from_problem(prob)
     lat.step(300)
     expect = lat.nusselt(prob.nu_axis)
@@ -53,6 +65,21 @@ def test_noalloc_nusselt_equals_handle_nusselt(clb, storage, kind):
     expect2 = lat.nusselt(prob.nu_axis)
     assert expect2 != expect
     assert noalloc_nusselt(clb, lat, prob) == pytest.approx(expect2, rel=1e-12, abs=1e-14)
+    lat.close()
+
+
+def test_noalloc_nusselt_matches_the_oracle(clb):
+    """Directly against the oracle's Eq. 29 on the oracle's own fields (FP64 storage)."""
+    import oracle
+    prob = W.cavity(40, Ra=2e4, ny=32, storage=F64)
+    lat = clb.Lattice.from_problem(prob)
+    lat.step(150)
+    ref = oracle.Oracle.from_problem(prob)
+    ref.step(150)
+    _, ux, uy, T = ref.fields()
+    expect = oracle.nusselt(ux, uy, T, prob.params, prob.nu_axis)
+    assert noalloc_nusselt(clb, lat, prob) == pytest.approx(expect, rel=1e-11, abs=1e-13)
+    lat.close()
 
 
 def test_noalloc_rejects_lattices_beyond_the_fixed_scratch(clb):

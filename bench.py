@@ -516,23 +516,121 @@ def thermal3d_run(steps: int, n: int = 256):
             "bytes_per_node": 68, "achieved_gbs": gbs, "hbm_frac": gbs / peak, "steps": steps, "storage": "f32"}
 
 
-def served_run(storage: int, count: int = 48, step_cap: int = 20000, tol: float = 1e-6, hi: int = 512,
-               hbm_budget_gb: int = 32):
+def served_run(storage: int, count: int = 48, step_cap: int = 500000, tol: float = 1e-6,
+               plain_tol: float = 1e-8, lo: int = 32, hi: int = 128, rb_Ra=(2.5e3, 2.5e4),
+               hbm_budget_gb: int = 32, plain_same_tol: bool = True):
     """A seeded Poisson request trace (mean 50 requests/s; periodic Taylor-Green, side-heated
-    cavity and Rayleigh-Benard; edges log-uniform 64-hi, aspect 1 or 2) served with continuous
-    batching in `storage`, against the plain FP64 one-at-a-time path on the same trace."""
+    cavity (Ra 1e3-1e6) and Rayleigh-Benard (Ra in rb_Ra, where the rolls are steady); edges
+    log-uniform lo-hi, aspect 1 or 2), each request run to steady state: served with continuous
+    batching in `storage` to E_R < tol (FP32 rounding keeps E_R above ~1e-7, so tol sits above that
+    floor), against the plain FP64 one-at-a-time path to E_R < plain_tol on the same trace (and,
+    with plain_same_tol, to the served tolerance as well). The Nusselt numbers of the two paths are
+    compared request by request."""
     from paper_1710_10569_gb300 import serve
-    trace = W.request_trace(count=count, seed=0, rate_hz=50.0, lo=64, hi=hi, storage=storage)
+    trace = W.request_trace(count=count, seed=0, rate_hz=50.0, lo=lo, hi=hi, storage=storage,
+                            rb_Ra_range=rb_Ra)
     s_sum, s_rec = serve.serve_trace(trace, storage, hbm_budget_bytes=hbm_budget_gb << 30, max_slots=256,
                                      chunk=100, step_cap=step_cap, tol=tol)
-    p_sum, p_rec = serve.plain_trace(trace, step_cap=step_cap, tol=tol)
-    return {"requests": count, "edges": [64, hi], "step_cap": step_cap, "tol": tol,
-            "node_updates": float(sum(r["nodes"] * r["steps"] for r in s_rec)),
-            "storage": W.STORAGE_NAMES[storage],
-            "served": s_sum, "plain_f64": p_sum,
-            "speedup_solves_per_s": s_sum["solves_per_s"] / p_sum["solves_per_s"],
-            "p99_ratio_plain_over_served": p_sum["p99_s"] / s_sum["p99_s"],
-            "nusselt_vs_plain_f64": serve.nusselt_agreement(s_rec, p_rec, tol)}
+    p_sum, p_rec = serve.plain_trace(trace, step_cap=step_cap, tol=plain_tol)
+    out = {"requests": count, "edges": [lo, hi], "rayleigh_benard_Ra": list(rb_Ra), "step_cap": step_cap,
+           "tol": tol, "plain_tol": plain_tol,
+           "node_updates": float(sum(r["nodes"] * r["steps"] for r in s_rec)),
+           "storage": W.STORAGE_NAMES[storage],
+           "served": s_sum, "plain_f64": p_sum,
+           "speedup_solves_per_s": s_sum["solves_per_s"] / p_sum["solves_per_s"],
+           "p99_ratio_plain_over_served": p_sum["p99_s"] / s_sum["p99_s"],
+           "nusselt_vs_plain_f64": serve.nusselt_agreement(s_rec, p_rec, tol, plain_tol)}
+    if plain_same_tol and plain_tol != tol:
+        q_sum, _ = serve.plain_trace(trace, step_cap=step_cap, tol=tol)
+        out["plain_f64_same_tol"] = q_sum
+        out["speedup_solves_per_s_same_tol"] = s_sum["solves_per_s"] / q_sum["solves_per_s"]
+        out["p99_ratio_same_tol"] = q_sum["p99_s"] / s_sum["p99_s"]
+    return out
+
+
+def batched_steady_run(count: int = 256, tol: float = 1e-6, plain_tol: float = 1e-8, cap: int = 500000,
+                       subset: int = 8, subset_max_edge: int = 160):
+    """The 256 uneven cavities (FP32) run to steady state with retirement (clb_batch_run: every 100
+    steps the instances with E_R < tol or at the cap leave the launch), against the plain FP64
+    one-at-a-time path to E_R < plain_tol on a seeded subset of `subset` instances drawn from those
+    with edges <= subset_max_edge (the cheapest for the plain path, so its solves/s is on the high
+    side). The Nusselt numbers of the subset are compared between the two paths."""
+    from paper_1710_10569_gb300 import clb
+    probs = W.batch_cavities(count, seed=0, storage=W.STORAGE_F32)
+    b = clb.Batch(probs)
+    t0 = time.perf_counter()
+    steps, er, status = b.run(tol, cap, DIAG_INTERVAL)
+    wall = time.perf_counter() - t0
+    _, _, _, nu = b.status()
+    b.close()
+    rng = np.random.default_rng(1)
+    small = [k for k, p in enumerate(probs) if p.nx <= subset_max_edge]
+    pick = sorted(int(k) for k in rng.choice(small, subset, replace=False))
+    rows = []
+    t1 = time.perf_counter()
+    for k in pick:
+        lat = clb.Lattice.from_problem(probs[k].with_storage(W.STORAGE_F64))
+        s64, e64 = lat.run(plain_tol, cap, DIAG_INTERVAL)
+        n64 = lat.nusselt(probs[k].nu_axis)
+        lat.close()
+        rows.append({"name": probs[k].name, "steps_plain": int(s64), "er_plain": float(e64),
+                     "nu_plain": float(n64), "steps": int(steps[k]), "nu": float(nu[k]),
+                     "rel": abs(float(nu[k]) - float(n64)) / abs(float(n64))})
+    wall_plain = time.perf_counter() - t1
+    nodes = sum(p.nodes for p in probs)
+    return {"instances": count, "nodes": nodes, "storage": "f32", "tol": tol, "cap": cap,
+            "wall_s": wall, "solves_per_s": count / wall,
+            "converged": int((er < tol).sum()), "at_cap": int((steps >= cap).sum()),
+            "status_nonzero": int((status != 0).sum()),
+            "steps_p50": float(np.median(steps)), "steps_max": int(steps.max()),
+            "node_updates": float(sum(p.nodes * int(s) for p, s in zip(probs, steps))),
+            "plain_f64_subset": {"instances": subset, "edges_max": subset_max_edge, "tol": plain_tol,
+                                 "wall_s": wall_plain, "solves_per_s": subset / wall_plain,
+                                 "converged": int(sum(r["er_plain"] < plain_tol for r in rows)),
+                                 "nusselt_rel_max": max(r["rel"] for r in rows), "rows": rows},
+            "speedup_solves_per_s": (count / wall) / (subset / wall_plain)}
+
+
+def rb_long_run(steps: int = 200000, window: int = 50000, interval: int = DIAG_INTERVAL):
+    """Rayleigh-Benard 2048 x 1024 at Ra = 1e7 stepped `steps` steps in each storage form (FP16
+    deviation storage, FP32 deviation storage, FP64), with the FP64 Nusselt number (Eq. 29) and
+    residual taken every `interval` steps (clb_check). The flow is chaotic, so the forms are
+    compared by statistics: the Nusselt number averaged over the last `window` steps (with the
+    standard error of that mean from 5 blocks of the window) and the residual's median and maximum
+    there, each form against FP64. Wall time and throughput include the checks."""
+    from paper_1710_10569_gb300 import clb
+    out = {"workload": "rayleigh_benard_2048x1024_Ra1e7_Pr0.71", "steps": steps, "window": window,
+           "check_interval": interval, "forms": {}}
+    for st in (W.STORAGE_F64, W.STORAGE_F32, W.STORAGE_F16DEV):
+        prob = workload(st)
+        lat = clb.Lattice.from_problem(prob)
+        nus, ers = [], []
+        t0 = time.perf_counter()
+        for _ in range(steps // interval):
+            lat.step(interval)
+            nu, er = lat.check(1)
+            nus.append(nu)
+            ers.append(er)
+        wall = time.perf_counter() - t0
+        lat.close()
+        nus, ers = np.array(nus), np.array(ers)
+        tail = window // interval
+        blocks = np.array([b.mean() for b in np.array_split(nus[-tail:], 5)])
+        onset = next((int((k + 1) * interval) for k, v in enumerate(nus) if v > 1.5), None)
+        out["forms"][W.STORAGE_NAMES[st]] = {
+            "mlups": prob.nodes * steps / wall / 1e6, "wall_s": wall,
+            "nu_mean": float(nus[-tail:].mean()), "nu_std": float(nus[-tail:].std()),
+            "nu_mean_stderr": float(blocks.std(ddof=1) / math.sqrt(len(blocks))),
+            "nu_final": float(nus[-1]), "residual_median": float(np.median(ers[-tail:])),
+            "residual_max": float(ers[-tail:].max()), "steps_to_nu_1.5": onset,
+            "nu_every_5000_steps": [round(float(v), 4) for v in nus[5000 // interval - 1::5000 // interval]]}
+    ref = out["forms"]["f64"]
+    for name, f in out["forms"].items():
+        if name != "f64":
+            f["nu_mean_rel_vs_f64"] = abs(f["nu_mean"] - ref["nu_mean"]) / ref["nu_mean"]
+            f["nu_mean_diff_in_stderr"] = abs(f["nu_mean"] - ref["nu_mean"]) / math.hypot(
+                f["nu_mean_stderr"], ref["nu_mean_stderr"])
+    return out
 
 
 def run_ours(args):
@@ -600,7 +698,10 @@ def run_ours(args):
     e2e = e2e_run(storage, args.steps, args.nx, args.ny) if rank == 0 else None
     thermal = thermal_run(storage, max(200, args.steps // 8)) if (rank == 0 and not args.no_variants) else None
     three_d = three_d_run(max(200, args.steps // 20)) if (rank == 0 and not args.no_variants) else None
+    rb_long = rb_long_run() if (rank == 0 and not args.no_long) else None
     batched = batched_run(storage) if (rank == 0 and not args.no_serve) else None
+    if batched is not None and not args.no_long:
+        batched["to_steady_state"] = batched_steady_run()
     served = served_run(storage) if (rank == 0 and not args.no_serve) else None
     if rank == 0:
         line = {
@@ -639,6 +740,7 @@ def run_ours(args):
             "three_d": three_d,
             "batched": batched,
             "served": served,
+            "rb_long": rb_long,
         }
         print(json.dumps(line), flush=True)
     lat.close()
@@ -692,12 +794,20 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched and served runs")
+    ap.add_argument("--no-long", action="store_true",
+                    help="skip the 200,000-step Rayleigh-Benard run in three storage forms")
+    ap.add_argument("--rb-long", action="store_true",
+                    help="run only the 200,000-step Rayleigh-Benard run in three storage forms "
+                         "(--steps sets its length) and print its JSON")
     ap.add_argument("--thermal-only", action="store_true",
                     help="run only the D2Q5 thermal-only step (4096 x 4096) and print its JSON")
     ap.add_argument("--three-d-only", action="store_true",
                     help="run only the 3-D workload (D3Q27 + D3Q7, 256 x 256 x 128) and print its JSON")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload (256 uneven cavities) and print its JSON")
+    ap.add_argument("--steady-only", action="store_true",
+                    help="run only the steady-state runs (256 batched cavities with retirement; the "
+                         "served trace) and print their JSON")
     ap.add_argument("--served-large", action="store_true",
                     help="run only a served trace over the full edge range (32 requests, edges "
                          "64-4096, cap 4,000 steps, tol 1e-8) against plain FP64, and print its JSON")
@@ -709,12 +819,18 @@ def main():
     elif args.thermal_only:
         st = {"f64": W.STORAGE_F64, "f32": W.STORAGE_F32, "f16dev": W.STORAGE_F16DEV}[args.storage]
         print(json.dumps(thermal_run(st, args.steps)), flush=True)
+    elif args.rb_long:
+        print(json.dumps(rb_long_run(args.steps, min(50000, args.steps // 4 // DIAG_INTERVAL * DIAG_INTERVAL))),
+              flush=True)
     elif args.three_d_only:
         print(json.dumps(three_d_run(args.steps)), flush=True)
     elif args.served_large:
         st = {"f64": W.STORAGE_F64, "f32": W.STORAGE_F32, "f16dev": W.STORAGE_F16DEV}[args.storage]
-        print(json.dumps(served_run(st, count=32, step_cap=4000, tol=1e-8, hi=4096, hbm_budget_gb=96)),
-              flush=True)
+        print(json.dumps(served_run(st, count=32, step_cap=4000, tol=1e-8, plain_tol=1e-8, lo=64, hi=4096,
+                                    rb_Ra=(1e3, 1e6), hbm_budget_gb=96)), flush=True)
+    elif args.steady_only:
+        st = {"f64": W.STORAGE_F64, "f32": W.STORAGE_F32, "f16dev": W.STORAGE_F16DEV}[args.storage]
+        print(json.dumps({"batched_to_steady_state": batched_steady_run(), "served": served_run(st)}), flush=True)
     elif args.batched_only:
         print(json.dumps(batched_run({"f64": W.STORAGE_F64, "f32": W.STORAGE_F32,
                                       "f16dev": W.STORAGE_F16DEV}[args.storage], steps=args.steps)), flush=True)

@@ -166,6 +166,11 @@ clb_status clb_nusselt_noalloc(const void *populations, int nx, int ny, const cl
  * max(sum|X|^2, N (1e-3 X_ref)^2)), X_ref = u_ref, dT_ref. FP64 on the GPU. Synchronous. */
 clb_status clb_residual(clb_handle *h, double *er_out);
 
+/* Both diagnostics from one FP64 pass over the lattice: the Nusselt number along axis (as
+ * clb_nusselt) and the residual E_R (as clb_residual, snapshot retaken). Either output may be
+ * NULL. Synchronous. CLB_ENAN when the fields are not finite. */
+clb_status clb_check(clb_handle *h, int axis, double *nu_out, double *er_out);
+
 /* Step until E_R < tol, checked every `interval` steps, or until max_steps steps have been taken
  * by this call. Outputs may be NULL. CLB_ENAN if the fields blow up. */
 clb_status clb_run(clb_handle *h, double tol, long max_steps, long interval, long *steps_out,

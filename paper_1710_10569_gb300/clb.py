@@ -76,6 +76,7 @@ _SIGS = {
     "clb_residual": [_VP, _D],
     "clb_nusselt_noalloc": [_VP, _I, _I, _P(clb_params), _I, _VP, _D],
     "clb_run": [_VP, ctypes.c_double, _L, _L, _P(_L), _D],
+    "clb_check": [_VP, _I, _D, _D],
     "clb_steps": [_VP, _P(_L)],
     "clb_sync": [_VP],
     "clb_save": [_VP, _VP, _P(_S)],
@@ -310,6 +311,12 @@ class Lattice:
         v = ctypes.c_double()
         _check(lib().clb_residual(self._h, ctypes.byref(v)))
         return v.value
+
+    def check(self, axis: int = 1):
+        """(Nusselt number along axis, residual E_R) from one FP64 pass; the snapshot is retaken."""
+        nu, er = ctypes.c_double(), ctypes.c_double()
+        _check(lib().clb_check(self._h, int(axis), ctypes.byref(nu), ctypes.byref(er)))
+        return nu.value, er.value
 
     def run(self, tol: float, max_steps: int, interval: int = 100):
         st, er = _L(), ctypes.c_double()

@@ -65,35 +65,48 @@ __global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(
     const int lane = threadIdx.x & 31;
     const int span = blockDim.x * V;
     int xt = tx * span, keep = 0;
+    // Columns [xs, xe) of the tile that no warp covers with the vector path: they are updated node
+    // by node, one (row, column) pair per thread of the block, so that the lanes of a warp work on
+    // different rows at once instead of one lane per row.
+    int xs = 0, xe = 0;
     // The last tile of a row that would run past the row's end is moved left to end on the last
-    // multiple of V below nx (tail), so that its warps take the vector path (walls included)
-    // instead of node-by-node gathers; the nodes it shares with the tile before it are computed
-    // alike and stored by that tile only, and the nx % V nodes from tail on are updated node by
-    // node by the thread holding the tile's last vector. The moved start stays a multiple of V, so the vector loads stay aligned.
-    // A tile that would store no vector node (xt == tail) is not moved.
+    // multiple of V below nx (tail), so that its warps take the vector path (walls included); the
+    // nodes it shares with the tile before it are computed alike and stored by that tile only, and
+    // the nx % V nodes from tail on go node by node. The moved start stays a multiple of V, so the
+    // vector loads stay aligned. A tile that would store no vector node (xt == tail), or a row
+    // shorter than a tile, goes node by node as a whole.
     const int tail = M.P.nx - M.P.nx % V;
-    const bool moved = xt + span > M.P.nx && xt < tail && tail >= span;
-    if (moved) {
-        keep = xt;
-        xt = tail - span;
+    bool vector = xt + span <= M.P.nx;
+    if (!vector) {
+        if (xt < tail && tail >= span) {
+            keep = xt;
+            xt = tail - span;
+            vector = true;
+            xs = tail;
+        } else {
+            xs = xt;
+        }
+        xe = M.P.nx;
     }
-    const int x0 = xt + threadIdx.x * V;
-    if (x0 - lane * V >= M.P.nx) return;  // whole warps only
     const E* src = (const E*)M.buf[parity];
     E* dst = (E*)M.buf[parity ^ 1];
     // The tile's rows: `groups` groups of blockDim.y rows, one group after another, so that the
     // descriptor fetched above serves several rows per warp.
     const int rows = blockDim.y * groups;
-    const int y_end = min(M.P.ny, (ty + 1) * rows);
-    for (int y = ty * rows + threadIdx.y; y < y_end; y += blockDim.y) {
-        step_warp_nodes<ST, V, false>(src, dst, M.P, x0, y, lane, keep);
-        if (moved && x0 + V == tail)
-            for (int x = tail; x < M.P.nx; ++x) {
-                A f[9], g[5];
-                gather(src, M.P, x, y, f, g);
-                collide_any<Storage<ST>::DEV>(M.P, f, g);
-                store_node(dst, M.P, x, y, f, g);
-            }
+    const int y0 = ty * rows;
+    const int y_end = min(M.P.ny, y0 + rows);
+    if (vector) {
+        const int x0 = xt + threadIdx.x * V;
+        for (int y = y0 + threadIdx.y; y < y_end; y += blockDim.y) step_warp_nodes<ST, V, false>(src, dst, M.P, x0, y, lane, keep);
+    }
+    const int nrow = y_end - y0;
+    const int nodes = nrow * (xe - xs);
+    for (int j = threadIdx.y * blockDim.x + threadIdx.x; j < nodes; j += blockDim.x * blockDim.y) {
+        const int y = y0 + j % nrow, x = xs + j / nrow;
+        A f[9], g[5];
+        gather(src, M.P, x, y, f, g);
+        collide_any<Storage<ST>::DEV>(M.P, f, g);
+        store_node(dst, M.P, x, y, f, g);
     }
 }
 

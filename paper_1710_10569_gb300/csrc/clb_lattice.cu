@@ -517,6 +517,18 @@ extern "C" clb_status clb_residual(clb_handle* h, double* er_out)
     return CLB_OK;
 }
 
+extern "C" clb_status clb_check(clb_handle* h, int axis, double* nu_out, double* er_out)
+{
+    TraceRange trace("clb_check");
+    CHECK_H(h);
+    if (axis != 0 && axis != 1) return set_error(CLB_EINVAL, "axis must be 0 or 1");
+    DeviceGuard dg(h->device);
+    CLB_TRY(run_diagnostics(h, axis, 1));
+    if (nu_out) *nu_out = h->host_diag[RS_N];
+    if (er_out) *er_out = h->host_diag[RS_N + 1];
+    return CLB_OK;
+}
+
 extern "C" clb_status clb_run(clb_handle* h, double tol, long max_steps, long interval,
                               long* steps_out, double* er_out)
 {

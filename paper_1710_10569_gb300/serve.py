@@ -19,11 +19,12 @@ from . import clb
 from . import workloads as W
 
 
-def _summary(records, wall):
+def _summary(records, wall, tol):
     lat = np.array([r["latency_s"] for r in records])
     return {"requests": len(records), "wall_s": wall, "solves_per_s": len(records) / wall,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_steps": float(np.mean([r["steps"] for r in records]))}
+            "mean_steps": float(np.mean([r["steps"] for r in records])), "tol": tol,
+            "converged": int(sum(r["residual"] < tol for r in records))}
 
 
 def serve_trace(trace, storage: int, hbm_budget_bytes: int, max_slots: int = 256, chunk: int = 100,
@@ -60,7 +61,7 @@ def serve_trace(trace, storage: int, hbm_budget_bytes: int, max_slots: int = 256
                 records.append(rec)
     wall = time.perf_counter() - t0
     srv.close()
-    return _summary(records, wall), records
+    return _summary(records, wall, tol), records
 
 
 def plain_trace(trace, step_cap: int = 20000, tol: float = 1e-6, interval: int = 100, stream=None):
@@ -81,13 +82,14 @@ def plain_trace(trace, step_cap: int = 20000, tol: float = 1e-6, interval: int =
                         "latency_s": time.perf_counter() - t0 - arrival, "steps": steps, "nu": nu,
                         "residual": er, "nodes": prob.nodes})
     wall = time.perf_counter() - t0
-    return _summary(records, wall), records
+    return _summary(records, wall, tol), records
 
 
-def nusselt_agreement(served, plain, tol: float):
+def nusselt_agreement(served, plain, tol: float, plain_tol: float | None = None):
     """Relative differences of the served Nusselt numbers from the plain FP64 ones, per request:
-    overall and over the requests that reached the residual tolerance in both paths (steady
-    states), with the worst requests listed."""
+    overall and over the requests that reached their residual tolerance in both paths (steady
+    states; `plain_tol` is the plain path's, `tol` by default), with the worst requests listed."""
+    plain_tol = tol if plain_tol is None else plain_tol
     by = {r["name"]: r for r in plain}
     rows = []
     for r in served:
@@ -96,10 +98,11 @@ def nusselt_agreement(served, plain, tol: float):
             continue
         rel = abs(r["nu"] - q["nu"]) / max(abs(q["nu"]), 1e-300)
         rows.append({"name": r["name"], "rel": rel, "steps": r["steps"], "steps_plain": q["steps"],
-                     "nu": r["nu"], "nu_plain": q["nu"], "converged": r["residual"] < tol and q["residual"] < tol})
+                     "nu": r["nu"], "nu_plain": q["nu"],
+                     "converged": r["residual"] < tol and q["residual"] < plain_tol})
     rels = np.array([x["rel"] for x in rows])
     conv = np.array([x["rel"] for x in rows if x["converged"]])
-    return {"max": float(rels.max()) if rels.size else None,
+    return {"requests": len(rows), "max": float(rels.max()) if rels.size else None,
             "median": float(np.median(rels)) if rels.size else None,
             "fraction_within_1e-3": float(np.mean(rels <= 1e-3)) if rels.size else None,
             "converged_requests": int(conv.size),

@@ -125,22 +125,34 @@ def cavity(n: int = 256, Ra: float = 1e5, Pr: float = 0.71, u_c: float = 0.1, no
                    nu_axis=0, meta=dict(Ra=Ra, Pr=Pr, u_c=u_c, seed=seed))
 
 
+def hydrostatic_density(s, g_beta: float, dT: float, H: float, rho0: float = 1.0):
+    """Density in hydrostatic balance with the buoyancy of the conduction profile T - T0 =
+    dT (1/2 - s) across a layer of height H (s = height / H in [0, 1]): the lattice equation of state
+    p = c_s^2 rho turns dp/dy = rho0 g beta (T - T0) into c_s^2 d(rho)/dy = rho0 g beta (T - T0),
+    integrated with the mean density rho0."""
+    return rho0 * (1.0 + g_beta * dT * H / CS ** 2 * (s / 2 - s * s / 2 - 1.0 / 12.0))
+
+
 def rayleigh_benard(nx: int = 2048, ny: int = 1024, Ra: float = 1e7, Pr: float = 0.71,
                     u_c: float = 0.1, perturb: float = 1e-3, seed: int = 0, storage=STORAGE_F64,
-                    T0: float = 0.0, dT: float = 1.0) -> Problem:
+                    T0: float = 0.0, dT: float = 1.0, hydrostatic: bool = True) -> Problem:
     """Rayleigh-Benard convection: periodic in x, bottom wall T0+dT/2, top wall T0-dT/2, at rest,
-    T = linear conduction profile + seeded uniform perturbation of amplitude `perturb`."""
+    T = linear conduction profile + seeded uniform perturbation of amplitude `perturb`. With
+    `hydrostatic` the density starts in balance with the buoyancy of the conduction profile, so the
+    run starts from the conduction state; a uniform density is out of balance and sets the whole
+    layer into a slow vertical acoustic oscillation that masks the onset of convection."""
     H = float(ny)
     nu, alpha, gb = convection_params(H, Ra, Pr, u_c, dT)
     rng = np.random.default_rng(seed)
     x, y = _grid(nx, ny)
     T = T0 + dT * (0.5 - (y + 0.5) / ny) + rng.uniform(-perturb, perturb, (ny, nx))
+    rho = hydrostatic_density((y + 0.5) / ny, gb, dT, H) if hydrostatic else np.ones((ny, nx))
     z = np.zeros((ny, nx))
     p = default_params(nu=nu, kappa=alpha, g_beta=gb, T0=T0, storage=storage,
                        wall=(WALL_PERIODIC, WALL_PERIODIC, WALL_DIRICHLET, WALL_DIRICHLET),
                        T_wall=(0.0, 0.0, T0 + 0.5 * dT, T0 - 0.5 * dT), T_ref=T0, u_ref=u_c,
                        dT_ref=dT)
-    return Problem(f"rayleigh_benard_{nx}x{ny}_Ra{Ra:g}", nx, ny, p, np.ones((ny, nx)), z.copy(),
+    return Problem(f"rayleigh_benard_{nx}x{ny}_Ra{Ra:g}", nx, ny, p, rho, z.copy(),
                    z.copy(), T, nu_axis=1, meta=dict(Ra=Ra, Pr=Pr, u_c=u_c, seed=seed))
 
 
@@ -253,11 +265,14 @@ def batch_cavities(count: int = 256, seed: int = 0, lo: int = 64, hi: int = 512,
 
 
 def request_trace(count: int = 64, seed: int = 0, rate_hz: float = 50.0, lo: int = 64,
-                  hi: int = 512, Ra_range=(1e3, 1e6), storage=STORAGE_F32, nu_cap: float = 0.1):
+                  hi: int = 512, Ra_range=(1e3, 1e6), storage=STORAGE_F32, nu_cap: float = 0.1,
+                  rb_Ra_range=None):
     """A finite Poisson request stream: (arrival_time_s, Problem) pairs. Kind is uniform over
     periodic Taylor-Green, side-heated cavity and Rayleigh-Benard; edge log-uniform in [lo, hi];
-    aspect ratio 1 or 2 with probability 1/2 each."""
+    aspect ratio 1 or 2 with probability 1/2 each; Ra log-uniform in Ra_range (rb_Ra_range for
+    the Rayleigh-Benard requests when given)."""
     rng = np.random.default_rng(seed)
+    rb_lo, rb_hi = rb_Ra_range if rb_Ra_range is not None else Ra_range
     t = 0.0
     out = []
     for k in range(count):
@@ -273,6 +288,8 @@ def request_trace(count: int = 64, seed: int = 0, rate_hz: float = 50.0, lo: int
             uc = min(0.1, 0.1 * nu_cap / (0.1 * n * math.sqrt(0.71 / Ra)))
             prob = cavity(n, Ra=Ra, u_c=uc, ny=n * aspect, seed=s, storage=storage)
         else:
+            if rb_Ra_range is not None:
+                Ra = rb_lo * (rb_hi / rb_lo) ** (math.log(Ra / Ra_range[0]) / math.log(Ra_range[1] / Ra_range[0]))
             uc = min(0.1, 0.1 * nu_cap / (0.1 * n * math.sqrt(0.71 / Ra)))
             prob = rayleigh_benard(n * aspect, n, Ra=Ra, u_c=uc, seed=s, storage=storage)
         prob.name = f"req{k}_" + prob.name
@@ -342,20 +359,22 @@ def _grid3(nx, ny, nz):
 
 
 def rayleigh_benard3d(nx: int, ny: int, nz: int, Ra: float, Pr: float = 0.71, u_c: float = 0.1,
-                      perturb: float = 1e-3, seed: int = 0, storage=STORAGE_F64) -> Problem3D:
+                      perturb: float = 1e-3, seed: int = 0, storage=STORAGE_F64,
+                      hydrostatic: bool = True) -> Problem3D:
     """Rayleigh-Benard convection in a box periodic in x and y, Dirichlet walls on the z faces
     (T = +0.5 below, -0.5 above), H = nz, fluid at rest, T on the conduction line plus seeded
-    uniform noise of amplitude `perturb`."""
+    uniform noise of amplitude `perturb`, density in hydrostatic balance with it (as in 2-D)."""
     H = float(nz)
     nu, alpha, gb = convection_params(H, Ra, Pr, u_c)
     rng = np.random.default_rng(seed)
     _, _, z = _grid3(nx, ny, nz)
     T = 0.5 - (z + 0.5) / H + rng.uniform(-perturb, perturb, (nz, ny, nx))
+    rho = hydrostatic_density((z + 0.5) / H, gb, 1.0, H) if hydrostatic else np.ones((nz, ny, nx))
     zero = np.zeros((nz, ny, nx))
     p = default_params3(nu=nu, kappa=alpha, g_beta=gb, T0=0.0, storage=storage,
                         wall=(WALL_PERIODIC,) * 4 + (WALL_DIRICHLET,) * 2,
                         T_wall=(0.0,) * 4 + (0.5, -0.5), u_ref=u_c, dT_ref=1.0)
-    return Problem3D(f"rayleigh_benard3d_{nx}x{ny}x{nz}", nx, ny, nz, p, np.ones((nz, ny, nx)),
+    return Problem3D(f"rayleigh_benard3d_{nx}x{ny}x{nz}", nx, ny, nz, p, rho,
                      zero.copy(), zero.copy(), zero.copy(), T, nu_axis=2,
                      meta=dict(Ra=Ra, Pr=Pr, u_c=u_c, seed=seed))
 

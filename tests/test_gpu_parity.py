@@ -183,13 +183,29 @@ def test_cavity_256_short(clb, storage):
     compare(f"cavity256_{W.STORAGE_NAMES[storage]}_400", got, exp, tol(storage, 400), prob.params)
 
 
+RB_FULL_STEPS = 200
+
+
+@pytest.fixture(scope="module")
+def rb_full_oracle():
+    """The oracle's fields of the bench workload (Rayleigh-Benard 2048 x 1024, Ra = 1e7) after
+    RB_FULL_STEPS steps; computed once for the three storage forms (FP64 arithmetic)."""
+    o = oracle.Oracle.from_problem(W.rayleigh_benard(2048, 1024, storage=F64))
+    o.step(RB_FULL_STEPS)
+    return o.fields()
+
+
 @pytest.mark.parametrize("storage", [F64, F32, F16])
-def test_rayleigh_benard_2048x1024_full_size(clb, storage):
-    """The bench workload at full size, the launch configuration bench.py times (graph chunks of
-    the fused kernel), a few steps, every node compared."""
+def test_rayleigh_benard_2048x1024_full_size(clb, storage, rb_full_oracle):
+    """The bench workload at full size in the launch configuration bench.py times (graph chunks of
+    the fused kernel plus single launches), 200 steps, every node compared."""
     prob = W.rayleigh_benard(2048, 1024, storage=storage)
-    _, _, got, exp = run_both(clb, prob, 6)
-    compare(f"rb2048_{W.STORAGE_NAMES[storage]}_6", got, exp, tol(storage, 6), prob.params)
+    lat = clb.Lattice.from_problem(prob)
+    lat.step(RB_FULL_STEPS)
+    got = lat.fields()
+    lat.close()
+    compare(f"rb2048_{W.STORAGE_NAMES[storage]}_{RB_FULL_STEPS}", got, rb_full_oracle,
+            tol(storage, RB_FULL_STEPS), prob.params)
 
 
 def test_graph_chunks_equal_single_launches(clb):

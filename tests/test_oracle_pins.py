@@ -631,3 +631,28 @@ def test_normal_plate_channel_with_the_papers_walls():
     assert out[0][0] < 2e-3 and out[0][1] < 5e-3
     for k in (0, 1):
         assert math.log(out[0][k] / out[1][k]) / math.log(2) > 1.7
+
+
+def test_hydrostatic_start_of_rayleigh_benard_is_at_rest():
+    """The Rayleigh-Benard workloads start with the density in hydrostatic balance with the
+    buoyancy of the conduction profile (c_s^2 d(rho)/dy = rho0 g beta (T - T0)). Under the oracle
+    that state stays at rest to within discretisation error (no perturbation, Ra = 1e5 on 4 x 128,
+    1,200 steps: max |u_y| < 3e-4 u_c), while a uniform initial density drives a vertical acoustic
+    oscillation of the layer at least ten times stronger. A wrong sign or factor in the balance
+    leaves an imbalance as large as the uniform start's."""
+    peak = {}
+    for hyd in (True, False):
+        prob = W.rayleigh_benard(4, 128, Ra=1e5, perturb=0.0, hydrostatic=hyd)
+        o = oracle.Oracle.from_problem(prob)
+        m = 0.0
+        for _ in range(6):
+            o.step(200)
+            m = max(m, float(np.max(np.abs(o.fields()[2]))))
+        peak[hyd] = m / prob.meta["u_c"]
+    assert peak[True] < 3e-4
+    assert peak[False] > 10 * peak[True]
+    # the balance itself: c_s^2 d(rho)/dy equals g beta (T - T0) of the conduction line
+    prob = W.rayleigh_benard(4, 128, Ra=1e5, perturb=0.0)
+    rho, T, gb = prob.rho[:, 0], prob.T[:, 0], prob.params["g_beta"]
+    np.testing.assert_allclose(np.diff(rho) / 3.0, gb * 0.5 * (T[1:] + T[:-1]), rtol=1e-9, atol=1e-15)
+    assert rho.mean() == pytest.approx(1.0, abs=1e-6)  # the continuous mean; nodes sample it at mid-cells

@@ -6,9 +6,12 @@ Dirichlet walls T = +-0.5 at the bottom/top, Ra = 1e7, Pr = 0.71, u_c = 0.1, see
 lattice (every node: pull, macroscopics, D2Q9 and D2Q5 central-moment collision, store).
 
 Metric: MLUPS (million coupled node updates per second), with the fused step kernel's fraction of
-the measured HBM copy bandwidth. The timed region runs K steps back to back from CUDA-graph chunks
-on the lattice's stream; the two population buffers (2 x 117 MB in FP32) exceed the 129 MB L2, and
-the DRAM bytes per launch measured by ncu are reported beside the algorithmic bytes.
+the measured HBM copy bandwidth. The timed region runs K steps through clb_run (the fused step every
+step, the FP64 Nusselt number and residual every 100 steps and after the last one) on the lattice's
+stream; the two population buffers (2 x 117 MB in FP32) exceed the 129 MB L2. The roofline times the
+step kernel alone over a fixed window of 2048 graph-replayed launches (both graph parities captured
+before the window), and the DRAM bytes per launch measured by ncu are reported beside the
+algorithmic bytes.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 (torchrun) every rank steps its own replica of the lattice (replicas only: the
@@ -19,9 +22,14 @@ Beside the headline the JSON line carries (rank 0, N = 1): `e2e` (the same run t
 from pinned host fields), `cpu_baseline` (the FP64 oracle on the host cores), `variants` (FP16
 deviation storage on 4096 x 2048, FP64), `thermal_only` (D2Q5 alone, 4096 x 4096), `three_d`
 (D3Q27 + D3Q7 on 256 x 256 x 128 in three storage forms, a batch of 48 uneven boxes, the D3Q7
-thermal-only step on 256^3), `batched` (256 uneven cavities in one launch per step) and `served`
-(a Poisson request trace against the plain FP64 path). `--served-large` runs a served trace over
-edges 64-4096 instead; `--thermal-only`, `--three-d-only` and `--batched-only` run one part alone.
+thermal-only step on 256^3), `batched` (256 uneven cavities in one launch per step, a fixed 1,000
+steps, and `to_steady_state`: every cavity run to E_R < 1e-6 or the 500k-step cap with retirement,
+against the plain FP64 path on a seeded subset), `served` (a Poisson request trace, every request run
+to steady state, against the plain FP64 one-at-a-time path) and `rb_long` (Rayleigh-Benard 2048 x
+1024 for 200,000 steps in FP64, FP32 and FP16 deviation storage, Nusselt statistics per form).
+`--served-large` runs a served trace over edges 64-4096 instead; `--thermal-only`, `--three-d-only`,
+`--batched-only`, `--steady-only` and `--rb-long` run one part alone; `--no-long` skips the
+steady-state and 200,000-step runs.
 """
 from __future__ import annotations
 

@@ -64,8 +64,11 @@ typedef enum {
 } clb_wall;
 
 /* Population storage. CLB_F64 stores f_i, g_i and computes in FP64. CLB_F32 and CLB_F16DEV store
- * the deviations from the rest state, f_i - w_i rho0 and g_i - w^T_i T_ref (w, w^T the rest
- * weights), in FP32 or IEEE half precision, and compute in FP32 on those deviations. */
+ * the deviations from a rest state, f_i - w_i rho0 and g_i - w^T_i T_b(y) (w, w^T the rest
+ * weights), in FP32 or IEEE half precision, and compute in FP32 on those deviations. T_b(y) is
+ * T_ref, except between two Dirichlet (or two wet) y walls with periodic x, where it is the
+ * conduction profile between the walls (linear in y), so that a layer near its conduction state
+ * stores only its small departures from it. The choice changes rounding only. */
 typedef enum { CLB_F64 = 0, CLB_F32 = 1, CLB_F16DEV = 2 } clb_storage;
 
 /* Problem parameters (Sec. 2, Sec. 3 defaults from clb_params_default). */
@@ -84,7 +87,7 @@ typedef struct clb_params {
     int wall[4];      /* clb_wall for sides -x, +x, -y, +y */
     double T_wall[4]; /* wall temperatures for CLB_WALL_DIRICHLET_T sides */
     int storage;      /* clb_storage */
-    double T_ref;     /* FP16 deviation base for g (normally T0) */
+    double T_ref;     /* FP32/FP16 deviation base for g (normally T0; see clb_storage) */
     double u_ref;     /* residual floor scale for u (0: no floor) */
     double dT_ref;    /* residual floor scale for T (0: no floor) */
     double u_wall[4][2]; /* velocity of each wall (sides -x, +x, -y, +y; ignored on periodic sides):

@@ -245,28 +245,27 @@ def matrices(params: dict, ux: float, uy: float) -> dict:
 
 
 def nusselt(ux, uy, T, params: dict, axis: int) -> float:
-    """Eq. (29): Nu = 1 + <u_axis (T - T0)> H / (alpha dT), the average taken over all nodes.
-    H is the node count along `axis` (walls halfway between nodes), one less for wet walls (walls
-    on the end rows of nodes, where the average is the trapezoid rule over [0, H]); dT is the
-    difference of the
-    wall temperatures on that axis, the sign chosen so that heat flowing from the hot wall counts
-    positive. alpha is the prescribed thermal diffusivity `kappa`."""
+    """Eq. (29): Nu = 1 + <u_axis (T - T0)> H / (alpha dT), the average taken over the system.
+    With walls halfway between nodes H is the node count along `axis` and the average is the plain
+    mean over nodes. Wet walls lie on the end rows (columns) of nodes: along a wet direction the
+    extent is one less and the average is the trapezoid rule (half weight on the two wall rows or
+    columns), in every wet direction. dT is the difference of the wall temperatures on `axis`, the
+    sign chosen so that heat flowing from the hot wall counts positive. alpha is the prescribed
+    thermal diffusivity `kappa`."""
     u = ux if axis == 0 else uy
-    H = T.shape[1] if axis == 0 else T.shape[0]
+    ny, nx = T.shape
     lo, hi = (0, 1) if axis == 0 else (2, 3)
     Tl, Th = params["T_wall"][lo], params["T_wall"][hi]
     dT = abs(Tl - Th) or 1.0
     sign = 1.0 if Tl >= Th else -1.0
     q = u * (T - params["T0"])
-    if params["wall"][lo] == WET:
-        # wet walls lie on the end rows of nodes: H = rows - 1 and the average over [0, H] is
-        # the trapezoid rule (half weight on the two wall rows)
-        H -= 1
-        w = np.ones(T.shape[0])
-        w[0] = w[-1] = 0.5
-        mean = float(np.sum(q * w[:, None]) / (T.shape[1] * H))
-    else:
-        mean = float(np.mean(q))
+    wx, wy = np.ones(nx), np.ones(ny)
+    if params["wall"][0] == WET:
+        wx[0] = wx[-1] = 0.5
+    if params["wall"][2] == WET:
+        wy[0] = wy[-1] = 0.5
+    mean = float(np.sum(q * wy[:, None] * wx[None, :]) / (wx.sum() * wy.sum()))
+    H = (wx if axis == 0 else wy).sum()
     return 1.0 + sign * mean * H / (params["kappa"] * dT)
 
 

@@ -26,13 +26,19 @@
  *       anti-bounce-back g_i = -g*_opp + 2 w^T_i T_w on Dirichlet walls and bounce-back g_i = g*_opp
  *       on adiabatic walls. w^T_i are the D2Q5 rest weights (g^eq at T=1, u=0).
  *   r19 Wet walls (ORC_WET, the paper's own conditions, Sec. 3 first paragraph): the wall row of
- *       nodes lies on the wall (y sides only, x periodic). After streaming, the populations that
- *       would come from beyond the wall are set by non-equilibrium bounce-back, f_i = f_opp +
+ *       nodes lies on the wall (r26: x sides alike, the roles of x and y exchanged). After
+ *       streaming, the populations that would come from beyond the wall are set by
+ *       non-equilibrium bounce-back, f_i = f_opp +
  *       [f^eq_i - f^eq_opp](rho, u'), with u' = u_w - F/(2 rho) so that the force-corrected velocity
  *       of Eq. (13) equals the wall's, rho from mass and normal momentum, and the tangential
  *       momentum closed on the two diagonals; g at the wall node is set by non-equilibrium
  *       extrapolation from the adjacent fluid node n, g_i = g^eq_i(T_w, u_w) + [g_i(n) -
  *       g^eq_i(T(n), u(n))].
+ *   r26 Corners of wet walls (a node on an x wall and a y wall): the y wall's velocity and the mean
+ *       of the two walls' temperatures; rho from the diagonal fluid neighbour; the unknowns whose
+ *       opposite is known by non-equilibrium bounce-back, the two buried diagonals sharing the
+ *       remaining mass equally; g by non-equilibrium extrapolation from the diagonal neighbour.
+ *       In the thermal-only mode wet walls set g only, with the node's prescribed velocity.
  * Parity is pinned by the tests in tests/test_oracle_pins.py (transform brute force, fixed point,
  * conservation, viscosity and diffusivity decay, Poiseuille, conduction, Table 1 Nusselt numbers).
  */
@@ -397,52 +403,96 @@ static void stream(orc_sim *s)
         }
 }
 
-/* The wet-wall boundary pass of reading r19, on the streamed (pre-collision) state. */
+/* One node on a wet wall (reading r19 on y sides, r26 on x sides and in corners), on the streamed
+ * (pre-collision) state: non-equilibrium bounce-back for f, non-equilibrium extrapolation for g from
+ * the fluid node q next to it (along the wall's normal; at a corner, the diagonal neighbour). Reads
+ * only the node's own streamed values and q's, and q is never a wall node (nx, ny >= 3), so the
+ * wall nodes can be processed in any order. */
+static void wet_node(orc_sim *s, int x, int y, int onx, int ony)
+{
+    const orc_params *p = &s->p;
+    const int nx = p->nx;
+    const size_t n = nodes(s);
+    const int sx = x == 0 ? 1 : -1, sy = y == 0 ? 1 : -1; /* directions into the fluid */
+    const int side_x = x == 0 ? 0 : 1, side_y = y == 0 ? 2 : 3;
+    const int side = ony ? side_y : side_x;
+    /* a corner takes the y wall's velocity and the mean of the two walls' temperatures */
+    const double uwx = p->u_wall[side][0], uwy = p->u_wall[side][1];
+    const double Tw = (onx && ony) ? 0.5 * (p->T_wall[side_x] + p->T_wall[side_y]) : p->T_wall[side];
+    const int qx = onx ? x + sx : x, qy = ony ? y + sy : y;
+    const size_t b = (size_t)y * nx + x, q = (size_t)qy * nx + qx;
+    double f[Q9], g[Q5], fq[Q9], gq[Q5];
+    for (int i = 0; i < Q9; ++i) f[i] = s->f[i * n + b];
+    for (int i = 0; i < Q9; ++i) fq[i] = s->f[i * n + q];
+    for (int i = 0; i < Q5; ++i) gq[i] = s->g[i * n + q];
+    double rq, uqx, uqy, Tq, Fqx, Fqy;
+    macroscopic(s, fq, gq, &rq, &uqx, &uqy, &Tq, &Fqx, &Fqy);
+    if (p->thermal_only) {
+        uqx = s->uxp[q];
+        uqy = s->uyp[q];
+    } else {
+        const double Fx = p->Fv[0], Fy = p->Fv[1] + p->rho0 * p->g_beta * (Tw - p->T0);
+        double rho, feq[Q9], gdum[Q5];
+        if (onx && ony) {
+            /* corner: rho from the diagonal neighbour; the unknowns whose opposite is known by
+             * non-equilibrium bounce-back; the two buried diagonals share the remaining mass */
+            rho = rq;
+            equilibrium(s, rho, uwx - 0.5 * Fx / rho, uwy - 0.5 * Fy / rho, Tw, feq, gdum);
+            int unknown[Q9];
+            for (int i = 0; i < Q9; ++i) unknown[i] = EX[i] == sx || EY[i] == sy;
+            double known = 0.0;
+            for (int i = 0; i < Q9; ++i) {
+                const int o = s->opp[i];
+                if (unknown[i] && !unknown[o]) f[i] = f[o] + (feq[i] - feq[o]);
+                if (!(unknown[i] && unknown[o])) known += f[i];
+            }
+            for (int i = 0; i < Q9; ++i)
+                if (unknown[i] && unknown[s->opp[i]]) f[i] = 0.5 * (rho - known);
+        } else {
+            /* one wall with normal along axis a: rho from mass and normal momentum, the unknowns
+             * by non-equilibrium bounce-back, the tangential momentum closed on the two diagonals */
+            const int *Ea = onx ? EX : EY, *Et = onx ? EY : EX;
+            const int nrm = onx ? sx : sy;
+            const double Fa = onx ? Fx : Fy, uwa = onx ? uwx : uwy;
+            double Z = 0.0, O = 0.0;
+            for (int i = 0; i < Q9; ++i) {
+                if (Ea[i] == 0) Z += f[i];
+                if (Ea[i] == -nrm) O += f[i];
+            }
+            rho = (Z + 2.0 * O - nrm * 0.5 * Fa) / (1.0 - nrm * uwa);
+            const double upx = uwx - 0.5 * Fx / rho, upy = uwy - 0.5 * Fy / rho;
+            equilibrium(s, rho, upx, upy, Tw, feq, gdum);
+            for (int i = 0; i < Q9; ++i)
+                if (Ea[i] == nrm) f[i] = f[s->opp[i]] + (feq[i] - feq[s->opp[i]]);
+            double St = 0.0;
+            for (int i = 0; i < Q9; ++i) St += f[i] * Et[i];
+            const double delta = 0.5 * (rho * (onx ? upy : upx) - St);
+            for (int i = 0; i < Q9; ++i)
+                if (Ea[i] == nrm && Et[i] != 0) f[i] += Et[i] * delta;
+        }
+        for (int i = 0; i < Q9; ++i) s->f[i * n + b] = f[i];
+    }
+    /* temperature: g_i = g^eq_i(T_w, u_w) + [g_i(q) - g^eq_i(T(q), u(q))]; in the thermal-only
+     * mode u is the prescribed velocity of the node and of q */
+    const double ubx = p->thermal_only ? s->uxp[b] : uwx, uby = p->thermal_only ? s->uyp[b] : uwy;
+    double fe[Q9], geqq[Q5], geqb[Q5];
+    equilibrium(s, rq, uqx, uqy, Tq, fe, geqq);
+    equilibrium(s, 1.0, ubx, uby, Tw, fe, geqb);
+    for (int i = 0; i < Q5; ++i) g[i] = geqb[i] + (gq[i] - geqq[i]);
+    for (int i = 0; i < Q5; ++i) s->g[i * n + b] = g[i];
+}
+
+/* The wet-wall boundary pass on the streamed (pre-collision) state. */
 static void apply_wet_walls(orc_sim *s)
 {
     const orc_params *p = &s->p;
-    const int nx = p->nx, ny = p->ny;
-    const size_t n = nodes(s);
-    for (int side = 2; side < 4; ++side) {
-        if (p->wall[side] != ORC_WET) continue;
-        const int yb = side == 2 ? 0 : ny - 1;
-        const int yn = side == 2 ? 1 : ny - 2;
-        const int nrm = side == 2 ? 1 : -1; /* direction into the fluid */
-        const double uwx = p->u_wall[side][0], uwy = p->u_wall[side][1], Tw = p->T_wall[side];
-        for (int x = 0; x < nx; ++x) {
-            const size_t b = (size_t)yb * nx + x, q = (size_t)yn * nx + x;
-            double f[Q9], g[Q5];
-            for (int i = 0; i < Q9; ++i) f[i] = s->f[i * n + b];
-            /* flow: non-equilibrium bounce-back */
-            const double Fx = p->Fv[0], Fy = p->Fv[1] + p->rho0 * p->g_beta * (Tw - p->T0);
-            double Z = 0.0, O = 0.0;
-            for (int i = 0; i < Q9; ++i) {
-                if (EY[i] == 0) Z += f[i];
-                if (EY[i] == -nrm) O += f[i];
-            }
-            const double rho = (Z + 2.0 * O - nrm * 0.5 * Fy) / (1.0 - nrm * uwy);
-            const double upx = uwx - 0.5 * Fx / rho, upy = uwy - 0.5 * Fy / rho;
-            double feq[Q9], geqw[Q5];
-            equilibrium(s, rho, upx, upy, Tw, feq, geqw);
-            for (int i = 0; i < Q9; ++i)
-                if (EY[i] == nrm) f[i] = f[s->opp[i]] + (feq[i] - feq[s->opp[i]]);
-            double Sx = 0.0;
-            for (int i = 0; i < Q9; ++i) Sx += f[i] * EX[i];
-            const double delta = 0.5 * (rho * upx - Sx);
-            for (int i = 0; i < Q9; ++i)
-                if (EY[i] == nrm && EX[i] != 0) f[i] += EX[i] * delta;
-            for (int i = 0; i < Q9; ++i) s->f[i * n + b] = f[i];
-            /* temperature: non-equilibrium extrapolation from the fluid node q */
-            double fq[Q9], gq[Q5], rq, uqx, uqy, Tq, Fqx, Fqy, fe[Q9], geqq[Q5], geqb[Q5];
-            for (int i = 0; i < Q9; ++i) fq[i] = s->f[i * n + q];
-            for (int i = 0; i < Q5; ++i) gq[i] = s->g[i * n + q];
-            macroscopic(s, fq, gq, &rq, &uqx, &uqy, &Tq, &Fqx, &Fqy);
-            equilibrium(s, rq, uqx, uqy, Tq, fe, geqq);
-            equilibrium(s, rho, uwx, uwy, Tw, fe, geqb);
-            for (int i = 0; i < Q5; ++i) g[i] = geqb[i] + (gq[i] - geqq[i]);
-            for (int i = 0; i < Q5; ++i) s->g[i * n + b] = g[i];
+    const int wx = p->wall[0] == ORC_WET, wy = p->wall[2] == ORC_WET;
+    if (!wx && !wy) return;
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            const int onx = wx && (x == 0 || x == p->nx - 1), ony = wy && (y == 0 || y == p->ny - 1);
+            if (onx || ony) wet_node(s, x, y, onx, ony);
         }
-    }
 }
 
 static void collide_all(orc_sim *s)
@@ -470,10 +520,14 @@ int orc_create(const orc_params *p, orc_sim **out)
 {
     *out = NULL;
     if (p->nx < 2 || p->ny < 2) return -1;
-    if (p->wall[0] == ORC_WET || p->wall[1] == ORC_WET) return -1; /* wet walls: y sides only */
-    if ((p->wall[2] == ORC_WET || p->wall[3] == ORC_WET) &&
-        (p->wall[0] != ORC_PERIODIC || p->ny < 3 || p->thermal_only))
-        return -1;
+    /* wet walls come in pairs (both x sides, or both y sides), need three nodes across, and the
+     * other pair of sides is periodic or wet as well */
+    for (int a = 0; a < 2; ++a) {
+        const int lo = p->wall[2 * a], hi = p->wall[2 * a + 1], other = p->wall[2 - 2 * a];
+        if ((lo == ORC_WET) != (hi == ORC_WET)) return -1;
+        if (lo == ORC_WET && ((a == 0 ? p->nx : p->ny) < 3 || (other != ORC_PERIODIC && other != ORC_WET)))
+            return -1;
+    }
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return -2;
     s->p = *p;

@@ -105,7 +105,7 @@ __global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(
         const int y = y0 + j % nrow, x = xs + j / nrow;
         A f[9], g[5];
         gather(src, M.P, x, y, f, g);
-        collide_any<Storage<ST>::DEV>(M.P, f, g);
+        collide_any<Storage<ST>::DEV>(M.P, f, g, row_base(M.P, y));
         store_node(dst, M.P, x, y, f, g);
     }
 }

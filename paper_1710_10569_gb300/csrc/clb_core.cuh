@@ -11,10 +11,17 @@
 // per node instead of the ~1,600 of literal 9x9 products, and the result is the same map.
 //
 // Storage. FP64 buffers hold the populations f_i, g_i themselves. FP32 and FP16 buffers hold
-// deviations from the rest state, h_i = f_i - w_i rho0 and t_i = g_i - w^T_i T_ref, and the
+// deviations from a rest state, h_i = f_i - w_i rho0 and t_i = g_i - w^T_i T_b(y), and the
 // collision is evaluated on those deviations (collide_dev): every intermediate is then small, so
 // FP32 rounding acts on quantities of the size of the non-equilibrium and velocity terms instead
-// of on the O(1) populations.
+// of on the O(1) populations. The temperature base T_b(y) = T_b + T_dy y is linear in the row: on
+// a lattice between two Dirichlet (or wet) y walls with periodic x it is the conduction profile
+// between the walls, so that the stored deviations of a layer near its conduction state are the
+// small departures from it (a constant base leaves them as large as the wall temperatures, and
+// the slow growth of convection near onset is then lost to the rounding of the store). A
+// population pulled from the row below (above) was stored against that row's base, so the pull
+// corrects it by the constant -w^T T_dy (+w^T T_dy); nothing else depends on the absolute base
+// except T in the velocity-dependent terms and in the force.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -129,10 +136,12 @@ struct LatParams {
     A s_nu, sp, sm, s_3, s_4; // D2Q9 rates; sp = (s_b + s_nu)/2, sm = (s_b - s_nu)/2
     A lambda1, lambda2, cs2T; // D2Q5 rates and sound speed squared
     A Fvx, Fvy, gb, T0;       // F = (Fvx, Fvy + gb (T - T0)), gb = rho0 * g_beta
-    A rho_b, T_b;             // rest state the buffers are stored against (0 for FP64)
+    A rho_b, T_b;             // rest state the buffers are stored against (0 for FP64); T_b at row 0
+    A T_dy, T_dyw;            // slope of the temperature base along y, and w^T_2 T_dy (pull correction)
+    A dTw[4];                 // wall temperature minus the base at the wall's row (wet walls)
     int moving;               // some wall moves: fbb holds its momentum terms
     A fbb[4][9];              // [f^eq_i - f^eq_opp](rho0, u_wall of the side), added on bounce-back
-    int wet_y;                // both y walls are wet walls (on the end rows of nodes)
+    int wet_x, wet_y;         // both x (y) walls are wet walls (on the end columns / rows of nodes)
     A Twall[4], uwall[4][2];  // wall temperature and velocity (wet walls)
 };
 
@@ -211,6 +220,9 @@ __device__ __forceinline__ void finish_pull(const LatParams<A>& P, const T raw[N
     for (int i = 0; i < 9; ++i) f[i] = to_a(raw[i]);
 #pragma unroll
     for (int i = 0; i < 5; ++i) g[i] = to_a(raw[9 + i]);
+    // g2 (g4) pulled from the row below (above) is re-based to this row; bounced values are not
+    g[2] = (wall_mask & 4) ? g[2] : g[2] - P.T_dyw;
+    g[4] = (wall_mask & 8) ? g[4] : g[4] + P.T_dyw;
     if (wall_mask) {
         if ((wall_mask & 1) && P.kind[0] == WALL_DIRICHLET) g[1] = P.Tw_c2[0] - g[1];
         if ((wall_mask & 2) && P.kind[1] == WALL_DIRICHLET) g[3] = P.Tw_c2[1] - g[3];
@@ -261,14 +273,22 @@ struct Macro {
     A rho, ux, uy, T, Fx, Fy, drho, dT;  // drho = rho - rho_b, dT = T - T_b
 };
 
+// Temperature base of row y (the T_b of deviation storage; 0 for FP64).
+template <typename S>
+__device__ __forceinline__ S row_base(const LatParams<S>& P, int y)
+{
+    return fma_(S(y), P.T_dy, P.T_b);
+}
+
+// Tb: the temperature base of the node's row (row_base), which the g deviations are taken against.
 template <typename A, typename S>
-__device__ __forceinline__ Macro<A> macroscopic(const LatParams<S>& P, const A f[9], const A g[5])
+__device__ __forceinline__ Macro<A> macroscopic(const LatParams<S>& P, const A f[9], const A g[5], A Tb)
 {
     Macro<A> m;
     m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     m.dT = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
     m.rho = A(P.rho_b) + m.drho;
-    m.T = A(P.T_b) + m.dT;
+    m.T = Tb + m.dT;
     m.Fx = A(P.Fvx);
     m.Fy = fma_(A(P.gb), m.T - A(P.T0), A(P.Fvy));
     const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
@@ -361,9 +381,9 @@ __device__ __forceinline__ void collide_d2q5(const LatParams<A>& P, A T, A ux, A
 
 // Collision of one node in place, populations form: Eqs. (6)-(11) for f, Eqs. (16)-(21) for g.
 template <typename A>
-__device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5])
+__device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5], A Tb)
 {
-    const Macro<A> m = macroscopic(P, f, g);
+    const Macro<A> m = macroscopic(P, f, g, Tb);
     const A ux = m.ux, uy = m.uy, rho = m.rho, T = m.T;
     const A cs2 = A(1) / A(3);
     A k[3][3];
@@ -448,9 +468,9 @@ __device__ __forceinline__ void collide_d2q5_dev(const LatParams<S>& P, A T, A d
 // moments are formed from the central moments of h plus those of w rho_b about u
 // (1-D: 1, -u, 1/3 + u^2) minus Eq. (9), with the O(1) parts cancelled analytically.
 template <typename A, typename S>
-__device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5])
+__device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5], A Tb)
 {
-    const Macro<A> m = macroscopic(P, f, g);
+    const Macro<A> m = macroscopic(P, f, g, Tb);
     const A ux = m.ux, uy = m.uy, rho = m.rho, T = m.T, dr = m.drho, dT = m.dT;
     const A rb = A(P.rho_b);
     const A cs2 = A(1.0 / 3.0), cs4 = A(1.0 / 9.0);
@@ -489,81 +509,133 @@ __device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5
 }
 
 template <bool DEV, typename A>
-__device__ __forceinline__ void collide_any(const LatParams<A>& P, A f[9], A g[5])
+__device__ __forceinline__ void collide_any(const LatParams<A>& P, A f[9], A g[5], A Tb)
 {
-    if constexpr (DEV) collide_dev(P, f, g);
-    else collide(P, f, g);
+    if constexpr (DEV) collide_dev(P, f, g, Tb);
+    else collide(P, f, g, Tb);
 }
 
-// Equilibria in stored form: f^eq(rho, u) and g^eq(T, u) (Eqs. 9, 20 back-transformed), minus the
-// rest state for deviation storage.
+// Equilibria in stored form, minus the rest state for deviation storage: f^eq(rho, u) (Eq. 9
+// back-transformed), and g^eq(T, u) (Eq. 20) with dT = T - (the temperature base of the row).
 template <bool DEV, typename A>
-__device__ __forceinline__ void equilibrium(const LatParams<A>& P, A rho, A ux, A uy, A T, A f[9],
-                                            A g[5])
+__device__ __forceinline__ void eq_f(const LatParams<A>& P, A rho, A ux, A uy, A f[9])
 {
     if (DEV) {
         eq_dev_d2q9(rho, rho - P.rho_b, ux, uy, f);
-        eq_dev_d2q5(T, T - P.T_b, ux, uy, P.cs2T, g);
     } else {
         const A cs2 = A(1) / A(3);
         A k[3][3] = {{rho, A(0), rho * cs2}, {A(0), A(0), A(0)}, {rho * cs2, A(0), rho * cs2 * cs2}};
         back_d2q9(k, ux, uy, f);
-        back_d2q5(T, A(0), A(0), T * P.cs2T, T * P.cs2T, ux, uy, g);
     }
 }
+template <bool DEV, typename A>
+__device__ __forceinline__ void eq_g(const LatParams<A>& P, A T, A dT, A ux, A uy, A g[5])
+{
+    if (DEV) eq_dev_d2q5(T, dT, ux, uy, P.cs2T, g);
+    else back_d2q5(T, A(0), A(0), T * P.cs2T, T * P.cs2T, ux, uy, g);
+}
+template <bool DEV, typename A>
+__device__ __forceinline__ void equilibrium(const LatParams<A>& P, A rho, A ux, A uy, A T, A f[9],
+                                            A g[5], A Tb)
+{
+    eq_f<DEV>(P, rho, ux, uy, f);
+    eq_g<DEV>(P, T, T - Tb, ux, uy, g);
+}
 
-// Wet walls (the paper's own conditions, Sec. 3 first paragraph; y sides only, x periodic): the wall
-// row of nodes lies on the wall. The populations that would come from beyond the wall are set by
+// Wet walls (the paper's own conditions, Sec. 3 first paragraph): the wall lies on the end row
+// (column) of nodes. The populations that would come from beyond the wall are set by
 // non-equilibrium bounce-back, f_i = f_opp + [f^eq_i - f^eq_opp](rho, u') with u' = u_w - F/(2 rho)
-// (so that the force-corrected velocity of Eq. 13 is the wall's), rho from mass and normal momentum,
-// and the tangential momentum closed on the two diagonals. g at the wall node is set by
-// non-equilibrium extrapolation from the fluid node next to it: g_i = g^eq_i(T_w, u_w) +
-// [g_i(n) - g^eq_i(T(n), u(n))]. All in stored form (the rest state cancels in both rules).
+// (so that the force-corrected velocity of Eq. 13 is the wall's), rho from mass and normal
+// momentum, and the tangential momentum closed on the two diagonals. g at the wall node is set by
+// non-equilibrium extrapolation from the fluid node q next to it: g_i = g^eq_i(T_w, u_w) +
+// [g_i(q) - g^eq_i(T(q), u(q))]. A corner node (on an x wall and a y wall) takes the y wall's
+// velocity and the mean of the two walls' temperatures, rho from its diagonal neighbour q, the
+// unknowns whose opposite is known by non-equilibrium bounce-back and the two buried diagonals
+// half the remaining mass each; g by extrapolation from q. All in stored form (the rest state
+// cancels in both rules).
 template <bool DEV, typename T, typename A>
 __device__ __forceinline__ void gather_wet(const T* __restrict__ src, const LatParams<A>& P, int x, int y,
                                            A f[9], A g[5])
 {
-    const bool bottom = y == 0;
-    const int side = bottom ? 2 : 3;
-    const A nrm = bottom ? A(1) : A(-1);
+    const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    const bool onx = P.wet_x && (x == 0 || x == P.nx - 1);
+    const bool ony = P.wet_y && (y == 0 || y == P.ny - 1);
+    const int sx = x == 0 ? 1 : -1, sy = y == 0 ? 1 : -1;  // directions into the fluid
+    const int side_x = x == 0 ? 0 : 1, side_y = y == 0 ? 2 : 3;
+    const int side = ony ? side_y : side_x;
     A fw[9], gw[5];
     gather_pull(src, P, x, y, fw, gw);
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = fw[i];
-    const A Tw = P.Twall[side], uwx = P.uwall[side][0], uwy = P.uwall[side][1];
+    // wall temperature, and its difference from the row's base (a corner has a flat base: the
+    // base slopes only between y walls with periodic x)
+    const A Tw = (onx && ony) ? A(0.5) * (P.Twall[side_x] + P.Twall[side_y]) : P.Twall[side];
+    const A dTw = (onx && ony) ? Tw - P.T_b : P.dTw[side];
+    const A uwx = P.uwall[side][0], uwy = P.uwall[side][1];
     const A Fx = P.Fvx, Fy = fma_(P.gb, Tw - P.T0, P.Fvy);
-    const A Z = (f[0] + f[1]) + f[3];
-    const A O = bottom ? (f[4] + f[7]) + f[8] : (f[2] + f[5]) + f[6];
-    const A num = fma_(-nrm * A(0.5), Fy, fma_(A(2), O, Z) + P.rho_b);
-    const A rho = num * rcp_(fma_(-nrm, uwy, A(1)));
-    const A inv = rcp_(rho);
-    const A upx = fma_(A(-0.5) * Fx, inv, uwx), upy = fma_(A(-0.5) * Fy, inv, uwy);
-    A feq[9], gdum[5];
-    equilibrium<DEV>(P, rho, upx, upy, Tw, feq, gdum);
-    if (bottom) {
-        f[2] = f[4] + (feq[2] - feq[4]);
-        f[5] = f[7] + (feq[5] - feq[7]);
-        f[6] = f[8] + (feq[6] - feq[8]);
-    } else {
-        f[4] = f[2] + (feq[4] - feq[2]);
-        f[7] = f[5] + (feq[7] - feq[5]);
-        f[8] = f[6] + (feq[8] - feq[6]);
-    }
-    const A Sx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const A delta = A(0.5) * fma_(rho, upx, -Sx);
-    if (bottom) {
-        f[5] = f[5] + delta;
-        f[6] = f[6] - delta;
-    } else {
-        f[8] = f[8] + delta;
-        f[7] = f[7] - delta;
-    }
     A fq[9], gq[5];
-    gather_pull(src, P, x, bottom ? 1 : P.ny - 2, fq, gq);
-    const Macro<A> mq = macroscopic(P, fq, gq);
-    A fe[9], geqq[5], geqb[5];
-    equilibrium<DEV>(P, mq.rho, mq.ux, mq.uy, mq.T, fe, geqq);
-    equilibrium<DEV>(P, rho, uwx, uwy, Tw, fe, geqb);
+    gather_pull(src, P, onx ? x + sx : x, ony ? y + sy : y, fq, gq);  // q: never a wall node
+    const int qy = ony ? y + sy : y;
+    const Macro<A> mq = macroscopic(P, fq, gq, row_base(P, qy));
+    A feq[9];
+    if (onx && ony) {
+        const A rho = mq.rho;
+        const A inv = rcp_(rho);
+        eq_f<DEV>(P, rho, fma_(A(-0.5) * Fx, inv, uwx), fma_(A(-0.5) * Fy, inv, uwy), feq);
+        // unknown: pulled from beyond a wall; buried: unknown with an unknown opposite
+        A known = A(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const bool unk = EX[i] == sx || EY[i] == sy;
+            const bool unk_o = -EX[i] == sx || -EY[i] == sy;
+            if (unk && !unk_o) f[i] = f[OPP[i]] + (feq[i] - feq[OPP[i]]);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const bool buried = (EX[i] == sx || EY[i] == sy) && (-EX[i] == sx || -EY[i] == sy);
+            if (!buried) known += f[i];
+        }
+        const A half = A(0.5) * ((rho - A(P.rho_b)) - known);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            if ((EX[i] == sx || EY[i] == sy) && (-EX[i] == sx || -EY[i] == sy)) f[i] = half;
+    } else {
+        const int nrm = onx ? sx : sy;
+        const A Fa = onx ? Fx : Fy, uwa = onx ? uwx : uwy;
+        A Z = A(0), O = A(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ea = onx ? EX[i] : EY[i];
+            if (ea == 0) Z += f[i];
+            if (ea == -nrm) O += f[i];
+        }
+        const A num = fma_(-A(nrm) * A(0.5), Fa, fma_(A(2), O, Z) + P.rho_b);
+        const A rho = num * rcp_(fma_(-A(nrm), uwa, A(1)));
+        const A inv = rcp_(rho);
+        const A upx = fma_(A(-0.5) * Fx, inv, uwx), upy = fma_(A(-0.5) * Fy, inv, uwy);
+        eq_f<DEV>(P, rho, upx, upy, feq);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            if ((onx ? EX[i] : EY[i]) == nrm) f[i] = f[OPP[i]] + (feq[i] - feq[OPP[i]]);
+        A St = A(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int et = onx ? EY[i] : EX[i];
+            if (et == 1) St += f[i];
+            if (et == -1) St -= f[i];
+        }
+        const A delta = A(0.5) * fma_(rho, onx ? upy : upx, -St);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int et = onx ? EY[i] : EX[i];
+            if ((onx ? EX[i] : EY[i]) == nrm && et != 0) f[i] = et > 0 ? f[i] + delta : f[i] - delta;
+        }
+    }
+    A geqq[5], geqb[5];
+    eq_g<DEV>(P, mq.T, mq.dT, mq.ux, mq.uy, geqq);
+    eq_g<DEV>(P, Tw, dTw, uwx, uwy, geqb);
 #pragma unroll
     for (int i = 0; i < 5; ++i) g[i] = geqb[i] + (gq[i] - geqq[i]);
 }
@@ -574,8 +646,19 @@ __device__ __forceinline__ void gather(const T* __restrict__ src, const LatParam
                                        A f[9], A g[5])
 {
     constexpr bool DEV = sizeof(T) < sizeof(double);
-    if (P.wet_y && (y == 0 || y == P.ny - 1)) gather_wet<DEV>(src, P, x, y, f, g);
+    if ((P.wet_y && (y == 0 || y == P.ny - 1)) || (P.wet_x && (x == 0 || x == P.nx - 1)))
+        gather_wet<DEV>(src, P, x, y, f, g);
     else gather_pull(src, P, x, y, f, g);
+}
+
+// Weight of node (x, y) in the Eq. 29 average: wet walls lie on the end rows (columns) of nodes,
+// so along a wet direction the average over [0, H] is the trapezoid rule (half weight there).
+template <typename A>
+__device__ __forceinline__ double wet_weight(const LatParams<A>& P, int x, int y)
+{
+    const double wy = (P.wet_y && (y == 0 || y == P.ny - 1)) ? 0.5 : 1.0;
+    const double wx = (P.wet_x && (x == 0 || x == P.nx - 1)) ? 0.5 : 1.0;
+    return wx * wy;
 }
 
 }  // namespace clb

@@ -113,10 +113,27 @@ LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
     P.plane = plane_elems(nx, ny, p.storage);
     P.per_x = p.wall[0] == CLB_PERIODIC;
     P.per_y = p.wall[2] == CLB_PERIODIC;
-    // deviation storage is taken against the rest state (w rho0, w^T T_ref); FP64 stores populations
+    // Deviation storage is taken against a rest state (w rho0, w^T T_b(y)); FP64 stores populations.
+    // Between two Dirichlet (or wet) y walls with periodic x the temperature base is the conduction
+    // profile between the walls (walls halfway between nodes: T_b(y) = T_lo + (T_hi - T_lo)
+    // (y + 1/2) / ny; wet walls on the end rows: T_lo + (T_hi - T_lo) y / (ny - 1)); otherwise T_ref.
     const bool dev = p.storage != ST_F64;
+    const bool ywalls = (p.wall[2] == CLB_WALL_DIRICHLET_T || p.wall[2] == CLB_WALL_WET) &&
+                        p.wall[3] == p.wall[2] && p.wall[0] == CLB_PERIODIC;
+    double Tb0 = p.T_ref, Tdy = 0.0;
+    if (ywalls) {
+        const bool wet = p.wall[2] == CLB_WALL_WET;
+        Tdy = (p.T_wall[3] - p.T_wall[2]) / (wet ? ny - 1 : ny);
+        Tb0 = p.T_wall[2] + (wet ? 0.0 : 0.5 * Tdy);
+    }
+    if (!dev) Tb0 = Tdy = 0.0;
     P.rho_b = dev ? A(p.rho0) : A(0);
-    P.T_b = dev ? A(p.T_ref) : A(0);
+    P.T_b = A(Tb0);
+    P.T_dy = A(Tdy);
+    P.T_dyw = A(0.5 * p.cs2_T * Tdy);
+    // base of the row each side's wall nodes (or wall-adjacent nodes) lie on; x sides only occur
+    // with a flat base
+    const double side_base[4] = {Tb0, Tb0, Tb0, Tb0 + Tdy * (ny - 1)};
     // Wall terms from the equilibria of the wall state (rho0, u_w) and (T_w, u_w): the moving-wall
     // bounce-back f_i = f*_opp + [f^eq_i - f^eq_opp] and the anti-bounce-back g_i = -g*_opp +
     // [g^eq_i + g^eq_opp] = -g*_opp + T_w (cs2_T + u_w,axis^2) for the pair i/opp along the wall's
@@ -130,7 +147,8 @@ LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
         P.kind[s] = p.wall[s];
         const double ux = p.u_wall[s][0], uy = p.u_wall[s][1];
         const double un = s < 2 ? ux : uy;
-        P.Tw_c2[s] = A(p.T_wall[s] * (p.cs2_T + un * un) - p.cs2_T * (dev ? p.T_ref : 0.0));
+        P.Tw_c2[s] = A(p.T_wall[s] * (p.cs2_T + un * un) - p.cs2_T * side_base[s]);
+        P.dTw[s] = A(p.T_wall[s] - side_base[s]);
         for (int i = 0; i < 9; ++i)
             P.fbb[s][i] = A(p.rho0 * (p1(ex[i], ux) * p1(ey[i], uy) - p1(-ex[i], ux) * p1(-ey[i], uy)));
         if (p.wall[s] != CLB_PERIODIC && p.wall[s] != CLB_WALL_WET && (ux != 0.0 || uy != 0.0)) P.moving = 1;
@@ -138,6 +156,7 @@ LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
         P.uwall[s][0] = A(ux);
         P.uwall[s][1] = A(uy);
     }
+    P.wet_x = p.wall[0] == CLB_WALL_WET;
     P.wet_y = p.wall[2] == CLB_WALL_WET;
     const double s_nu = rate_nu(p.nu);
     P.s_nu = A(s_nu);
@@ -164,13 +183,12 @@ inline NuGeom nu_geom(int nx, int ny, const clb_params& p, int axis)
 {
     const int lo = axis == 0 ? 0 : 2, hi = lo + 1;
     NuGeom g;
-    g.H = axis == 0 ? nx : ny;
-    g.cells = double(nx) * ny;
-    if (axis == 1 && p.wall[2] == CLB_WALL_WET) {
-        // wet walls on the end rows: H = ny - 1, trapezoid average over nx * H cells
-        g.H = ny - 1;
-        g.cells = double(nx) * (ny - 1);
-    }
+    // wet walls lie on the end rows (columns) of nodes: one interval fewer along a wet direction,
+    // and the trapezoid weights of the average sum to it
+    const int Lx = p.wall[0] == CLB_WALL_WET ? nx - 1 : nx;
+    const int Ly = p.wall[2] == CLB_WALL_WET ? ny - 1 : ny;
+    g.H = axis == 0 ? Lx : Ly;
+    g.cells = double(Lx) * Ly;
     const double d = std::fabs(p.T_wall[lo] - p.T_wall[hi]);
     g.dT = d > 0 ? d : 1.0;
     g.sign = p.T_wall[lo] >= p.T_wall[hi] ? 1.0 : -1.0;

@@ -101,6 +101,7 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
         for (int k = 0; k < V; ++k)
             mask[k] = rowmask | ((wallL && lane == 0 && k == 0) ? 1 : 0) | ((wallR && lane == 31 && k == V - 1) ? 2 : 0);
         PK out[NPOP];
+        const A Tb = row_base(P, y);
         if constexpr (Storage<ST>::DEV && V % 2 == 0) {
             // FP32 arithmetic: two nodes per packed f32x2 instruction
 #pragma unroll
@@ -113,7 +114,7 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
                 for (int i = 0; i < 9; ++i) f[i] = F2(fa[i], fb[i]);
 #pragma unroll
                 for (int i = 0; i < 5; ++i) g[i] = F2(ga[i], gb[i]);
-                collide_dev(P, f, g);
+                collide_dev(P, f, g, F2(Tb));
 #pragma unroll
                 for (int i = 0; i < NPOP; ++i) from_a2(i < 9 ? f[i] : g[i - 9], out[i].e[k], out[i].e[k + 1]);
             }
@@ -122,7 +123,7 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
             for (int k = 0; k < V; ++k) {
                 A f[9], g[5];
                 finish_pull(P, raw[k], mask[k], f, g);
-                collide_any<Storage<ST>::DEV>(P, f, g);
+                collide_any<Storage<ST>::DEV>(P, f, g, Tb);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) out[i].e[k] = from_a(f[i], (E*)nullptr);
 #pragma unroll
@@ -148,7 +149,8 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
 {
     using A = typename Storage<ST>::A;
     const int wx0 = x0 - lane * V, wx1 = wx0 + 32 * V - 1;
-    if (wx1 < P.nx && !(P.wet_y && (y == 0 || y == P.ny - 1))) {
+    // warps on a wet row or touching a wet column gather node by node (gather_wet)
+    if (wx1 < P.nx && !(P.wet_y && (y == 0 || y == P.ny - 1)) && !(P.wet_x && (wx0 == 0 || wx1 == P.nx - 1))) {
         const bool walls =
             (!P.per_y && (y == 0 || y == P.ny - 1)) || (!P.per_x && (wx0 == 0 || wx1 == P.nx - 1));
         if (!SPLIT || walls) warp_vector<ST, V, true>(src, dst, P, x0, y, lane, keep);
@@ -160,7 +162,7 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
             if (x < P.nx && x >= keep) {
                 A f[9], g[5];
                 gather(src, P, x, y, f, g);
-                collide_any<Storage<ST>::DEV>(P, f, g);
+                collide_any<Storage<ST>::DEV>(P, f, g, row_base(P, y));
                 store_node(dst, P, x, y, f, g);
             }
         }
@@ -279,6 +281,7 @@ __device__ __forceinline__ void stage_compute(typename Storage<ST>::T* __restric
     const long long pl = P.plane;
     const int x0 = wx0 + lane * V;
     PK out[NPOP];
+    const A Tb = row_base(P, y);
     if constexpr (Storage<ST>::DEV && V % 2 == 0) {
 #pragma unroll
         for (int k = 0; k < V; k += 2) {
@@ -287,7 +290,10 @@ __device__ __forceinline__ void stage_compute(typename Storage<ST>::T* __restric
             for (int i = 0; i < 9; ++i) f[i] = F2(to_a(raw[k][i]), to_a(raw[k + 1][i]));
 #pragma unroll
             for (int i = 0; i < 5; ++i) g[i] = F2(to_a(raw[k][9 + i]), to_a(raw[k + 1][9 + i]));
-            collide_dev(P, f, g);
+            // rows here have no wall: g2 and g4 are pulled from the rows below and above
+            g[2] = g[2] - F2(P.T_dyw);
+            g[4] = g[4] + F2(P.T_dyw);
+            collide_dev(P, f, g, F2(Tb));
 #pragma unroll
             for (int i = 0; i < NPOP; ++i) {
                 float lo, hi;
@@ -301,7 +307,7 @@ __device__ __forceinline__ void stage_compute(typename Storage<ST>::T* __restric
         for (int k = 0; k < V; ++k) {
             A f[9], g[5];
             finish_pull(P, raw[k], 0, f, g);
-            collide_any<Storage<ST>::DEV>(P, f, g);
+            collide_any<Storage<ST>::DEV>(P, f, g, Tb);
 #pragma unroll
             for (int i = 0; i < 9; ++i) out[i].e[k] = from_a(f[i], (E*)nullptr);
 #pragma unroll
@@ -382,7 +388,7 @@ __global__ void k_init(typename Storage<ST>::T* __restrict__ dst, const LatParam
     const long long n = (long long)y * P.nx + x;
     A f[9], g[5];
     equilibrium<Storage<ST>::DEV>(P, rho ? A(rho[n]) : A(rho0), ux ? A(ux[n]) : A(0),
-                                  uy ? A(uy[n]) : A(0), T ? A(T[n]) : P.T0, f, g);
+                                  uy ? A(uy[n]) : A(0), T ? A(T[n]) : P.T0, f, g, row_base(P, y));
     const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
@@ -409,6 +415,9 @@ __global__ void k_init(typename Storage<ST>::T* __restrict__ dst, const LatParam
         if (i < 5) {
             A v = g[i];
             if (side >= 0 && P.kind[side] == WALL_DIRICHLET) v = P.Tw_c2[side] - v;
+            // a value the pull reads from the row below (above) is stored against that row's base
+            if (side < 0 && EY[i] == 1) v = v + P.T_dyw;
+            if (side < 0 && EY[i] == -1) v = v - P.T_dyw;
             dst[(9 + plane) * P.plane + slot] = from_a(v, (E*)nullptr);
         }
     }
@@ -426,12 +435,12 @@ __global__ void k_fields(const typename Storage<ST>::T* __restrict__ src,
     if (x >= P.nx || y >= P.ny) return;
     A f[9], g[5];
     gather(src, P, x, y, f, g);
-    const Macro<A> m = macroscopic(P, f, g);
+    const Macro<A> m = macroscopic(P, f, g, row_base(P, y));
     const long long n = (long long)y * P.nx + x;
     if (rho) rho[n] = double(P.rho_b) + double(m.drho);
     if (ux) ux[n] = double(m.ux);
     if (uy) uy[n] = double(m.uy);
-    if (T) T[n] = double(P.T_b) + double(m.dT);
+    if (T) T[n] = fma(double(y), double(P.T_dy), double(P.T_b)) + double(m.dT);
 }
 
 // Pre-collision populations at the current time as double f[9][ny][nx], g[5][ny][nx]
@@ -451,7 +460,8 @@ __global__ void k_pops(const typename Storage<ST>::T* __restrict__ src,
 #pragma unroll
     for (int i = 0; i < 9; ++i) f_out[i * N + n] = double(f[i]) + double(w9<A>(i)) * double(P.rho_b);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) g_out[i * N + n] = double(g[i]) + double(w5<A>(i, P.cs2T)) * double(P.T_b);
+    for (int i = 0; i < 5; ++i)
+        g_out[i * N + n] = double(g[i]) + double(w5<A>(i, P.cs2T)) * fma(double(y), double(P.T_dy), double(P.T_b));
 }
 
 constexpr int kReduceThreads = 256;
@@ -480,30 +490,29 @@ __device__ __forceinline__ void block_sum(double v[RS_N], double* out)
 template <typename A, typename S>
 __device__ __forceinline__ A nu_term(const LatParams<S>& P, const Macro<A>& m, int axis, A& T_out)
 {
-    const A T = A(P.T_b) + m.dT;
-    T_out = T;
-    return (axis == 0 ? m.ux : m.uy) * (T - A(P.T0));
+    T_out = m.T;
+    return (axis == 0 ? m.ux : m.uy) * (m.T - A(P.T0));
 }
 
 // One node's terms of the diagnostics sums, added to v: the fields come from the pulled populations,
 // the terms are formed in the arithmetic precision A (FP64 for FP64 storage, FP32 for the FP32 and
 // FP16 forms, whose fields carry FP32 rounding anyway; GB300 issues FP64 slowly) and accumulated in
-// FP64. With update != 0 the node's snapshot entries are replaced by the current fields. wrow
-// weights the Nusselt term (wet-wall rows count half, the trapezoid rule over [0, H]).
+// FP64. With update != 0 the node's snapshot entries are replaced by the current fields. The
+// Nusselt term is weighted by wet_weight (wet-wall rows and columns count half: the trapezoid rule
+// over [0, H]).
 template <typename E, typename A>
 __device__ __forceinline__ void node_diag(const E* __restrict__ src, const LatParams<A>& P, int x, int y,
-                                          int axis, double* __restrict__ snap, int update, double wrow,
-                                          double v[RS_N])
+                                          int axis, double* __restrict__ snap, int update, double v[RS_N])
 {
     const long long N = (long long)P.nx * P.ny;
     A f[9], g[5];
     gather(src, P, x, y, f, g);
-    const Macro<A> m = macroscopic(P, f, g);
+    const Macro<A> m = macroscopic(P, f, g, row_base(P, y));
     A T;
     const A q = nu_term(P, m, axis, T);
     const long long n = (long long)y * P.nx + x;
     const A dux = m.ux - A(snap[n]), duy = m.uy - A(snap[N + n]), dT = T - A(snap[2 * N + n]);
-    v[RS_UT] += wrow * double(q);
+    v[RS_UT] += wet_weight(P, x, y) * double(q);
     v[RS_DU] += double(dux * dux + duy * duy);
     v[RS_U] += double(m.ux * m.ux + m.uy * m.uy);
     v[RS_DT] += double(dT * dT);
@@ -527,10 +536,8 @@ __device__ __forceinline__ void reduce_row(const E* __restrict__ src, const LatP
                                            int axis, double* __restrict__ snap, int update,
                                            double* __restrict__ partial_row)
 {
-    // wet walls lie on the end rows: the average over [0, H] gives those rows half weight
-    const double wrow = (P.wet_y && axis == 1 && (y == 0 || y == P.ny - 1)) ? 0.5 : 1.0;
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
-    for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, wrow, v);
+    for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, v);
     block_sum(v, partial_row);
 }
 
@@ -549,9 +556,8 @@ __global__ void __launch_bounds__(kReduceThreads, 4) k_reduce_nodes(
 {
     const int seg = blockIdx.x % nseg, y = blockIdx.x / nseg;
     const int x0 = seg * kDiagNodes, x1 = min(P.nx, x0 + kDiagNodes);
-    const double wrow = (P.wet_y && axis == 1 && (y == 0 || y == P.ny - 1)) ? 0.5 : 1.0;
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
-    for (int x = x0 + threadIdx.x; x < x1; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, wrow, v);
+    for (int x = x0 + threadIdx.x; x < x1; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, v);
     block_sum(v, partial + (long long)blockIdx.x * RS_N);
 }
 

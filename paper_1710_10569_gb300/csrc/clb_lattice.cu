@@ -61,11 +61,15 @@ clb_status validate(int nx, int ny, const clb_params* p)
     if ((p->wall[0] == CLB_PERIODIC) != (p->wall[1] == CLB_PERIODIC) ||
         (p->wall[2] == CLB_PERIODIC) != (p->wall[3] == CLB_PERIODIC))
         return set_error(CLB_EINVAL, "periodic sides must come in pairs");
-    if (p->wall[0] == CLB_WALL_WET || p->wall[1] == CLB_WALL_WET ||
-        (p->wall[2] == CLB_WALL_WET) != (p->wall[3] == CLB_WALL_WET))
-        return set_error(CLB_EINVAL, "wet walls go on both y sides (not on x sides)");
-    if (p->wall[2] == CLB_WALL_WET && (p->wall[0] != CLB_PERIODIC || ny < 3))
-        return set_error(CLB_EINVAL, "wet walls need periodic x sides and ny >= 3");
+    for (int a = 0; a < 2; ++a) {
+        const int lo = p->wall[2 * a], hi = p->wall[2 * a + 1], other = p->wall[2 - 2 * a];
+        if ((lo == CLB_WALL_WET) != (hi == CLB_WALL_WET))
+            return set_error(CLB_EINVAL, "wet walls go on both sides of an axis");
+        if (lo == CLB_WALL_WET && (a == 0 ? nx : ny) < 3)
+            return set_error(CLB_EINVAL, "wet walls need at least 3 nodes across");
+        if (lo == CLB_WALL_WET && other != CLB_PERIODIC && other != CLB_WALL_WET)
+            return set_error(CLB_EINVAL, "the sides next to wet walls must be periodic or wet");
+    }
     if (p->storage < CLB_F64 || p->storage > CLB_F16DEV)
         return set_error(CLB_EINVAL, "storage %d is not a clb_storage", p->storage);
     return CLB_OK;

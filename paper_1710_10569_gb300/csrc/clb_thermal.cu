@@ -56,6 +56,9 @@ __device__ __forceinline__ void thermal_gather(const E* __restrict__ src, const 
     thermal_slots(P, x, y, idx, mask);
 #pragma unroll
     for (int i = 0; i < NT; ++i) g[i] = to_a(src[idx[i]]);
+    // g2 (g4) pulled from the row below (above) is re-based to this row; bounced values are not
+    g[2] = (mask & 4) ? g[2] : g[2] - P.T_dyw;
+    g[4] = (mask & 8) ? g[4] : g[4] + P.T_dyw;
     if (mask) {
         if ((mask & 1) && P.kind[0] == WALL_DIRICHLET) g[1] = P.Tw_c2[0] - g[1];
         if ((mask & 2) && P.kind[1] == WALL_DIRICHLET) g[3] = P.Tw_c2[1] - g[3];
@@ -64,16 +67,54 @@ __device__ __forceinline__ void thermal_gather(const E* __restrict__ src, const 
     }
 }
 
+// D2Q5 equilibrium g^eq(T, u) in stored form (minus w^T T_b(y) for deviation storage; dT = T - T_b(y)).
+template <bool DEV, typename A>
+__device__ __forceinline__ void thermal_eq(const LatParams<A>& P, A T, A dT, A u, A v, A g[NT])
+{
+    if constexpr (DEV) eq_dev_d2q5(T, dT, u, v, P.cs2T, g);
+    else back_d2q5(T, A(0), A(0), T * P.cs2T, T * P.cs2T, u, v, g);
+}
+
+// Pulled populations of node (x, y) with the wall rules, including wet walls: a node on a wet
+// wall takes g_i = g^eq_i(T_w, u) + [g_i(q) - g^eq_i(T(q), u(q))] from the fluid node q next to it
+// (along the normal; the diagonal neighbour at a corner, where T_w is the mean of the two walls'
+// temperatures), u being the prescribed velocity of each node (the paper's non-equilibrium
+// extrapolation, Sec. 3).
+template <bool DEV, typename E, typename A, typename VT>
+__device__ __forceinline__ void thermal_gather_node(const E* __restrict__ src, const LatParams<A>& P,
+                                                    const VT* __restrict__ ux, const VT* __restrict__ uy,
+                                                    int x, int y, A g[NT])
+{
+    const bool onx = P.wet_x && (x == 0 || x == P.nx - 1);
+    const bool ony = P.wet_y && (y == 0 || y == P.ny - 1);
+    if (!onx && !ony) {
+        thermal_gather(src, P, x, y, g);
+        return;
+    }
+    const int qx = onx ? (x == 0 ? 1 : x - 1) : x, qy = ony ? (y == 0 ? 1 : y - 1) : y;
+    const int side_x = x == 0 ? 0 : 1, side_y = y == 0 ? 2 : 3;
+    const A Tw = (onx && ony) ? A(0.5) * (P.Twall[side_x] + P.Twall[side_y]) : P.Twall[ony ? side_y : side_x];
+    const A dTw = (onx && ony) ? Tw - P.T_b : P.dTw[ony ? side_y : side_x];
+    A gq[NT], eq_q[NT], eq_b[NT];
+    thermal_gather(src, P, qx, qy, gq);
+    const A dTq = (gq[0] + gq[1]) + (gq[2] + gq[3]) + gq[4];
+    const long long nq = (long long)qy * P.nx + qx, nb = (long long)y * P.nx + x;
+    thermal_eq<DEV>(P, row_base(P, qy) + dTq, dTq, A(ux[nq]), A(uy[nq]), eq_q);
+    thermal_eq<DEV>(P, Tw, dTw, A(ux[nb]), A(uy[nb]), eq_b);
+#pragma unroll
+    for (int i = 0; i < NT; ++i) g[i] = eq_b[i] + (gq[i] - eq_q[i]);
+}
+
 // One node's collision (Eqs. 16-21) with its prescribed velocity.
 template <int ST>
 __device__ __forceinline__ void thermal_collide(const LatParams<typename Storage<ST>::A>& P,
                                                 typename Storage<ST>::A u, typename Storage<ST>::A v,
-                                                typename Storage<ST>::A g[NT])
+                                                typename Storage<ST>::A g[NT], typename Storage<ST>::A Tb)
 {
     using A = typename Storage<ST>::A;
     const A dT = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
-    if constexpr (Storage<ST>::DEV) collide_d2q5_dev(P, P.T_b + dT, dT, u, v, g);
-    else collide_d2q5(P, P.T_b + dT, u, v, g);
+    if constexpr (Storage<ST>::DEV) collide_d2q5_dev(P, Tb + dT, dT, u, v, g);
+    else collide_d2q5(P, Tb + dT, u, v, g);
 }
 
 // One time step, two neighbouring nodes x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x) and x0 + 1
@@ -113,13 +154,19 @@ __global__ void __launch_bounds__(256) k_thermal_step(const typename Storage<ST>
         gb[3] = to_a(src[3 * pl + here + 2]);
         ga[4] = to_a(c4.e[0]);
         gb[4] = to_a(c4.e[1]);
+        // re-based to this row (see thermal_gather)
+        ga[2] = ga[2] - P.T_dyw;
+        gb[2] = gb[2] - P.T_dyw;
+        ga[4] = ga[4] + P.T_dyw;
+        gb[4] = gb[4] + P.T_dyw;
     } else {
-        thermal_gather(src, P, x0, y, ga);
-        if (two) thermal_gather(src, P, x0 + 1, y, gb);
+        thermal_gather_node<Storage<ST>::DEV>(src, P, ux, uy, x0, y, ga);
+        if (two) thermal_gather_node<Storage<ST>::DEV>(src, P, ux, uy, x0 + 1, y, gb);
     }
-    thermal_collide<ST>(P, A(ux[n]), A(uy[n]), ga);
+    const A Tb = row_base(P, y);
+    thermal_collide<ST>(P, A(ux[n]), A(uy[n]), ga, Tb);
     if (two) {
-        thermal_collide<ST>(P, A(ux[n + 1]), A(uy[n + 1]), gb);
+        thermal_collide<ST>(P, A(ux[n + 1]), A(uy[n + 1]), gb, Tb);
         // here is even (x0 and the row pitch are): one aligned pair per plane
 #pragma unroll
         for (int i = 0; i < NT; ++i) {
@@ -154,7 +201,7 @@ __global__ void k_thermal_init(typename Storage<ST>::T* __restrict__ dst, VelT<S
     uys[n] = v;
     A g[NT];
     if constexpr (Storage<ST>::DEV) {
-        eq_dev_d2q5(t, t - P.T_b, u, v, P.cs2T, g);
+        eq_dev_d2q5(t, t - row_base(P, y), u, v, P.cs2T, g);
     } else {
         back_d2q5(t, A(0), A(0), t * P.cs2T, t * P.cs2T, u, v, g);
     }
@@ -180,26 +227,30 @@ __global__ void k_thermal_init(typename Storage<ST>::T* __restrict__ dst, VelT<S
             slot = (long long)y * P.pitch + x;
             if (P.kind[side] == WALL_DIRICHLET) val = P.Tw_c2[side] - val;
         }
+        // a value the pull reads from the row below (above) is stored against that row's base
+        if (side < 0 && EY[i] == 1) val = val + P.T_dyw;
+        if (side < 0 && EY[i] == -1) val = val - P.T_dyw;
         dst[plane * P.plane + slot] = from_a(val, (E*)nullptr);
     }
 }
 
 template <int ST>
 __global__ void k_thermal_out(const typename Storage<ST>::T* __restrict__ src,
-                              const LatParams<typename Storage<ST>::A> P, double* __restrict__ T,
-                              double* __restrict__ pops)
+                              const LatParams<typename Storage<ST>::A> P, const VelT<ST>* __restrict__ ux,
+                              const VelT<ST>* __restrict__ uy, double* __restrict__ T, double* __restrict__ pops)
 {
     using A = typename Storage<ST>::A;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     A g[NT];
-    thermal_gather(src, P, x, y, g);
+    thermal_gather_node<Storage<ST>::DEV>(src, P, ux, uy, x, y, g);
     const long long n = (long long)y * P.nx + x, N = (long long)P.nx * P.ny;
-    if (T) T[n] = double(P.T_b) + double((g[0] + g[1]) + (g[2] + g[3]) + g[4]);
+    const double base = fma(double(y), double(P.T_dy), double(P.T_b));
+    if (T) T[n] = base + double((g[0] + g[1]) + (g[2] + g[3]) + g[4]);
     if (pops)
 #pragma unroll
-        for (int i = 0; i < NT; ++i) pops[i * N + n] = double(g[i]) + double(w5<A>(i, P.cs2T)) * double(P.T_b);
+        for (int i = 0; i < NT; ++i) pops[i * N + n] = double(g[i]) + double(w5<A>(i, P.cs2T)) * base;
 }
 
 constexpr int kChunkT = 32;
@@ -258,12 +309,21 @@ clb_status thermal_launch(clb_thermal* h, int from, cudaStream_t s)
 
 clb_status thermal_out(clb_thermal* h, double* T, double* pops)
 {
-    const dim3 block(128, 1), grid((h->nx + 255) / 256, h->ny);  // two nodes per thread
+    const dim3 block(128, 1), grid((h->nx + 127) / 128, h->ny);  // one node per thread
     const void* a = h->buf[h->cur];
     switch (h->p.storage) {
-    case CLB_F64: k_thermal_out<ST_F64><<<grid, block, 0, h->stream>>>((const double*)a, h->Pd, T, pops); break;
-    case CLB_F32: k_thermal_out<ST_F32><<<grid, block, 0, h->stream>>>((const float*)a, h->Pf, T, pops); break;
-    default: k_thermal_out<ST_F16DEV><<<grid, block, 0, h->stream>>>((const __half*)a, h->Pf, T, pops); break;
+    case CLB_F64:
+        k_thermal_out<ST_F64><<<grid, block, 0, h->stream>>>((const double*)a, h->Pd, (const double*)h->vel[0],
+                                                             (const double*)h->vel[1], T, pops);
+        break;
+    case CLB_F32:
+        k_thermal_out<ST_F32><<<grid, block, 0, h->stream>>>((const float*)a, h->Pf, (const float*)h->vel[0],
+                                                             (const float*)h->vel[1], T, pops);
+        break;
+    default:
+        k_thermal_out<ST_F16DEV><<<grid, block, 0, h->stream>>>((const __half*)a, h->Pf, (const float*)h->vel[0],
+                                                                (const float*)h->vel[1], T, pops);
+        break;
     }
     CLB_CUDA(cudaGetLastError());
     return CLB_OK;
@@ -276,7 +336,6 @@ extern "C" clb_status clb_thermal_create(int nx, int ny, const clb_params* p, vo
     if (!out) return set_error(CLB_EINVAL, "out is NULL");
     *out = nullptr;
     CLB_TRY(validate(nx, ny, p));
-    if (p->wall[2] == CLB_WALL_WET) return set_error(CLB_EINVAL, "wet walls are not available in the thermal-only mode");
     auto* h = new (std::nothrow) clb_thermal;
     if (!h) return host_alloc_failed();
     h->nx = nx;
@@ -336,7 +395,7 @@ extern "C" clb_status clb_thermal_init(clb_thermal* h, const double* T, const do
             CLB_CUDA(cudaMemcpyAsync(h->stage + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
             dev[k] = h->stage + k * N;
         }
-    const dim3 block(128, 1), grid((h->nx + 255) / 256, h->ny);  // two nodes per thread
+    const dim3 block(128, 1), grid((h->nx + 127) / 128, h->ny);  // one node per thread
     void* d = h->buf[h->cur];
     switch (h->p.storage) {
     case CLB_F64: k_thermal_init<ST_F64><<<grid, block, 0, h->stream>>>((double*)d, (double*)h->vel[0], (double*)h->vel[1], h->Pd, dev[0], dev[1], dev[2]); break;

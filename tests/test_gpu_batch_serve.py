@@ -23,6 +23,11 @@ def clb():
 
 def mixed_problems(storage, count=6):
     probs = [W.random_problem(17 + 13 * k, 11 + 7 * k, seed=k, storage=storage) for k in range(count - 2)]
+    if count >= 6:
+        # the paper's own walls on the x sides, and on all four sides (corners)
+        probs[2] = W.random_problem(43, 25, seed=2, storage=storage, walls=(W.WALL_WET, W.WALL_WET, W.WALL_PERIODIC,
+                                                                             W.WALL_PERIODIC), moving=True)
+        probs[3] = W.random_problem(56, 32, seed=3, storage=storage, walls=(W.WALL_WET,) * 4, moving=True)
     probs.append(W.cavity(40, Ra=1e4, storage=storage))
     probs.append(W.taylor_green(24, ny=48, storage=storage))
     return probs

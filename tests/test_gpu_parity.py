@@ -159,6 +159,29 @@ def test_wet_walls(clb, storage, seed):
         assert lat.nusselt(1) == pytest.approx(o.nusselt(1), rel=1e-12, abs=1e-12)
 
 
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+@pytest.mark.parametrize("walls", [(W.WALL_WET, W.WALL_WET, P, P), (W.WALL_WET,) * 4], ids=["wet_x", "wet_box"])
+@pytest.mark.parametrize("shape", [(23, 70), (333, 9), (3, 3)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_wet_walls_on_x_sides_and_in_corners(clb, storage, walls, shape):
+    """The paper's own wall conditions on the x sides (walls on the end columns), and on all four
+    sides of a closed box (the corner rule), with moving/injecting walls, body force and buoyancy,
+    against the oracle; rows wide enough for interior warps on the vector path, the smallest box
+    (one fluid node), and the Nusselt number along both axes (trapezoid weights in every wet
+    direction)."""
+    nx, ny = shape
+    prob = W.random_problem(nx, ny, seed=nx, storage=storage, walls=walls, moving=True)
+    _, _, got, exp = run_both(clb, prob, 40)
+    compare(f"wet_{'box' if walls[2] == W.WALL_WET else 'x'}{nx}x{ny}_{W.STORAGE_NAMES[storage]}", got, exp,
+            tol(storage, 40), prob.params)
+    if storage == F64:
+        lat = clb.Lattice.from_problem(prob)
+        lat.step(40)
+        o = oracle.Oracle.from_problem(prob)
+        o.step(40)
+        for axis in (0, 1):
+            assert lat.nusselt(axis) == pytest.approx(o.nusselt(axis), rel=1e-12, abs=1e-12)
+
+
 def test_initial_fields_match_oracle(clb):
     """Step 0: the inverse-stream initialisation reproduces the oracle's f(x,0) = f^eq exactly,
     walls included."""
@@ -222,8 +245,9 @@ def test_graph_chunks_equal_single_launches(clb):
 
 
 @pytest.mark.parametrize("storage", [F64, F32, F16])
-@pytest.mark.parametrize("walls", [(P, P, P, P), (D, D, A, A), (P, P, D, D), (P, P, W.WALL_WET, W.WALL_WET)],
-                         ids=["periodic", "cavity", "rb", "wet"])
+@pytest.mark.parametrize("walls", [(P, P, P, P), (D, D, A, A), (P, P, D, D), (P, P, W.WALL_WET, W.WALL_WET),
+                                   (W.WALL_WET, W.WALL_WET, P, P), (W.WALL_WET,) * 4],
+                         ids=["periodic", "cavity", "rb", "wet", "wet_x", "wet_box"])
 def test_launch_shapes_are_bitwise_equal(clb, storage, walls):
     """Vector interior path, scalar wall/ragged path and every launch shape give the same bits."""
     prob = W.random_problem(333, 37, seed=3, storage=storage, walls=walls)

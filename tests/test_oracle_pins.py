@@ -656,3 +656,120 @@ def test_hydrostatic_start_of_rayleigh_benard_is_at_rest():
     rho, T, gb = prob.rho[:, 0], prob.T[:, 0], prob.params["g_beta"]
     np.testing.assert_allclose(np.diff(rho) / 3.0, gb * 0.5 * (T[1:] + T[:-1]), rtol=1e-9, atol=1e-15)
     assert rho.mean() == pytest.approx(1.0, abs=1e-6)  # the continuous mean; nodes sample it at mid-cells
+
+
+# ----------------------------------------------------------------------------- wet walls on x sides, corners
+
+WET = W.WALL_WET
+
+
+def _wet_problem(nx, ny, walls, seed, T_wall=(0.3, -0.2, 0.4, -0.1), u_wall=((0, 0),) * 4, g_beta=0.0,
+                 Fv=(0.0, 0.0), thermal_only=0):
+    rng = np.random.default_rng(seed)
+    p = W.default_params(nu=0.05, kappa=0.04, g_beta=g_beta, Fv=Fv, wall=walls, T_wall=T_wall,
+                         u_wall=u_wall, lambda2=1.1, s_b=1.2)
+    if thermal_only:
+        p = dict(p, thermal_only=1)
+    rho = 1.0 + rng.uniform(-1e-3, 1e-3, (ny, nx))
+    ux = rng.uniform(-0.02, 0.02, (ny, nx))
+    uy = rng.uniform(-0.02, 0.02, (ny, nx))
+    T = rng.uniform(-0.3, 0.3, (ny, nx))
+    return p, rho, ux, uy, T
+
+
+def test_wet_x_walls_are_the_transpose_of_wet_y_walls():
+    """Wet walls on the x sides (reading r26) give exactly the transpose of the same problem with
+    wet walls on the y sides (reading r19, pinned by the exact profiles and Table 1): the moment
+    set, the relaxation matrix and the wall rules are symmetric under exchanging x and y, moving
+    walls (tangential motion and normal injection) and a body force included (no buoyancy, which
+    has a direction)."""
+    nx, ny = 5, 9
+    uw = ((0, 0), (0, 0), (0.03, 0.01), (-0.02, -0.01))
+    p1, rho, ux, uy, T = _wet_problem(nx, ny, (P, P, WET, WET), 1, u_wall=uw, Fv=(2e-5, -1e-5))
+    o1 = oracle.Oracle(nx, ny, p1)
+    o1.init(rho, ux, uy, T)
+    p2 = dict(p1, wall=(WET, WET, P, P), T_wall=(p1["T_wall"][2], p1["T_wall"][3], 0.0, 0.0),
+              u_wall=((uw[2][1], uw[2][0]), (uw[3][1], uw[3][0]), (0, 0), (0, 0)), Fv=(-1e-5, 2e-5))
+    o2 = oracle.Oracle(ny, nx, p2)
+    o2.init(rho.T.copy(), uy.T.copy(), ux.T.copy(), T.T.copy())
+    o1.step(60)
+    o2.step(60)
+    r1, x1, y1, t1 = o1.fields()
+    r2, x2, y2, t2 = o2.fields()
+    for a, b in ((r2, r1.T), (x2, y1.T), (y2, x1.T), (t2, t1.T)):
+        np.testing.assert_allclose(a, b, atol=1e-14, rtol=0)
+
+
+def test_wet_x_walls_exact_couette_and_conduction():
+    """Between wet x walls (periodic y) the steady states are exact: Couette flow u_y linear
+    between a resting wall and one moving along the wall, and T linear between the wall
+    temperatures, the walls on the end columns (L = nx - 1)."""
+    nx, ny = 9, 4
+    p = W.default_params(nu=0.1, kappa=0.1, wall=(WET, WET, P, P), T_wall=(0.3, -0.2, 0, 0),
+                         u_wall=((0, 0), (0, 0.02), (0, 0), (0, 0)))
+    o = oracle.Oracle(nx, ny, p)
+    o.init(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    o.step(6000)
+    _, ux, uy, T = o.fields()
+    s = np.arange(nx) / (nx - 1)
+    np.testing.assert_allclose(uy, np.broadcast_to(0.02 * s, (ny, nx)), atol=1e-12)
+    np.testing.assert_allclose(ux, 0.0, atol=1e-12)
+    np.testing.assert_allclose(T, np.broadcast_to(0.3 - 0.5 * s, (ny, nx)), atol=1e-12)
+
+
+def test_wet_box_rest_state_is_a_fixed_point():
+    """A closed box of wet walls (all four sides, corners included) at rest with every wall at the
+    fluid's temperature and no force stays exactly at rest."""
+    nx, ny = 7, 6
+    p = W.default_params(nu=0.05, kappa=0.04, wall=(WET,) * 4, T_wall=(0.25,) * 4)
+    o = oracle.Oracle(nx, ny, p)
+    o.init(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)), np.full((ny, nx), 0.25))
+    o.step(200)
+    rho, ux, uy, T = o.fields()
+    np.testing.assert_allclose(rho, 1.0, atol=1e-14)
+    np.testing.assert_allclose(ux, 0.0, atol=1e-15)
+    np.testing.assert_allclose(uy, 0.0, atol=1e-15)
+    np.testing.assert_allclose(T, 0.25, atol=1e-14)
+
+
+def test_wet_box_symmetries_through_the_corners():
+    """A square closed box of wet walls: (a) without buoyancy, with the left and bottom walls hot
+    and the others cold and transpose-symmetric initial fields, the state stays symmetric under
+    exchanging x and y (each corner's rule, mean wall temperature and diagonal neighbour map onto
+    its transposed corner's); (b) with buoyancy (hot bottom, cold top, side walls at T0) and
+    mirror-symmetric initial fields, the state stays mirror-symmetric in x."""
+    n = 10
+    rng = np.random.default_rng(3)
+    A_, B_, C_ = rng.uniform(-0.2, 0.2, (3, n, n))
+    p = W.default_params(nu=0.05, kappa=0.04, wall=(WET,) * 4, T_wall=(0.5, -0.5, 0.5, -0.5))
+    o = oracle.Oracle(n, n, p)
+    o.init(1.0 + 1e-3 * (C_ + C_.T), 0.02 * B_, 0.02 * B_.T, A_ + A_.T)
+    o.step(80)
+    rho, ux, uy, T = o.fields()
+    np.testing.assert_allclose(T, T.T, atol=1e-13)
+    np.testing.assert_allclose(rho, rho.T, atol=1e-14)
+    np.testing.assert_allclose(ux, uy.T, atol=1e-14)
+    p = W.default_params(nu=0.05, kappa=0.04, g_beta=1e-3, wall=(WET,) * 4, T_wall=(0.0, 0.0, 0.5, -0.5))
+    o = oracle.Oracle(n, n, p)
+    Ts = A_ + A_[:, ::-1]
+    o.init(np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)), Ts)
+    o.step(300)
+    rho, ux, uy, T = o.fields()
+    assert np.max(np.abs(uy)) > 1e-4  # buoyancy has set the fluid moving
+    np.testing.assert_allclose(T, T[:, ::-1], atol=1e-13)
+    np.testing.assert_allclose(uy, uy[:, ::-1], atol=1e-14)
+    np.testing.assert_allclose(ux, -ux[:, ::-1], atol=1e-14)
+
+
+@pytest.mark.parametrize("U", [0.0, 0.05])
+def test_thermal_only_wet_walls_exact_conduction(U):
+    """Thermal-only mode with wet y walls: with no velocity, or a uniform velocity along the walls
+    (which does not advect an x-uniform field), T is linear between the wall temperatures."""
+    nx, ny = 4, 11
+    p = dict(W.default_params(kappa=0.1, wall=(P, P, WET, WET), T_wall=(0, 0, 0.4, -0.1)), thermal_only=1)
+    o = oracle.Oracle(nx, ny, p)
+    o.init(np.ones((ny, nx)), np.full((ny, nx), U), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    o.step(5000)
+    T = o.fields()[3]
+    np.testing.assert_allclose(T, np.broadcast_to((0.4 - 0.5 * np.arange(ny) / (ny - 1))[:, None], (ny, nx)),
+                               atol=1e-12)

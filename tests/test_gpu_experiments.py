@@ -48,14 +48,12 @@ def test_table1_rayleigh_benard_batch(clb, storage):
     """Sec. 3.3, Table 1: the eight Rayleigh numbers stepped together in one batch from the paper's
     initial state. In FP64 the Nusselt numbers at 10k, 20k and 30k steps equal the oracle's to 1e-9,
     and at 200k steps the oracle's to 1e-6 and the analytic values of Table 1 within 2.5% (0.5% for
-    Ra <= 1e4). FP32 storage cannot grow the rolls from the paper's 1e-3 density disturbance near
-    onset (the per-step change of the temperature populations is below one FP32 ulp), so FP32 is
-    checked for Ra >= 3000 at 200k steps (1e-3 relative to the oracle)."""
+    Ra <= 1e4). FP32 storage, whose temperature populations are stored against the conduction line
+    between the walls, grows the rolls from the paper's 1e-3 density disturbance at every Ra,
+    onset included, and meets the oracle's steady values to 1e-4 at 200k steps."""
     gold = _golden("table1_oracle.json")
     paper = _table1_paper()
     ras = sorted(int(k) for k in gold)
-    if storage != F64:
-        ras = [ra for ra in ras if ra >= 3000]
     probs = [W.rayleigh_benard_table1(float(ra), storage=storage) for ra in ras]
     b = clb.Batch(probs)
     done = 0
@@ -72,9 +70,25 @@ def test_table1_rayleigh_benard_batch(clb, storage):
     nu, _ = b.diagnostics()
     for k, ra in enumerate(ras):
         steady = gold[str(ra)]["steady"]
-        assert nu[k] == pytest.approx(steady, rel=1e-6 if storage == F64 else 1e-3), ra
+        assert nu[k] == pytest.approx(steady, rel=1e-6 if storage == F64 else 1e-4), ra
         analytic = paper[ra][0]
         assert nu[k] == pytest.approx(analytic, rel=5e-3 if ra <= 10000 else 2.5e-2), ra
+
+
+def test_table1_fp16_stalls_below_its_resolution(clb):
+    """FP16 deviation storage keeps about 11 bits: near onset the per-step growth of the roll stays
+    below half a unit in the last place of the stored deviations, so from the paper's 1e-3 density
+    disturbance the layer stays at conduction (Nu within 1e-3 of 1) for Ra <= 1e4 over 200k steps,
+    and the developed rolls at Ra >= 2e4 come out within 6% of the oracle. This bounds the FP16
+    form: it is for developed flows, not for onset."""
+    from paper_1710_10569_gb300 import experiments as X
+    gold = _golden("table1_oracle.json")
+    r16 = X.table1(storage=F16)
+    for ra, nu in r16.items():
+        if ra <= 10000:
+            assert nu == pytest.approx(1.0, abs=1e-3), ra
+        else:
+            assert nu == pytest.approx(gold[str(ra)]["steady"], rel=0.06), ra
 
 
 def test_table1_fp32_follows_onset_when_seeded(clb):

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_rows_batched(
     __shared__ Member<A> M;
     load_member(mem + row_owner[blockIdx.x], M);
     const int y = blockIdx.x - M.row_begin;
-    reduce_row((const E*)M.buf[parity], M.P, y, M.axis, M.snap, update, M.partial + (long long)y * RS_N);
+    reduce_row((const E*)M.buf[parity], M.P, y, M.axis, (A*)M.snap, update, M.partial + (long long)y * RS_N);
 }
 
 template <typename A>
@@ -474,15 +474,15 @@ public:
         if (storage == CLB_F64) {
             const LatParams<double> P = make_lat_params<double>(L->nx, L->ny, L->p);
             k_init<ST_F64><<<grid, block, 0, stream>>>((double*)d, P, rho, ux, uy, T, L->p.rho0);
-            k_fields<ST_F64><<<grid, block, 0, stream>>>((const double*)d, P, nullptr, L->snap, L->snap + N, L->snap + 2 * N);
+            k_snap<ST_F64><<<grid, block, 0, stream>>>((const double*)d, P, L->snap);
         } else {
             const LatParams<float> P = make_lat_params<float>(L->nx, L->ny, L->p);
             if (storage == CLB_F32) {
                 k_init<ST_F32><<<grid, block, 0, stream>>>((float*)d, P, rho, ux, uy, T, L->p.rho0);
-                k_fields<ST_F32><<<grid, block, 0, stream>>>((const float*)d, P, nullptr, L->snap, L->snap + N, L->snap + 2 * N);
+                k_snap<ST_F32><<<grid, block, 0, stream>>>((const float*)d, P, (float*)L->snap);
             } else {
                 k_init<ST_F16DEV><<<grid, block, 0, stream>>>((__half*)d, P, rho, ux, uy, T, L->p.rho0);
-                k_fields<ST_F16DEV><<<grid, block, 0, stream>>>((const __half*)d, P, nullptr, L->snap, L->snap + N, L->snap + 2 * N);
+                k_snap<ST_F16DEV><<<grid, block, 0, stream>>>((const __half*)d, P, (float*)L->snap);
             }
         }
         CLB_CUDA(cudaGetLastError());

@@ -496,13 +496,15 @@ __device__ __forceinline__ A nu_term(const LatParams<S>& P, const Macro<A>& m, i
 
 // One node's terms of the diagnostics sums, added to v: the fields come from the pulled populations,
 // the terms are formed in the arithmetic precision A (FP64 for FP64 storage, FP32 for the FP32 and
-// FP16 forms, whose fields carry FP32 rounding anyway; GB300 issues FP64 slowly) and accumulated in
-// FP64. With update != 0 the node's snapshot entries are replaced by the current fields. The
-// Nusselt term is weighted by wet_weight (wet-wall rows and columns count half: the trapezoid rule
-// over [0, H]).
+// FP16 forms, whose fields are FP32 values) and accumulated in FP64. The residual's snapshot is kept
+// in A as well: it holds those same values exactly, and GB300 issues FP64 instructions (the
+// conversions included) slowly enough that they bound this pass. With update != 0 the node's
+// snapshot entries are replaced by the current fields. The Nusselt term is weighted by wet_weight
+// (wet-wall rows and columns count half: the trapezoid rule over [0, H]; 1, 1/2 and 1/4 scale
+// exactly in A). Non-finite nodes are counted in nbad.
 template <typename E, typename A>
 __device__ __forceinline__ void node_diag(const E* __restrict__ src, const LatParams<A>& P, int x, int y,
-                                          int axis, double* __restrict__ snap, int update, double v[RS_N])
+                                          int axis, A* __restrict__ snap, int update, double v[RS_N], int& nbad)
 {
     const long long N = (long long)P.nx * P.ny;
     A f[9], g[5];
@@ -511,18 +513,36 @@ __device__ __forceinline__ void node_diag(const E* __restrict__ src, const LatPa
     A T;
     const A q = nu_term(P, m, axis, T);
     const long long n = (long long)y * P.nx + x;
-    const A dux = m.ux - A(snap[n]), duy = m.uy - A(snap[N + n]), dT = T - A(snap[2 * N + n]);
-    v[RS_UT] += wet_weight(P, x, y) * double(q);
+    const A dux = m.ux - snap[n], duy = m.uy - snap[N + n], dT = T - snap[2 * N + n];
+    v[RS_UT] += double(q * A(wet_weight(P, x, y)));
     v[RS_DU] += double(dux * dux + duy * duy);
     v[RS_U] += double(m.ux * m.ux + m.uy * m.uy);
     v[RS_DT] += double(dT * dT);
     v[RS_T] += double(T * T);
-    v[RS_BAD] += (isfinite(m.ux) && isfinite(m.uy) && isfinite(T) && isfinite(m.rho)) ? 0.0 : 1.0;
+    nbad += (isfinite(m.ux) && isfinite(m.uy) && isfinite(T) && isfinite(m.rho)) ? 0 : 1;
     if (update) {
-        snap[n] = double(m.ux);
-        snap[N + n] = double(m.uy);
-        snap[2 * N + n] = double(T);
+        snap[n] = m.ux;
+        snap[N + n] = m.uy;
+        snap[2 * N + n] = T;
     }
+}
+
+// The residual's snapshot of the current fields (u_x, u_y, T as A [3][ny][nx]), as node_diag keeps it.
+template <int ST>
+__global__ void k_snap(const typename Storage<ST>::T* __restrict__ src, const LatParams<typename Storage<ST>::A> P,
+                       typename Storage<ST>::A* __restrict__ snap)
+{
+    using A = typename Storage<ST>::A;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    A f[9], g[5];
+    gather(src, P, x, y, f, g);
+    const Macro<A> m = macroscopic(P, f, g, row_base(P, y));
+    const long long n = (long long)y * P.nx + x, N = (long long)P.nx * P.ny;
+    snap[n] = m.ux;
+    snap[N + n] = m.uy;
+    snap[2 * N + n] = m.T;
 }
 
 // Per-row FP64 partial sums for the diagnostics: sum u_axis (T - T0), sum |u - u_snap|^2,
@@ -533,11 +553,13 @@ __device__ __forceinline__ void node_diag(const E* __restrict__ src, const LatPa
 // lattice uses the row-segment form below.)
 template <typename E, typename A>
 __device__ __forceinline__ void reduce_row(const E* __restrict__ src, const LatParams<A>& P, int y,
-                                           int axis, double* __restrict__ snap, int update,
+                                           int axis, A* __restrict__ snap, int update,
                                            double* __restrict__ partial_row)
 {
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
-    for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, v);
+    int nbad = 0;
+    for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, v, nbad);
+    v[RS_BAD] = double(nbad);
     block_sum(v, partial_row);
 }
 
@@ -552,12 +574,14 @@ constexpr int kDiagNodes = kReduceThreads * 8;
 template <int ST>
 __global__ void __launch_bounds__(kReduceThreads, 4) k_reduce_nodes(
     const typename Storage<ST>::T* __restrict__ src, const LatParams<typename Storage<ST>::A> P,
-    int axis, double* __restrict__ snap, int update, double* __restrict__ partial, int nseg)
+    int axis, typename Storage<ST>::A* __restrict__ snap, int update, double* __restrict__ partial, int nseg)
 {
     const int seg = blockIdx.x % nseg, y = blockIdx.x / nseg;
     const int x0 = seg * kDiagNodes, x1 = min(P.nx, x0 + kDiagNodes);
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
-    for (int x = x0 + threadIdx.x; x < x1; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, v);
+    int nbad = 0;
+    for (int x = x0 + threadIdx.x; x < x1; x += kReduceThreads) node_diag(src, P, x, y, axis, snap, update, v, nbad);
+    v[RS_BAD] = double(nbad);
     block_sum(v, partial + (long long)blockIdx.x * RS_N);
 }
 

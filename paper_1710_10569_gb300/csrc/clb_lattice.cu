@@ -274,8 +274,8 @@ clb_status run_diagnostics(clb_handle* h, int axis, int update)
     const int rows = h->ny * nseg;  // partial entries
     switch (h->p.storage) {
     case CLB_F64: k_reduce_nodes<ST_F64><<<rows, kReduceThreads, 0, h->stream>>>((const double*)s, h->Pd, axis, h->snap, update, h->partial, nseg); break;
-    case CLB_F32: k_reduce_nodes<ST_F32><<<rows, kReduceThreads, 0, h->stream>>>((const float*)s, h->Pf, axis, h->snap, update, h->partial, nseg); break;
-    default: k_reduce_nodes<ST_F16DEV><<<rows, kReduceThreads, 0, h->stream>>>((const __half*)s, h->Pf, axis, h->snap, update, h->partial, nseg); break;
+    case CLB_F32: k_reduce_nodes<ST_F32><<<rows, kReduceThreads, 0, h->stream>>>((const float*)s, h->Pf, axis, (float*)h->snap, update, h->partial, nseg); break;
+    default: k_reduce_nodes<ST_F16DEV><<<rows, kReduceThreads, 0, h->stream>>>((const __half*)s, h->Pf, axis, (float*)h->snap, update, h->partial, nseg); break;
     }
     CLB_CUDA(cudaGetLastError());
     const NuGeom g = nu_geom(h->nx, h->ny, h->p, axis);
@@ -290,10 +290,18 @@ clb_status run_diagnostics(clb_handle* h, int axis, int update)
     return CLB_OK;
 }
 
+// The residual's snapshot of the current fields, in the arithmetic precision (k_snap).
 clb_status take_snapshot(clb_handle* h)
 {
-    const size_t N = (size_t)h->nx * h->ny;
-    return launch_fields(h, nullptr, h->snap, h->snap + N, h->snap + 2 * N);
+    const dim3 block(128, 1), grid = grid_for(h, 128, 1);
+    const void* s = h->buf[h->cur];
+    switch (h->p.storage) {
+    case CLB_F64: k_snap<ST_F64><<<grid, block, 0, h->stream>>>((const double*)s, h->Pd, h->snap); break;
+    case CLB_F32: k_snap<ST_F32><<<grid, block, 0, h->stream>>>((const float*)s, h->Pf, (float*)h->snap); break;
+    default: k_snap<ST_F16DEV><<<grid, block, 0, h->stream>>>((const __half*)s, h->Pf, (float*)h->snap); break;
+    }
+    CLB_CUDA(cudaGetLastError());
+    return CLB_OK;
 }
 
 std::mutex g_tune_mu;

@@ -62,15 +62,17 @@ __global__ void __launch_bounds__(kReduceThreads) k_nusselt_rows_noalloc(
     using A = typename Storage<ST>::A;
     const int y = blockIdx.x;
     double v[RS_N] = {0, 0, 0, 0, 0, 0};
+    int nbad = 0;
     for (int x = threadIdx.x; x < P.nx; x += kReduceThreads) {
         A f[9], g[5];
         gather(src, P, x, y, f, g);
         const Macro<A> m = macroscopic(P, f, g, row_base(P, y));
         A T;
         const A q = nu_term(P, m, axis, T);  // the same term as the handle-based diagnostics
-        v[RS_UT] += wet_weight(P, x, y) * double(q);
-        v[RS_BAD] += (isfinite(m.ux) && isfinite(m.uy) && isfinite(T) && isfinite(m.rho)) ? 0.0 : 1.0;
+        v[RS_UT] += double(q * A(wet_weight(P, x, y)));
+        nbad += (isfinite(m.ux) && isfinite(m.uy) && isfinite(T) && isfinite(m.rho)) ? 0 : 1;
     }
+    v[RS_BAD] = double(nbad);
     block_sum(v, scratch + (long long)y * RS_N);
 }
 

@@ -377,3 +377,19 @@ def test_autotune_keeps_state(clb):
     assert a.launch() == shape
     for x, y in zip(a.fields(), before):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+def test_check_equals_nusselt_and_residual(clb, storage):
+    """clb_check gives, from one pass, what clb_nusselt and clb_residual give (bitwise), and its
+    snapshot serves the next residual the same way."""
+    prob = W.rayleigh_benard(96, 48, Ra=2e4, storage=storage)
+    a, b = clb.Lattice.from_problem(prob), clb.Lattice.from_problem(prob)
+    for n in (150, 150):
+        a.step(n)
+        b.step(n)
+        nu, er = a.check(1)
+        assert nu == b.nusselt(1)
+        assert er == b.residual()
+    a.close()
+    b.close()

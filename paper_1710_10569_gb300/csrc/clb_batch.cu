@@ -12,7 +12,7 @@
 #include <memory>
 #include <vector>
 
-#include "clb_kernels.cuh"
+#include "clb_diag.cuh"
 
 using namespace clb;
 

@@ -10,7 +10,7 @@
 #include <tuple>
 #include <vector>
 
-#include "clb_kernels.cuh"
+#include "clb_diag.cuh"
 
 using namespace clb;
 

@@ -21,7 +21,7 @@
 
 #include <mutex>
 
-#include "clb_kernels.cuh"
+#include "clb_diag.cuh"
 
 using namespace clb;
 

@@ -124,7 +124,7 @@ __device__ __forceinline__ void thermal_collide(const LatParams<typename Storage
 // an odd row) gather node by node with the wall rules. The values are those of the node-by-node
 // path.
 template <int ST>
-__global__ void __launch_bounds__(256) k_thermal_step(const typename Storage<ST>::T* __restrict__ src,
+__global__ void __launch_bounds__(128, ST == ST_F64 ? 8 : 12) k_thermal_step(const typename Storage<ST>::T* __restrict__ src,
                                                       typename Storage<ST>::T* __restrict__ dst,
                                                       const VelT<ST>* __restrict__ ux,
                                                       const VelT<ST>* __restrict__ uy,

@@ -66,6 +66,12 @@ def test_footprint_scales_with_storage(clb):
     (dict(wall=(0, 1, 0, 0)), 8, 8),
     (dict(wall=(1, 1, 0, 2)), 8, 8),
     (dict(wall=(7, 7, 0, 0)), 8, 8),
+    (dict(wall=(3, 0, 0, 0)), 8, 8),      # wet walls come in pairs
+    (dict(wall=(0, 0, 3, 1)), 8, 8),
+    (dict(wall=(3, 3, 1, 1)), 8, 8),      # beside wet walls: periodic or wet sides only
+    (dict(wall=(2, 2, 3, 3)), 8, 8),
+    (dict(wall=(3, 3, 0, 0)), 2, 8),      # three nodes across a wet pair
+    (dict(wall=(0, 0, 3, 3)), 8, 2),
     (dict(storage=5), 8, 8),
     (dict(nu=float("nan")), 8, 8),
     ({}, 1, 8),
@@ -81,6 +87,12 @@ def test_invalid_arguments_are_rejected(clb, kw, nx, ny):
     p = clb.params(W.default_params(**kw))
     assert clb.lib().clb_create(nx, ny, ctypes.byref(p), None, None, 0, ctypes.byref(h)) == clb.CLB_EINVAL
     assert not h.value
+
+
+@pytest.mark.parametrize("wall,nx,ny", [((3, 3, 0, 0), 3, 2), ((0, 0, 3, 3), 2, 3), ((3, 3, 3, 3), 3, 3)])
+def test_wet_walls_on_either_axis_and_closed_boxes_are_accepted(clb, wall, nx, ny):
+    st, n = footprint(clb, nx, ny, wall=wall)
+    assert st == clb.CLB_OK and n > 0
 
 
 def test_null_handles_are_rejected(clb):

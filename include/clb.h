@@ -115,7 +115,9 @@ void clb_destroy(clb_handle *h);
 
 /* f(x, 0) = f^eq(rho, u), g(x, 0) = g^eq(T, u) with f^eq = M^-1 N(u)^-1 Gamma~eq (Eq. 9) and
  * g^eq = M_T^-1 N_T(u)^-1 Gamma~T,eq (Eq. 20). Host arrays; synchronous. Resets the step count
- * and takes the residual snapshot. */
+ * and takes the residual snapshot. Pinned host arrays (cudaMallocHost, cudaHostAlloc,
+ * cudaHostRegister) are read by the initialisation kernel directly over the CPU-GPU link;
+ * pageable arrays are copied to device staging first. */
 clb_status clb_init_fields(clb_handle *h, const double *rho, const double *ux, const double *uy,
                            const double *T);
 /* Same from device arrays; asynchronous on the handle's stream. */
@@ -127,7 +129,8 @@ clb_status clb_init_fields_device(clb_handle *h, const double *rho, const double
 clb_status clb_step(clb_handle *h, long n);
 
 /* rho, u (force-corrected, Eq. 13) and T (Eq. 23) at the current time, into host arrays (any may
- * be NULL). Synchronous. */
+ * be NULL). Synchronous. Pinned host arrays are written by the field kernel directly; pageable
+ * ones through device staging. */
 clb_status clb_fields(clb_handle *h, double *rho, double *ux, double *uy, double *T);
 /* Same into device arrays (any may be NULL); asynchronous. */
 clb_status clb_fields_device(clb_handle *h, double *rho, double *ux, double *uy, double *T);

@@ -415,6 +415,21 @@ extern "C" clb_status clb_init_fields_device(clb_handle* h, const double* rho, c
     return take_snapshot(h);
 }
 
+namespace {
+// The address at which the current device reads or writes host memory directly: pinned host
+// memory (cudaMallocHost, cudaHostAlloc, cudaHostRegister; mapped under unified addressing), over
+// the CPU-GPU link. NULL for ordinary pageable memory, which goes through a staging copy instead.
+void* device_view(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+}  // namespace
+
 extern "C" clb_status clb_init_fields(clb_handle* h, const double* rho, const double* ux,
                                       const double* uy, const double* T)
 {
@@ -426,6 +441,9 @@ extern "C" clb_status clb_init_fields(clb_handle* h, const double* rho, const do
     const double* dev[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int k = 0; k < 4; ++k)
         if (src[k]) {
+            // pinned host arrays are read by the initialisation kernel itself; pageable ones are staged
+            dev[k] = (const double*)device_view(src[k]);
+            if (dev[k]) continue;
             CLB_CUDA(cudaMemcpyAsync(h->stage + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
             dev[k] = h->stage + k * N;
         }
@@ -474,10 +492,16 @@ extern "C" clb_status clb_fields(clb_handle* h, double* rho, double* ux, double*
     const size_t N = (size_t)h->nx * h->ny;
     double* host[4] = {rho, ux, uy, T};
     double* dev[4];
-    for (int k = 0; k < 4; ++k) dev[k] = host[k] ? h->stage + k * N : nullptr;
+    bool staged[4];
+    for (int k = 0; k < 4; ++k) {
+        // pinned host arrays are written by the field kernel itself; pageable ones through staging
+        dev[k] = host[k] ? (double*)device_view(host[k]) : nullptr;
+        staged[k] = host[k] && !dev[k];
+        if (staged[k]) dev[k] = h->stage + k * N;
+    }
     CLB_TRY(launch_fields(h, dev[0], dev[1], dev[2], dev[3]));
     for (int k = 0; k < 4; ++k)
-        if (host[k]) CLB_CUDA(cudaMemcpyAsync(host[k], dev[k], N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (staged[k]) CLB_CUDA(cudaMemcpyAsync(host[k], dev[k], N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CLB_CUDA(cudaStreamSynchronize(h->stream));
     return CLB_OK;
 }

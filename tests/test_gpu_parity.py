@@ -393,3 +393,30 @@ def test_check_equals_nusselt_and_residual(clb, storage):
         assert er == b.residual()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("storage", [F64, F32])
+def test_pinned_and_pageable_host_fields_agree(clb, storage):
+    """clb_init_fields reads pinned host arrays directly and stages pageable ones; clb_fields
+    writes pinned arrays directly and pageable ones through staging. Both routes give the same
+    bits, also when the two kinds are mixed in one call."""
+    import torch
+    prob = W.random_problem(130, 41, seed=5, storage=storage)
+    n = prob.nodes
+    pin = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(8)]
+    for t, a in zip(pin[:4], prob.fields()):
+        t.numpy()[:] = a.ravel()
+    a = clb.Lattice(prob.nx, prob.ny, prob.params)
+    a.init_fields(*[t.numpy() for t in pin[:4]])
+    b = clb.Lattice(prob.nx, prob.ny, prob.params)
+    b.init_fields(prob.rho, pin[1].numpy(), prob.uy, pin[3].numpy())  # mixed kinds
+    for lat in (a, b):
+        lat.step(37)
+    ref = a.fields()  # pageable outputs
+    a.fields_into(*[t.numpy() for t in pin[4:]])
+    for t, r in zip(pin[4:], ref):
+        assert np.array_equal(t.numpy().reshape(prob.ny, prob.nx), r)
+    for x, y in zip(b.fields(), ref):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()

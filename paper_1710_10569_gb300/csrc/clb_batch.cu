@@ -52,7 +52,9 @@ __device__ __forceinline__ void load_member(const Member<A>* __restrict__ src, M
 // Register cap: the FP32 two-nodes-per-thread form (the default tile) is held at 96 registers so
 // that five 128-thread blocks stay resident per SM; the other forms take what they need (blocks
 // have at most 256 threads).
-template <int ST, int V>
+// HI1: every lattice of the launch has s_3 = s_4 = 1 (the form of collide that does not form the
+// third- and fourth-order moments).
+template <int ST, int V, bool HI1>
 __global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(const Member<typename Storage<ST>::A>* __restrict__ mem,
                                                       const int* __restrict__ owner, int parity, int groups)
 {
@@ -97,7 +99,7 @@ __global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(
     const int y_end = min(M.P.ny, y0 + rows);
     if (vector) {
         const int x0 = xt + threadIdx.x * V;
-        for (int y = y0 + threadIdx.y; y < y_end; y += blockDim.y) step_warp_nodes<ST, V, false>(src, dst, M.P, x0, y, lane, keep);
+        for (int y = y0 + threadIdx.y; y < y_end; y += blockDim.y) step_warp_nodes<ST, V, false, HI1>(src, dst, M.P, x0, y, lane, keep);
     }
     const int nrow = y_end - y0;
     const int nodes = nrow * (xe - xs);
@@ -105,30 +107,35 @@ __global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(
         const int y = y0 + j % nrow, x = xs + j / nrow;
         A f[9], g[5];
         gather(src, M.P, x, y, f, g);
-        collide_any<Storage<ST>::DEV>(M.P, f, g, row_base(M.P, y));
+        collide_any<Storage<ST>::DEV, HI1>(M.P, f, g, row_base(M.P, y));
         store_node(dst, M.P, x, y, f, g);
     }
 }
 
-// Blocks of k_step_batched<ST, V> resident on the whole device at once.
-template <int ST, int V>
+// Blocks of k_step_batched<ST, V, HI1> resident on the whole device at once.
+template <int ST, int V, bool HI1>
 long resident_blocks_of(int threads)
 {
     int dev = 0, sms = 1, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batched<ST, V>, threads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batched<ST, V, HI1>, threads, 0) != cudaSuccess) {
         cudaGetLastError();
         per_sm = 1;
     }
     return (long)std::max(1, sms) * std::max(1, per_sm);
 }
 
-template <int ST>
+template <int ST, bool HI1>
 long resident_blocks_npt(int npt, int threads)
 {
-    return npt == 4 ? resident_blocks_of<ST, 4>(threads)
-                    : npt == 2 ? resident_blocks_of<ST, 2>(threads) : resident_blocks_of<ST, 1>(threads);
+    return npt == 4 ? resident_blocks_of<ST, 4, HI1>(threads)
+                    : npt == 2 ? resident_blocks_of<ST, 2, HI1>(threads) : resident_blocks_of<ST, 1, HI1>(threads);
+}
+template <int ST>
+long resident_blocks_npt(int npt, int threads, bool hi1)
+{
+    return hi1 ? resident_blocks_npt<ST, true>(npt, threads) : resident_blocks_npt<ST, false>(npt, threads);
 }
 
 template <int ST>
@@ -246,6 +253,7 @@ public:
     cudaStream_t cap = nullptr;
     int tile_x = 128, tile_y = 1, npt = 1;
     int groups = 1;  // row groups per block (kBlockNodes): a tile is (tile_x * npt) x (tile_y * groups) nodes
+    bool hi1 = false;  // every active lattice has s_3 = s_4 = 1 (set by rebuild)
     int parity = 0;  // every resident lattice holds its current data in buf[parity]
     std::vector<Lattice*> members;  // launch order
 
@@ -316,9 +324,9 @@ public:
     void choose_groups()
     {
         const int threads = tile_x * tile_y;
-        const long resident = storage == CLB_F64 ? resident_blocks_npt<ST_F64>(npt, threads)
-                              : storage == CLB_F32 ? resident_blocks_npt<ST_F32>(npt, threads)
-                                                   : resident_blocks_npt<ST_F16DEV>(npt, threads);
+        const long resident = storage == CLB_F64 ? resident_blocks_npt<ST_F64>(npt, threads, hi1)
+                              : storage == CLB_F32 ? resident_blocks_npt<ST_F32>(npt, threads, hi1)
+                                                   : resident_blocks_npt<ST_F16DEV>(npt, threads, hi1);
         groups = 1;
         for (int g = 2; g * threads * npt <= kBlockNodes && tiles_with(g) >= kMinWaves * resident; g *= 2) groups = g;
     }
@@ -329,8 +337,12 @@ public:
         if (!dirty) return CLB_OK;
         drop_graphs();
         active.clear();
+        hi1 = true;
         for (Lattice* L : members)
-            if (L->active) active.push_back(L);
+            if (L->active) {
+                active.push_back(L);
+                hi1 = hi1 && L->p.s_3 == 1.0 && L->p.s_4 == 1.0;
+            }
         choose_groups();
         const long tiles = tiles_with(groups);
         long rows = 0;
@@ -380,9 +392,15 @@ public:
         const dim3 block(tile_x, tile_y);
         const Member<A>* m = (const Member<A>*)((char*)d_tables + off_members);
         const int* owner = (const int*)((char*)d_tables + off_owner);
-        if (npt == 4) k_step_batched<ST, 4><<<ntiles, block, 0, s>>>(m, owner, par, groups);
-        else if (npt == 2) k_step_batched<ST, 2><<<ntiles, block, 0, s>>>(m, owner, par, groups);
-        else k_step_batched<ST, 1><<<ntiles, block, 0, s>>>(m, owner, par, groups);
+        if (hi1) {
+            if (npt == 4) k_step_batched<ST, 4, true><<<ntiles, block, 0, s>>>(m, owner, par, groups);
+            else if (npt == 2) k_step_batched<ST, 2, true><<<ntiles, block, 0, s>>>(m, owner, par, groups);
+            else k_step_batched<ST, 1, true><<<ntiles, block, 0, s>>>(m, owner, par, groups);
+        } else {
+            if (npt == 4) k_step_batched<ST, 4, false><<<ntiles, block, 0, s>>>(m, owner, par, groups);
+            else if (npt == 2) k_step_batched<ST, 2, false><<<ntiles, block, 0, s>>>(m, owner, par, groups);
+            else k_step_batched<ST, 1, false><<<ntiles, block, 0, s>>>(m, owner, par, groups);
+        }
     }
 
     clb_status launch_step(cudaStream_t s, int par)

@@ -380,7 +380,11 @@ __device__ __forceinline__ void collide_d2q5(const LatParams<A>& P, A T, A ux, A
 }
 
 // Collision of one node in place, populations form: Eqs. (6)-(11) for f, Eqs. (16)-(21) for g.
-template <typename A>
+// HI1: the third- and fourth-order rates are 1 (s_3 = s_4 = 1, the paper's setting, Sec. 3), so
+// k~21, k~12 and k~22 relax to their equilibrium and forcing terms whatever their value; they are
+// then not formed (the compiler drops that part of the forward transform). The results are the
+// same bits as with HI1 = false: (1 - s) k is an exact zero for s = 1.
+template <bool HI1 = false, typename A>
 __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5], A Tb)
 {
     const Macro<A> m = macroscopic(P, f, g, Tb);
@@ -400,9 +404,15 @@ __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5], A
     q[0][2] = fma_(-P.sp, a02, fma_(-P.sm, a20, k[0][2]));
     q[1][1] = (A(1) - P.s_nu) * k[1][1];
     const A half3 = (A(1) - A(0.5) * P.s_3) * cs2;
-    q[2][1] = fma_(A(1) - P.s_3, k[2][1], half3 * m.Fy);
-    q[1][2] = fma_(A(1) - P.s_3, k[1][2], half3 * m.Fx);
-    q[2][2] = fma_(A(1) - P.s_4, k[2][2], P.s_4 * rho * (cs2 * cs2));
+    if constexpr (HI1) {
+        q[2][1] = half3 * m.Fy;
+        q[1][2] = half3 * m.Fx;
+        q[2][2] = P.s_4 * rho * (cs2 * cs2);
+    } else {
+        q[2][1] = fma_(A(1) - P.s_3, k[2][1], half3 * m.Fy);
+        q[1][2] = fma_(A(1) - P.s_3, k[1][2], half3 * m.Fx);
+        q[2][2] = fma_(A(1) - P.s_4, k[2][2], P.s_4 * rho * (cs2 * cs2));
+    }
     back_d2q9(q, ux, uy, f);
 
     collide_d2q5(P, T, ux, uy, g);
@@ -467,7 +477,7 @@ __device__ __forceinline__ void collide_d2q5_dev(const LatParams<S>& P, A T, A d
 // f* = f^eq + M^-1 N^-1 [(I - S)(Gamma~ - Gamma~eq) + (I - S/2) C]; the non-equilibrium central
 // moments are formed from the central moments of h plus those of w rho_b about u
 // (1-D: 1, -u, 1/3 + u^2) minus Eq. (9), with the O(1) parts cancelled analytically.
-template <typename A, typename S>
+template <bool HI1 = false, typename A, typename S>
 __device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5], A Tb)
 {
     const Macro<A> m = macroscopic(P, f, g, Tb);
@@ -483,9 +493,6 @@ __device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5
     const A d20 = fma_(-dr, cs2, fma_(rb, x2, k[2][0]));
     const A d02 = fma_(-dr, cs2, fma_(rb, y2, k[0][2]));
     const A d11 = fma_(rb * ux, uy, k[1][1]);
-    const A d21 = fma_(-rb * (cs2 + x2), uy, k[2][1]);
-    const A d12 = fma_(-rb * ux, cs2 + y2, k[1][2]);
-    const A d22 = fma_(rb, fma_(cs2, x2 + y2, x2 * y2), fma_(-dr, cs4, k[2][2]));
     // relaxed non-equilibrium plus forcing, Eqs. (8), (11)
     const A sp = A(P.sp), sm = A(P.sm);
     const A half3 = A((1.0f - 0.5f * P.s_3) * (1.0f / 3.0f));
@@ -496,9 +503,19 @@ __device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5
     q[2][0] = fma_(-sm, d02, fma_(-sp, d20, d20));
     q[0][2] = fma_(-sp, d02, fma_(-sm, d20, d02));
     q[1][1] = A(1.0f - P.s_nu) * d11;
-    q[2][1] = fma_(A(1.0f - P.s_3), d21, half3 * m.Fy);
-    q[1][2] = fma_(A(1.0f - P.s_3), d12, half3 * m.Fx);
-    q[2][2] = A(1.0f - P.s_4) * d22;
+    if constexpr (HI1) {
+        // s_3 = s_4 = 1: (1 - s) d is an exact zero (see collide)
+        q[2][1] = half3 * m.Fy;
+        q[1][2] = half3 * m.Fx;
+        q[2][2] = A(0);
+    } else {
+        const A d21 = fma_(-rb * (cs2 + x2), uy, k[2][1]);
+        const A d12 = fma_(-rb * ux, cs2 + y2, k[1][2]);
+        const A d22 = fma_(rb, fma_(cs2, x2 + y2, x2 * y2), fma_(-dr, cs4, k[2][2]));
+        q[2][1] = fma_(A(1.0f - P.s_3), d21, half3 * m.Fy);
+        q[1][2] = fma_(A(1.0f - P.s_3), d12, half3 * m.Fx);
+        q[2][2] = A(1.0f - P.s_4) * d22;
+    }
     A e[9];
     eq_dev_d2q9(rho, dr, ux, uy, e);
     back_d2q9(q, ux, uy, f);
@@ -508,11 +525,11 @@ __device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5
     collide_d2q5_dev(P, T, dT, ux, uy, g);
 }
 
-template <bool DEV, typename A>
+template <bool DEV, bool HI1 = false, typename A>
 __device__ __forceinline__ void collide_any(const LatParams<A>& P, A f[9], A g[5], A Tb)
 {
-    if constexpr (DEV) collide_dev(P, f, g, Tb);
-    else collide(P, f, g, Tb);
+    if constexpr (DEV) collide_dev<HI1>(P, f, g, Tb);
+    else collide<HI1>(P, f, g, Tb);
 }
 
 // Equilibria in stored form, minus the rest state for deviation storage: f^eq(rho, u) (Eq. 9

@@ -33,7 +33,7 @@ __device__ __forceinline__ E lane_down(E v) { return __shfl_down_sync(0xffffffff
 //
 // warp_vector is the vector body. WALLS = false is the interior of the lattice (no wall next to any node of the
 // warp), where every wall term folds away at compile time.
-template <int ST, int V, bool WALLS>
+template <int ST, int V, bool WALLS, bool HI1 = false>
 __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __restrict__ src,
                                             typename Storage<ST>::T* __restrict__ dst,
                                             const LatParams<typename Storage<ST>::A>& P, int x0, int y,
@@ -114,7 +114,7 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
                 for (int i = 0; i < 9; ++i) f[i] = F2(fa[i], fb[i]);
 #pragma unroll
                 for (int i = 0; i < 5; ++i) g[i] = F2(ga[i], gb[i]);
-                collide_dev(P, f, g, F2(Tb));
+                collide_dev<HI1>(P, f, g, F2(Tb));
 #pragma unroll
                 for (int i = 0; i < NPOP; ++i) from_a2(i < 9 ? f[i] : g[i - 9], out[i].e[k], out[i].e[k + 1]);
             }
@@ -123,7 +123,7 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
             for (int k = 0; k < V; ++k) {
                 A f[9], g[5];
                 finish_pull(P, raw[k], mask[k], f, g);
-                collide_any<Storage<ST>::DEV>(P, f, g, Tb);
+                collide_any<Storage<ST>::DEV, HI1>(P, f, g, Tb);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) out[i].e[k] = from_a(f[i], (E*)nullptr);
 #pragma unroll
@@ -141,7 +141,7 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
 // issue-limited). The batched kernel keeps one copy: the second raises its register count past an
 // occupancy step. Nodes x < keep are computed but not stored (they belong to another warp: see the
 // shifted last tile of a row in the batched kernel).
-template <int ST, int V, bool SPLIT = true>
+template <int ST, int V, bool SPLIT = true, bool HI1 = false>
 __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* __restrict__ src,
                                                 typename Storage<ST>::T* __restrict__ dst,
                                                 const LatParams<typename Storage<ST>::A>& P, int x0,
@@ -153,8 +153,8 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
     if (wx1 < P.nx && !(P.wet_y && (y == 0 || y == P.ny - 1)) && !(P.wet_x && (wx0 == 0 || wx1 == P.nx - 1))) {
         const bool walls =
             (!P.per_y && (y == 0 || y == P.ny - 1)) || (!P.per_x && (wx0 == 0 || wx1 == P.nx - 1));
-        if (!SPLIT || walls) warp_vector<ST, V, true>(src, dst, P, x0, y, lane, keep);
-        else warp_vector<ST, V, false>(src, dst, P, x0, y, lane, keep);
+        if (!SPLIT || walls) warp_vector<ST, V, true, HI1>(src, dst, P, x0, y, lane, keep);
+        else warp_vector<ST, V, false, HI1>(src, dst, P, x0, y, lane, keep);
     } else {
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -162,7 +162,7 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
             if (x < P.nx && x >= keep) {
                 A f[9], g[5];
                 gather(src, P, x, y, f, g);
-                collide_any<Storage<ST>::DEV>(P, f, g, row_base(P, y));
+                collide_any<Storage<ST>::DEV, HI1>(P, f, g, row_base(P, y));
                 store_node(dst, P, x, y, f, g);
             }
         }
@@ -172,7 +172,9 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
 // One time step over the lattice: thread (tx, ty) of block (bx, by) updates nodes
 // x0 = (bx * blockDim.x + tx) * V .. x0 + V - 1 of row by * blockDim.y + ty. blockDim.x is a
 // multiple of 32, so each warp lies in one row.
-template <int ST, int V>
+// HI1: the form for third- and fourth-order rates of 1 (see collide), which the host picks when
+// s_3 = s_4 = 1.
+template <int ST, int V, bool HI1>
 __global__ void __launch_bounds__(256) k_step(const typename Storage<ST>::T* __restrict__ src,
                                               typename Storage<ST>::T* __restrict__ dst,
                                               const LatParams<typename Storage<ST>::A> P)
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(256) k_step(const typename Storage<ST>::T* __r
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (y >= P.ny || x0 - lane * V >= P.nx) return;  // whole warps only
-    step_warp_nodes<ST, V>(src, dst, P, x0, y, lane);
+    step_warp_nodes<ST, V, true, HI1>(src, dst, P, x0, y, lane);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -52,8 +52,8 @@ __device__ __forceinline__ void load_member(const Member<A>* __restrict__ src, M
 // Register cap: the FP32 two-nodes-per-thread form (the default tile) is held at 96 registers so
 // that five 128-thread blocks stay resident per SM; the other forms take what they need (blocks
 // have at most 256 threads).
-// HI1: every lattice of the launch has s_3 = s_4 = 1 (the form of collide that does not form the
-// third- and fourth-order moments).
+// HI1: every lattice of the launch has s_3 = s_4 = lambda2 = 1 (the form of collide that does not
+// form the moments those rates discard).
 template <int ST, int V, bool HI1>
 __global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(const Member<typename Storage<ST>::A>* __restrict__ mem,
                                                       const int* __restrict__ owner, int parity, int groups)
@@ -341,7 +341,7 @@ public:
         for (Lattice* L : members)
             if (L->active) {
                 active.push_back(L);
-                hi1 = hi1 && L->p.s_3 == 1.0 && L->p.s_4 == 1.0;
+                hi1 = hi1 && L->p.s_3 == 1.0 && L->p.s_4 == 1.0 && L->p.lambda2 == 1.0;
             }
         choose_groups();
         const long tiles = tiles_with(groups);

@@ -363,8 +363,9 @@ __device__ __forceinline__ void central_d2q9(const A f[9], A ux, A uy, A k[3][3]
     for (int a = 0; a < 3; ++a) central3(r0[a], rp[a], rm[a], uy, k[a][0], k[a][1], k[a][2]);
 }
 
-// D2Q5 collision in populations form (Eqs. 16-21) for temperature T and velocity u.
-template <typename A>
+// D2Q5 collision in populations form (Eqs. 16-21) for temperature T and velocity u. HI1: lambda2 = 1,
+// so the second-order central moments relax to equilibrium whatever their value (not formed).
+template <bool HI1 = false, typename A>
 __device__ __forceinline__ void collide_d2q5(const LatParams<A>& P, A T, A ux, A uy, A g[5])
 {
     const A d1 = g[1] - g[3], s1 = g[1] + g[3];
@@ -376,14 +377,15 @@ __device__ __forceinline__ void collide_d2q5(const LatParams<A>& P, A T, A ux, A
     const A om1 = A(1) - P.lambda1;
     const A om2 = A(1) - P.lambda2;
     const A eqT = P.lambda2 * T * P.cs2T;
-    back_d2q5(T, om1 * t10, om1 * t01, fma_(om2, t20, eqT), fma_(om2, t02, eqT), ux, uy, g);
+    if constexpr (HI1) back_d2q5(T, om1 * t10, om1 * t01, eqT, eqT, ux, uy, g);
+    else back_d2q5(T, om1 * t10, om1 * t01, fma_(om2, t20, eqT), fma_(om2, t02, eqT), ux, uy, g);
 }
 
 // Collision of one node in place, populations form: Eqs. (6)-(11) for f, Eqs. (16)-(21) for g.
-// HI1: the third- and fourth-order rates are 1 (s_3 = s_4 = 1, the paper's setting, Sec. 3), so
-// k~21, k~12 and k~22 relax to their equilibrium and forcing terms whatever their value; they are
-// then not formed (the compiler drops that part of the forward transform). The results are the
-// same bits as with HI1 = false: (1 - s) k is an exact zero for s = 1.
+// HI1: the high-order rates are 1 (s_3 = s_4 = lambda2 = 1, the paper's setting, Sec. 3), so k~21,
+// k~12, k~22 and the second-order D2Q5 moments relax to their equilibrium and forcing terms
+// whatever their value; they are then not formed (the compiler drops that part of the forward
+// transforms). The results are the same as with HI1 = false: (1 - s) k is an exact zero for s = 1.
 template <bool HI1 = false, typename A>
 __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5], A Tb)
 {
@@ -415,7 +417,7 @@ __device__ __forceinline__ void collide(const LatParams<A>& P, A f[9], A g[5], A
     }
     back_d2q9(q, ux, uy, f);
 
-    collide_d2q5(P, T, ux, uy, g);
+    collide_d2q5<HI1>(P, T, ux, uy, g);
 }
 
 // Deviation of the D2Q9 equilibrium from the rest state, f^eq_i(rho, u) - w_i rho_b, written as
@@ -451,8 +453,9 @@ __device__ __forceinline__ void eq_dev_d2q5(A T, A dT, A ux, A uy, A c2, A g[5])
     g[4] = fma_(dT, hc, hT * fma_(uy, uy, -uy));
 }
 
-// D2Q5 collision on deviations t = g - w^T T_b (Eqs. 16-21) for T = T_b + dT and velocity u.
-template <typename A, typename S>
+// D2Q5 collision on deviations t = g - w^T T_b (Eqs. 16-21) for T = T_b + dT and velocity u (HI1:
+// lambda2 = 1, as in collide_d2q5).
+template <bool HI1 = false, typename A, typename S>
 __device__ __forceinline__ void collide_d2q5_dev(const LatParams<S>& P, A T, A dT, A ux, A uy, A g[5])
 {
     const A c2 = A(P.cs2T);
@@ -467,7 +470,8 @@ __device__ __forceinline__ void collide_d2q5_dev(const LatParams<S>& P, A T, A d
     const A om2 = A(1.0f - P.lambda2);
     A eT[5], gq[5];
     eq_dev_d2q5(T, dT, ux, uy, c2, eT);
-    back_d2q5(A(0), om1 * t10, om1 * t01, om2 * t20, om2 * t02, ux, uy, gq);
+    if constexpr (HI1) back_d2q5(A(0), om1 * t10, om1 * t01, A(0), A(0), ux, uy, gq);
+    else back_d2q5(A(0), om1 * t10, om1 * t01, om2 * t20, om2 * t02, ux, uy, gq);
 #pragma unroll
     for (int i = 0; i < 5; ++i) g[i] = gq[i] + eT[i];
 }
@@ -522,7 +526,7 @@ __device__ __forceinline__ void collide_dev(const LatParams<S>& P, A f[9], A g[5
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] += e[i];
 
-    collide_d2q5_dev(P, T, dT, ux, uy, g);
+    collide_d2q5_dev<HI1>(P, T, dT, ux, uy, g);
 }
 
 template <bool DEV, bool HI1 = false, typename A>

@@ -172,8 +172,8 @@ __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* _
 // One time step over the lattice: thread (tx, ty) of block (bx, by) updates nodes
 // x0 = (bx * blockDim.x + tx) * V .. x0 + V - 1 of row by * blockDim.y + ty. blockDim.x is a
 // multiple of 32, so each warp lies in one row.
-// HI1: the form for third- and fourth-order rates of 1 (see collide), which the host picks when
-// s_3 = s_4 = 1.
+// HI1: the form for high-order rates of 1 (see collide), which the host picks when
+// s_3 = s_4 = lambda2 = 1.
 template <int ST, int V, bool HI1>
 __global__ void __launch_bounds__(256) k_step(const typename Storage<ST>::T* __restrict__ src,
                                               typename Storage<ST>::T* __restrict__ dst,

@@ -184,8 +184,13 @@ void enqueue_step(const clb_handle* h, const void* a, void* b, cudaStream_t s, i
     using A = typename Storage<ST>::A;
     const dim3 block(bx, by), grid((h->nx + bx * NPT - 1) / (bx * NPT), (h->ny + by - 1) / by);
     const LatParams<A>& P = *reinterpret_cast<const LatParams<A>*>(ST == ST_F64 ? (const void*)&h->Pd : (const void*)&h->Pf);
-    if (h->p.s_3 == 1.0 && h->p.s_4 == 1.0 && h->p.lambda2 == 1.0) k_step<ST, NPT, true><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
-    else k_step<ST, NPT, false><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
+    const bool hi1 = h->p.s_3 == 1.0 && h->p.s_4 == 1.0 && h->p.lambda2 == 1.0;
+    if (ST == ST_F16DEV && NPT == 4 && hi1)
+        k_step_f16x4_hi1<<<grid, block, 0, s>>>((const __half*)a, (__half*)b, h->Pf);
+    else if (hi1)
+        k_step<ST, NPT, true><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
+    else
+        k_step<ST, NPT, false><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
 }
 
 template <int ST>

@@ -38,6 +38,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -60,11 +61,25 @@ KERNEL_SOURCES = ["paper_1710_10569_gb300/csrc/clb_core.cuh", "paper_1710_10569_
 KERNEL3D_SOURCES = ["paper_1710_10569_gb300/csrc/clb_core.cuh", "paper_1710_10569_gb300/csrc/clb3d.cu"]
 
 
+_CODE_TOKENS = re.compile(r'"(?:\\.|[^"\\\n])*"|//[^\n]*|/\*.*?\*/|\s+', re.S)
+
+
+def _code_only(text: str) -> str:
+    """The source with its comments dropped (string literals kept) and each run of white space
+    made one blank, so that an edit of comments or layout leaves the hash alone."""
+    def keep(m):
+        t = m.group(0)
+        return t if t.startswith('"') else " "
+    return re.sub(r"\s+", " ", _CODE_TOKENS.sub(keep, text)).strip()
+
+
 def kernel_hash(sources=KERNEL_SOURCES) -> str:
+    """Hash of the code (not the comments) of the kernel sources the committed ncu counts were
+    taken on."""
     h = hashlib.sha256()
     for rel in sources:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

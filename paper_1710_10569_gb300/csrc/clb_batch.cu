@@ -48,7 +48,8 @@ __device__ __forceinline__ void load_member(const Member<A>* __restrict__ src, M
 
 // One time step of every lattice: block b covers tile (b - tile_begin) of lattice owner[b]; a
 // tile is (blockDim.x * V) x (blockDim.y * groups) nodes, V consecutive nodes per thread (the
-// same per-warp update as the single-lattice step), each warp stepping `groups` rows.
+// same per-warp update as the single-lattice step), each warp stepping `groups` rows; warps
+// clear of every wall take the copy of the vector body without the wall terms.
 // Register cap: the FP32 two-nodes-per-thread form (the default tile) is held at 96 registers so
 // that five 128-thread blocks stay resident per SM; the other forms take what they need (blocks
 // have at most 256 threads).
@@ -99,7 +100,7 @@ __global__ void __maxnreg__((ST == ST_F32 && V == 2) ? 96 : 255) k_step_batched(
     const int y_end = min(M.P.ny, y0 + rows);
     if (vector) {
         const int x0 = xt + threadIdx.x * V;
-        for (int y = y0 + threadIdx.y; y < y_end; y += blockDim.y) step_warp_nodes<ST, V, false, HI1>(src, dst, M.P, x0, y, lane, keep);
+        for (int y = y0 + threadIdx.y; y < y_end; y += blockDim.y) step_warp_nodes<ST, V, true, HI1>(src, dst, M.P, x0, y, lane, keep);
     }
     const int nrow = y_end - y0;
     const int nodes = nrow * (xe - xs);

@@ -138,8 +138,7 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
 
 // step_warp_nodes picks the path. SPLIT = true compiles the vector body twice, with and without
 // the wall terms, and interior warps take the lean copy (fewer instructions; the FP16 form is
-// issue-limited). The batched kernel keeps one copy: the second raises its register count past an
-// occupancy step. Nodes x < keep are computed but not stored (they belong to another warp: see the
+// issue-limited). Nodes x < keep are computed but not stored (they belong to another warp: see the
 // shifted last tile of a row in the batched kernel).
 template <int ST, int V, bool SPLIT = true, bool HI1 = false>
 __device__ __forceinline__ void step_warp_nodes(const typename Storage<ST>::T* __restrict__ src,

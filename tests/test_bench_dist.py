@@ -50,3 +50,14 @@ def test_aggregate_two_ranks():
 def test_aggregate_single_rank():
     import bench
     assert bench.aggregate(10.0, 2.0, 1) == (10.0, 2.0)
+
+
+def test_kernel_hash_ignores_comments_not_code():
+    """The hash that ties the committed ncu counts to the kernel source changes with the code and
+    not with comments or layout (a `//` inside a string literal is code)."""
+    import bench
+    base = 'int x; // a comment\n  /* block\n comment */ asm("add %0; // in string");\n'
+    same = 'int x;\nasm("add %0; // in string");'
+    assert bench._code_only(base) == bench._code_only(same)
+    assert bench._code_only(base) != bench._code_only(same.replace("x", "y"))
+    assert bench._code_only(base) != bench._code_only(same.replace("in string", "in strung"))

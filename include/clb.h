@@ -214,8 +214,13 @@ clb_status clb_get_pipeline(clb_handle *h, int *stages, int *rows);
 void *clb_stream(clb_handle *h);
 
 /* Device address of the current post-collision population buffer and of the other buffer, and
- * the element stride between population planes (for profiling and checkpoint tools). */
-clb_status clb_buffers(clb_handle *h, void **cur, void **other, size_t *plane_elems, int *pitch);
+ * their layout (for profiling and checkpoint tools): chunked rows. Row y holds ceil(nx / chunk)
+ * chunks of chunk consecutive nodes, the last one padded; a chunk holds its nodes' 14 populations
+ * (f_0..f_8, g_0..g_4) one after another, chunk values each. Element (i, x, y) lies at
+ *   y * row_elems + (x / chunk) * 14 * chunk + i * chunk + x % chunk
+ * in elements of the storage type (chunk = 64, row_elems = 14 * 64 * ceil(nx / 64)). Any output
+ * pointer may be NULL. */
+clb_status clb_buffers(clb_handle *h, void **cur, void **other, size_t *row_elems, int *chunk);
 
 const char *clb_last_error(void);
 const char *clb_version(void);

@@ -366,10 +366,12 @@ class Lattice:
         return st.value, rows.value
 
     def buffers(self):
-        cur, oth, pl, pitch = _VP(), _VP(), _S(), _I()
-        _check(lib().clb_buffers(self._h, ctypes.byref(cur), ctypes.byref(oth), ctypes.byref(pl),
-                                 ctypes.byref(pitch)))
-        return cur.value, oth.value, pl.value, pitch.value
+        """(current buffer, other buffer, elements per chunked row, nodes per chunk): element
+        (i, x, y) lies at y * row_elems + (x // chunk) * 14 * chunk + i * chunk + x % chunk."""
+        cur, oth, row, chunk = _VP(), _VP(), _S(), _I()
+        _check(lib().clb_buffers(self._h, ctypes.byref(cur), ctypes.byref(oth), ctypes.byref(row),
+                                 ctypes.byref(chunk)))
+        return cur.value, oth.value, row.value, chunk.value
 
 
 class Thermal:

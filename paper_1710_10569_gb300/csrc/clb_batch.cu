@@ -1117,7 +1117,7 @@ extern "C" clb_status clb_serve_progress(clb_server* s, long chunk, int* active,
             r->L->mem = mem;
             carve(*r->L, mem);
             const size_t N = (size_t)r->L->nx * r->L->ny;
-            // keep the padding between rows and planes defined (it is never read)
+            // keep the padding of each row's last chunk defined (it is never read)
             CLB_CUDA(cudaMemsetAsync(mem, 0, 2 * buffer_slot_bytes(r->L->nx, r->L->ny, r->L->p.storage), s->E.stream));
             const double* h = r->init.data();
             // pageable source: the copies have left the host array when they return

@@ -33,6 +33,19 @@ enum { WALL_PERIODIC = 0, WALL_DIRICHLET = 1, WALL_ADIABATIC = 2 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2 };
 enum { NPOP = 14 };  // 9 flow + 5 temperature planes per buffer
 
+// Population layout of a coupled lattice: chunked rows. Row y is cut into chunks of kRowChunk
+// consecutive nodes (the last one padded), and a chunk holds its nodes' 14 populations plane after
+// plane (kRowChunk consecutive values each), so element (i, x, y) lies at
+//   y * P.crow + chunk_off(x) + i * kRowChunk,   P.crow = NPOP * kRowChunk * ceil(nx / kRowChunk).
+// A warp's access to one population of 32 V consecutive nodes is 32 V / kRowChunk runs of kRowChunk
+// values (one 128-byte line per chunk in FP16), and the 14 populations of a node sit at fixed
+// offsets i * kRowChunk from one address, so an access needs no per-population address arithmetic.
+constexpr int kRowChunk = 64;
+__host__ __device__ __forceinline__ long long chunk_off(int x)
+{
+    return (long long)((unsigned)x / kRowChunk) * (NPOP * kRowChunk) + (long long)((unsigned)x % kRowChunk);
+}
+
 // Storage traits: element type in HBM, arithmetic type in registers, deviation form or not.
 template <int ST> struct Storage;
 template <> struct Storage<ST_F64> { using T = double; using A = double; static constexpr bool DEV = false; };
@@ -128,9 +141,11 @@ __device__ __forceinline__ F2 rcp_(F2 a)
 // Per-lattice constants in the arithmetic precision A.
 template <typename A>
 struct LatParams {
-    int nx, ny, pitch;        // pitch: elements per row (row starts are 128-byte aligned)
+    int nx, ny;
+    long long crow;           // elements per chunked row (coupled lattice: see chunk_off)
+    int pitch;                // thermal-only mode (plane-major): elements per row, 128-byte aligned
+    long long plane;          // thermal-only mode: elements between population planes
     int per_x, per_y;         // periodic flags
-    long long plane;          // elements between population planes
     int kind[4];              // wall kind per side (-x, +x, -y, +y)
     A Tw_c2[4];               // anti-bounce-back constant cs2_T (T_wall - T_b) (= 2 w_i T_w, shifted)
     A s_nu, sp, sm, s_3, s_4; // D2Q9 rates; sp = (s_b + s_nu)/2, sm = (s_b - s_nu)/2
@@ -179,21 +194,22 @@ __device__ __forceinline__ Slots pull_slots(const LatParams<A>& P, int x, int y)
     const bool inT = P.per_y || y < P.ny - 1;
     const int xm = x > 0 ? x - 1 : P.nx - 1;
     const int xp = x < P.nx - 1 ? x + 1 : 0;
-    const long long r0 = (long long)y * P.pitch;
-    const long long rm = (long long)(y > 0 ? y - 1 : P.ny - 1) * P.pitch;
-    const long long rp = (long long)(y < P.ny - 1 ? y + 1 : 0) * P.pitch;
-    const long long here = r0 + x;
-    const long long pl = P.plane;
+    const long long r0 = (long long)y * P.crow;
+    const long long rm = (long long)(y > 0 ? y - 1 : P.ny - 1) * P.crow;
+    const long long rp = (long long)(y < P.ny - 1 ? y + 1 : 0) * P.crow;
+    const long long cx = chunk_off(x), cm = chunk_off(xm), cp = chunk_off(xp);
+    const long long here = r0 + cx;
+    constexpr long long C = kRowChunk;
     s.idx[0] = here;
-    s.idx[1] = inL ? 1 * pl + r0 + xm : 3 * pl + here;
-    s.idx[2] = inB ? 2 * pl + rm + x : 4 * pl + here;
-    s.idx[3] = inR ? 3 * pl + r0 + xp : 1 * pl + here;
-    s.idx[4] = inT ? 4 * pl + rp + x : 2 * pl + here;
-    s.idx[5] = (inL && inB) ? 5 * pl + rm + xm : 7 * pl + here;
-    s.idx[6] = (inR && inB) ? 6 * pl + rm + xp : 8 * pl + here;
-    s.idx[7] = (inR && inT) ? 7 * pl + rp + xp : 5 * pl + here;
-    s.idx[8] = (inL && inT) ? 8 * pl + rp + xm : 6 * pl + here;
-    const long long g0 = 9 * pl;
+    s.idx[1] = inL ? r0 + cm + 1 * C : here + 3 * C;
+    s.idx[2] = inB ? rm + cx + 2 * C : here + 4 * C;
+    s.idx[3] = inR ? r0 + cp + 3 * C : here + 1 * C;
+    s.idx[4] = inT ? rp + cx + 4 * C : here + 2 * C;
+    s.idx[5] = (inL && inB) ? rm + cm + 5 * C : here + 7 * C;
+    s.idx[6] = (inR && inB) ? rm + cp + 6 * C : here + 8 * C;
+    s.idx[7] = (inR && inT) ? rp + cp + 7 * C : here + 5 * C;
+    s.idx[8] = (inL && inT) ? rp + cm + 8 * C : here + 6 * C;
+    const long long g0 = 9 * C;  // g_j lies 9 planes after f_j in the same chunk
     s.idx[9] = g0 + here;
     s.idx[10] = g0 + s.idx[1];
     s.idx[11] = g0 + s.idx[2];
@@ -258,12 +274,11 @@ template <typename T, typename A>
 __device__ __forceinline__ void store_node(T* __restrict__ dst, const LatParams<A>& P, int x, int y,
                                            const A f[9], const A g[5])
 {
-    const long long here = (long long)y * P.pitch + x;
-    const long long pl = P.plane;
+    T* here = dst + (long long)y * P.crow + chunk_off(x);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) dst[i * pl + here] = from_a(f[i], (T*)nullptr);
+    for (int i = 0; i < 9; ++i) here[i * kRowChunk] = from_a(f[i], (T*)nullptr);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) dst[(9 + i) * pl + here] = from_a(g[i], (T*)nullptr);
+    for (int i = 0; i < 5; ++i) here[(9 + i) * kRowChunk] = from_a(g[i], (T*)nullptr);
 }
 
 // Macroscopic fields, Eqs. (3), (13), (23), from stored values (populations, or deviations from

@@ -58,14 +58,21 @@ inline size_t elem_size(int storage)
     return storage == ST_F64 ? 8 : storage == ST_F32 ? 4 : 2;
 }
 
-// Row pitch in elements: rows start on 128-byte boundaries.
+// Elements per chunked row of a coupled lattice (see chunk_off): ceil(nx / kRowChunk) chunks of
+// NPOP * kRowChunk elements.
+inline long long chunked_row_elems(int nx)
+{
+    return (long long)((nx + kRowChunk - 1) / kRowChunk) * NPOP * kRowChunk;
+}
+
+// Thermal-only mode (plane-major layout): row pitch in elements, rows on 128-byte boundaries.
 inline int row_pitch(int nx, int storage)
 {
     const int per = int(128 / elem_size(storage));
     return (nx + per - 1) / per * per;
 }
 
-// Elements between population planes: planes start on 256-byte boundaries.
+// Thermal-only mode: elements between population planes, planes on 256-byte boundaries.
 inline long long plane_elems(int nx, int ny, int storage)
 {
     const long long per = 256 / (long long)elem_size(storage);
@@ -73,17 +80,19 @@ inline long long plane_elems(int nx, int ny, int storage)
     return (e + per - 1) / per * per;
 }
 
+// Bytes of one population buffer of a coupled lattice (chunked rows; a row is a multiple of
+// NPOP * 64 elements, so rows start on 1,792-byte (FP16) or larger boundaries).
 inline size_t buffer_bytes(int nx, int ny, int storage)
 {
-    return (size_t)NPOP * (size_t)plane_elems(nx, ny, storage) * elem_size(storage);
+    return (size_t)ny * (size_t)chunked_row_elems(nx) * elem_size(storage);
 }
 
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-// Device bytes reserved per population buffer: the buffer plus a 1 KB guard. The vector loads of
-// the last warp of a row may run up to 32 * V - 1 elements past the row's last node (at most 127
-// elements of 8 bytes or less: under 1 KB), and the 4-byte asynchronous copy of an edge pair of
-// half-precision values one element past it; the guard keeps those reads inside the allocation.
+// Device bytes reserved per population buffer: the buffer plus a 1 KB guard. Every access of the
+// kernels lies inside the chunks of the lattice's rows (the vector path covers whole warps inside a
+// row, and the 4-byte copy of an edge pair of half-precision values stays inside its chunk); the
+// guard is a margin against a change of that.
 inline size_t buffer_slot_bytes(int nx, int ny, int storage)
 {
     return align256(buffer_bytes(nx, ny, storage)) + 1024;
@@ -109,6 +118,7 @@ LatParams<A> make_lat_params(int nx, int ny, const clb_params& p)
     std::memset(&P, 0, sizeof(P));
     P.nx = nx;
     P.ny = ny;
+    P.crow = chunked_row_elems(nx);
     P.pitch = row_pitch(nx, p.storage);
     P.plane = plane_elems(nx, ny, p.storage);
     P.per_x = p.wall[0] == CLB_PERIODIC;

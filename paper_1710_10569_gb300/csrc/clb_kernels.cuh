@@ -50,10 +50,14 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
         const bool wallR = WALLS && !P.per_x && wx1 == P.nx - 1;
         const int ym = y > 0 ? y - 1 : P.ny - 1;
         const int yp = y < P.ny - 1 ? y + 1 : 0;
-        const int rc = y * P.pitch, rm = ym * P.pitch, rp = yp * P.pitch;
+        const long long rc = (long long)y * P.crow, rm = (long long)ym * P.crow, rp = (long long)yp * P.crow;
         const int xl = wx0 > 0 ? wx0 - 1 : P.nx - 1;  // column left of the warp (lane 0)
         const int xr = wx1 < P.nx - 1 ? wx1 + 1 : 0;  // column right of the warp (lane 31)
-        const long long pl = P.plane;
+        // the thread's V nodes lie in one chunk (x0 and kRowChunk are multiples of V), so each
+        // population of them is one aligned V-wide vector at a fixed offset from these addresses
+        const E* sc = src + rc + chunk_off(x0);
+        const E* sm = src + rm + chunk_off(x0);
+        const E* sp = src + rp + chunk_off(x0);
         // plane, row (0: y, 1: y-1, 2: y+1) and x shift (+1: pulled from x-1, -1: from x+1)
         const int SHIFT[NPOP] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 1, 0, -1, 0};
         const int ROWSEL[NPOP] = {0, 0, 1, 0, 2, 1, 1, 2, 2, 0, 0, 1, 0, 2};
@@ -65,14 +69,16 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
             // a pull across the bottom (top) wall reads the node's own opposite plane
             const bool across = (wallB && ROWSEL[i] == 1) || (wallT && ROWSEL[i] == 2);
             const int plane = across ? OPP[i] : i;
-            const int r = across ? rc : (ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp);
+            const bool rowc = across || ROWSEL[i] == 0;
+            const long long r = rowc ? rc : ROWSEL[i] == 1 ? rm : rp;
+            const E* sr = rowc ? sc : ROWSEL[i] == 1 ? sm : sp;
             const int sh = across ? 0 : SHIFT[i];
-            pk[i] = *reinterpret_cast<const PK*>(src + plane * pl + r + x0);
+            pk[i] = *reinterpret_cast<const PK*>(sr + plane * kRowChunk);
             edge[i] = E(0);
             if (sh == 1 && lane == 0)
-                edge[i] = wallL ? src[OPP[i] * pl + rc + 0] : src[plane * pl + r + xl];
+                edge[i] = wallL ? src[rc + chunk_off(0) + OPP[i] * kRowChunk] : src[r + chunk_off(xl) + plane * kRowChunk];
             if (sh == -1 && lane == 31)
-                edge[i] = wallR ? src[OPP[i] * pl + rc + (P.nx - 1)] : src[plane * pl + r + xr];
+                edge[i] = wallR ? src[rc + chunk_off(P.nx - 1) + OPP[i] * kRowChunk] : src[r + chunk_off(xr) + plane * kRowChunk];
         }
         E raw[V][NPOP];
 #pragma unroll
@@ -130,9 +136,11 @@ __device__ __forceinline__ void warp_vector(const typename Storage<ST>::T* __res
                 for (int i = 0; i < 5; ++i) out[9 + i].e[k] = from_a(g[i], (E*)nullptr);
             }
         }
-        if (x0 >= keep)
+        if (x0 >= keep) {
+            E* dc = dst + rc + chunk_off(x0);
 #pragma unroll
-            for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];
+            for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dc + i * kRowChunk) = out[i];
+        }
     }
 }
 
@@ -239,27 +247,27 @@ __device__ __forceinline__ void stage_issue(const typename Storage<ST>::T* __res
     const int wx1 = wx0 + 32 * V - 1;
     const int ym = y > 0 ? y - 1 : P.ny - 1;
     const int yp = y < P.ny - 1 ? y + 1 : 0;
-    const int rc = y * P.pitch, rm = ym * P.pitch, rp = yp * P.pitch;
+    const long long rc = (long long)y * P.crow, rm = (long long)ym * P.crow, rp = (long long)yp * P.crow;
     const int xl = wx0 > 0 ? wx0 - 1 : P.nx - 1;
     const int xr = wx1 < P.nx - 1 ? wx1 + 1 : 0;
-    const long long pl = P.plane;
     const int SHIFT[NPOP] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 1, 0, -1, 0};
     const int ROWSEL[NPOP] = {0, 0, 1, 0, 2, 1, 1, 2, 2, 0, 0, 1, 0, 2};
     constexpr bool HALF = sizeof(E) == 2;
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) {
-        const int r = ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp;
-        const E* row = src + i * pl + r;
+        const long long r = ROWSEL[i] == 0 ? rc : ROWSEL[i] == 1 ? rm : rp;
+        const E* row = src + r + i * kRowChunk;  // population i of the row: at chunk_off(x) from here
         E* sp = stage + i * G::PS;
         constexpr int VB = V * (int)sizeof(E);  // 4, 8, 16 or 32 bytes: copy in pieces of <= 16
 #pragma unroll
         for (int c = 0; c < (VB > 16 ? VB / 16 : 1); ++c)
-            cp_async_bytes(sp + lane * V + c * (16 / (int)sizeof(E)), row + wx0 + lane * V + c * (16 / (int)sizeof(E)),
+            cp_async_bytes(sp + lane * V + c * (16 / (int)sizeof(E)), row + chunk_off(wx0 + lane * V) + c * (16 / (int)sizeof(E)),
                            VB > 16 ? 16 : VB);
+        // an aligned half pair lies inside one chunk (kRowChunk is even)
         if (SHIFT[i] == 1 && lane == 0)
-            cp_async_bytes(sp + 32 * V, row + (HALF ? (xl & ~1) : xl), HALF ? 4 : (int)sizeof(E));
+            cp_async_bytes(sp + 32 * V, row + chunk_off(HALF ? (xl & ~1) : xl), HALF ? 4 : (int)sizeof(E));
         if (SHIFT[i] == -1 && lane == 31)
-            cp_async_bytes(sp + 32 * V + G::RIGHT, row + (HALF ? (xr & ~1) : xr), HALF ? 4 : (int)sizeof(E));
+            cp_async_bytes(sp + 32 * V + G::RIGHT, row + chunk_off(HALF ? (xr & ~1) : xr), HALF ? 4 : (int)sizeof(E));
     }
 }
 
@@ -292,8 +300,6 @@ __device__ __forceinline__ void stage_compute(typename Storage<ST>::T* __restric
             raw[k][i] = sp[idx];
         }
     }
-    const int rc = y * P.pitch;
-    const long long pl = P.plane;
     const int x0 = wx0 + lane * V;
     PK out[NPOP];
     const A Tb = row_base(P, y);
@@ -329,8 +335,9 @@ __device__ __forceinline__ void stage_compute(typename Storage<ST>::T* __restric
             for (int i = 0; i < 5; ++i) out[9 + i].e[k] = from_a(g[i], (E*)nullptr);
         }
     }
+    E* dc = dst + (long long)y * P.crow + chunk_off(x0);
 #pragma unroll
-    for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dst + i * pl + rc + x0) = out[i];
+    for (int i = 0; i < NPOP; ++i) *reinterpret_cast<PK*>(dc + i * kRowChunk) = out[i];
 }
 
 // Block = kPipeWarps warps side by side along x; block (bx, by) covers columns
@@ -420,20 +427,20 @@ __global__ void k_init(typename Storage<ST>::T* __restrict__ dst, const LatParam
         A fv = f[i];
         if (side < 0) {
             plane = i;
-            slot = (long long)sy * P.pitch + sx;
+            slot = (long long)sy * P.crow + chunk_off(sx);
         } else {
             plane = OPP[i];
-            slot = (long long)y * P.pitch + x;
+            slot = (long long)y * P.crow + chunk_off(x);
             if (P.moving) fv = fv - P.fbb[side][i];
         }
-        dst[plane * P.plane + slot] = from_a(fv, (E*)nullptr);
+        dst[slot + plane * kRowChunk] = from_a(fv, (E*)nullptr);
         if (i < 5) {
             A v = g[i];
             if (side >= 0 && P.kind[side] == WALL_DIRICHLET) v = P.Tw_c2[side] - v;
             // a value the pull reads from the row below (above) is stored against that row's base
             if (side < 0 && EY[i] == 1) v = v + P.T_dyw;
             if (side < 0 && EY[i] == -1) v = v - P.T_dyw;
-            dst[(9 + plane) * P.plane + slot] = from_a(v, (E*)nullptr);
+            dst[slot + (9 + plane) * kRowChunk] = from_a(v, (E*)nullptr);
         }
     }
 }

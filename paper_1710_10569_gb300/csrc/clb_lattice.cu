@@ -382,7 +382,7 @@ extern "C" clb_status clb_create(int nx, int ny, const clb_params* p, void* stre
                 h->pipe_rows = it->second[4];
             }
         }
-        // the padding between rows and planes is never read, but keep it defined
+        // the padding of each row's last chunk is never read, but keep it defined
         e = cudaMemsetAsync(h->mem, 0, L.snap, h->stream);
         if (e != cudaSuccess) return fail(set_error(CLB_ECUDA, "memset: %s", cudaGetErrorString(e)));
         clb_status st = launch_init(h, nullptr, nullptr, nullptr, nullptr);
@@ -634,7 +634,7 @@ extern "C" clb_status clb_save(clb_handle* h, void* buf, size_t* bytes)
     DeviceGuard dg(h->device);
     CkptHeader hd;
     std::memset(&hd, 0, sizeof(hd));
-    std::memcpy(hd.magic, "CLBCKPT1", 8);
+    std::memcpy(hd.magic, "CLBCKPT2", 8);
     hd.nx = h->nx;
     hd.ny = h->ny;
     hd.storage = h->p.storage;
@@ -654,7 +654,7 @@ extern "C" clb_status clb_load(clb_handle* h, const void* buf, size_t bytes)
     CkptHeader hd;
     std::memcpy(&hd, buf, sizeof(hd));
     const size_t bb = buffer_bytes(h->nx, h->ny, h->p.storage);
-    if (std::memcmp(hd.magic, "CLBCKPT1", 8) != 0 || hd.nx != h->nx || hd.ny != h->ny ||
+    if (std::memcmp(hd.magic, "CLBCKPT2", 8) != 0 || hd.nx != h->nx || hd.ny != h->ny ||
         hd.storage != h->p.storage || hd.bytes != bb || bytes < sizeof(hd) + bb)
         return set_error(CLB_EINVAL, "checkpoint does not match this lattice");
     DeviceGuard dg(h->device);
@@ -802,12 +802,12 @@ extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y, in
 
 extern "C" void* clb_stream(clb_handle* h) { return h ? (void*)h->stream : nullptr; }
 
-extern "C" clb_status clb_buffers(clb_handle* h, void** cur, void** other, size_t* plane_elems_out, int* pitch)
+extern "C" clb_status clb_buffers(clb_handle* h, void** cur, void** other, size_t* row_elems, int* chunk)
 {
     CHECK_H(h);
     if (cur) *cur = h->buf[h->cur];
     if (other) *other = h->buf[h->cur ^ 1];
-    if (plane_elems_out) *plane_elems_out = (size_t)plane_elems(h->nx, h->ny, h->p.storage);
-    if (pitch) *pitch = row_pitch(h->nx, h->p.storage);
+    if (row_elems) *row_elems = (size_t)chunked_row_elems(h->nx);
+    if (chunk) *chunk = kRowChunk;
     return CLB_OK;
 }

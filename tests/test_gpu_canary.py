@@ -1,6 +1,6 @@
 """Out-of-bounds checks without a sanitizer: a lattice built in caller-owned device memory with a
-guard region of a known byte pattern on each side, and the padding of every row and plane filled
-with NaN, is stepped, reduced, read, autotuned and checkpointed. Afterwards the guards and the
+guard region of a known byte pattern on each side, and the padding of every row's last chunk
+filled with NaN, is stepped, reduced, read, autotuned and checkpointed. Afterwards the guards and the
 padding must be unchanged (nothing writes outside the nodes), and every field must equal that of
 the same lattice run without canaries (nothing reads the padding: a NaN read would spread)."""
 import ctypes
@@ -48,21 +48,22 @@ def guarded_lattice(clb, prob):
 
 
 def padding_views(clb, lat, storage):
-    """Views of the padding elements (row tails x >= nx and plane tails) of both buffers."""
+    """Views of the padding elements (the nodes x >= nx of each row's last chunk, every population)
+    of both buffers."""
     import torch
     dt = {F64: torch.float64, F32: torch.float32, F16: torch.float16}[storage]
     es = {F64: 8, F32: 4, F16: 2}[storage]
-    cur, oth, plane, pitch = lat.buffers()
+    cur, oth, row, chunk = lat.buffers()
+    nchunk = -(-lat.nx // chunk)
+    assert row == nchunk * 14 * chunk
     base = lat._mem.data_ptr()
     views = []
     for ptr in (cur, oth):
         off = ptr - base
         assert off % es == 0 and GUARD <= off < GUARD + lat.footprint
-        buf = lat._mem[off:off + 14 * plane * es].view(dt).view(14, plane)
-        rows = buf[:, :lat.ny * pitch].view(14, lat.ny, pitch)
-        views.append(rows[:, :, lat.nx:])
-        views.append(buf[:, lat.ny * pitch:])
-    return views, pitch
+        buf = lat._mem[off:off + lat.ny * row * es].view(dt).view(lat.ny, nchunk, 14, chunk)
+        views.append(buf[:, nchunk - 1, :, lat.nx - (nchunk - 1) * chunk:])
+    return views, nchunk * chunk
 
 
 CASES = {

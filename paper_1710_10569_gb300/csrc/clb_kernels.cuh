@@ -194,9 +194,9 @@ __global__ void __launch_bounds__(256) k_step(const typename Storage<ST>::T* __r
 }
 
 // The FP16 form with 4 nodes per thread (its default) and high-order rates of 1, held at 96
-// registers: 5 blocks of 128 per SM instead of 4 (118 registers), at the cost of 72 bytes of spills;
-// 87.6 against 88.7-89.0 us per step on 4096 x 2048 (88 registers: 91 us). The general-rate form
-// would spill 168 bytes at this cap and stays uncapped. Same per-node arithmetic as k_step.
+// registers: 5 blocks of 128 per SM instead of 4 (116 registers), at the cost of 80 bytes of spills;
+// 83.1 against 86.0 us per step on 4096 x 2048 (88 registers: 86.7 us). The general-rate form
+// would spill more at this cap and stays uncapped. Same per-node arithmetic as k_step.
 static __global__ void __maxnreg__(96) k_step_f16x4_hi1(const __half* __restrict__ src, __half* __restrict__ dst,
                                                         const LatParams<float> P)
 {

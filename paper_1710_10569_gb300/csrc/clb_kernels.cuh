@@ -193,18 +193,71 @@ __global__ void __launch_bounds__(256) k_step(const typename Storage<ST>::T* __r
     step_warp_nodes<ST, V, true, HI1>(src, dst, P, x0, y, lane);
 }
 
-// The FP16 form with 4 nodes per thread (its default) and high-order rates of 1, held at 96
-// registers: 5 blocks of 128 per SM instead of 4 (116 registers), at the cost of 80 bytes of spills;
-// 83.1 against 86.0 us per step on 4096 x 2048 (88 registers: 86.7 us). The general-rate form
-// would spill more at this cap and stays uncapped. Same per-node arithmetic as k_step.
-static __global__ void __maxnreg__(96) k_step_f16x4_hi1(const __half* __restrict__ src, __half* __restrict__ dst,
-                                                        const LatParams<float> P)
+// Split step. The warps of the interior of the lattice (32 V nodes inside the row, no wall next to
+// any of them: not on a wall row, not in a wall column, not at a ragged row end) run in
+// k_step_inner, which holds only the wall-free vector body; the other warps run in k_step_edge,
+// which holds every path. Compiled into one kernel, the wall and node-by-node paths raise the
+// register pressure of the whole kernel and push spills into the interior path (FP16 at 96
+// registers: 80 bytes of spills with them, 20 without; 83.1 -> 77.6 us per step on 4096 x 2048).
+// The two kernels update disjoint sets of nodes from the same source buffer, so the host runs them
+// side by side on two streams. Each node's arithmetic is the same as in k_step.
+struct SplitGeom {
+    int y0, y1;    // interior rows [y0, y1)
+    int c0, c1;    // interior warp columns [c0, c1) (warp column c: nodes c 32 V .. c 32 V + 32 V - 1)
+    int nw;        // warp columns per row
+    int yb[2], nyb;  // wall rows, every column in k_step_edge
+    int cb[2], ncb;  // edge columns of the interior rows
+    __host__ __device__ int edge_warps() const { return nyb * nw + (y1 - y0) * ncb; }
+};
+
+// Interior warps: thread (tx, ty) of block (bx, by) is lane tx % 32 of warp column
+// c0 + (bx blockDim.x + tx) / 32 in row y0 + by blockDim.y + ty.
+template <int ST, int V, bool HI1>
+__global__ void __launch_bounds__(256) k_step_inner(const typename Storage<ST>::T* __restrict__ src,
+                                                    typename Storage<ST>::T* __restrict__ dst,
+                                                    const LatParams<typename Storage<ST>::A> P, int y0, int y1,
+                                                    int c0, int c1)
 {
     const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (y >= P.ny || x0 - lane * 4 >= P.nx) return;  // whole warps only
-    step_warp_nodes<ST_F16DEV, 4, true, true>(src, dst, P, x0, y, lane);
+    const int c = c0 + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int y = y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (y >= y1 || c >= c1) return;  // whole warps only
+    warp_vector<ST, V, false, HI1>(src, dst, P, c * 32 * V + lane * V, y, lane, 0);
+}
+
+// The FP16 form with 4 nodes per thread (its default) and high-order rates of 1, held at 96
+// registers: 5 blocks of 128 per SM instead of 4 (120 registers uncapped), 20 bytes of spills.
+static __global__ void __maxnreg__(96) k_step_inner_f16x4_hi1(const __half* __restrict__ src, __half* __restrict__ dst,
+                                                              const LatParams<float> P, int y0, int y1, int c0, int c1)
+{
+    const int lane = threadIdx.x & 31;
+    const int c = c0 + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int y = y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (y >= y1 || c >= c1) return;  // whole warps only
+    warp_vector<ST_F16DEV, 4, false, true>(src, dst, P, c * 32 * 4 + lane * 4, y, lane, 0);
+}
+
+// Edge warps, one per 32 threads: the wall rows first (every column), then the edge columns of the
+// interior rows.
+template <int ST, int V, bool HI1>
+__global__ void __launch_bounds__(128) k_step_edge(const typename Storage<ST>::T* __restrict__ src,
+                                                   typename Storage<ST>::T* __restrict__ dst,
+                                                   const LatParams<typename Storage<ST>::A> P, const SplitGeom G)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nr = G.nyb * G.nw;
+    int y, c;
+    if (w < nr) {
+        y = G.yb[w / G.nw];
+        c = w % G.nw;
+    } else {
+        const int v = w - nr;
+        if (v >= (G.y1 - G.y0) * G.ncb) return;  // whole warps only
+        y = G.y0 + v / G.ncb;
+        c = G.cb[v % G.ncb];
+    }
+    step_warp_nodes<ST, V, true, HI1>(src, dst, P, c * 32 * V + lane * V, y, lane);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -143,6 +143,8 @@ struct clb_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only to capture graphs
+    cudaStream_t side = nullptr; // private stream of the split step's edge kernel
+    cudaEvent_t fork = nullptr, join = nullptr;  // the split step's fork and join points
     char* mem = nullptr;
     bool own_mem = false;
     Layout L{};
@@ -177,28 +179,101 @@ dim3 grid_for(const clb_handle* h, int bx, int by)
     return dim3((h->nx + bx - 1) / bx, (h->ny + by - 1) / by);
 }
 
+// The split step (k_step_inner beside k_step_edge) for the FP16 form, which sits at the issue
+// limit: 83.0 -> 77.9 us per step on 4096 x 2048. The FP32 form is bound by memory (one kernel:
+// 35.0 us, split: 35.2-35.6 us, the fork and join costing more than the registers save) and FP64
+// by its arithmetic (602 us either way); they keep the one kernel that holds every path.
+template <int ST>
+constexpr bool split_step()
+{
+    return ST == ST_F16DEV;
+}
+
+// Interior rows and warp columns of the split step for V nodes per thread: rows next to a y wall
+// (or on a wet y wall) and the columns next to an x wall (or on a wet x wall, or holding the ragged
+// end of the rows) go to the edge kernel.
+SplitGeom split_geom(const clb_handle* h, int V)
+{
+    const LatParams<float>& P = h->Pf;
+    const int W = 32 * V;
+    SplitGeom G{};
+    G.nw = (h->nx + W - 1) / W;
+    if (!P.per_y || P.wet_y) {
+        G.nyb = h->ny > 1 ? 2 : 1;
+        G.yb[0] = 0;
+        G.yb[1] = h->ny - 1;
+        G.y0 = 1;
+        G.y1 = std::max(1, h->ny - 1);
+    } else {
+        G.nyb = 0;
+        G.y0 = 0;
+        G.y1 = h->ny;
+    }
+    const bool xwall = !P.per_x || P.wet_x;
+    const bool left = xwall, right = xwall || h->nx % W != 0;
+    G.c0 = left ? 1 : 0;
+    G.c1 = std::max(G.c0, right ? G.nw - 1 : G.nw);
+    G.ncb = 0;
+    if (left) G.cb[G.ncb++] = 0;
+    if (right && !(left && G.nw == 1)) G.cb[G.ncb++] = G.nw - 1;
+    return G;
+}
+
 template <int ST, int NPT>
-void enqueue_step(const clb_handle* h, const void* a, void* b, cudaStream_t s, int bx, int by)
+cudaError_t enqueue_step(const clb_handle* h, const void* a, void* b, cudaStream_t s, int bx, int by)
 {
     using E = typename Storage<ST>::T;
     using A = typename Storage<ST>::A;
-    const dim3 block(bx, by), grid((h->nx + bx * NPT - 1) / (bx * NPT), (h->ny + by - 1) / by);
     const LatParams<A>& P = *reinterpret_cast<const LatParams<A>*>(ST == ST_F64 ? (const void*)&h->Pd : (const void*)&h->Pf);
     const bool hi1 = h->p.s_3 == 1.0 && h->p.s_4 == 1.0 && h->p.lambda2 == 1.0;
-    if (ST == ST_F16DEV && NPT == 4 && hi1)
-        k_step_f16x4_hi1<<<grid, block, 0, s>>>((const __half*)a, (__half*)b, h->Pf);
-    else if (hi1)
-        k_step<ST, NPT, true><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
-    else
-        k_step<ST, NPT, false><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
+    const dim3 block(bx, by);
+    if constexpr (!split_step<ST>()) {
+        const dim3 grid((h->nx + bx * NPT - 1) / (bx * NPT), (h->ny + by - 1) / by);
+        if (hi1) k_step<ST, NPT, true><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
+        else k_step<ST, NPT, false><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
+        return cudaSuccess;
+    } else {
+        const SplitGeom G = split_geom(h, NPT);
+        const int ncol = G.c1 - G.c0, nrow = G.y1 - G.y0, nedge = G.edge_warps();
+        const bool inner = ncol > 0 && nrow > 0;
+        cudaStream_t se = s;
+        if (inner && nedge > 0) {
+            // fork: the edge warps run on the side stream beside the interior (under graph capture
+            // the event pulls the side stream into the capture, and the join closes it)
+            cudaError_t e = cudaEventRecord(h->fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->fork, 0);
+            if (e != cudaSuccess) return e;
+            se = h->side;
+        }
+        if (nedge > 0) {
+            const dim3 ge((nedge * 32 + 127) / 128);
+            if (hi1) k_step_edge<ST, NPT, true><<<ge, 128, 0, se>>>((const E*)a, (E*)b, P, G);
+            else k_step_edge<ST, NPT, false><<<ge, 128, 0, se>>>((const E*)a, (E*)b, P, G);
+        }
+        if (inner) {
+            const dim3 gi((ncol * 32 + bx - 1) / bx, (nrow + by - 1) / by);
+            if (ST == ST_F16DEV && NPT == 4 && hi1)
+                k_step_inner_f16x4_hi1<<<gi, block, 0, s>>>((const __half*)a, (__half*)b, h->Pf, G.y0, G.y1, G.c0, G.c1);
+            else if (hi1)
+                k_step_inner<ST, NPT, true><<<gi, block, 0, s>>>((const E*)a, (E*)b, P, G.y0, G.y1, G.c0, G.c1);
+            else
+                k_step_inner<ST, NPT, false><<<gi, block, 0, s>>>((const E*)a, (E*)b, P, G.y0, G.y1, G.c0, G.c1);
+        }
+        if (se != s) {
+            cudaError_t e = cudaEventRecord(h->join, se);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->join, 0);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
 }
 
 template <int ST>
-void enqueue_step_npt(const clb_handle* h, const void* a, void* b, cudaStream_t s, int bx, int by, int npt)
+cudaError_t enqueue_step_npt(const clb_handle* h, const void* a, void* b, cudaStream_t s, int bx, int by, int npt)
 {
-    if (npt == 4) enqueue_step<ST, 4>(h, a, b, s, bx, by);
-    else if (npt == 2) enqueue_step<ST, 2>(h, a, b, s, bx, by);
-    else enqueue_step<ST, 1>(h, a, b, s, bx, by);
+    if (npt == 4) return enqueue_step<ST, 4>(h, a, b, s, bx, by);
+    if (npt == 2) return enqueue_step<ST, 2>(h, a, b, s, bx, by);
+    return enqueue_step<ST, 1>(h, a, b, s, bx, by);
 }
 
 struct Launch {
@@ -217,11 +292,13 @@ clb_status launch_step(clb_handle* h, int from, cudaStream_t s, const Launch& L)
                                                L.stages, L.rows);
         if (e != cudaSuccess) return set_error(CLB_ECUDA, "pipelined step: %s", cudaGetErrorString(e));
     } else {
+        cudaError_t e;
         switch (h->p.storage) {
-        case CLB_F64: enqueue_step_npt<ST_F64>(h, a, b, s, L.bx, L.by, L.npt); break;
-        case CLB_F32: enqueue_step_npt<ST_F32>(h, a, b, s, L.bx, L.by, L.npt); break;
-        default: enqueue_step_npt<ST_F16DEV>(h, a, b, s, L.bx, L.by, L.npt); break;
+        case CLB_F64: e = enqueue_step_npt<ST_F64>(h, a, b, s, L.bx, L.by, L.npt); break;
+        case CLB_F32: e = enqueue_step_npt<ST_F32>(h, a, b, s, L.bx, L.by, L.npt); break;
+        default: e = enqueue_step_npt<ST_F16DEV>(h, a, b, s, L.bx, L.by, L.npt); break;
         }
+        if (e != cudaSuccess) return set_error(CLB_ECUDA, "step: %s", cudaGetErrorString(e));
     }
     CLB_CUDA(cudaGetLastError());
     return CLB_OK;
@@ -350,6 +427,9 @@ extern "C" clb_status clb_create(int nx, int ny, const clb_params* p, void* stre
             return st;
         };
         cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
         if (e != cudaSuccess) return fail(set_error(CLB_ECUDA, "stream: %s", cudaGetErrorString(e)));
         if (dev_mem) {
             h->mem = (char*)dev_mem;
@@ -407,7 +487,11 @@ extern "C" void clb_destroy(clb_handle* h)
     drop_graphs(h);
     if (h->own_mem && h->mem) cudaFree(h->mem);
     if (h->host_diag) cudaFreeHost(h->host_diag);
+    if (h->side) cudaStreamSynchronize(h->side);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     delete h;
 }
 

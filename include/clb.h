@@ -157,8 +157,7 @@ clb_status clb_nusselt(clb_handle *h, int axis, double *nu_out);
  * Scratch is a fixed array of CLB_NOALLOC_MAX_ROWS rows of FP64 partial sums that the library keeps
  * in device memory on every device it is used on until the process exits; ny above that limit
  * returns CLB_EINVAL. The first call on a device looks up that array's address (with the device
- * current) and keeps it for later calls on that device; make that first call before any stream
- * capture. A cudaDeviceReset invalidates the kept address: do not call this entry point on a
+ * current) and keeps it for later calls on that device. A cudaDeviceReset invalidates the kept address: do not call this entry point on a
  * device again after resetting it. All calls share the one array, so calls whose kernels overlap
  * on the GPU race: serialise them. Returns CLB_ENAN when the fields are not finite. The result
  * equals clb_nusselt on the same populations within rounding (bitwise for nx <= 2048; wider rows

@@ -268,6 +268,31 @@ def test_launch_shapes_are_bitwise_equal(clb, storage, walls):
             assert np.array_equal(x, y), shape
 
 
+EDGE_SHAPES = [(2, 2), (3, 257), (257, 3), (129, 2), (128, 5), (256, 4), (131, 9)]
+EDGE_WALLS = {"periodic": (P, P, P, P), "cavity": (D, D, A, A), "rb": (P, P, D, D), "wet_x": (W.WALL_WET, W.WALL_WET, P, P),
+              "wet_y": (P, P, W.WALL_WET, W.WALL_WET)}
+
+
+@pytest.mark.parametrize("rates", ["general", "one"])
+@pytest.mark.parametrize("storage", [F32, F16])
+@pytest.mark.parametrize("walls", sorted(EDGE_WALLS))
+@pytest.mark.parametrize("shape", EDGE_SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
+def test_small_and_edge_shapes_reduced_precision(clb, storage, walls, shape, rates):
+    """Lattices where the FP16 step's split into interior warps and edge warps degenerates (no
+    interior row or column, one warp per row, a ragged last warp, two rows) and where the FP32
+    vector path covers few or no warps, with random rates and with the high-order rates at 1 (the
+    forms the host picks between): within the parity bar of the oracle at every node."""
+    w = EDGE_WALLS[walls]
+    nx, ny = shape
+    if (w[0] == W.WALL_WET and nx < 3) or (w[2] == W.WALL_WET and ny < 3):
+        pytest.skip("a wet wall pair needs at least 3 nodes across")
+    prob = W.random_problem(nx, ny, seed=11, storage=storage, walls=w)
+    if rates == "one":
+        prob.params.update(s_3=1.0, s_4=1.0, lambda2=1.0)
+    _, _, got, exp = run_both(clb, prob, 40)
+    compare(f"edge{shape}_{walls}_{rates}_{W.STORAGE_NAMES[storage]}", got, exp, tol(storage, 40), prob.params)
+
+
 # ------------------------------------------------------------------ diagnostics
 
 

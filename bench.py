@@ -108,8 +108,10 @@ def profile_counts():
 
 def flops_per_node():
     """Floating-point operations per node update (an FMA counted as two), from the FP64 step's
-    committed ncu instruction counts (the FP32 and FP16 forms evaluate the same expressions), if
-    they were taken on the current kernel source (else None)."""
+    committed ncu instruction counts, if they were taken on the current kernel source (else None).
+    The FP32 and FP16 forms evaluate the same expressions except the ten 1-D inverse pairs
+    (s + d)/2, (s - d)/2 per node, which their packed pairs form as two sums and two halvings (4
+    flops) where FP64 uses one halving and two FMAs (5 flops): 8 flops fewer per node."""
     ops = profile_counts().get("fp64_ops_per_node")
     if not ops:
         return None

@@ -278,8 +278,7 @@ __device__ __forceinline__ void collide_d3q7(const Lat3<A>& P, const A u[3], A d
         const A r1 = fma_(u[d], dT, kd[d]);
         const A r2 = fma_(u[d] * u[d], dT, fma_(A(2) * u[d], kd[d], kdd[d]));
         rest = rest - r2;
-        g[1 + 2 * d] = A(0.5) * (r2 + r1);
-        g[2 + 2 * d] = A(0.5) * (r2 - r1);
+        half_sum_diff(r2, r1, g[1 + 2 * d], g[2 + 2 * d]);
     }
     g[0] = rest;
 }
@@ -314,8 +313,7 @@ __device__ __forceinline__ void equilibrium_d3q7(const Lat3<A>& P, const A u[3],
         const A r1 = fma_(u[d], dT, kd);
         const A r2 = fma_(u[d] * u[d], dT, fma_(A(2) * u[d], kd, kdd));
         rest = rest - r2;
-        g[1 + 2 * d] = A(0.5) * (r2 + r1);
-        g[2 + 2 * d] = A(0.5) * (r2 - r1);
+        half_sum_diff(r2, r1, g[1 + 2 * d], g[2 + 2 * d]);
     }
     g[0] = rest;
 }

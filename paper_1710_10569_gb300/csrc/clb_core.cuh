@@ -326,6 +326,24 @@ __device__ __forceinline__ void central3(A c, A p, A m, A u, A& k0, A& k1, A& k2
     k2 = fma_(u * u, s0, fma_(A(-2) * u, d, s));
 }
 
+// (s + d) / 2 and (s - d) / 2 as two FMAs on the exact half of s: the values of the two sums halved
+// (halving is exact and commutes with rounding to nearest outside the subnormal range) in three
+// instructions instead of four.
+template <typename A>
+__device__ __forceinline__ void half_sum_diff(A s, A d, A& plus, A& minus)
+{
+    const A h = A(0.5) * s;
+    plus = fma_(A(0.5), d, h);
+    minus = fma_(A(-0.5), d, h);
+}
+// Packed pairs keep the sums and the halvings (same values): in the FP16 step, issue-limited on the
+// FMA pipe, the three-instruction form measured 78.4 against 77.9 us.
+__device__ __forceinline__ void half_sum_diff(F2 s, F2 d, F2& plus, F2& minus)
+{
+    plus = F2(0.5f) * (s + d);
+    minus = F2(0.5f) * (s - d);
+}
+
 // Inverse of central3: raw moments about 0 (shift back by u), then the 1-D inverse moment map.
 template <typename A>
 __device__ __forceinline__ void uncentral3(A k0, A k1, A k2, A u, A& c, A& p, A& m)
@@ -333,8 +351,7 @@ __device__ __forceinline__ void uncentral3(A k0, A k1, A k2, A u, A& c, A& p, A&
     const A r1 = fma_(u, k0, k1);
     const A r2 = fma_(u * u, k0, fma_(A(2) * u, k1, k2));
     c = k0 - r2;
-    p = A(0.5) * (r2 + r1);
-    m = A(0.5) * (r2 - r1);
+    half_sum_diff(r2, r1, p, m);  // p = (r2 + r1) / 2, m = (r2 - r1) / 2
 }
 
 // f = M^-1 N(u)^-1 k for central moments k[a][b] (a: x order, b: y order).
@@ -360,10 +377,8 @@ __device__ __forceinline__ void back_d2q5(A T, A k10, A k01, A k20, A k02, A ux,
     const A r01 = fma_(uy, T, k01);
     const A r02 = fma_(uy * uy, T, fma_(A(2) * uy, k01, k02));
     g[0] = T - r20 - r02;
-    g[1] = A(0.5) * (r20 + r10);
-    g[3] = A(0.5) * (r20 - r10);
-    g[2] = A(0.5) * (r02 + r01);
-    g[4] = A(0.5) * (r02 - r01);
+    half_sum_diff(r20, r10, g[1], g[3]);
+    half_sum_diff(r02, r01, g[2], g[4]);
 }
 
 // D2Q9 central moments k[a][b] = sum f (e_x - u_x)^a (e_y - u_y)^b (Eq. 5b).
@@ -443,8 +458,11 @@ __device__ __forceinline__ void eq_dev_d2q9(A rho, A drho, A ux, A uy, A f[9])
 {
     const A w0 = A(2.0 / 3.0), w1 = A(1.0 / 6.0);
     const A x2 = ux * ux, y2 = uy * uy;
-    const A dx[3] = {-x2, A(0.5) * (x2 + ux), A(0.5) * (x2 - ux)};  // e = 0, +1, -1
-    const A dy[3] = {-y2, A(0.5) * (y2 + uy), A(0.5) * (y2 - uy)};
+    A dx[3], dy[3];  // e = 0, +1, -1: -u^2, (u^2 + u) / 2, (u^2 - u) / 2
+    dx[0] = -x2;
+    dy[0] = -y2;
+    half_sum_diff(x2, ux, dx[1], dx[2]);
+    half_sum_diff(y2, uy, dy[1], dy[2]);
     const A wv[3] = {w0, w1, w1};
     const int ax[9] = {0, 1, 0, 2, 0, 1, 2, 2, 1};
     const int ay[9] = {0, 0, 1, 0, 2, 1, 1, 2, 2};

@@ -212,6 +212,18 @@ clb_status clb_get_pipeline(clb_handle *h, int *stages, int *rows);
 /* The CUDA stream the handle enqueues on (to time its work with events on that stream). */
 void *clb_stream(clb_handle *h);
 
+/* How the FP16 storage form splits a time step (host only, no device work; for tools and tests).
+ * The warps of the interior, whose 32 * npt nodes lie inside the row with no wall next to any of
+ * them, run in one kernel; the others (rows next to a y wall or on a wet y wall, the columns next to
+ * an x wall or on a wet x wall or holding the ragged end of the rows) run in a second kernel beside
+ * it. Warp column c covers nodes c * 32 * npt .. c * 32 * npt + 32 * npt - 1 of a row. For a lattice
+ * of nx x ny nodes with parameters p and npt nodes per thread (1, 2 or 4), geom receives 11 ints:
+ * [0, 1] the interior rows [y0, y1); [2, 3] the interior warp columns [c0, c1); [4] warp columns per
+ * row; [5] the number of edge rows and [6, 7] those rows (-1 if absent), every column of which goes
+ * to the edge kernel; [8] the number of edge columns and [9, 10] those columns (-1 if absent), taken
+ * in the rows [y0, y1). CLB_EINVAL for parameters that clb_create rejects or another npt. */
+clb_status clb_step_partition(int nx, int ny, const clb_params *p, int npt, int *geom);
+
 /* Device address of the current post-collision population buffer and of the other buffer, and
  * their layout (for profiling and checkpoint tools): chunked rows. Row y holds ceil(nx / chunk)
  * chunks of chunk consecutive nodes, the last one padded; a chunk holds its nodes' 14 populations

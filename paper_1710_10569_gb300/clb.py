@@ -88,6 +88,7 @@ _SIGS = {
     "clb_get_pipeline": [_VP, _P(_I), _P(_I)],
     "clb_stream": [_VP],
     "clb_buffers": [_VP, _P(_VP), _P(_VP), _P(_S), _P(_I)],
+    "clb_step_partition": [_I, _I, _P(clb_params), _I, _P(_I)],
     "clb_last_error": [],
     "clb_version": [],
     "clb_thermal_create": [_I, _I, _P(clb_params), _VP, _P(_VP)],
@@ -176,6 +177,17 @@ def lib():
 def _check(status: int):
     if status != CLB_OK:
         raise CLBError(status, lib().clb_last_error().decode(errors="replace"))
+
+
+def step_partition(nx: int, ny: int, p: dict, npt: int = 4) -> dict:
+    """clb_step_partition: how the FP16 form splits a step into interior and edge warps (host
+    only). Returns the interior rows and warp columns, the warp columns per row, and the edge rows
+    and edge columns."""
+    g = (_I * 11)()
+    cp = params(p)
+    _check(lib().clb_step_partition(int(nx), int(ny), ctypes.byref(cp), int(npt), g))
+    return {"rows": (g[0], g[1]), "cols": (g[2], g[3]), "warp_cols": g[4],
+            "edge_rows": [g[6 + k] for k in range(g[5])], "edge_cols": [g[9 + k] for k in range(g[8])]}
 
 
 def params(p: dict) -> clb_params:

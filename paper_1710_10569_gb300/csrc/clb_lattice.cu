@@ -192,25 +192,24 @@ constexpr bool split_step()
 // Interior rows and warp columns of the split step for V nodes per thread: rows next to a y wall
 // (or on a wet y wall) and the columns next to an x wall (or on a wet x wall, or holding the ragged
 // end of the rows) go to the edge kernel.
-SplitGeom split_geom(const clb_handle* h, int V)
+SplitGeom split_geom(int nx, int ny, const LatParams<float>& P, int V)
 {
-    const LatParams<float>& P = h->Pf;
     const int W = 32 * V;
     SplitGeom G{};
-    G.nw = (h->nx + W - 1) / W;
+    G.nw = (nx + W - 1) / W;
     if (!P.per_y || P.wet_y) {
-        G.nyb = h->ny > 1 ? 2 : 1;
+        G.nyb = ny > 1 ? 2 : 1;
         G.yb[0] = 0;
-        G.yb[1] = h->ny - 1;
+        G.yb[1] = ny - 1;
         G.y0 = 1;
-        G.y1 = std::max(1, h->ny - 1);
+        G.y1 = std::max(1, ny - 1);
     } else {
         G.nyb = 0;
         G.y0 = 0;
-        G.y1 = h->ny;
+        G.y1 = ny;
     }
     const bool xwall = !P.per_x || P.wet_x;
-    const bool left = xwall, right = xwall || h->nx % W != 0;
+    const bool left = xwall, right = xwall || nx % W != 0;
     G.c0 = left ? 1 : 0;
     G.c1 = std::max(G.c0, right ? G.nw - 1 : G.nw);
     G.ncb = 0;
@@ -233,7 +232,7 @@ cudaError_t enqueue_step(const clb_handle* h, const void* a, void* b, cudaStream
         else k_step<ST, NPT, false><<<grid, block, 0, s>>>((const E*)a, (E*)b, P);
         return cudaSuccess;
     } else {
-        const SplitGeom G = split_geom(h, NPT);
+        const SplitGeom G = split_geom(h->nx, h->ny, h->Pf, NPT);
         const int ncol = G.c1 - G.c0, nrow = G.y1 - G.y0, nedge = G.edge_warps();
         const bool inner = ncol > 0 && nrow > 0;
         cudaStream_t se = s;
@@ -885,6 +884,23 @@ extern "C" clb_status clb_autotune(clb_handle* h, int* block_x, int* block_y, in
 }
 
 extern "C" void* clb_stream(clb_handle* h) { return h ? (void*)h->stream : nullptr; }
+
+extern "C" clb_status clb_step_partition(int nx, int ny, const clb_params* p, int npt, int* geom)
+{
+    if (!p || !geom) return set_error(CLB_EINVAL, "params or geom is NULL");
+    if (npt != 1 && npt != 2 && npt != 4) return set_error(CLB_EINVAL, "nodes per thread %d: 1, 2 or 4", npt);
+    const clb_status st = validate(nx, ny, p);
+    if (st != CLB_OK) return st;
+    try {
+        const SplitGeom G = split_geom(nx, ny, make_lat_params<float>(nx, ny, *p), npt);
+        const int out[11] = {G.y0, G.y1, G.c0, G.c1, G.nw, G.nyb, G.nyb > 0 ? G.yb[0] : -1, G.nyb > 1 ? G.yb[1] : -1,
+                             G.ncb, G.ncb > 0 ? G.cb[0] : -1, G.ncb > 1 ? G.cb[1] : -1};
+        std::memcpy(geom, out, sizeof(out));
+        return CLB_OK;
+    } catch (const std::bad_alloc&) {
+        return host_alloc_failed();
+    }
+}
 
 extern "C" clb_status clb_buffers(clb_handle* h, void** cur, void** other, size_t* row_elems, int* chunk)
 {

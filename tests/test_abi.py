@@ -189,3 +189,51 @@ def test_headers_are_plain_c(header):
     r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Werror", "-x", "c", "-std=c99", path],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+PARTITION_WALLS = {
+    "periodic": (W.WALL_PERIODIC,) * 4,
+    "rb": (W.WALL_PERIODIC, W.WALL_PERIODIC, W.WALL_DIRICHLET, W.WALL_DIRICHLET),
+    "cavity": (W.WALL_DIRICHLET, W.WALL_DIRICHLET, W.WALL_ADIABATIC, W.WALL_ADIABATIC),
+    "channel": (W.WALL_PERIODIC, W.WALL_PERIODIC, W.WALL_ADIABATIC, W.WALL_ADIABATIC),
+    "wet_y": (W.WALL_PERIODIC, W.WALL_PERIODIC, W.WALL_WET, W.WALL_WET),
+    "wet_x": (W.WALL_WET, W.WALL_WET, W.WALL_PERIODIC, W.WALL_PERIODIC),
+    "wet_box": (W.WALL_WET,) * 4,
+}
+
+
+@pytest.mark.parametrize("walls", sorted(PARTITION_WALLS))
+@pytest.mark.parametrize("npt", [1, 2, 4])
+def test_step_partition_covers_every_warp_once(clb, walls, npt):
+    """The FP16 step's split (clb_step_partition): the interior warps and the warps the edge kernel
+    enumerates cover every (row, warp column) of the lattice exactly once, and no interior warp has
+    a wall next to any of its nodes or runs past the end of its row."""
+    w = PARTITION_WALLS[walls]
+    wall_y = w[2] != W.WALL_PERIODIC
+    wall_x = w[0] != W.WALL_PERIODIC
+    width = 32 * npt
+    for nx, ny in [(3, 3), (4, 3), (31, 5), (127, 5), (128, 5), (129, 5), (256, 3), (257, 3), (384, 7),
+                   (1000, 4), (33, 33), (64, 64), (4096, 6)]:
+        g = clb.step_partition(nx, ny, W.default_params(wall=w, storage=W.STORAGE_F16DEV), npt)
+        nw = g["warp_cols"]
+        assert nw == -(-nx // width)
+        (y0, y1), (c0, c1) = g["rows"], g["cols"]
+        inner = {(y, c) for y in range(y0, y1) for c in range(c0, c1)}
+        edge = [(y, c) for y in g["edge_rows"] for c in range(nw)]
+        edge += [(y, c) for y in range(y0, y1) for c in g["edge_cols"]]
+        assert len(edge) == len(set(edge)), (nx, ny, g)
+        assert not inner & set(edge), (nx, ny, g)
+        assert inner | set(edge) == {(y, c) for y in range(ny) for c in range(nw)}, (nx, ny, g)
+        for y, c in inner:
+            x0, x1 = c * width, c * width + width - 1
+            assert x1 < nx
+            assert not wall_y or 0 < y < ny - 1
+            assert not wall_x or (x0 > 0 and x1 < nx - 1)
+
+
+def test_step_partition_rejects_bad_arguments(clb):
+    p = W.default_params(storage=W.STORAGE_F16DEV)
+    with pytest.raises(clb.CLBError):
+        clb.step_partition(64, 64, p, npt=3)
+    with pytest.raises(clb.CLBError):
+        clb.step_partition(1, 64, p)

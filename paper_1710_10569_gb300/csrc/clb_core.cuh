@@ -300,14 +300,16 @@ template <typename A, typename S>
 __device__ __forceinline__ Macro<A> macroscopic(const LatParams<S>& P, const A f[9], const A g[5], A Tb)
 {
     Macro<A> m;
-    m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    m.dT = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    // sums over the rows of equal e_y (centre, +x, -x) as central3 forms them, and over the D2Q5
+    // axis pairs as the D2Q5 collision forms them, so that the compiler shares them
+    m.drho = ((f[0] + (f[1] + f[3])) + (f[2] + (f[5] + f[6]))) + (f[4] + (f[8] + f[7]));
+    m.dT = (g[0] + (g[1] + g[3])) + (g[2] + g[4]);
     m.rho = A(P.rho_b) + m.drho;
     m.T = Tb + m.dT;
     m.Fx = A(P.Fvx);
     m.Fy = fma_(A(P.gb), m.T - A(P.T0), A(P.Fvy));
     const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const A jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const A jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[8] + f[7]);
     const A inv = rcp_(m.rho);
     m.ux = fma_(A(0.5), m.Fx, jx) * inv;
     m.uy = fma_(A(0.5), m.Fy, jy) * inv;
